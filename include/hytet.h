@@ -1,0 +1,190 @@
+/*
+ * hytet.h - C ABI of the GB300 matrix-free P1/P2 library.
+ *
+ * The calls follow the paper's statement of the problem (Kohl, Bauer, Boehm,
+ * Ruede, "Fundamental data structures for matrix-free finite elements on
+ * hybrid tetrahedral grids"): build the macro mesh (Sec. 2, macro-primitive
+ * graph), refine it to a range of levels (Sec. 3.1, Bey's rule; Sec. 5.1,
+ * functions on level ranges), apply an operator (Sec. 5.2, apply()), and run
+ * geometric multigrid on the refinement hierarchy (Sec. 1/5.1, multigrid by
+ * design).
+ *
+ * Conventions
+ * -----------
+ * - Every function returns 0 (HG_OK) or a negative HG_ERR_* code; the
+ *   message of the last error on the calling thread is hg_last_error().
+ * - Handles are opaque and owned by the library; *_destroy frees them.
+ *   Passing NULL to a destroy function is a no-op.
+ * - Vectors are caller-owned device buffers (plain pointers), laid out as
+ *   "stored" vectors: macro cell c occupies elements
+ *   [c*cell_stride, (c+1)*cell_stride).  Inside a cell the micro-vertex
+ *   (i,j,k), i+j+k <= n (n = 2^level), is at t_{n+1}(i,j,k) (Sec. 4,
+ *   linearisation t_w).  For P2 the cell block holds the vertex array
+ *   followed by the edge subgroups x,y,z,xy,xz,yz (width n) and xyz
+ *   (width n-1), each in t_w order of its anchors (Sec. 5.1, P2 composition).
+ *   Tail padding of each cell block is zero and never written.
+ *   Micro-vertices on macro faces/edges/vertices are stored once per macro
+ *   cell that contains them; every library call leaves all copies equal.
+ * - The library never frees caller memory.  It allocates its own device
+ *   tables (maps, stencils, work vectors) when a handle is created.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are asynchronous with respect to the host unless stated.
+ * - Dirichlet DoFs are those on macro faces with one incident macro cell and
+ *   on the edges/vertices of such faces.  HG_MASK_INNER leaves them
+ *   untouched in the destination; HG_MASK_ALL computes the full Neumann rows.
+ */
+#ifndef HYTET_H
+#define HYTET_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HG_OK = 0,
+  HG_ERR_INVALID_ARG = -1,
+  HG_ERR_BAD_MESH = -2,
+  HG_ERR_LEVEL_RANGE = -3,
+  HG_ERR_CUDA = -4,
+  HG_ERR_NOT_CONVERGED = -5,
+  HG_ERR_TIMEOUT = -6,
+  HG_ERR_UNSUPPORTED = -7
+};
+
+enum { HG_F32 = 0, HG_F64 = 1 };
+enum { HG_SPACE_P1 = 1, HG_SPACE_P2 = 2 };
+enum { HG_REPLACE = 0, HG_ADD = 1 };
+enum { HG_MASK_INNER = 0, HG_MASK_ALL = 1 };
+
+/* Operator kinds (Sec. 5.2, operator examples). */
+enum {
+  HG_OP_P1_LAPLACE = 0,  /* -div grad, constant-coefficient 15-point stencils     */
+  HG_OP_P1_MASS = 1,     /* P1 mass, constant-coefficient stencils               */
+  HG_OP_P1_DIVKGRAD = 2, /* -div(k grad), element-wise, k_T = mean of vertex k   */
+  HG_OP_P2_LAPLACE = 3,  /* P2 -div grad, element-wise                           */
+  HG_OP_P2_MASS = 4,     /* P2 mass, element-wise                                */
+  HG_OP_P2_DIVKGRAD = 5  /* P2 -div(k grad), k(x) = a + b sin2pix sin2piy sin2piz
+                            by quadrature on the fly                             */
+};
+
+typedef struct hg_mesh hg_mesh;
+typedef struct hg_hier hg_hier;
+typedef struct hg_op hg_op;
+typedef struct hg_gmg hg_gmg;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* hg_last_error(void);
+
+/* ---------------------------------------------------------------- mesh --
+ * Macro mesh (Sec. 2: triangulation conditions; macro-primitive graph of
+ * vertices/edges/faces/cells with neighbour links).
+ *   xyz   : host, nv*3 doubles, vertex coordinates.
+ *   cells : host, nc*4 int64 vertex ids; the order in each row is the local
+ *           vertex order v0..v3 of the macro cell and fixes its refinement
+ *           (inner edge v02-v13, Sec. 3.1).
+ * Checks: ids in range, no repeated vertex in a cell, nonzero volume, every
+ * face shared by at most two cells.  Errors: HG_ERR_INVALID_ARG,
+ * HG_ERR_BAD_MESH.  Copies the input; caller keeps ownership. */
+int hg_mesh_create(const double* xyz, int64_t nv, const int64_t* cells, int64_t nc,
+                   hg_mesh** out);
+void hg_mesh_destroy(hg_mesh* mesh);
+/* counts[0..5] = macro vertices, edges, faces, cells, boundary faces,
+ * interior faces. */
+int hg_mesh_counts(const hg_mesh* mesh, int64_t counts[6]);
+
+/* --------------------------------------------------------- hierarchy --
+ * Refinement of every macro cell to levels lmin..lmax (Sec. 3.1, Bey's
+ * rule applied recursively; Sec. 5.1, functions allocated on a level range).
+ * 0 <= lmin <= lmax <= 9.  Uploads per-level maps to the current device.
+ * Errors: HG_ERR_LEVEL_RANGE, HG_ERR_CUDA. */
+int hg_hier_create(const hg_mesh* mesh, int lmin, int lmax, hg_hier** out);
+void hg_hier_destroy(hg_hier* hier);
+
+/* Sizes of a stored vector (n_stored, including per-cell copies and padding),
+ * the number of unique DoFs (n_unique) and of non-Dirichlet unique DoFs
+ * (n_inner), and the per-cell stride.  Any output may be NULL. */
+int hg_function_size(const hg_hier* hier, int space, int level, int64_t* n_stored,
+                     int64_t* n_unique, int64_t* n_inner, int64_t* cell_stride);
+
+/* Canonical order of unique DoFs: ascending (z, y, x) of the exact lattice
+ * point (P2: of the doubled lattice, edge DoFs at midpoints).  Host outputs:
+ *   stored_to_canon : n_stored int64, -1 for padding     (may be NULL)
+ *   xyz             : n_unique*3 doubles, coordinates    (may be NULL)
+ *   dirichlet       : n_unique uint8, 1 on the boundary  (may be NULL)
+ * Requires vertex coordinates that are integers after scaling by some
+ * D <= 64 (HG_ERR_UNSUPPORTED otherwise). */
+int hg_canonical_info(const hg_hier* hier, int space, int level, int64_t* stored_to_canon,
+                      double* xyz, uint8_t* dirichlet);
+
+/* Device gather stored -> canonical (one value per unique DoF) and scatter
+ * canonical -> every stored copy (padding untouched).  dtype HG_F32/HG_F64. */
+int hg_to_canonical(const hg_hier* hier, int space, int level, int dtype, const void* stored,
+                    void* canonical, void* stream);
+int hg_from_canonical(const hg_hier* hier, int space, int level, int dtype,
+                      const void* canonical, void* stored, void* stream);
+
+/* ----------------------------------------------------- index functions --
+ * t_w(i,j,k) = N_tet(w) - N_tet(w-k) + N_tri(w-k) - N_tri(w-k-j) + i
+ * (Sec. 4).  Host evaluation; HG_ERR_INVALID_ARG if (i,j,k) not in I_tet(w). */
+int hg_index_tw(int64_t w, int64_t i, int64_t j, int64_t k, int64_t* out);
+
+/* Device enumeration of I_tet(w) with the same traversal the operator
+ * kernels use: out[t_w(i,j,k)] = i + (j << 20) + (k << 40) for every point.
+ * out: device, N_tet(w) int64.  1 <= w <= 1025. */
+int hg_index_enumerate(int64_t w, int64_t* out, void* stream);
+
+/* Device dump of the interface ("ghost-layer") map of a level: for every
+ * shared or boundary macro primitive (vertex/edge/face) point, the cells and
+ * cell-local indices of all its copies, in the order the exchange kernel sums
+ * them.  Output (device int64): rows of 2*max_copies+1 entries
+ * [ncopies, cell_0, local_0, cell_1, local_1, ...], unused entries -1.
+ * *n_rows receives the row count (host); call with out == NULL to query
+ * n_rows and max_copies first. */
+int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
+                      int64_t* n_rows, int64_t* max_copies, void* stream);
+
+/* ---------------------------------------------------------- operators --
+ * kind: HG_OP_*.  coeff: for HG_OP_P1_DIVKGRAD, host array of k at the
+ * unique vertices of level lmax in canonical order (injected to coarser
+ * levels); for HG_OP_P2_DIVKGRAD, host {a, b}; otherwise NULL.
+ * Element matrices/stencils are computed per macro cell and level in FP64
+ * (Sec. 5.2: constant-coefficient stencils precomputed per macro primitive,
+ * element matrices on the fly for variable coefficients). */
+int hg_op_create(const hg_hier* hier, int kind, const double* coeff, hg_op** out);
+void hg_op_destroy(hg_op* op);
+
+/* y = A x (HG_REPLACE) or y += A x (HG_ADD) on one level; the ghost-layer
+ * exchange between macro cells is part of the call (Sec. 5.2 apply()).
+ * x and y are distinct stored vectors of the operator's space/level/dtype. */
+int hg_apply(const hg_op* op, int level, int dtype, const void* x, void* y, int mode,
+             int mask, void* stream);
+
+/* r = b - A x on the non-Dirichlet DoFs, r = 0 on Dirichlet DoFs. */
+int hg_residual(const hg_op* op, int level, int dtype, const void* x, const void* b, void* r,
+                void* stream);
+
+/* Weighted Jacobi step x_out = x + omega D^-1 (b - A x) on non-Dirichlet
+ * DoFs; Dirichlet DoFs copied from x.  x and x_out must not alias. */
+int hg_jacobi(const hg_op* op, int level, int dtype, double omega, const void* x,
+              const void* b, void* x_out, void* stream);
+
+/* Grid transfers between level and level-1 (nodal interpolation P and its
+ * transpose): r_coarse = P^T r_fine (Dirichlet DoFs of r_coarse set to 0);
+ * x_fine += P e_coarse (Dirichlet DoFs of x_fine untouched). */
+int hg_restrict(const hg_hier* hier, int space, int fine_level, int dtype, const void* r_fine,
+                void* r_coarse, void* stream);
+int hg_prolong_add(const hg_hier* hier, int space, int fine_level, int dtype,
+                   const void* e_coarse, void* x_fine, void* stream);
+
+/* Deterministic FP64 dot product over unique DoFs (each counted once),
+ * non-Dirichlet only (HG_MASK_INNER) or all (HG_MASK_ALL).  The result is
+ * written to *result (host) after the call synchronises `stream`. */
+int hg_dot(const hg_hier* hier, int space, int level, int dtype, const void* x, const void* y,
+           int mask, double* result, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYTET_H */

@@ -1,0 +1,252 @@
+"""Python binding of the GB300 matrix-free P1/P2 library (``include/hytet.h``).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of ``lib/libhytet.so``.  Device vectors are torch CUDA tensors (used
+for memory and streams); they are passed to the C ABI as raw pointers.  The
+library is loaded on first use and every call fails loudly (RuntimeError) if
+it has not been built or a call returns an error code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libhytet.so")
+
+HG_F32, HG_F64 = 0, 1
+HG_SPACE_P1, HG_SPACE_P2 = 1, 2
+HG_REPLACE, HG_ADD = 0, 1
+HG_MASK_INNER, HG_MASK_ALL = 0, 1
+HG_OP_P1_LAPLACE, HG_OP_P1_MASS, HG_OP_P1_DIVKGRAD = 0, 1, 2
+HG_OP_P2_LAPLACE, HG_OP_P2_MASS, HG_OP_P2_DIVKGRAD = 3, 4, 5
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_int64
+_D = ctypes.c_double
+_PL = ctypes.POINTER(ctypes.c_int64)
+_PD = ctypes.POINTER(ctypes.c_double)
+
+# name -> (restype, argtypes); every function declared in include/hytet.h
+SIGNATURES = {
+    "hg_last_error": (ctypes.c_char_p, []),
+    "hg_mesh_create": (_I, [_P, _L, _P, _L, ctypes.POINTER(_P)]),
+    "hg_mesh_destroy": (None, [_P]),
+    "hg_mesh_counts": (_I, [_P, _PL]),
+    "hg_hier_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
+    "hg_hier_destroy": (None, [_P]),
+    "hg_function_size": (_I, [_P, _I, _I, _PL, _PL, _PL, _PL]),
+    "hg_canonical_info": (_I, [_P, _I, _I, _P, _P, _P]),
+    "hg_to_canonical": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "hg_from_canonical": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "hg_index_tw": (_I, [_L, _L, _L, _L, _PL]),
+    "hg_index_enumerate": (_I, [_L, _P, _P]),
+    "hg_interface_dump": (_I, [_P, _I, _I, _P, _PL, _PL, _P]),
+    "hg_op_create": (_I, [_P, _I, _P, ctypes.POINTER(_P)]),
+    "hg_op_destroy": (None, [_P]),
+    "hg_apply": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
+    "hg_residual": (_I, [_P, _I, _I, _P, _P, _P, _P]),
+    "hg_jacobi": (_I, [_P, _I, _I, _D, _P, _P, _P, _P]),
+    "hg_restrict": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "hg_prolong_add": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "hg_dot": (_I, [_P, _I, _I, _I, _P, _P, _I, _PD, _P]),
+}
+
+_lib = None
+
+
+class HGError(RuntimeError):
+    def __init__(self, name, code, msg):
+        super().__init__(f"{name} failed with code {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """The loaded shared library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "paper_2308_01792_gb300.build.build() (nvcc, sm_103a)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _call(name, *args):
+    r = getattr(lib(), name)(*args)
+    if r != 0:
+        raise HGError(name, r, lib().hg_last_error().decode())
+    return r
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float32:
+        return HG_F32
+    if t.dtype == torch.float64:
+        return HG_F64
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _ptr(t, n=None):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"tensor has {t.numel()} elements, need {n}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Mesh:
+    """Macro mesh (Sec. 2): vertices (nv,3) float64, cells (nc,4) int64."""
+
+    def __init__(self, xyz, cells):
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        cells = np.ascontiguousarray(cells, dtype=np.int64)
+        h = _P()
+        _call("hg_mesh_create", xyz.ctypes.data_as(_P), len(xyz), cells.ctypes.data_as(_P),
+              len(cells), ctypes.byref(h))
+        self._h = h
+        self.n_cells = len(cells)
+
+    def counts(self):
+        c = (ctypes.c_int64 * 6)()
+        _call("hg_mesh_counts", self._h, c)
+        return dict(zip(["vertices", "edges", "faces", "cells", "boundary_faces",
+                         "interior_faces"], list(c)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hg_mesh_destroy(self._h)
+            self._h = None
+
+
+class Hierarchy:
+    """Levels lmin..lmax of the refined macro mesh (Sec. 3.1, Sec. 5.1)."""
+
+    def __init__(self, mesh: Mesh, lmin: int, lmax: int):
+        h = _P()
+        _call("hg_hier_create", mesh._h, lmin, lmax, ctypes.byref(h))
+        self._h = h
+        self.mesh = mesh
+        self.lmin, self.lmax = lmin, lmax
+
+    def size(self, level, space=HG_SPACE_P1):
+        v = [ctypes.c_int64() for _ in range(4)]
+        _call("hg_function_size", self._h, space, level, *[ctypes.byref(x) for x in v])
+        return tuple(x.value for x in v)   # n_stored, n_unique, n_inner, cell_stride
+
+    def canonical_info(self, level, space=HG_SPACE_P1):
+        ns, nu, _, _ = self.size(level, space)
+        s2c = np.empty(ns, dtype=np.int64)
+        xyz = np.empty((nu, 3), dtype=np.float64)
+        dirich = np.empty(nu, dtype=np.uint8)
+        _call("hg_canonical_info", self._h, space, level, s2c.ctypes.data_as(_P),
+              xyz.ctypes.data_as(_P), dirich.ctypes.data_as(_P))
+        return s2c, xyz, dirich.astype(bool)
+
+    def zeros(self, level, dtype, space=HG_SPACE_P1):
+        import torch
+        return torch.zeros(self.size(level, space)[0], dtype=dtype, device="cuda")
+
+    def to_canonical(self, level, x, space=HG_SPACE_P1, stream=None):
+        import torch
+        ns, nu, _, _ = self.size(level, space)
+        out = torch.empty(nu, dtype=x.dtype, device=x.device)
+        _call("hg_to_canonical", self._h, space, level, _dtype_code(x), _ptr(x, ns),
+              _ptr(out), _stream(stream))
+        return out
+
+    def from_canonical(self, level, c, out=None, space=HG_SPACE_P1, stream=None):
+        import torch
+        ns, nu, _, _ = self.size(level, space)
+        if out is None:
+            out = torch.zeros(ns, dtype=c.dtype, device=c.device)
+        _call("hg_from_canonical", self._h, space, level, _dtype_code(c), _ptr(c, nu),
+              _ptr(out, ns), _stream(stream))
+        return out
+
+    def interface_dump(self, level, space=HG_SPACE_P1, stream=None):
+        import torch
+        nr, mc = ctypes.c_int64(), ctypes.c_int64()
+        _call("hg_interface_dump", self._h, space, level, None, ctypes.byref(nr),
+              ctypes.byref(mc), _stream(stream))
+        out = torch.full((max(nr.value, 1), 2 * mc.value + 1), -1, dtype=torch.int64,
+                         device="cuda")
+        _call("hg_interface_dump", self._h, space, level, _ptr(out), ctypes.byref(nr),
+              ctypes.byref(mc), _stream(stream))
+        return out[:nr.value]
+
+    def restrict(self, fine_level, r_fine, r_coarse, space=HG_SPACE_P1, stream=None):
+        _call("hg_restrict", self._h, space, fine_level, _dtype_code(r_fine), _ptr(r_fine),
+              _ptr(r_coarse), _stream(stream))
+
+    def prolong_add(self, fine_level, e_coarse, x_fine, space=HG_SPACE_P1, stream=None):
+        _call("hg_prolong_add", self._h, space, fine_level, _dtype_code(e_coarse),
+              _ptr(e_coarse), _ptr(x_fine), _stream(stream))
+
+    def dot(self, level, x, y, mask=HG_MASK_INNER, space=HG_SPACE_P1, stream=None):
+        r = ctypes.c_double()
+        _call("hg_dot", self._h, space, level, _dtype_code(x), _ptr(x), _ptr(y), mask,
+              ctypes.byref(r), _stream(stream))
+        return r.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hg_hier_destroy(self._h)
+            self._h = None
+
+
+class Operator:
+    """A matrix-free operator (Sec. 5.2) on every level of a hierarchy."""
+
+    def __init__(self, hier: Hierarchy, kind=HG_OP_P1_LAPLACE, coeff=None):
+        h = _P()
+        carr = None
+        if coeff is not None:
+            carr = np.ascontiguousarray(coeff, dtype=np.float64)
+        _call("hg_op_create", hier._h, kind, carr.ctypes.data_as(_P) if carr is not None else None,
+              ctypes.byref(h))
+        self._h = h
+        self.hier = hier
+        self.kind = kind
+
+    def apply(self, level, x, y, mode=HG_REPLACE, mask=HG_MASK_INNER, stream=None):
+        _call("hg_apply", self._h, level, _dtype_code(x), _ptr(x), _ptr(y), mode, mask,
+              _stream(stream))
+
+    def residual(self, level, x, b, r, stream=None):
+        _call("hg_residual", self._h, level, _dtype_code(x), _ptr(x), _ptr(b), _ptr(r),
+              _stream(stream))
+
+    def jacobi(self, level, x, b, x_out, omega=2.0 / 3.0, stream=None):
+        _call("hg_jacobi", self._h, level, _dtype_code(x), float(omega), _ptr(x), _ptr(b),
+              _ptr(x_out), _stream(stream))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hg_op_destroy(self._h)
+            self._h = None
+
+
+def index_tw(w, i, j, k):
+    out = ctypes.c_int64()
+    _call("hg_index_tw", w, i, j, k, ctypes.byref(out))
+    return out.value
+
+
+def index_enumerate(w, out, stream=None):
+    _call("hg_index_enumerate", w, _ptr(out), _stream(stream))

@@ -1,0 +1,735 @@
+// Host side of the library: macro mesh and primitive graph (Sec. 2), the
+// per-level device maps of the refinement hierarchy (Sec. 3-4), per-cell
+// stencil tables of constant-coefficient operators (Sec. 5.2), and the C ABI
+// glue for everything except multigrid (hg_gmg.cpp).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <set>
+#include <vector>
+
+#include "hg_host.h"
+
+namespace hg {
+
+static thread_local std::string g_err;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("CUDA error %d (%s) in %s", (int)e, cudaGetErrorString(e), what);
+  return HG_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------ mesh
+int Mesh::build(const double* xyz_, int64_t nv_, const int64_t* cells_, int64_t nc_) {
+  nv = nv_;
+  nc = nc_;
+  xyz.assign(xyz_, xyz_ + 3 * nv);
+  cells.resize(nc);
+  for (int64_t c = 0; c < nc; ++c) {
+    std::array<int64_t, 4> v;
+    for (int m = 0; m < 4; ++m) {
+      v[m] = cells_[4 * c + m];
+      if (v[m] < 0 || v[m] >= nv) {
+        set_error("cell %lld references vertex %lld outside [0,%lld)", (long long)c,
+                  (long long)v[m], (long long)nv);
+        return HG_ERR_BAD_MESH;
+      }
+    }
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        if (v[a] == v[b]) {
+          set_error("cell %lld repeats vertex %lld", (long long)c, (long long)v[a]);
+          return HG_ERR_BAD_MESH;
+        }
+    cells[c] = v;
+    double J[9];
+    cell_jacobian(c, J);
+    double det = J[0] * (J[4] * J[8] - J[5] * J[7]) - J[1] * (J[3] * J[8] - J[5] * J[6]) +
+                 J[2] * (J[3] * J[7] - J[4] * J[6]);
+    double scale = 0;
+    for (int q = 0; q < 9; ++q) scale = std::max(scale, std::fabs(J[q]));
+    if (!(std::fabs(det) > 1e-14 * scale * scale * scale)) {
+      set_error("cell %lld has zero volume", (long long)c);
+      return HG_ERR_BAD_MESH;
+    }
+  }
+  // primitives: faces (opposite local vertex f), edges, vertices
+  std::map<std::array<int64_t, 3>, int> fmap;
+  std::map<std::array<int64_t, 2>, int> emap;
+  cell_face.assign(nc, {});
+  cell_edge.assign(nc, {});
+  for (int64_t c = 0; c < nc; ++c) {
+    for (int f = 0; f < 4; ++f) {
+      std::array<int64_t, 3> key;
+      int q = 0;
+      for (int m = 0; m < 4; ++m)
+        if (m != f) key[q++] = cells[c][m];
+      std::sort(key.begin(), key.end());
+      auto it = fmap.find(key);
+      int id;
+      if (it == fmap.end()) {
+        id = (int)faces.size();
+        fmap.emplace(key, id);
+        faces.push_back({{key[0], key[1], key[2]}, {}});
+      } else {
+        id = it->second;
+      }
+      faces[id].cells.push_back((int)c);
+      cell_face[c][f] = id;
+    }
+    for (int e = 0; e < 6; ++e) {
+      std::array<int64_t, 2> key = {cells[c][kEdgeVerts[e][0]], cells[c][kEdgeVerts[e][1]]};
+      std::sort(key.begin(), key.end());
+      auto it = emap.find(key);
+      int id;
+      if (it == emap.end()) {
+        id = (int)edges.size();
+        emap.emplace(key, id);
+        edges.push_back({{key[0], key[1], -1}, {}});
+      } else {
+        id = it->second;
+      }
+      edges[id].cells.push_back((int)c);
+      cell_edge[c][e] = id;
+    }
+  }
+  verts.assign(nv, {});
+  for (int64_t v = 0; v < nv; ++v) verts[v].vid = {v, -1, -1};
+  for (int64_t c = 0; c < nc; ++c)
+    for (int m = 0; m < 4; ++m) verts[cells[c][m]].cells.push_back((int)c);
+  n_boundary_faces = 0;
+  for (auto& f : faces) {
+    if (f.cells.size() > 2) {
+      set_error("face (%lld,%lld,%lld) shared by %zu cells: not conforming",
+                (long long)f.vid[0], (long long)f.vid[1], (long long)f.vid[2], f.cells.size());
+      return HG_ERR_BAD_MESH;
+    }
+    f.dirichlet = f.cells.size() == 1;
+    n_boundary_faces += f.dirichlet;
+  }
+  std::vector<char> vb(nv, 0);
+  std::set<std::array<int64_t, 2>> be;
+  for (auto& f : faces)
+    if (f.dirichlet) {
+      for (int m = 0; m < 3; ++m) vb[f.vid[m]] = 1;
+      for (int a = 0; a < 3; ++a)
+        for (int b = a + 1; b < 3; ++b) be.insert({f.vid[a], f.vid[b]});
+    }
+  for (auto& e : edges) e.dirichlet = be.count({e.vid[0], e.vid[1]}) > 0;
+  for (int64_t v = 0; v < nv; ++v) verts[v].dirichlet = vb[v] != 0;
+  for (auto* prims : {&faces, &edges, &verts})
+    for (auto& p : *prims) std::sort(p.cells.begin(), p.cells.end());
+  // integer lattice: smallest D <= 64 making every coordinate an integer
+  grid_denom = 0;
+  for (int D = 1; D <= 64 && !grid_denom; ++D) {
+    bool ok = true;
+    for (double x : xyz) {
+      double s = x * D;
+      if (std::fabs(s - std::nearbyint(s)) > 1e-9 || std::fabs(s) > 1e6) {
+        ok = false;
+        break;
+      }
+    }
+    if (ok) grid_denom = D;
+  }
+  if (grid_denom) {
+    ixyz.resize(3 * nv);
+    for (int64_t q = 0; q < 3 * nv; ++q) ixyz[q] = (int64_t)std::nearbyint(xyz[q] * grid_denom);
+  }
+  return HG_OK;
+}
+
+void Mesh::cell_jacobian(int64_t c, double J[9]) const {
+  // columns x1-x0, x2-x0, x3-x0 ; J[r*3+col]
+  const double* p0 = &xyz[3 * cells[c][0]];
+  for (int col = 0; col < 3; ++col) {
+    const double* p = &xyz[3 * cells[c][col + 1]];
+    for (int r = 0; r < 3; ++r) J[r * 3 + col] = p[r] - p0[r];
+  }
+}
+
+// Primitive of a class (bit f = on the face opposite local vertex f) of cell c.
+const Prim* Mesh::class_prim(int64_t c, int cls) const {
+  int nb = __builtin_popcount(cls);
+  if (nb == 0 || nb == 4) return nullptr;
+  if (nb == 1) {
+    int f = __builtin_ctz(cls);
+    return &faces[cell_face[c][f]];
+  }
+  int rest[4], q = 0;
+  for (int m = 0; m < 4; ++m)
+    if (!(cls >> m & 1)) rest[q++] = m;
+  if (nb == 3) return &verts[cells[c][rest[0]]];
+  for (int e = 0; e < 6; ++e)
+    if (kEdgeVerts[e][0] == rest[0] && kEdgeVerts[e][1] == rest[1]) return &edges[cell_edge[c][e]];
+  return nullptr;
+}
+
+uint8_t Mesh::class_flags(int64_t c, int cls) const {
+  if (cls == 0) return CF_OWNER;
+  const Prim* p = class_prim(c, cls);
+  if (!p) return 0;
+  uint8_t f = 0;
+  if (p->dirichlet) f |= CF_DIRICHLET;
+  if (p->cells.front() == (int)c) f |= CF_OWNER;
+  return f;
+}
+
+// ------------------------------------------------------------ hierarchy
+template <class T>
+static int upload(T** dst, const std::vector<T>& src) {
+  *dst = nullptr;
+  if (src.empty()) return HG_OK;
+  HG_CUDA(cudaMalloc((void**)dst, src.size() * sizeof(T)));
+  HG_CUDA(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HG_OK;
+}
+
+int Hier::build_level(int l) {
+  LevelHost& H = lv[l - lmin];
+  LevelDev& L = H.dev;
+  memset(&L, 0, sizeof L);
+  L.level = l;
+  L.n = 1 << l;
+  L.w = L.n + 1;
+  L.ncells = (int)mesh->nc;
+  L.cell_stride = (ntet(L.w) + 31) / 32 * 32;
+  L.n_stored = L.cell_stride * mesh->nc;
+  const int n = L.n, w = L.w;
+  // class flags
+  std::vector<uint8_t> fl(16 * mesh->nc);
+  for (int64_t c = 0; c < mesh->nc; ++c)
+    for (int cls = 0; cls < 16; ++cls) fl[16 * c + cls] = mesh->class_flags(c, cls);
+  H.cls_flags = fl;
+  if (int r = upload(&L.cls_flags, fl)) return r;
+  // interface primitives: non-Dirichlet first, then Dirichlet
+  std::vector<IfacePrim> prims;
+  std::vector<IfaceCopy> copies;
+  for (int pass = 0; pass < 2; ++pass) {
+    auto add = [&](const Prim& p, int dim) {
+      if ((int)p.dirichlet != pass || prim_points(dim, n) <= 0) return;
+      IfacePrim ip;
+      ip.dim = dim;
+      ip.ncopies = (int)p.cells.size();
+      ip.first_copy = (int)copies.size();
+      ip.dirichlet = p.dirichlet;
+      for (int c : p.cells) {
+        IfaceCopy cp;
+        cp.cell = c;
+        for (int m = 0; m < 4; ++m) cp.loc[m] = -1;
+        for (int m = 0; m <= dim; ++m)
+          for (int q = 0; q < 4; ++q)
+            if (mesh->cells[c][q] == p.vid[m]) cp.loc[m] = (int8_t)q;
+        copies.push_back(cp);
+      }
+      prims.push_back(ip);
+      if (pass == 0) L.n_prims_inner++;
+      L.max_copies = std::max(L.max_copies, ip.ncopies);
+    };
+    for (auto& p : mesh->faces) add(p, 2);
+    for (auto& p : mesh->edges) add(p, 1);
+    for (auto& p : mesh->verts) add(p, 0);
+  }
+  L.n_prims = (int)prims.size();
+  std::vector<int32_t> pbase(prims.size() + 1, 0);
+  for (size_t q = 0; q < prims.size(); ++q) pbase[q + 1] = pbase[q] + prim_points(prims[q].dim, n);
+  H.prims = prims;
+  H.copies = copies;
+  H.prim_point_base = pbase;
+  if (int r = upload(&L.prims, prims)) return r;
+  if (int r = upload(&L.copies, copies)) return r;
+  if (int r = upload(&L.prim_point_base, pbase)) return r;
+  // canonical numbering by exact lattice coordinates
+  if (mesh->grid_denom) {
+    std::vector<int64_t> keys(L.n_stored, -1);
+    const int64_t off = 1 << 20;
+    for (int64_t c = 0; c < mesh->nc; ++c) {
+      const int64_t* X[4];
+      for (int m = 0; m < 4; ++m) X[m] = &mesh->ixyz[3 * mesh->cells[c][m]];
+      for (int k = 0; k <= n; ++k)
+        for (int j = 0; j + k <= n; ++j)
+          for (int i = 0; i + j + k <= n; ++i) {
+            int64_t P[3];
+            for (int r = 0; r < 3; ++r)
+              P[r] = X[0][r] * n + i * (X[1][r] - X[0][r]) + j * (X[2][r] - X[0][r]) +
+                     k * (X[3][r] - X[0][r]) + off;
+            keys[c * L.cell_stride + tw(w, i, j, k)] = (P[2] << 42) | (P[1] << 21) | P[0];
+          }
+    }
+    std::vector<int64_t> uniq;
+    uniq.reserve(L.n_stored);
+    for (int64_t kk : keys)
+      if (kk >= 0) uniq.push_back(kk);
+    std::sort(uniq.begin(), uniq.end());
+    uniq.erase(std::unique(uniq.begin(), uniq.end()), uniq.end());
+    L.n_unique = (int64_t)uniq.size();
+    std::vector<int32_t> canon(L.n_stored, -1);
+    std::vector<int64_t> rep(L.n_unique, -1);
+    std::vector<uint8_t> dir(L.n_unique, 0);
+    for (int64_t c = 0; c < mesh->nc; ++c)
+      for (int k = 0; k <= n; ++k)
+        for (int j = 0; j + k <= n; ++j)
+          for (int i = 0; i + j + k <= n; ++i) {
+            int64_t s = c * L.cell_stride + tw(w, i, j, k);
+            int64_t u = std::lower_bound(uniq.begin(), uniq.end(), keys[s]) - uniq.begin();
+            canon[s] = (int32_t)u;
+            if (rep[u] < 0) rep[u] = s;
+            dir[u] = (fl[16 * c + point_class(n, i, j, k)] & CF_DIRICHLET) ? 1 : 0;
+          }
+    H.canon = canon;
+    H.canon_rep = rep;
+    H.dirichlet = dir;
+    H.canon_xyz.resize(3 * L.n_unique);
+    const double den = (double)mesh->grid_denom * n;
+    for (int64_t u = 0; u < L.n_unique; ++u) {
+      int64_t kk = uniq[u];
+      H.canon_xyz[3 * u + 0] = (double)((kk & ((1 << 21) - 1)) - off) / den;
+      H.canon_xyz[3 * u + 1] = (double)(((kk >> 21) & ((1 << 21) - 1)) - off) / den;
+      H.canon_xyz[3 * u + 2] = (double)((kk >> 42) - off) / den;
+    }
+    L.n_inner = 0;
+    for (auto d : dir) L.n_inner += d == 0;
+    if (int r = upload(&L.canon, canon)) return r;
+    if (int r = upload(&L.canon_rep, rep)) return r;
+  } else {
+    // without an exact lattice the unique count follows from the primitive graph
+    int64_t nu = (int64_t)mesh->nc * ntet(n - 3) + (int64_t)mesh->faces.size() * ntri(n - 2) +
+                 (int64_t)mesh->edges.size() * std::max(n - 1, 0) + mesh->nv;
+    L.n_unique = nu;
+    int64_t nb = 0;
+    for (auto& f : mesh->faces) nb += f.dirichlet ? ntri(n - 2) : 0;
+    for (auto& e : mesh->edges) nb += e.dirichlet ? std::max(n - 1, 0) : 0;
+    for (auto& v : mesh->verts) nb += v.dirichlet;
+    L.n_inner = nu - nb;
+  }
+  // scratch for deterministic dot products
+  return HG_OK;
+}
+
+int Hier::build(const Mesh* m, int lmin_, int lmax_) {
+  mesh = m;
+  lmin = lmin_;
+  lmax = lmax_;
+  lv.resize(lmax - lmin + 1);
+  int64_t scratch = 0;
+  for (int l = lmin; l <= lmax; ++l) {
+    if (int r = build_level(l)) return r;
+    scratch = std::max(scratch, dot_scratch_len(lv[l - lmin].dev));
+  }
+  HG_CUDA(cudaMalloc(&dot_scratch, scratch * sizeof(double)));
+  HG_CUDA(cudaMalloc(&dot_result, sizeof(double)));
+  HG_CUDA(cudaMallocHost(&dot_host, sizeof(double)));
+  return HG_OK;
+}
+
+Hier::~Hier() {
+  for (auto& H : lv) {
+    LevelDev& L = H.dev;
+    cudaFree(L.cls_flags);
+    cudaFree(L.canon);
+    cudaFree(L.canon_rep);
+    cudaFree(L.prims);
+    cudaFree(L.copies);
+    cudaFree(L.prim_point_base);
+  }
+  cudaFree(dot_scratch);
+  cudaFree(dot_result);
+  if (dot_host) cudaFreeHost(dot_host);
+}
+
+// --------------------------------------------------- element matrices
+// The six micro-cell subgroups (Sec. 3.2): vertex offsets of the cell
+// anchored at p, and the polytope side length w = n - delta.
+const int kTypeOff[6][4][3] = {
+    {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}},  // I-up (w = n)
+    {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}},  // I-down (w = n-2)
+    {{0, 1, 0}, {1, 0, 1}, {1, 0, 0}, {0, 0, 1}},  // octahedral, w = n-1 (4 cells around
+    {{0, 1, 0}, {1, 0, 1}, {0, 0, 1}, {0, 1, 1}},  // the inner edge p+e2 -- p+e1+e3)
+    {{0, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 0}},
+    {{0, 1, 0}, {1, 0, 1}, {1, 1, 0}, {1, 0, 0}}};
+const int kTypeDelta[6] = {0, 2, 1, 1, 1, 1};
+const int kEdgeVerts[6][2] = {{0, 1}, {0, 2}, {0, 3}, {1, 2}, {1, 3}, {2, 3}};
+
+void micro_cell_coords(const Mesh& m, int64_t c, int n, int type, double X[4][3]) {
+  const double* V[4];
+  for (int q = 0; q < 4; ++q) V[q] = &m.xyz[3 * m.cells[c][q]];
+  for (int a = 0; a < 4; ++a)
+    for (int r = 0; r < 3; ++r) {
+      const int* o = kTypeOff[type][a];
+      X[a][r] = V[0][r] + (o[0] * (V[1][r] - V[0][r]) + o[1] * (V[2][r] - V[0][r]) +
+                           o[2] * (V[3][r] - V[0][r])) / (double)n;
+    }
+}
+
+// Barycentric gradients G[4][3] and volume of a tetrahedron.
+void bary_gradients(const double X[4][3], double G[4][3], double* vol) {
+  double J[3][3];
+  for (int r = 0; r < 3; ++r)
+    for (int col = 0; col < 3; ++col) J[r][col] = X[col + 1][r] - X[0][r];
+  double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+               J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+               J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+  double inv[3][3];
+  inv[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) / det;
+  inv[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) / det;
+  inv[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) / det;
+  inv[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) / det;
+  inv[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) / det;
+  inv[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) / det;
+  inv[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) / det;
+  inv[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) / det;
+  inv[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) / det;
+  for (int d = 0; d < 3; ++d) {
+    G[0][d] = 0;
+    for (int q = 0; q < 3; ++q) {
+      G[q + 1][d] = inv[q][d];
+      G[0][d] -= inv[q][d];
+    }
+  }
+  *vol = std::fabs(det) / 6.0;
+}
+
+void p1_element_matrix(int kind, const double X[4][3], double K[4][4]) {
+  double G[4][3], vol;
+  bary_gradients(X, G, &vol);
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      if (kind == HG_OP_P1_MASS) {
+        K[a][b] = vol * (a == b ? 2.0 : 1.0) / 20.0;
+      } else {
+        K[a][b] = vol * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
+      }
+    }
+}
+
+int dir_index(int di, int dj, int dk) {
+  for (int d = 0; d < kNDir; ++d) {
+    int a, b, c;
+    dir_offset(d, a, b, c);
+    if (a == di && b == dj && c == dk) return d;
+  }
+  return -1;
+}
+
+// Is the micro-cell of `type` that has the point in class `cls` as its corner
+// `a` inside the macro cell?  Exact for the six subgroups (see kTypeOff).
+bool incident_inside(int cls, int type, int a) {
+  const int* o = kTypeOff[type][a];
+  for (int r = 0; r < 3; ++r)
+    if (o[r] && (cls >> (r + 1) & 1)) return false;  // needs coordinate r >= 1
+  int s = o[0] + o[1] + o[2];
+  if (s == kTypeDelta[type] && (cls & 1)) return false;  // needs i+j+k <= n-1
+  return true;
+}
+
+// Stencil tables S[cls][dir] of one macro cell at n intervals (FP64).
+void p1_cell_stencils(const Mesh& m, int64_t c, int n, int kind, double S[16][16]) {
+  double K[6][4][4];
+  for (int t = 0; t < 6; ++t) {
+    double X[4][3];
+    micro_cell_coords(m, c, n, t, X);
+    p1_element_matrix(kind, X, K[t]);
+  }
+  for (int cls = 0; cls < 16; ++cls) {
+    for (int d = 0; d < 16; ++d) S[cls][d] = 0.0;
+    for (int t = 0; t < 6; ++t)
+      for (int a = 0; a < 4; ++a) {
+        if (!incident_inside(cls, t, a)) continue;
+        for (int b = 0; b < 4; ++b) {
+          const int* oa = kTypeOff[t][a];
+          const int* ob = kTypeOff[t][b];
+          int d = dir_index(ob[0] - oa[0], ob[1] - oa[1], ob[2] - oa[2]);
+          S[cls][d] += K[t][a][b];
+        }
+      }
+  }
+}
+
+int Op::build(const Hier* h, int kind_, const double* coeff) {
+  hier = h;
+  kind = kind_;
+  if (kind != HG_OP_P1_LAPLACE && kind != HG_OP_P1_MASS) {
+    set_error("operator kind %d not available in this build", kind);
+    return HG_ERR_UNSUPPORTED;
+  }
+  (void)coeff;
+  sten64.resize(h->lmax - h->lmin + 1, nullptr);
+  sten32.resize(h->lmax - h->lmin + 1, nullptr);
+  for (int l = h->lmin; l <= h->lmax; ++l) {
+    const int n = 1 << l;
+    std::vector<double> s64(256 * h->mesh->nc);
+    std::vector<float> s32(256 * h->mesh->nc);
+    for (int64_t c = 0; c < h->mesh->nc; ++c) {
+      double S[16][16];
+      p1_cell_stencils(*h->mesh, c, n, kind, S);
+      for (int q = 0; q < 256; ++q) {
+        s64[256 * c + q] = S[q / 16][q % 16];
+        s32[256 * c + q] = (float)S[q / 16][q % 16];
+      }
+    }
+    if (int r = upload(&sten64[l - h->lmin], s64)) return r;
+    if (int r = upload(&sten32[l - h->lmin], s32)) return r;
+  }
+  return HG_OK;
+}
+
+Op::~Op() {
+  for (auto p : sten64) cudaFree(p);
+  for (auto p : sten32) cudaFree(p);
+}
+
+}  // namespace hg
+
+// ==================================================================== C ABI
+using namespace hg;
+
+struct hg_mesh : Mesh {};
+struct hg_hier : Hier {};
+struct hg_op : Op {};
+
+#define HG_CHECK(cond, code, ...) \
+  do {                            \
+    if (!(cond)) {                \
+      set_error(__VA_ARGS__);     \
+      return code;                \
+    }                             \
+  } while (0)
+
+extern "C" {
+
+const char* hg_last_error(void) { return g_err.c_str(); }
+
+int hg_mesh_create(const double* xyz, int64_t nv, const int64_t* cells, int64_t nc,
+                   hg_mesh** out) {
+  HG_CHECK(xyz && cells && out && nv >= 4 && nc >= 1, HG_ERR_INVALID_ARG,
+           "hg_mesh_create: null pointer or empty mesh");
+  g_err.clear();
+  auto m = std::make_unique<hg_mesh>();
+  if (int r = m->build(xyz, nv, cells, nc)) return r;
+  *out = m.release();
+  return HG_OK;
+}
+
+void hg_mesh_destroy(hg_mesh* mesh) { delete mesh; }
+
+int hg_mesh_counts(const hg_mesh* m, int64_t counts[6]) {
+  HG_CHECK(m && counts, HG_ERR_INVALID_ARG, "hg_mesh_counts: null argument");
+  counts[0] = m->nv;
+  counts[1] = (int64_t)m->edges.size();
+  counts[2] = (int64_t)m->faces.size();
+  counts[3] = m->nc;
+  counts[4] = m->n_boundary_faces;
+  counts[5] = (int64_t)m->faces.size() - m->n_boundary_faces;
+  return HG_OK;
+}
+
+int hg_hier_create(const hg_mesh* mesh, int lmin, int lmax, hg_hier** out) {
+  HG_CHECK(mesh && out, HG_ERR_INVALID_ARG, "hg_hier_create: null argument");
+  HG_CHECK(0 <= lmin && lmin <= lmax && lmax <= 9, HG_ERR_LEVEL_RANGE,
+           "hg_hier_create: need 0 <= lmin <= lmax <= 9, got %d..%d", lmin, lmax);
+  auto h = std::make_unique<hg_hier>();
+  if (int r = h->build(mesh, lmin, lmax)) return r;
+  *out = h.release();
+  return HG_OK;
+}
+
+void hg_hier_destroy(hg_hier* h) { delete h; }
+
+int hg_function_size(const hg_hier* h, int space, int level, int64_t* n_stored,
+                     int64_t* n_unique, int64_t* n_inner, int64_t* cell_stride) {
+  HG_CHECK(h, HG_ERR_INVALID_ARG, "hg_function_size: null hierarchy");
+  HG_CHECK(space == HG_SPACE_P1, HG_ERR_UNSUPPORTED, "space %d not available", space);
+  HG_CHECK(level >= h->lmin && level <= h->lmax, HG_ERR_LEVEL_RANGE, "level %d outside %d..%d",
+           level, h->lmin, h->lmax);
+  const LevelDev& L = h->lv[level - h->lmin].dev;
+  if (n_stored) *n_stored = L.n_stored;
+  if (n_unique) *n_unique = L.n_unique;
+  if (n_inner) *n_inner = L.n_inner;
+  if (cell_stride) *cell_stride = L.cell_stride;
+  return HG_OK;
+}
+
+int hg_canonical_info(const hg_hier* h, int space, int level, int64_t* s2c, double* xyz,
+                      uint8_t* dirichlet) {
+  HG_CHECK(h, HG_ERR_INVALID_ARG, "hg_canonical_info: null hierarchy");
+  HG_CHECK(space == HG_SPACE_P1, HG_ERR_UNSUPPORTED, "space %d not available", space);
+  HG_CHECK(level >= h->lmin && level <= h->lmax, HG_ERR_LEVEL_RANGE, "level out of range");
+  HG_CHECK(h->mesh->grid_denom, HG_ERR_UNSUPPORTED,
+           "canonical order needs vertex coordinates on a lattice of spacing 1/D, D <= 64");
+  const LevelHost& H = h->lv[level - h->lmin];
+  if (s2c)
+    for (size_t q = 0; q < H.canon.size(); ++q) s2c[q] = H.canon[q];
+  if (xyz) std::copy(H.canon_xyz.begin(), H.canon_xyz.end(), xyz);
+  if (dirichlet) std::copy(H.dirichlet.begin(), H.dirichlet.end(), dirichlet);
+  return HG_OK;
+}
+
+static const LevelDev* level_of(const Hier* h, int space, int level) {
+  if (!h) {
+    set_error("null hierarchy");
+    return nullptr;
+  }
+  if (space != HG_SPACE_P1) {
+    set_error("space %d not available", space);
+    return nullptr;
+  }
+  if (level < h->lmin || level > h->lmax) {
+    set_error("level %d outside %d..%d", level, h->lmin, h->lmax);
+    return nullptr;
+  }
+  return &h->lv[level - h->lmin].dev;
+}
+
+int hg_to_canonical(const hg_hier* h, int space, int level, int dtype, const void* st,
+                    void* can, void* stream) {
+  const LevelDev* L = level_of(h, space, level);
+  if (!L) return HG_ERR_INVALID_ARG;
+  HG_CHECK(h->mesh->grid_denom, HG_ERR_UNSUPPORTED, "mesh has no exact lattice");
+  HG_CHECK(st && can && (dtype == HG_F32 || dtype == HG_F64), HG_ERR_INVALID_ARG,
+           "hg_to_canonical: bad argument");
+  return launch_to_canonical(*L, dtype, st, can, (cudaStream_t)stream);
+}
+
+int hg_from_canonical(const hg_hier* h, int space, int level, int dtype, const void* can,
+                      void* st, void* stream) {
+  const LevelDev* L = level_of(h, space, level);
+  if (!L) return HG_ERR_INVALID_ARG;
+  HG_CHECK(h->mesh->grid_denom, HG_ERR_UNSUPPORTED, "mesh has no exact lattice");
+  HG_CHECK(st && can && (dtype == HG_F32 || dtype == HG_F64), HG_ERR_INVALID_ARG,
+           "hg_from_canonical: bad argument");
+  return launch_from_canonical(*L, dtype, can, st, (cudaStream_t)stream);
+}
+
+int hg_index_tw(int64_t w, int64_t i, int64_t j, int64_t k, int64_t* out) {
+  HG_CHECK(out && w >= 1 && i >= 0 && j >= 0 && k >= 0 && i + j + k < w, HG_ERR_INVALID_ARG,
+           "hg_index_tw: (%lld,%lld,%lld) not in I_tet(%lld)", (long long)i, (long long)j,
+           (long long)k, (long long)w);
+  *out = tw(w, i, j, k);
+  return HG_OK;
+}
+
+int hg_index_enumerate(int64_t w, int64_t* out, void* stream) {
+  HG_CHECK(out && w >= 1 && w <= 1025, HG_ERR_INVALID_ARG, "hg_index_enumerate: bad argument");
+  return launch_index_enumerate((int)w, out, (cudaStream_t)stream);
+}
+
+int hg_interface_dump(const hg_hier* h, int space, int level, int64_t* out, int64_t* n_rows,
+                      int64_t* max_copies, void* stream) {
+  const LevelDev* L = level_of(h, space, level);
+  if (!L) return HG_ERR_INVALID_ARG;
+  const LevelHost& H = h->lv[level - h->lmin];
+  if (n_rows) *n_rows = H.prim_point_base.back();
+  if (max_copies) *max_copies = L->max_copies;
+  if (!out) return HG_OK;
+  return launch_interface_dump(*L, out, (cudaStream_t)stream);
+}
+
+int hg_op_create(const hg_hier* h, int kind, const double* coeff, hg_op** out) {
+  HG_CHECK(h && out, HG_ERR_INVALID_ARG, "hg_op_create: null argument");
+  auto op = std::make_unique<hg_op>();
+  if (int r = op->build(h, kind, coeff)) return r;
+  *out = op.release();
+  return HG_OK;
+}
+
+void hg_op_destroy(hg_op* op) { delete op; }
+
+static int run_cell_op(const hg_op* op, int level, int dtype, StencilArgs a, cudaStream_t s) {
+  HG_CHECK(op, HG_ERR_INVALID_ARG, "null operator");
+  const LevelDev* L = level_of(op->hier, HG_SPACE_P1, level);
+  if (!L) return HG_ERR_LEVEL_RANGE;
+  HG_CHECK(dtype == HG_F32 || dtype == HG_F64, HG_ERR_INVALID_ARG, "bad dtype %d", dtype);
+  HG_CHECK(a.x && a.out && a.x != a.out, HG_ERR_INVALID_ARG,
+           "input and output must be distinct non-null device pointers");
+  a.sten = dtype == HG_F64 ? (const void*)op->sten64[level - op->hier->lmin]
+                           : (const void*)op->sten32[level - op->hier->lmin];
+  return launch_p1_const(*L, dtype, a, s);
+}
+
+int hg_apply(const hg_op* op, int level, int dtype, const void* x, void* y, int mode, int mask,
+             void* stream) {
+  HG_CHECK(mode == HG_REPLACE || mode == HG_ADD, HG_ERR_INVALID_ARG, "bad mode %d", mode);
+  HG_CHECK(mask == HG_MASK_INNER || mask == HG_MASK_ALL, HG_ERR_INVALID_ARG, "bad mask %d", mask);
+  StencilArgs a{};
+  a.x = x;
+  a.out = y;
+  a.op = OP_APPLY;
+  a.mode = mode;
+  a.mask = mask;
+  return run_cell_op(op, level, dtype, a, (cudaStream_t)stream);
+}
+
+int hg_residual(const hg_op* op, int level, int dtype, const void* x, const void* b, void* r,
+                void* stream) {
+  HG_CHECK(b && b != r, HG_ERR_INVALID_ARG, "hg_residual: b must be distinct from r");
+  StencilArgs a{};
+  a.x = x;
+  a.b = b;
+  a.out = r;
+  a.op = OP_RESID;
+  a.mask = HG_MASK_INNER;
+  return run_cell_op(op, level, dtype, a, (cudaStream_t)stream);
+}
+
+int hg_jacobi(const hg_op* op, int level, int dtype, double omega, const void* x, const void* b,
+              void* x_out, void* stream) {
+  HG_CHECK(b && b != x_out, HG_ERR_INVALID_ARG, "hg_jacobi: b must be distinct from x_out");
+  StencilArgs a{};
+  a.x = x;
+  a.b = b;
+  a.out = x_out;
+  a.omega = omega;
+  a.op = OP_JACOBI;
+  a.mask = HG_MASK_INNER;
+  return run_cell_op(op, level, dtype, a, (cudaStream_t)stream);
+}
+
+int hg_restrict(const hg_hier* h, int space, int fine_level, int dtype, const void* rf, void* rc,
+                void* stream) {
+  const LevelDev* F = level_of(h, space, fine_level);
+  const LevelDev* C = level_of(h, space, fine_level - 1);
+  if (!F || !C) return HG_ERR_LEVEL_RANGE;
+  HG_CHECK(rf && rc && rf != rc, HG_ERR_INVALID_ARG, "hg_restrict: bad pointers");
+  return launch_restrict_p1(*F, *C, dtype, rf, rc, (cudaStream_t)stream);
+}
+
+int hg_prolong_add(const hg_hier* h, int space, int fine_level, int dtype, const void* ec,
+                   void* xf, void* stream) {
+  const LevelDev* F = level_of(h, space, fine_level);
+  const LevelDev* C = level_of(h, space, fine_level - 1);
+  if (!F || !C) return HG_ERR_LEVEL_RANGE;
+  HG_CHECK(ec && xf && ec != xf, HG_ERR_INVALID_ARG, "hg_prolong_add: bad pointers");
+  return launch_prolong_p1(*F, *C, dtype, ec, xf, (cudaStream_t)stream);
+}
+
+int hg_dot(const hg_hier* h, int space, int level, int dtype, const void* x, const void* y,
+           int mask, double* result, void* stream) {
+  const LevelDev* L = level_of(h, space, level);
+  if (!L) return HG_ERR_LEVEL_RANGE;
+  HG_CHECK(x && y && result, HG_ERR_INVALID_ARG, "hg_dot: null pointer");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = launch_dot(*L, dtype, x, y, mask, h->dot_scratch, h->dot_result, s)) return r;
+  HG_CUDA(cudaMemcpyAsync(h->dot_host, h->dot_result, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HG_CUDA(cudaStreamSynchronize(s));
+  *result = *h->dot_host;
+  return HG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,82 @@
+// Host-side data structures: macro mesh with its primitive graph, the level
+// hierarchy and operators.  Internal to the library.
+#pragma once
+
+#include <array>
+#include <vector>
+
+#include "hg_internal.h"
+
+namespace hg {
+
+extern const int kTypeOff[6][4][3];
+extern const int kTypeDelta[6];
+extern const int kEdgeVerts[6][2];
+
+// A macro primitive (vertex, edge or face) with the macro cells containing it
+// (ascending id).  vid: its macro vertex ids, ascending (unused = -1).
+struct Prim {
+  std::array<int64_t, 3> vid;
+  std::vector<int> cells;
+  bool dirichlet = false;
+};
+
+// Macro mesh and its primitive graph (Sec. 2: one data structure per coarse
+// vertex/edge/face/cell with links to the neighbours).
+struct Mesh {
+  int64_t nv = 0, nc = 0;
+  std::vector<double> xyz;
+  std::vector<std::array<int64_t, 4>> cells;
+  std::vector<Prim> faces, edges, verts;
+  std::vector<std::array<int, 4>> cell_face;  // face opposite local vertex f
+  std::vector<std::array<int, 6>> cell_edge;  // local edge e = kEdgeVerts[e]
+  int64_t n_boundary_faces = 0;
+  int grid_denom = 0;                         // D with integer xyz*D, 0 if none
+  std::vector<int64_t> ixyz;
+
+  int build(const double* xyz, int64_t nv, const int64_t* cells, int64_t nc);
+  void cell_jacobian(int64_t c, double J[9]) const;
+  const Prim* class_prim(int64_t c, int cls) const;
+  uint8_t class_flags(int64_t c, int cls) const;
+};
+
+struct LevelHost {
+  LevelDev dev{};
+  std::vector<uint8_t> cls_flags;
+  std::vector<IfacePrim> prims;
+  std::vector<IfaceCopy> copies;
+  std::vector<int32_t> prim_point_base;
+  std::vector<int32_t> canon;
+  std::vector<int64_t> canon_rep;
+  std::vector<uint8_t> dirichlet;
+  std::vector<double> canon_xyz;
+};
+
+struct Hier {
+  const Mesh* mesh = nullptr;
+  int lmin = 0, lmax = 0;
+  std::vector<LevelHost> lv;
+  double* dot_scratch = nullptr;
+  double* dot_result = nullptr;
+  double* dot_host = nullptr;
+
+  int build(const Mesh* m, int lmin, int lmax);
+  int build_level(int l);
+  ~Hier();
+};
+
+struct Op {
+  const Hier* hier = nullptr;
+  int kind = 0;
+  std::vector<double*> sten64;  // per level [ncells][16][16]
+  std::vector<float*> sten32;
+
+  int build(const Hier* h, int kind, const double* coeff);
+  ~Op();
+};
+
+void micro_cell_coords(const Mesh& m, int64_t c, int n, int type, double X[4][3]);
+void bary_gradients(const double X[4][3], double G[4][3], double* vol);
+void p1_cell_stencils(const Mesh& m, int64_t c, int n, int kind, double S[16][16]);
+
+}  // namespace hg

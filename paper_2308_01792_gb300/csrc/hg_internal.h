@@ -1,0 +1,168 @@
+// Internal declarations shared by the host code (hg_host.cpp, hg_gmg.cpp) and
+// the CUDA kernels (*.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hytet.h"
+
+#if defined(__CUDACC__)
+#define HG_HD __host__ __device__ __forceinline__
+#else
+#define HG_HD inline
+#endif
+
+namespace hg {
+
+// ---------------------------------------------------------------- indexing
+// Tetrahedral / triangular numbers and the linearisation t_w (Sec. 4).
+HG_HD int64_t ntet(int64_t w) { return w > 0 ? w * (w + 1) * (w + 2) / 6 : 0; }
+HG_HD int64_t ntri(int64_t w) { return w > 0 ? w * (w + 1) / 2 : 0; }
+HG_HD int64_t tw(int64_t w, int64_t i, int64_t j, int64_t k) {
+  return ntet(w) - ntet(w - k) + ntri(w - k) - ntri(w - k - j) + i;
+}
+// 32-bit variants for device loops (valid for w <= 1025).
+HG_HD int ntet32(int w) { return w > 0 ? w * (w + 1) * (w + 2) / 6 : 0; }
+HG_HD int ntri32(int w) { return w > 0 ? w * (w + 1) / 2 : 0; }
+HG_HD int tw32(int w, int i, int j, int k) {
+  return ntet32(w) - ntet32(w - k) + ntri32(w - k) - ntri32(w - k - j) + i;
+}
+// Start of row (j,k) of I_tet(w) and the offset of plane k.
+HG_HD int row_start(int w, int j, int k) { return tw32(w, 0, j, k); }
+
+// 15-point neighbourhood of a micro-vertex: centre + 7 lattice edge
+// directions and their negatives.  Order fixed here and used everywhere.
+//   0:(0,0,0)
+//   1:(+1,0,0)  2:(-1,0,0)  3:(0,+1,0)  4:(0,-1,0)  5:(0,0,+1)  6:(0,0,-1)
+//   7:(-1,+1,0) 8:(+1,-1,0) 9:(-1,0,+1) 10:(+1,0,-1)
+//  11:(0,-1,+1) 12:(0,+1,-1) 13:(+1,-1,+1) 14:(-1,+1,-1)
+constexpr int kNDir = 15;
+#if defined(__CUDACC__)
+__host__ __device__
+#endif
+inline void dir_offset(int d, int& di, int& dj, int& dk) {
+  const signed char t[15][3] = {{0, 0, 0},  {1, 0, 0},  {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+                                {0, 0, 1},  {0, 0, -1}, {-1, 1, 0}, {1, -1, 0}, {-1, 0, 1},
+                                {1, 0, -1}, {0, -1, 1}, {0, 1, -1}, {1, -1, 1}, {-1, 1, -1}};
+  di = t[d][0];
+  dj = t[d][1];
+  dk = t[d][2];
+}
+
+// Boundary class of a cell-local point: bit0 on face opposite v0
+// (i+j+k = n), bit1 on i = 0 (opposite v1), bit2 on j = 0, bit3 on k = 0.
+HG_HD int point_class(int n, int i, int j, int k) {
+  return (i + j + k == n ? 1 : 0) | (i == 0 ? 2 : 0) | (j == 0 ? 4 : 0) | (k == 0 ? 8 : 0);
+}
+
+// Per-(cell, class) flags.
+enum : uint8_t { CF_DIRICHLET = 1, CF_OWNER = 2 };
+
+// Point of a macro primitive, seen from one of the cells that contain it.
+struct IfaceCopy {
+  int32_t cell;
+  int8_t loc[4];  // cell-local vertex index (0..3) of the primitive's vertex m; -1 unused
+};
+// A macro primitive (vertex, edge or face) shared by >= 1 cells.
+struct IfacePrim {
+  int32_t dim;         // 0 vertex, 1 edge, 2 face
+  int32_t ncopies;     // cells containing it (sorted ascending cell id)
+  int32_t first_copy;  // index into the copy array
+  int32_t dirichlet;   // 1 if on the domain boundary
+};
+
+// Number of interior points of a primitive at n intervals per macro edge.
+HG_HD int prim_points(int dim, int n) {
+  return dim == 0 ? 1 : dim == 1 ? (n - 1 > 0 ? n - 1 : 0) : (int)ntri(n - 2);
+}
+// Barycentric weights (over the primitive's vertices, sorted by global id)
+// of point p of a primitive.  Faces: rows b = 1..n-2, a = 1..n-1-b.
+HG_HD void prim_point_weights(int dim, int n, int p, int wts[3]) {
+  if (dim == 0) {
+    wts[0] = n; wts[1] = 0; wts[2] = 0;
+  } else if (dim == 1) {
+    int t = p + 1;
+    wts[0] = n - t; wts[1] = t; wts[2] = 0;
+  } else {
+    // row b has n-1-b points (a = 1..n-1-b); rows b = 1..n-2
+    int b = 1, rem = p;
+    while (rem >= n - 1 - b) { rem -= n - 1 - b; ++b; }
+    int a = rem + 1;
+    wts[0] = n - a - b; wts[1] = a; wts[2] = b;
+  }
+}
+// Cell-local (i,j,k) of a primitive point given the copy's local vertex ids.
+HG_HD void copy_local_ijk(const IfaceCopy& c, int dim, const int wts[3], int& i, int& j, int& k) {
+  int lam[4] = {0, 0, 0, 0};
+  for (int m = 0; m <= dim; ++m) lam[c.loc[m]] += wts[m];
+  i = lam[1]; j = lam[2]; k = lam[3];
+}
+
+// Device-resident description of one level of one hierarchy (P1 vertex lattice).
+struct LevelDev {
+  int level, n, w;           // w = n + 1 vertices per macro edge
+  int ncells;
+  int64_t cell_stride;       // stored elements per cell (padded)
+  int64_t n_stored, n_unique, n_inner;
+  // device arrays
+  uint8_t* cls_flags;        // [ncells*16]
+  int32_t* canon;            // [n_stored] stored -> canonical, -1 padding
+  int64_t* canon_rep;        // [n_unique] a stored index of each unique DoF
+  IfacePrim* prims;          // [n_prims], non-Dirichlet first
+  IfaceCopy* copies;
+  int n_prims, n_prims_inner, max_copies;
+  int32_t* prim_point_base;  // [n_prims+1] prefix sums of prim_points
+};
+
+// Dense FP64 coarse-grid solver data.
+struct CoarseDev {
+  int n;                 // interior unknowns
+  double* ainv;          // [n*n] row-major inverse of the coarse matrix
+  int64_t* stored_rep;   // [n] stored index of the owner copy of each unknown
+  int32_t* canon_of_stored;  // reuse of LevelDev::canon (not owned)
+};
+
+// ------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+#define HG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return ::hg::cuda_fail(e_, #call); \
+  } while (0)
+
+// ------------------------------------------------------------ launchers
+// Operation of the cell kernel + interface kernel pair.
+enum CellOp : int { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2 };
+
+struct StencilArgs {
+  const void* x;        // input
+  const void* b;        // rhs (RESID/JACOBI)
+  void* out;            // output
+  const void* sten;     // [ncells][16][16] T (class, direction)
+  double omega;
+  int op, mode, mask;
+};
+
+int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);
+int launch_index_enumerate(int w, int64_t* out, cudaStream_t s);
+int launch_interface_dump(const LevelDev& L, int64_t* out, cudaStream_t s);
+int launch_to_canonical(const LevelDev& L, int dtype, const void* st, void* can, cudaStream_t s);
+int launch_from_canonical(const LevelDev& L, int dtype, const void* can, void* st, cudaStream_t s);
+int launch_restrict_p1(const LevelDev& F, const LevelDev& C, int dtype, const void* rf, void* rc,
+                       cudaStream_t s);
+int launch_prolong_p1(const LevelDev& F, const LevelDev& C, int dtype, const void* ec, void* xf,
+                      cudaStream_t s);
+// FP64 dot over owned points; partial sums go to `scratch` (>= dot_scratch_len(L) doubles),
+// the final value to `result_dev` (device double).
+int64_t dot_scratch_len(const LevelDev& L);
+int launch_dot(const LevelDev& L, int dtype, const void* x, const void* y, int mask,
+               double* scratch, double* result_dev, cudaStream_t s);
+int launch_coarse_solve(const LevelDev& L, const CoarseDev& C, int dtype, const void* b, void* x,
+                        cudaStream_t s);
+
+}  // namespace hg

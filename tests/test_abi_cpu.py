@@ -1,0 +1,75 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol,
+and its host-only logic (mesh checks, t_w) behaves.  No GPU calls."""
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import paper_2308_01792_gb300 as hg
+import synthgen as sg
+from oracle import indexing as ix
+
+HDR = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "hytet.h")
+
+
+def _declared():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hg_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def built():
+    if not os.path.exists(hg.LIB_PATH):
+        from paper_2308_01792_gb300 import build
+        build.build()
+    return hg.lib()
+
+
+def test_every_declared_symbol_is_exported(built):
+    out = subprocess.run(["nm", "-D", "--defined-only", hg.LIB_PATH], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (hg_[a-z0-9_]+)", out))
+    declared = _declared()
+    assert declared, "no declarations parsed"
+    missing = [d for d in declared if d not in exported]
+    assert not missing, missing
+    assert set(declared) == set(hg.SIGNATURES), "binding and header disagree"
+
+
+def test_host_tw_matches_oracle(built):
+    for w in (1, 2, 3, 9, 33, 129):
+        for (i, j, k) in ix.index_set_tet(w)[:: max(1, ix.n_tet(w) // 500)]:
+            assert hg.index_tw(w, i, j, k) == ix.tw(w, i, j, k)
+    with pytest.raises(hg.HGError):
+        hg.index_tw(3, 2, 1, 0)
+
+
+def test_mesh_primitive_graph_counts(built):
+    for m in (1, 2, 3):
+        mm = sg.kuhn_cube(m)
+        c = hg.Mesh(mm.xyz, mm.cells).counts()
+        assert c["cells"] == 6 * m ** 3 and c["vertices"] == (m + 1) ** 3
+        assert c["boundary_faces"] == 12 * m * m
+        # Euler characteristic of the macro mesh of a ball
+        assert c["vertices"] - c["edges"] + c["faces"] - c["cells"] == 1
+    r = sg.reference_tet()
+    assert hg.Mesh(r.xyz, r.cells).counts()["boundary_faces"] == 4
+
+
+def test_bad_meshes_are_rejected(built):
+    r = sg.reference_tet()
+    with pytest.raises(hg.HGError) as e:
+        hg.Mesh(r.xyz, np.array([[0, 1, 2, 2]]))
+    assert e.value.code == -2
+    with pytest.raises(hg.HGError):
+        hg.Mesh(r.xyz, np.array([[0, 1, 2, 7]]))
+    flat = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0]], dtype=float)
+    with pytest.raises(hg.HGError):
+        hg.Mesh(flat, np.array([[0, 1, 2, 3]]))
+    # three cells on one face: not conforming
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 1]], float)
+    with pytest.raises(hg.HGError):
+        hg.Mesh(xyz, np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]]))
