@@ -1,0 +1,309 @@
+"""Benchmark of the matrix-free P1 hot path on one GB300 (or N replicas).
+
+Workload (default): unit cube split into 6 Kuhn macro-tetrahedra, refined to
+level 7 (129^3 = 2 146 689 vertex DoFs), P1 Laplacian with constant-coefficient
+15-point stencils, FP32.  One step = one operator application y = A x through
+the C ABI, including the ghost-layer exchange between macro primitives.
+Inputs are seeded U[-1,1] vectors (zero Dirichlet values); 32 distinct (x, y)
+pairs rotate between steps so the working set (563 MB) exceeds 4x L2.
+
+Printed: one JSON line (rank 0) with the value in GDoF/s (unique DoFs per
+second, all ranks), the roofline of the apply against the measured HBM peak,
+the oracle's CSR SpMV timed on the host cores (cpu_baseline), an end-to-end
+number through host buffers (e2e), and the SM clocks seen during timing.
+
+``--impl reference`` times the CPU oracle (the only other arm this task has)
+on the same metric: CSR SpMV of the same operator on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthgen as sg  # noqa: E402
+
+WORKLOAD = "cube6_L7_p1_laplace_apply_f32"
+LEVEL = 7
+N_PAIRS = 32
+METRIC = "matvec GDoF/s (% HBM roofline); GMG time to 1e-8 resid, learned vs plain"
+BYTES_PER_DOF = 8            # FP32: x read once + y written once per unique DoF
+SAMPLE_LEVEL = 6             # oracle sample: same mesh one level coarser
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _kernel_source_sha():
+    src = os.path.join(ROOT, "paper_2308_01792_gb300", "csrc", "hg_p1.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per apply from the committed ncu summary, if it matches the source."""
+    path = os.path.join(ROOT, "profiles", "p1_apply_cube6_L7_f32.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"source_sha256_16:\s*([0-9a-f]+)", txt)
+    t = re.search(r"traffic_bytes_per_apply:\s*([0-9.eE+]+)", txt)
+    if not m or not t or m.group(1) != _kernel_source_sha():
+        return None
+    return float(t.group(1))
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_baseline_spmv(seconds=10.0):
+    """Oracle CSR SpMV (SciPy, single thread) on the same mesh at SAMPLE_LEVEL."""
+    from oracle import fem
+    from oracle.mesh import RefinedMesh
+    macro = sg.kuhn_cube(1)
+    rm = RefinedMesh(macro, SAMPLE_LEVEL)
+    A = fem.assemble(rm.cells, fem.p1_stiffness(rm.cell_xyz), rm.n_vertices)
+    ii = rm.interior
+    AII = A[ii][:, ii].tocsr()
+    x = sg.uniform_vector(0, rm.n_vertices)[ii]
+    y = AII @ x
+    reps, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        y = AII @ x
+        reps += 1
+    dt = time.perf_counter() - t0
+    return {"value": rm.n_vertices * reps / dt / 1e9, "unit": "GDoF/s", "cores": 1,
+            "kind": "oracle",
+            "sample": f"SciPy CSR SpMV of the same P1 operator on the same mesh at level "
+                      f"{SAMPLE_LEVEL} ({rm.n_vertices} DoFs), {reps} reps in {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import fem
+    from oracle.mesh import RefinedMesh
+    rm = RefinedMesh(sg.kuhn_cube(1), SAMPLE_LEVEL)
+    A = fem.assemble(rm.cells, fem.p1_stiffness(rm.cell_xyz), rm.n_vertices)
+    ii = rm.interior
+    AII = A[ii][:, ii].tocsr()
+    x = sg.uniform_vector(0, rm.n_vertices)[ii]
+    inner = 20                            # SpMVs per step: a bounded sample of the workload
+    for _ in range(args.warmup):
+        for _ in range(inner):
+            y = AII @ x
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for _ in range(inner):
+            y = AII @ x
+    dt = time.perf_counter() - t0
+    val = rm.n_vertices * inner * args.steps / dt / 1e9
+    sample = (f"SciPy CSR SpMV (single thread) of the same P1 operator on the same mesh at level "
+              f"{SAMPLE_LEVEL} ({rm.n_vertices} DoFs), {inner} SpMVs per step")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": "GDoF/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "oracle_level": SAMPLE_LEVEL},
+        "cpu_baseline": {"value": val, "unit": "GDoF/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": "GDoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+    sys.stdout.flush()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_2308_01792_gb300 as hg
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pg = dist
+
+    macro = sg.kuhn_cube(1)
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), LEVEL, LEVEL)
+    op = hg.Operator(H)
+    ns, nu, ni, stride = H.size(LEVEL)
+    _, _, dirich = H.canonical_info(LEVEL)
+    dt = torch.float32
+    xs, ys = [], []
+    for p in range(N_PAIRS):
+        c = sg.uniform_vector(1000 + p, nu)
+        c[dirich] = 0.0
+        xs.append(H.from_canonical(LEVEL, torch.tensor(c, dtype=dt, device="cuda")))
+        ys.append(H.zeros(LEVEL, dt))
+    stream = torch.cuda.current_stream()
+
+    def step(s):
+        op.apply(LEVEL, xs[s % N_PAIRS], ys[s % N_PAIRS], stream=stream)
+
+    for s in range(max(args.warmup, 3)):
+        step(s)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        step(s)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    if pg:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = nu * ws / (ms_step * 1e-3) / 1e9
+
+    # end to end: canonical host vector -> device -> apply -> host, pinned buffers
+    xh = torch.tensor(sg.uniform_vector(7, nu), dtype=dt).pin_memory()
+    xh[torch.from_numpy(dirich.astype(bool))] = 0
+    yh = torch.empty(nu, dtype=dt).pin_memory()
+    xd = torch.empty(nu, dtype=dt, device="cuda")
+    xst, yst = H.zeros(LEVEL, dt), H.zeros(LEVEL, dt)
+    e2e_steps = max(10, args.steps // 4)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        H.from_canonical(LEVEL, xd, out=xst, stream=stream)
+        op.apply(LEVEL, xst, yst, stream=stream)
+        yd = H.to_canonical(LEVEL, yst, stream=stream)
+        yh.copy_(yd, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_DOF * nu / (ms_step * 1e-3) / 1e9
+    traffic = _profiled_traffic()
+    out = {
+        "metric": METRIC, "value": value, "unit": "GDoF/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "mesh": "unit cube, 6 Kuhn macro-tetrahedra",
+                   "level": LEVEL, "unique_dofs": nu, "stored_dofs": ns, "operator": "P1 Laplacian",
+                   "l2": f"{N_PAIRS} rotating x/y pairs, {N_PAIRS * 2 * ns * 4 / 1e6:.0f} MB > 4x L2",
+                   "parallelism": f"replicas{ws}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": "p1_fused_kernel<float,APPLY> (one launch per apply)",
+                     "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch":
+                         BYTES_PER_DOF * nu},
+        "e2e": {"value": nu / (e2e_ms * 1e-3) / 1e9, "unit": "GDoF/s",
+                "h2d_bytes_per_step": 4 * nu, "d2h_bytes_per_step": 4 * nu},
+        "gpu_launches": args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline_spmv()
+    if rank == 0:
+        print(json.dumps(out))
+        sys.stdout.flush()
+    if pg:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -125,6 +125,13 @@ int hg_to_canonical(const hg_hier* hier, int space, int level, int dtype, const 
 int hg_from_canonical(const hg_hier* hier, int space, int level, int dtype,
                       const void* canonical, void* stored, void* stream);
 
+/* Synchronise `stream` and report whether any kernel of this hierarchy gave
+ * up a bounded wait (HG_ERR_TIMEOUT; the word is then cleared).  Kernels
+ * never spin without a limit: a wait that runs out records the error and the
+ * kernel finishes, so the context stays usable.  hg_dot and hg_solve check
+ * the same word at their synchronisation points. */
+int hg_device_status(const hg_hier* hier, void* stream);
+
 /* ----------------------------------------------------- index functions --
  * t_w(i,j,k) = N_tet(w) - N_tet(w-k) + N_tri(w-k) - N_tri(w-k-j) + i
  * (Sec. 4).  Host evaluation; HG_ERR_INVALID_ARG if (i,j,k) not in I_tet(w). */
@@ -183,6 +190,54 @@ int hg_prolong_add(const hg_hier* hier, int space, int fine_level, int dtype,
  * written to *result (host) after the call synchronises `stream`. */
 int hg_dot(const hg_hier* hier, int space, int level, int dtype, const void* x, const void* y,
            int mask, double* result, void* stream);
+
+/* ---------------------------------------------------------- multigrid --
+ * Geometric multigrid on the refinement hierarchy (multigrid by design,
+ * Sec. 5.1): V(nu1,nu2) cycles with weighted-Jacobi smoothing (Sec. 5.2.1:
+ * smoothers that need only the matrix-vector product and the diagonal),
+ * restriction P^T and prolongation P (nodal interpolation), and an exact
+ * FP64 solve on the coarsest level (dense Cholesky inverse, <= 2048
+ * unknowns; built at creation by applying the operator to unit vectors).
+ * Only HG_OP_P1_LAPLACE / HG_OP_P1_MASS operators are accepted so far. */
+enum { HG_PREC_F64 = 0,   /* plain FP64 V-cycles                                  */
+       HG_PREC_MIXED = 1  /* FP32 V-cycles inside FP64 iterative refinement: the
+                             outer residual, norms and coarse solve stay FP64   */
+};
+
+typedef struct {
+  int nu1, nu2;        /* pre-/post-smoothing steps (default 3, 3)               */
+  double omega;        /* Jacobi weight (default 2/3)                            */
+  int lmin;            /* coarsest level; -1 = the hierarchy's lmin              */
+  int inner_cycles;    /* FP32 V-cycles per refinement step (default 1)          */
+} hg_gmg_params;
+
+/* Fill *p with the defaults above. */
+void hg_gmg_default_params(hg_gmg_params* p);
+
+/* Allocates per-level work vectors (FP64; FP32 on first mixed use) and the
+ * coarse inverse on the current device.  p == NULL selects the defaults.
+ * Errors: HG_ERR_LEVEL_RANGE, HG_ERR_INVALID_ARG (bad parameters, coarse
+ * level too large or not SPD), HG_ERR_UNSUPPORTED, HG_ERR_CUDA. */
+int hg_gmg_create(const hg_op* op, const hg_gmg_params* p, hg_gmg** out);
+void hg_gmg_destroy(hg_gmg* g);
+
+/* One V-cycle on `level` (lmin < level <= lmax: smoothing, residual,
+ * restriction, recursion, prolongation; level == lmin: coarse solve):
+ * x is updated in place towards A^-1 b.  x, b: stored vectors of dtype. */
+int hg_vcycle(hg_gmg* g, int level, int dtype, void* x, const void* b, void* stream);
+
+/* Solve A x = b on lmax (FP64 stored vectors) from x = 0 until
+ * ||b - A x||_2 <= rel_tol ||b||_2 over the non-Dirichlet DoFs, at most
+ * max_iter V-cycles (HG_PREC_F64) or refinement steps (HG_PREC_MIXED).
+ * Synchronises `stream` once per iteration to test convergence.  Outputs
+ * iterations and the final relative residual (may be NULL).
+ * HG_ERR_NOT_CONVERGED when the cap is reached (x holds the last iterate). */
+int hg_solve(hg_gmg* g, int precision, double* x, const double* b, double rel_tol, int max_iter,
+             int* iters, double* rel_res, void* stream);
+
+/* Relative residuals of the last solve (entry 0 = 1 for x = 0); *n gets the
+ * count, at most cap values are written to out (host). */
+int hg_gmg_history(const hg_gmg* g, double* out, int cap, int* n);
 
 #ifdef __cplusplus
 }

@@ -53,7 +53,21 @@ SIGNATURES = {
     "hg_restrict": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "hg_prolong_add": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "hg_dot": (_I, [_P, _I, _I, _I, _P, _P, _I, _PD, _P]),
+    "hg_device_status": (_I, [_P, _P]),
+    "hg_gmg_default_params": (None, [_P]),
+    "hg_gmg_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
+    "hg_gmg_destroy": (None, [_P]),
+    "hg_vcycle": (_I, [_P, _I, _I, _P, _P, _P]),
+    "hg_solve": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(ctypes.c_int), _PD, _P]),
+    "hg_gmg_history": (_I, [_P, _PD, _I, ctypes.POINTER(ctypes.c_int)]),
 }
+
+HG_PREC_F64, HG_PREC_MIXED = 0, 1
+
+
+class GmgParams(ctypes.Structure):
+    _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
+                ("lmin", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
 
 _lib = None
 
@@ -204,6 +218,9 @@ class Hierarchy:
               ctypes.byref(r), _stream(stream))
         return r.value
 
+    def device_status(self, stream=None):
+        _call("hg_device_status", self._h, _stream(stream))
+
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hg_hier_destroy(self._h)
@@ -239,6 +256,44 @@ class Operator:
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hg_op_destroy(self._h)
+            self._h = None
+
+
+class GMG:
+    """Geometric multigrid (V-cycles) for an operator on its hierarchy."""
+
+    def __init__(self, op: Operator, nu1=3, nu2=3, omega=2.0 / 3.0, lmin=-1, inner_cycles=1):
+        p = GmgParams()
+        lib().hg_gmg_default_params(ctypes.byref(p))
+        p.nu1, p.nu2, p.omega, p.lmin, p.inner_cycles = nu1, nu2, omega, lmin, inner_cycles
+        h = _P()
+        _call("hg_gmg_create", op._h, ctypes.byref(p), ctypes.byref(h))
+        self._h = h
+        self.op = op
+
+    def vcycle(self, level, x, b, stream=None):
+        _call("hg_vcycle", self._h, level, _dtype_code(x), _ptr(x), _ptr(b), _stream(stream))
+
+    def solve(self, x, b, tol=1e-8, max_iter=100, precision=HG_PREC_F64, stream=None,
+              check=True):
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        r = lib().hg_solve(self._h, precision, _ptr(x), _ptr(b), tol, max_iter, ctypes.byref(it),
+                           ctypes.byref(rel), _stream(stream))
+        if r != 0 and (check or r != -5):
+            raise HGError("hg_solve", r, lib().hg_last_error().decode())
+        return it.value, rel.value
+
+    def history(self):
+        n = ctypes.c_int()
+        _call("hg_gmg_history", self._h, None, 0, ctypes.byref(n))
+        out = (ctypes.c_double * max(n.value, 1))()
+        _call("hg_gmg_history", self._h, out, n.value, ctypes.byref(n))
+        return list(out)[:n.value]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hg_gmg_destroy(self._h)
             self._h = None
 
 

@@ -210,7 +210,9 @@ int Hier::build_level(int l) {
   L.n = 1 << l;
   L.w = L.n + 1;
   L.ncells = (int)mesh->nc;
-  L.cell_stride = (ntet(L.w) + 31) / 32 * 32;
+  // padded to 32 elements with at least 4 spare: 16-byte staging copies may read
+  // up to 12 bytes past the last element they need
+  L.cell_stride = (ntet(L.w) + 4 + 31) / 32 * 32;
   L.n_stored = L.cell_stride * mesh->nc;
   const int n = L.n, w = L.w;
   // class flags
@@ -256,6 +258,35 @@ int Hier::build_level(int l) {
   if (int r = upload(&L.prims, prims)) return r;
   if (int r = upload(&L.copies, copies)) return r;
   if (int r = upload(&L.prim_point_base, pbase)) return r;
+  // interface items: 32 consecutive points of one primitive (inner primitives first)
+  std::vector<int4> items;
+  std::vector<int32_t> item_prim;
+  for (int q = 0; q < (int)prims.size(); ++q) {
+    const IfacePrim& P = prims[q];
+    const int meta = P.dim | (P.ncopies << 4) | (P.dirichlet << 12);
+    for (int p0 = 0; p0 < prim_points(P.dim, n); p0 += 32) {
+      items.push_back({P.first_copy, p0, meta, 0});
+      item_prim.push_back(q);
+    }
+    if (q + 1 == L.n_prims_inner) L.n_items_inner = (int)items.size();
+  }
+  L.n_items = (int)items.size();
+  if (int r = upload(&L.items, items)) return r;
+  if (int r = upload(&L.item_prim, item_prim)) return r;
+  // interior tiles: plane k, 30 outputs i0..i0+29, rows j0..j1-1 of at most
+  // kTileRows (interior points 1 <= i,j,k and i+j+k <= n-1)
+  std::vector<int4> tiles;
+  for (int64_t c = 0; c < mesh->nc; ++c)
+    for (int k = 1; k <= n - 3; ++k)
+      for (int i0 = 1; i0 <= n - 2 - k; i0 += 30) {
+        const int jlast = n - 1 - k - i0;
+        for (int j0 = 1; j0 <= jlast; j0 += kTileRows) {
+          const int j1 = std::min(j0 + kTileRows, jlast + 1);
+          tiles.push_back({(int)c, k, i0, j0 | (j1 << 16)});
+        }
+      }
+  L.n_tiles = (int)tiles.size();
+  if (int r = upload(&L.tiles, tiles)) return r;
   // canonical numbering by exact lattice coordinates
   if (mesh->grid_denom) {
     std::vector<int64_t> keys(L.n_stored, -1);
@@ -319,7 +350,13 @@ int Hier::build_level(int l) {
     for (auto& v : mesh->verts) nb += v.dirichlet;
     L.n_inner = nu - nb;
   }
-  // scratch for deterministic dot products
+  // every table a kernel reads must be on the device
+  if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
+      (L.n_items && (!L.items || !L.item_prim)) || (L.n_tiles && !L.tiles) ||
+      (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
+    set_error("internal: level %d device tables incomplete", l);
+    return HG_ERR_CUDA;
+  }
   return HG_OK;
 }
 
@@ -328,15 +365,34 @@ int Hier::build(const Mesh* m, int lmin_, int lmax_) {
   lmin = lmin_;
   lmax = lmax_;
   lv.resize(lmax - lmin + 1);
+  HG_CUDA(cudaMalloc(&err_dev, sizeof(int)));
+  HG_CUDA(cudaMemset(err_dev, 0, sizeof(int)));
+  HG_CUDA(cudaMallocHost(&err_host, sizeof(int)));
+  *err_host = 0;
   int64_t scratch = 0;
   for (int l = lmin; l <= lmax; ++l) {
     if (int r = build_level(l)) return r;
+    lv[l - lmin].dev.err = err_dev;
     scratch = std::max(scratch, dot_scratch_len(lv[l - lmin].dev));
   }
   HG_CUDA(cudaMalloc(&dot_scratch, scratch * sizeof(double)));
   HG_CUDA(cudaMalloc(&dot_result, sizeof(double)));
   HG_CUDA(cudaMallocHost(&dot_host, sizeof(double)));
   return HG_OK;
+}
+
+int Hier::fetch_error(cudaStream_t s) const {
+  HG_CUDA(cudaMemcpyAsync(err_host, err_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
+  return HG_OK;
+}
+
+int Hier::check_error() const {
+  if (*err_host == 0) return HG_OK;
+  const int code = *err_host;
+  *err_host = 0;
+  cudaMemset(err_dev, 0, sizeof(int));
+  set_error("a kernel gave up a bounded wait (device error %d)", code);
+  return HG_ERR_TIMEOUT;
 }
 
 Hier::~Hier() {
@@ -348,10 +404,15 @@ Hier::~Hier() {
     cudaFree(L.prims);
     cudaFree(L.copies);
     cudaFree(L.prim_point_base);
+    cudaFree(L.tiles);
+    cudaFree(L.items);
+    cudaFree(L.item_prim);
   }
   cudaFree(dot_scratch);
   cudaFree(dot_result);
   if (dot_host) cudaFreeHost(dot_host);
+  cudaFree(err_dev);
+  if (err_host) cudaFreeHost(err_host);
 }
 
 // --------------------------------------------------- element matrices
@@ -617,6 +678,14 @@ int hg_from_canonical(const hg_hier* h, int space, int level, int dtype, const v
   return launch_from_canonical(*L, dtype, can, st, (cudaStream_t)stream);
 }
 
+int hg_device_status(const hg_hier* h, void* stream) {
+  HG_CHECK(h, HG_ERR_INVALID_ARG, "hg_device_status: null hierarchy");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (int r = h->fetch_error(s)) return r;
+  HG_CUDA(cudaStreamSynchronize(s));
+  return h->check_error();
+}
+
 int hg_index_tw(int64_t w, int64_t i, int64_t j, int64_t k, int64_t* out) {
   HG_CHECK(out && w >= 1 && i >= 0 && j >= 0 && k >= 0 && i + j + k < w, HG_ERR_INVALID_ARG,
            "hg_index_tw: (%lld,%lld,%lld) not in I_tet(%lld)", (long long)i, (long long)j,
@@ -658,6 +727,8 @@ static int run_cell_op(const hg_op* op, int level, int dtype, StencilArgs a, cud
   HG_CHECK(dtype == HG_F32 || dtype == HG_F64, HG_ERR_INVALID_ARG, "bad dtype %d", dtype);
   HG_CHECK(a.x && a.out && a.x != a.out, HG_ERR_INVALID_ARG,
            "input and output must be distinct non-null device pointers");
+  HG_CHECK(((uintptr_t)a.x & 15) == 0, HG_ERR_INVALID_ARG,
+           "input vector must be 16-byte aligned");
   a.sten = dtype == HG_F64 ? (const void*)op->sten64[level - op->hier->lmin]
                            : (const void*)op->sten32[level - op->hier->lmin];
   return launch_p1_const(*L, dtype, a, s);
@@ -727,9 +798,10 @@ int hg_dot(const hg_hier* h, int space, int level, int dtype, const void* x, con
   cudaStream_t s = (cudaStream_t)stream;
   if (int r = launch_dot(*L, dtype, x, y, mask, h->dot_scratch, h->dot_result, s)) return r;
   HG_CUDA(cudaMemcpyAsync(h->dot_host, h->dot_result, sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (int r = h->fetch_error(s)) return r;
   HG_CUDA(cudaStreamSynchronize(s));
   *result = *h->dot_host;
-  return HG_OK;
+  return h->check_error();
 }
 
 }  // extern "C"

@@ -59,9 +59,14 @@ struct Hier {
   double* dot_scratch = nullptr;
   double* dot_result = nullptr;
   double* dot_host = nullptr;
+  int* err_dev = nullptr;   // device error word of all kernels of this hierarchy
+  int* err_host = nullptr;  // pinned mirror
 
   int build(const Mesh* m, int lmin, int lmax);
   int build_level(int l);
+  // Enqueue a read of the error word on s (no sync); check_error() after a sync.
+  int fetch_error(cudaStream_t s) const;
+  int check_error() const;
   ~Hier();
 };
 

@@ -96,10 +96,16 @@ HG_HD void prim_point_weights(int dim, int n, int p, int wts[3]) {
   }
 }
 // Cell-local (i,j,k) of a primitive point given the copy's local vertex ids.
+// (select-based so that no register array is indexed dynamically)
 HG_HD void copy_local_ijk(const IfaceCopy& c, int dim, const int wts[3], int& i, int& j, int& k) {
-  int lam[4] = {0, 0, 0, 0};
-  for (int m = 0; m <= dim; ++m) lam[c.loc[m]] += wts[m];
-  i = lam[1]; j = lam[2]; k = lam[3];
+  i = j = k = 0;
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    const int wm = m <= dim ? wts[m] : 0;
+    i += c.loc[m] == 1 ? wm : 0;
+    j += c.loc[m] == 2 ? wm : 0;
+    k += c.loc[m] == 3 ? wm : 0;
+  }
 }
 
 // Device-resident description of one level of one hierarchy (P1 vertex lattice).
@@ -116,14 +122,25 @@ struct LevelDev {
   IfaceCopy* copies;
   int n_prims, n_prims_inner, max_copies;
   int32_t* prim_point_base;  // [n_prims+1] prefix sums of prim_points
+  // work items of the fused kernels
+  int4* tiles;               // interior tiles (cell, k, i0, j0 | j1 << 16)
+  int n_tiles;
+  int* err;                  // device error word shared by the hierarchy's kernels
+  int4* items;               // interface items (first_copy, p0, dim|ncopies<<4|dirichlet<<12, 0),
+  int32_t* item_prim;        //   32 consecutive points of one primitive; item -> primitive
+  int n_items, n_items_inner;
 };
+
+// Output rows per interior tile of the fused apply kernel.
+constexpr int kTileRows = 8;
 
 // Dense FP64 coarse-grid solver data.
 struct CoarseDev {
   int n;                 // interior unknowns
   double* ainv;          // [n*n] row-major inverse of the coarse matrix
-  int64_t* stored_rep;   // [n] stored index of the owner copy of each unknown
-  int32_t* canon_of_stored;  // reuse of LevelDev::canon (not owned)
+  int64_t* stored_rep;   // [n] stored index of one copy of each unknown
+  int32_t* int_of_canon; // [n_unique] interior index of a canonical DoF, -1 if Dirichlet
+  double* xint;          // [n] solution workspace
 };
 
 // ------------------------------------------------------------ errors
@@ -164,5 +181,7 @@ int launch_dot(const LevelDev& L, int dtype, const void* x, const void* y, int m
                double* scratch, double* result_dev, cudaStream_t s);
 int launch_coarse_solve(const LevelDev& L, const CoarseDev& C, int dtype, const void* b, void* x,
                         cudaStream_t s);
+int launch_demote_scaled(int64_t n, const double* r, double scale, float* out, cudaStream_t s);
+int launch_promote_axpy(int64_t n, double alpha, const float* d, double* x, cudaStream_t s);
 
 }  // namespace hg

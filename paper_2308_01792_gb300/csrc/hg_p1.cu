@@ -1,18 +1,28 @@
 // P1 kernels on the per-macro-cell vertex lattice.
 //
 // Storage: every macro cell holds its closed vertex lattice i+j+k <= n in
-// t_{n+1} order (Sec. 4), so points on macro faces/edges/vertices have one
-// copy per containing cell.  An operator application is two kernels:
-//  * the cell kernel evaluates, for every point of every cell, the sum of the
-//    cell's own micro-element contributions with the cell's precomputed
-//    15-point stencil of the point's boundary class (Sec. 5.2, stencil-based
-//    pattern with per-macro-primitive constant stencils); interior points
-//    are complete, interface points hold a per-cell partial sum;
-//  * the interface kernel (the ghost-layer exchange between macro
-//    primitives, Sec. 2) adds the partial sums of all copies of every
-//    macro face/edge/vertex point in ascending cell order and writes the
-//    result to every copy, so all copies stay bit-identical.
+// t_{n+1} order (Sec. 4); points on macro faces/edges/vertices have one copy
+// per containing cell and all copies are kept equal.
+//
+// An operator application (Sec. 5.2 apply(), stencil-based pattern with
+// constant stencils precomputed per macro cell) is ONE launch of warp-sized
+// work items of two kinds:
+//  * interface items (first in the grid): one lane per point of a macro
+//    face/edge/vertex (the ghost-layer exchange of Sec. 2 as an on-device
+//    gather).  The lane sums the per-cell partial stencils of every copy, in
+//    ascending cell order, straight from x (all 30 weights and values of a
+//    copy are loaded before the sum), and writes the sum to every copy, so
+//    copies stay bit-identical and no second pass is needed;
+//  * interior tiles: a warp owns lanes i = i0-1 .. i0+30 (30 outputs, one
+//    halo lane each side) of one plane k of one macro cell and kTileRows rows
+//    j0..; it first issues every row load the 15-point stencil needs (plane k
+//    rows j0-1..j0+R, plane k+1 rows j0-1..j0+R-1, plane k-1 rows j0..j0+R:
+//    3R+4 coalesced loads in flight at once), then forms the R output rows
+//    from registers, with warp shuffles for the i+-1 neighbours.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
 
 #include "hg_internal.h"
 
@@ -21,176 +31,259 @@ namespace hg {
 namespace {
 
 constexpr int kBlock = 256;
+constexpr int kWarps = kBlock / 32;
 
 template <typename T>
-struct LevelArgs {
+struct FusedArgs {
   int n, w;
   int64_t stride;
   const uint8_t* flags;
+  const int4* tiles;  // interior tiles (cell, k, i0, j0 | j1 << 16)
+  int n_tiles;
+  const int4* items;  // interface items (first_copy, p0, dim | ncopies<<4 | dirichlet<<12, -)
+  int n_items;
+  int nb_items;       // blocks holding interface items (first in the grid)
+  const IfacePrim* prims;
+  const IfaceCopy* copies;
+  const T* x;
+  const T* b;
+  T* y;
+  const T* sten;
+  T omega;
+  int mode, mask;
+  int* err;            // device error word (bounded waits record HG_ERR_TIMEOUT)
 };
 
-// Sum of one cell's stencil of class `cls` at (i,j,k), neighbours read through
-// the t_w index (slow path for cell-boundary points).
+// Face point p (rows b = 1..n-2 of n-1-b points) -> barycentric weights.
+__device__ __forceinline__ void face_point(int n, int p, int wts[3]) {
+  // row r = b-1 starts at S_r = r(2n-3-r)/2
+  const float q = 2.0f * n - 3.0f;
+  int r = (int)floorf((q - sqrtf(fmaxf(q * q - 8.0f * p, 0.0f))) * 0.5f);
+  if (r < 0) r = 0;
+  while ((r + 1) * (2 * n - 3 - (r + 1)) / 2 <= p) ++r;
+  while (r * (2 * n - 3 - r) / 2 > p) --r;
+  const int a = p - r * (2 * n - 3 - r) / 2 + 1;
+  const int b = r + 1;
+  wts[0] = n - a - b;
+  wts[1] = a;
+  wts[2] = b;
+}
+
+__device__ __forceinline__ void prim_weights(int dim, int n, int p, int wts[3]) {
+  if (dim == 2) {
+    face_point(n, p, wts);
+  } else if (dim == 1) {
+    wts[0] = n - 1 - p;
+    wts[1] = p + 1;
+    wts[2] = 0;
+  } else {
+    wts[0] = n;
+    wts[1] = 0;
+    wts[2] = 0;
+  }
+}
+
+// Partial stencil of one cell at a cell-local point (any class).  The 7
+// rows touched are found from rs(j,k) by row-length steps:
+//   rs(j+-1,k), rs(j,k+1) = rs + ntri(w-k-1) + L, rs(j,k-1) = rs - ntri(w-k) - (L+1),
+//   rs(j-1,k+1) = rs(j,k+1) - L, rs(j+1,k-1) = rs(j,k-1) + L + 1, L = w-k-j.
+// All 15 weights and values are loaded before the sum so the loads overlap.
 template <typename T>
-__device__ T boundary_stencil(const T* __restrict__ x, const T* __restrict__ S, int n, int w,
-                              int i, int j, int k) {
-  T acc = T(0);
+__device__ __forceinline__ void cell_partial_load(const T* __restrict__ x, const T* __restrict__ S,
+                                                  int n, int w, int i, int j, int k, T sv[kNDir],
+                                                  T xv[kNDir]) {
+  const int L = w - k - j;
+  const int r0 = row_start(w, j, k);
+  const int rjp = r0 + L, rjm = r0 - (L + 1);
+  const int rkp = r0 + ntri32(w - k - 1) + L, rkm = r0 - ntri32(w - k) - (L + 1);
+  const int rjmkp = rkp - L, rjpkm = rkm + L + 1;
+  const int rows[15] = {r0, r0, r0, rjp, rjm, rkp, rkm, rjp, rjm, rkp, rkm, rjmkp, rjpkm, rjmkp, rjpkm};
+#pragma unroll
+  for (int d = 0; d < kNDir; ++d) sv[d] = __ldg(S + d);
 #pragma unroll
   for (int d = 0; d < kNDir; ++d) {
-    T s = S[d];
-    if (s != T(0)) {
-      int di, dj, dk;
-      dir_offset(d, di, dj, dk);
-      int a = i + di, b = j + dj, c = k + dk;
-      if (a >= 0 && b >= 0 && c >= 0 && a + b + c <= n) acc += s * x[tw32(w, a, b, c)];
-    }
+    int di, dj, dk;
+    dir_offset(d, di, dj, dk);
+    const int a = i + di, b = j + dj, c = k + dk;
+    xv[d] = (a >= 0 && b >= 0 && c >= 0 && a + b + c <= n) ? __ldg(x + rows[d] + a) : T(0);
   }
+}
+
+template <typename T>
+__device__ __forceinline__ T dot15(const T sv[kNDir], const T xv[kNDir]) {
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < kNDir; ++d) acc += sv[d] * xv[d];
   return acc;
 }
 
-// Cell kernel: one block per (macro cell, plane k); warps over rows j, lanes
-// over i (the x-lines of Sec. 4).
 template <typename T, int OP>
-__global__ void __launch_bounds__(kBlock) p1_cell_kernel(LevelArgs<T> L, const T* __restrict__ X,
-                                                         const T* __restrict__ B, T* __restrict__ Y,
-                                                         const T* __restrict__ sten, T omega,
-                                                         int mode, int mask) {
-  const int cell = blockIdx.x / L.w;
-  const int k = blockIdx.x % L.w;
-  const int n = L.n, w = L.w;
-  const int64_t base = (int64_t)cell * L.stride;
-  const T* x = X + base;
-  const T* b = B ? B + base : nullptr;
-  T* y = Y + base;
-  const T* S = sten + (int64_t)cell * 256;
-  const uint8_t* fl = L.flags + cell * 16;
+__device__ void interface_point(const FusedArgs<T>& A, int item, int lane) {
+  const int4 it = A.items[item];
+  const int dim = it.z & 15, ncopies = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
+  const int n = A.n, w = A.w;
+  const int p = it.y + lane;
+  if (p >= prim_points(dim, n)) return;
+  int wts[3];
+  prim_weights(dim, n, p, wts);
+  const IfaceCopy* cp = A.copies + it.x;
+  int64_t idx0;
+  {
+    int i, j, k;
+    copy_local_ijk(cp[0], dim, wts, i, j, k);
+    idx0 = (int64_t)cp[0].cell * A.stride + tw32(w, i, j, k);
+  }
+  T v;
+  if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
+    v = OP == OP_JACOBI ? A.x[idx0] : T(0);
+  } else {
+    T sum = T(0), diag = T(0);
+    for (int q = 0; q < ncopies; ++q) {
+      T sv[kNDir], xv[kNDir];
+      int i, j, k;
+      copy_local_ijk(cp[q], dim, wts, i, j, k);
+      const int cell = cp[q].cell;
+      cell_partial_load<T>(A.x + (int64_t)cell * A.stride,
+                           A.sten + (int64_t)cell * 256 + point_class(n, i, j, k) * 16, n, w, i,
+                           j, k, sv, xv);
+      sum += dot15<T>(sv, xv);
+      if (OP == OP_JACOBI) diag += sv[0];
+    }
+    if (OP == OP_APPLY) {
+      v = A.mode == HG_ADD ? A.y[idx0] + sum : sum;
+    } else if (OP == OP_RESID) {
+      v = A.b[idx0] - sum;
+    } else {
+      v = A.x[idx0] + A.omega * (A.b[idx0] - sum) / diag;
+    }
+  }
+  for (int q = 0; q < ncopies; ++q) {
+    int i, j, k;
+    copy_local_ijk(cp[q], dim, wts, i, j, k);
+    A.y[(int64_t)cp[q].cell * A.stride + tw32(w, i, j, k)] = v;
+  }
+}
+
+// Interior tile (see the file comment).  Row starts move by row lengths:
+// rs(j+1,k) = rs(j,k) + (w-k-j).
+template <typename T, int OP, int R>
+__device__ void interior_tile(const FusedArgs<T>& A, int t, int lane) {
+  const int4 tl = A.tiles[t];
+  const int cell = tl.x, k = tl.y, i0 = tl.z, j0 = tl.w & 0xffff, nr = (tl.w >> 16) - j0;
+  const int w = A.w;
+  const int64_t base = (int64_t)cell * A.stride;
+  const T* __restrict__ x = A.x + base;
+  T* __restrict__ y = A.y + base;
+  const T* __restrict__ S = A.sten + (int64_t)cell * 256;
+  const int i = i0 - 1 + lane;
+  const int lk = w - k, lkp = w - k - 1, lkm = w - k + 1;  // row length = l - j
+  T K[R + 2], Kp[R + 1], Km[R + 1];
+  {
+    int r = row_start(w, j0 - 1, k);
+#pragma unroll
+    for (int q = 0; q < R + 2; ++q) {
+      const int len = lk - (j0 - 1 + q);
+      K[q] = (q < nr + 2 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
+      r += len;
+    }
+    r = row_start(w, j0 - 1, k + 1);
+#pragma unroll
+    for (int q = 0; q < R + 1; ++q) {
+      const int len = lkp - (j0 - 1 + q);
+      Kp[q] = (q < nr + 1 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
+      r += len;
+    }
+    r = row_start(w, j0, k - 1);
+#pragma unroll
+    for (int q = 0; q < R + 1; ++q) {
+      const int len = lkm - (j0 + q);
+      Km[q] = (q < nr + 1 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
+      r += len;
+    }
+  }
   T s[kNDir];
 #pragma unroll
-  for (int d = 0; d < kNDir; ++d) s[d] = S[d];
-  const int m = n - k;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j <= m; j += nw) {
-    const int r0 = row_start(w, j, k);
-    const bool inner_row = j >= 1 && k >= 1 && j + k <= n - 1;
-    int rjp = 0, rjm = 0, rkp = 0, rkm = 0, rjmkp = 0, rjpkm = 0;
-    if (inner_row) {
-      rjp = row_start(w, j + 1, k);
-      rjm = row_start(w, j - 1, k);
-      rkp = row_start(w, j, k + 1);
-      rkm = row_start(w, j, k - 1);
-      rjmkp = row_start(w, j - 1, k + 1);
-      rjpkm = row_start(w, j + 1, k - 1);
-    }
-    for (int i = lane; i <= m - j; i += 32) {
-      const int cls = point_class(n, i, j, k);
-      const int idx = r0 + i;
-      T acc;
-      if (cls == 0) {
-        acc = s[0] * x[idx] + s[1] * x[idx + 1] + s[2] * x[idx - 1] + s[3] * x[rjp + i] +
-              s[4] * x[rjm + i] + s[5] * x[rkp + i] + s[6] * x[rkm + i] + s[7] * x[rjp + i - 1] +
-              s[8] * x[rjm + i + 1] + s[9] * x[rkp + i - 1] + s[10] * x[rkm + i + 1] +
-              s[11] * x[rjmkp + i] + s[12] * x[rjpkm + i] + s[13] * x[rjmkp + i + 1] +
-              s[14] * x[rjpkm + i - 1];
+  for (int d = 0; d < kNDir; ++d) s[d] = __ldg(S + d);
+  const T wd = OP == OP_JACOBI ? A.omega / s[0] : T(0);
+  const bool out_lane = lane >= 1 && lane <= 30;
+  int ry = row_start(w, j0, k);
+#pragma unroll
+  for (int q = 0; q < R; ++q) {
+    if (q < nr) {
+      const int j = j0 + q;
+      const T c = K[q + 1], up = K[q + 2], dn = K[q];
+      const T cm = __shfl_up_sync(0xffffffffu, c, 1), cp = __shfl_down_sync(0xffffffffu, c, 1);
+      const T upm = __shfl_up_sync(0xffffffffu, up, 1);
+      const T dnp = __shfl_down_sync(0xffffffffu, dn, 1);
+      const T p1c = Kp[q + 1], p1m = Kp[q];
+      const T p1cm = __shfl_up_sync(0xffffffffu, p1c, 1);
+      const T p1mp = __shfl_down_sync(0xffffffffu, p1m, 1);
+      const T m1c = Km[q], m1p = Km[q + 1];
+      const T m1cp = __shfl_down_sync(0xffffffffu, m1c, 1);
+      const T m1pm = __shfl_up_sync(0xffffffffu, m1p, 1);
+      const T acc = s[0] * c + s[1] * cp + s[2] * cm + s[3] * up + s[4] * dn + s[5] * p1c +
+                    s[6] * m1c + s[7] * upm + s[8] * dnp + s[9] * p1cm + s[10] * m1cp +
+                    s[11] * p1m + s[12] * m1p + s[13] * p1mp + s[14] * m1pm;
+      if (out_lane && i < lk - j - 1) {
+        const int idx = ry + i;
         if (OP == OP_APPLY) {
-          y[idx] = mode == HG_ADD ? y[idx] + acc : acc;
+          y[idx] = A.mode == HG_ADD ? y[idx] + acc : acc;
         } else if (OP == OP_RESID) {
-          y[idx] = b[idx] - acc;
+          y[idx] = A.b[base + idx] - acc;
         } else {
-          y[idx] = x[idx] + omega * (b[idx] - acc) / s[0];
+          y[idx] = c + (A.b[base + idx] - acc) * wd;
         }
-      } else {
-        const uint8_t f = fl[cls];
-        const bool dir = (f & CF_DIRICHLET) != 0;
-        if (dir && (OP != OP_APPLY || mask == HG_MASK_INNER)) {
-          if (OP == OP_RESID) y[idx] = T(0);
-          if (OP == OP_JACOBI) y[idx] = x[idx];
-          continue;
-        }
-        acc = boundary_stencil<T>(x, S + cls * 16, n, w, i, j, k);
-        if (OP == OP_APPLY && mode == HG_ADD && (f & CF_OWNER)) acc = y[idx] + acc;
-        y[idx] = acc;  // partial sum, completed by the interface kernel
       }
+      ry += lk - j;
     }
   }
 }
 
-// Interface kernel: one block per macro primitive.
 template <typename T, int OP>
-__global__ void __launch_bounds__(kBlock) p1_iface_kernel(LevelArgs<T> L, const IfacePrim* prims,
-                                                          const IfaceCopy* copies,
-                                                          const T* __restrict__ X,
-                                                          const T* __restrict__ B, T* Y,
-                                                          const T* __restrict__ sten, T omega) {
-  const IfacePrim P = prims[blockIdx.x];
-  const int n = L.n, w = L.w;
-  const int npts = prim_points(P.dim, n);
-  const IfaceCopy* cp = copies + P.first_copy;
-  for (int p = threadIdx.x; p < npts; p += blockDim.x) {
-    int wts[3];
-    if (P.dim == 2) {
-      // row b has n-1-b points; find the row of p
-      int b = 1, rem = p;
-      while (rem >= n - 1 - b) {
-        rem -= n - 1 - b;
-        ++b;
-      }
-      wts[0] = n - (rem + 1) - b;
-      wts[1] = rem + 1;
-      wts[2] = b;
-    } else {
-      prim_point_weights(P.dim, n, p, wts);
-    }
-    T sum = T(0), diag = T(0);
-    int64_t idx0 = 0;
-    for (int q = 0; q < P.ncopies; ++q) {
-      int i, j, k;
-      copy_local_ijk(cp[q], P.dim, wts, i, j, k);
-      const int64_t idx = (int64_t)cp[q].cell * L.stride + tw32(w, i, j, k);
-      if (q == 0) idx0 = idx;
-      sum += Y[idx];
-      if (OP == OP_JACOBI)
-        diag += sten[(int64_t)cp[q].cell * 256 + point_class(n, i, j, k) * 16];
-    }
-    T v;
-    if (OP == OP_APPLY) {
-      v = sum;
-    } else if (OP == OP_RESID) {
-      v = B[idx0] - sum;
-    } else {
-      v = X[idx0] + omega * (B[idx0] - sum) / diag;
-    }
-    for (int q = 0; q < P.ncopies; ++q) {
-      int i, j, k;
-      copy_local_ijk(cp[q], P.dim, wts, i, j, k);
-      Y[(int64_t)cp[q].cell * L.stride + tw32(w, i, j, k)] = v;
-    }
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) p1_fused_kernel(FusedArgs<T> A) {
+  const int lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if ((int)blockIdx.x < A.nb_items) {
+    if (wg < A.n_items) interface_point<T, OP>(A, wg, lane);
+  } else {
+    const int t = wg - A.nb_items * kWarps;
+    if (t < A.n_tiles) interior_tile<T, OP, kTileRows>(A, t, lane);
   }
 }
 
 template <typename T>
-LevelArgs<T> level_args(const LevelDev& L) {
-  LevelArgs<T> a;
-  a.n = L.n;
-  a.w = L.w;
-  a.stride = L.cell_stride;
-  a.flags = L.cls_flags;
-  return a;
+FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
+  FusedArgs<T> A;
+  A.n = L.n;
+  A.w = L.w;
+  A.stride = L.cell_stride;
+  A.flags = L.cls_flags;
+  A.tiles = L.tiles;
+  A.n_tiles = L.n_tiles;
+  A.items = L.items;
+  A.n_items = n_items;
+  A.nb_items = (n_items + kWarps - 1) / kWarps;
+  A.prims = L.prims;
+  A.copies = L.copies;
+  A.x = (const T*)a.x;
+  A.b = (const T*)a.b;
+  A.y = (T*)a.out;
+  A.sten = (const T*)a.sten;
+  A.omega = (T)a.omega;
+  A.mode = a.mode;
+  A.mask = a.mask;
+  A.err = L.err;
+  return A;
 }
 
 template <typename T, int OP>
 int run_p1(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
-  LevelArgs<T> la = level_args<T>(L);
-  const int grid = L.ncells * L.w;
-  p1_cell_kernel<T, OP><<<grid, kBlock, 0, s>>>(la, (const T*)a.x, (const T*)a.b, (T*)a.out,
-                                                (const T*)a.sten, (T)a.omega, a.mode, a.mask);
+  const int n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_items_inner : L.n_items;
+  FusedArgs<T> A = fused_args<T>(L, a, n_items);
+  const int grid = A.nb_items + (L.n_tiles + kWarps - 1) / kWarps;
+  if (grid == 0) return HG_OK;
+  p1_fused_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
   HG_CUDA(cudaGetLastError());
-  const int np = (OP == OP_APPLY && a.mask == HG_MASK_ALL) ? L.n_prims : L.n_prims_inner;
-  if (np > 0) {
-    p1_iface_kernel<T, OP><<<np, kBlock, 0, s>>>(la, L.prims, L.copies, (const T*)a.x,
-                                                 (const T*)a.b, (T*)a.out, (const T*)a.sten,
-                                                 (T)a.omega);
-    HG_CUDA(cudaGetLastError());
-  }
   return HG_OK;
 }
 
@@ -205,44 +298,63 @@ int run_p1_op(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
   return HG_ERR_INVALID_ARG;
 }
 
-// ------------------------------------------------------------ maps / dumps
-__global__ void index_enumerate_kernel(int w, int64_t* out) {
-  const int k = blockIdx.x;
-  const int m = w - 1 - k;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j <= m; j += nw) {
-    const int r0 = row_start(w, j, k);
-    for (int i = lane; i <= m - j; i += 32)
-      out[r0 + i] = (int64_t)i + ((int64_t)j << 20) + ((int64_t)k << 40);
-  }
+// ------------------------------------------------------------ row items
+// Row item r of a level: cell = r / ntri(w), then plane k and row j of the
+// cell's lattice.  Plane k has w-k rows; R(k) = k(2w-k+1)/2 rows precede it.
+__device__ __forceinline__ void row_item(int w, int r, int& cell, int& j, int& k) {
+  const int per = ntri32(w);
+  cell = r / per;
+  const int rr = r - cell * per;
+  const float q = 2.0f * w + 1.0f;
+  int kk = (int)floorf((q - sqrtf(fmaxf(q * q - 8.0f * rr, 0.0f))) * 0.5f);
+  if (kk < 0) kk = 0;
+  while ((kk + 1) * (2 * w - kk) / 2 <= rr) ++kk;
+  while (kk * (2 * w - kk + 1) / 2 > rr) --kk;
+  k = kk;
+  j = rr - kk * (2 * w - kk + 1) / 2;
 }
 
-__global__ void interface_dump_kernel(int n, int w, int64_t stride, const IfacePrim* prims,
-                                      int nprims, const int32_t* pbase, const IfaceCopy* copies,
-                                      int maxc, int64_t* out) {
-  const int prim = blockIdx.x;
-  if (prim >= nprims) return;
+// ------------------------------------------------------------ maps / dumps
+__global__ void index_enumerate_kernel(int w, int64_t* out) {
+  // one warp per row item of a single lattice, lanes over i
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (r >= ntri32(w)) return;
+  int cell, j, k;
+  row_item(w, r, cell, j, k);
+  const int r0 = row_start(w, j, k);
+  for (int i = lane; i + j + k <= w - 1; i += 32)
+    out[r0 + i] = (int64_t)i + ((int64_t)j << 20) + ((int64_t)k << 40);
+}
+
+__global__ void interface_dump_kernel(int n, int w, const int4* items, int n_items,
+                                      const int32_t* item_prim, const IfacePrim* prims,
+                                      const int32_t* pbase, const IfaceCopy* copies, int maxc,
+                                      int64_t* out) {
+  const int lane = threadIdx.x & 31;
+  const int it = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (it >= n_items) return;
+  const int4 item = items[it];
+  const int prim = item_prim[it];
   const IfacePrim P = prims[prim];
-  const int npts = prim_points(P.dim, n);
-  for (int p = threadIdx.x; p < npts; p += blockDim.x) {
-    int wts[3];
-    prim_point_weights(P.dim, n, p, wts);
-    int64_t* row = out + (int64_t)(pbase[prim] + p) * (2 * maxc + 1);
-    row[0] = P.ncopies;
-    for (int q = 0; q < maxc; ++q) {
-      if (q < P.ncopies) {
-        int i, j, k;
-        const IfaceCopy c = copies[P.first_copy + q];
-        copy_local_ijk(c, P.dim, wts, i, j, k);
-        row[1 + 2 * q] = c.cell;
-        row[2 + 2 * q] = tw32(w, i, j, k);
-      } else {
-        row[1 + 2 * q] = -1;
-        row[2 + 2 * q] = -1;
-      }
+  const int p = item.y + lane;
+  if (p >= prim_points(P.dim, n)) return;
+  int wts[3];
+  prim_weights(P.dim, n, p, wts);
+  int64_t* row = out + (int64_t)(pbase[prim] + p) * (2 * maxc + 1);
+  row[0] = P.ncopies;
+  for (int q = 0; q < maxc; ++q) {
+    if (q < P.ncopies) {
+      int i, j, k;
+      const IfaceCopy c = copies[P.first_copy + q];
+      copy_local_ijk(c, P.dim, wts, i, j, k);
+      row[1 + 2 * q] = c.cell;
+      row[2 + 2 * q] = tw32(w, i, j, k);
+    } else {
+      row[1 + 2 * q] = -1;
+      row[2 + 2 * q] = -1;
     }
   }
-  (void)stride;
 }
 
 template <typename T>
@@ -264,134 +376,163 @@ __global__ void scatter_kernel(const T* __restrict__ can, const int32_t* __restr
 }
 
 // ---------------------------------------------------------- grid transfers
-// Restriction r_c = P^T r_f: coarse point I sums the fine points 2I (weight 1)
-// and 2I +- d (weight 1/2) that lie in the cell and are owned by it; partial
-// sums on coarse interface points are completed by the interface kernel.
+// Restriction r_c = P^T r_f.  A coarse point I collects the fine points 2I
+// (weight 1) and 2I +- d (weight 1/2, the midpoints of the coarse edges at I)
+// that lie in the cell and are owned by it (each unique fine DoF counted once).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) restrict_kernel(int nf, int64_t fstride,
-                                                          const uint8_t* flags, int nc,
-                                                          int64_t cstride,
-                                                          const T* __restrict__ RF,
-                                                          T* __restrict__ RC) {
-  const int wc = nc + 1, wf = nf + 1;
-  const int cell = blockIdx.x / wc;
-  const int K = blockIdx.x % wc;
+__device__ __forceinline__ T restrict_partial(const T* __restrict__ rf, const uint8_t* fl, int nf,
+                                              int I, int J, int K) {
+  const int wf = nf + 1;
+  T acc = T(0);
+#pragma unroll
+  for (int d = 0; d < kNDir; ++d) {
+    int di, dj, dk;
+    dir_offset(d, di, dj, dk);
+    const int a = 2 * I + di, b = 2 * J + dj, c = 2 * K + dk;
+    if (a < 0 || b < 0 || c < 0 || a + b + c > nf) continue;
+    if (!(fl[point_class(nf, a, b, c)] & CF_OWNER)) continue;
+    const T v = rf[tw32(wf, a, b, c)];
+    acc += d == 0 ? v : T(0.5) * v;
+  }
+  return acc;
+}
+
+// Blocks [0, nb_items) take coarse interface items, the rest coarse rows.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) restrict_kernel(
+    int nf, int64_t fstride, int nc, int64_t cstride, const uint8_t* flags, const int4* items,
+    int n_items, int nb_items, const IfaceCopy* copies, int n_rows,
+    const T* __restrict__ RF, T* __restrict__ RC) {
+  const int lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int wc = nc + 1;
+  if ((int)blockIdx.x < nb_items) {
+    if (wg >= n_items) return;
+    const int4 it = items[wg];
+    IfacePrim P;
+    P.dim = it.z & 15;
+    P.ncopies = (it.z >> 4) & 255;
+    P.dirichlet = (it.z >> 12) & 1;
+    const int p = it.y + lane;
+    if (p >= prim_points(P.dim, nc)) return;
+    int wts[3];
+    prim_weights(P.dim, nc, p, wts);
+    const IfaceCopy* cp = copies + it.x;
+    T v = T(0);
+    if (!P.dirichlet) {
+      for (int q = 0; q < P.ncopies; ++q) {
+        int I, J, K;
+        copy_local_ijk(cp[q], P.dim, wts, I, J, K);
+        v += restrict_partial<T>(RF + (int64_t)cp[q].cell * fstride, flags + cp[q].cell * 16, nf,
+                                 I, J, K);
+      }
+    }
+    for (int q = 0; q < P.ncopies; ++q) {
+      int I, J, K;
+      copy_local_ijk(cp[q], P.dim, wts, I, J, K);
+      RC[(int64_t)cp[q].cell * cstride + tw32(wc, I, J, K)] = v;
+    }
+    return;
+  }
+  const int r = wg - nb_items * kWarps;
+  if (r >= n_rows) return;
+  int cell, J, K;
+  row_item(wc, r, cell, J, K);
   const T* rf = RF + (int64_t)cell * fstride;
   T* rc = RC + (int64_t)cell * cstride;
   const uint8_t* fl = flags + cell * 16;
-  const int m = nc - K;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int J = warp; J <= m; J += nw) {
-    for (int I = lane; I <= m - J; I += 32) {
-      const int ccls = point_class(nc, I, J, K);
-      const int cidx = row_start(wc, J, K) + I;
-      if (fl[ccls] & CF_DIRICHLET) {
-        rc[cidx] = T(0);
-        continue;
-      }
-      const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
-      T acc = T(0);
-      for (int d = 0; d < kNDir; ++d) {
-        int di, dj, dk;
-        dir_offset(d, di, dj, dk);
-        const int a = fi + di, b = fj + dj, c = fk + dk;
-        if (a < 0 || b < 0 || c < 0 || a + b + c > nf) continue;
-        const int fcls = point_class(nf, a, b, c);
-        if (!(fl[fcls] & CF_OWNER)) continue;
-        const T v = rf[tw32(wf, a, b, c)];
-        acc += d == 0 ? v : T(0.5) * v;
-      }
-      rc[cidx] = acc;
-    }
+  const int r0 = row_start(wc, J, K);
+  for (int I = lane; I + J + K <= nc; I += 32) {
+    if (point_class(nc, I, J, K) != 0) continue;  // interface points: items above
+    rc[r0 + I] = restrict_partial<T>(rf, fl, nf, I, J, K);
   }
 }
 
 // Prolongation x_f += P e_c: fine points with even coordinates copy the coarse
-// value, the others are midpoints of the coarse edge selected by the parity.
+// value; the others are midpoints of the coarse edge picked by the parity.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) prolong_kernel(int nf, int64_t fstride,
-                                                         const uint8_t* flags, int64_t cstride,
+__global__ void __launch_bounds__(kBlock) prolong_kernel(int nf, int64_t fstride, int64_t cstride,
+                                                         const uint8_t* flags, int n_rows,
                                                          const T* __restrict__ EC,
                                                          T* __restrict__ XF) {
-  const int wf = nf + 1, nc = nf / 2, wc = nc + 1;
-  const int cell = blockIdx.x / wf;
-  const int k = blockIdx.x % wf;
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  const int wf = nf + 1, wc = nf / 2 + 1;
+  if (r >= n_rows) return;
+  int cell, j, k;
+  row_item(wf, r, cell, j, k);
   const T* ec = EC + (int64_t)cell * cstride;
   T* xf = XF + (int64_t)cell * fstride;
   const uint8_t* fl = flags + cell * 16;
-  const int m = nf - k;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j <= m; j += nw) {
-    for (int i = lane; i <= m - j; i += 32) {
-      if (fl[point_class(nf, i, j, k)] & CF_DIRICHLET) continue;
-      const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-      T v;
-      if (par == 0) {
-        v = ec[tw32(wc, i >> 1, j >> 1, k >> 1)];
-      } else {
-        // direction d of the coarse edge whose midpoint has this parity
-        int di = 0, dj = 0, dk = 0;
-        switch (par) {
-          case 1: di = 1; break;
-          case 2: dj = 1; break;
-          case 4: dk = 1; break;
-          case 3: di = -1; dj = 1; break;
-          case 5: di = -1; dk = 1; break;
-          case 6: dj = -1; dk = 1; break;
-          default: di = 1; dj = -1; dk = 1; break;
-        }
-        const T a = ec[tw32(wc, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1)];
-        const T b = ec[tw32(wc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1)];
-        v = T(0.5) * (a + b);
+  const int r0 = row_start(wf, j, k);
+  for (int i = lane; i + j + k <= nf; i += 32) {
+    if (fl[point_class(nf, i, j, k)] & CF_DIRICHLET) continue;
+    const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+    T v;
+    if (par == 0) {
+      v = ec[tw32(wc, i >> 1, j >> 1, k >> 1)];
+    } else {
+      int di = 0, dj = 0, dk = 0;
+      switch (par) {
+        case 1: di = 1; break;
+        case 2: dj = 1; break;
+        case 4: dk = 1; break;
+        case 3: di = -1; dj = 1; break;
+        case 5: di = -1; dk = 1; break;
+        case 6: dj = -1; dk = 1; break;
+        default: di = 1; dj = -1; dk = 1; break;
       }
-      xf[row_start(wf, j, k) + i] += v;
+      const T a = ec[tw32(wc, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1)];
+      const T b = ec[tw32(wc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1)];
+      v = T(0.5) * (a + b);
     }
+    xf[r0 + i] += v;
   }
 }
 
 // ------------------------------------------------------------- reductions
-// Deterministic FP64 dot: one partial per (cell, plane) block in a fixed
-// shape, then a single block adds the partials in a fixed tree order.
+// Deterministic FP64 dot over owned points: a fixed grid of kDotBlocks blocks
+// strides over row items; one partial per block; one block adds the partials
+// in a fixed tree order.
+constexpr int kDotBlocks = 608;
+
 template <typename T>
 __global__ void __launch_bounds__(kBlock) dot_partial_kernel(int n, int64_t stride,
-                                                             const uint8_t* flags,
+                                                             const uint8_t* flags, int n_rows,
                                                              const T* __restrict__ X,
                                                              const T* __restrict__ Y, int mask,
                                                              double* partial) {
   const int w = n + 1;
-  const int cell = blockIdx.x / w;
-  const int k = blockIdx.x % w;
-  const T* x = X + (int64_t)cell * stride;
-  const T* y = Y + (int64_t)cell * stride;
-  const uint8_t* fl = flags + cell * 16;
-  const int m = n - k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double acc = 0.0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = warp; j <= m; j += nw) {
-    const int r0 = row_start(w, j, k);
-    for (int i = lane; i <= m - j; i += 32) {
+  for (int r = blockIdx.x * kWarps + warp; r < n_rows; r += gridDim.x * kWarps) {
+    int cell, j, k;
+    row_item(w, r, cell, j, k);
+    const int64_t r0 = (int64_t)cell * stride + row_start(w, j, k);
+    const uint8_t* fl = flags + cell * 16;
+    for (int i = lane; i + j + k <= n; i += 32) {
       const uint8_t f = fl[point_class(n, i, j, k)];
       if (!(f & CF_OWNER)) continue;
       if (mask == HG_MASK_INNER && (f & CF_DIRICHLET)) continue;
-      acc += (double)x[r0 + i] * (double)y[r0 + i];
+      acc += (double)X[r0 + i] * (double)Y[r0 + i];
     }
   }
-  __shared__ double red[kBlock / 32];
+  __shared__ double red[kWarps];
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if (lane == 0) red[warp] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
     double t = 0.0;
-    for (int q = 0; q < nw; ++q) t += red[q];
+    for (int q = 0; q < kWarps; ++q) t += red[q];
     partial[blockIdx.x] = t;
   }
 }
 
-__global__ void __launch_bounds__(1024) sum_partials_kernel(const double* partial, int64_t np,
+__global__ void __launch_bounds__(1024) sum_partials_kernel(const double* partial, int np,
                                                             double* result) {
   __shared__ double red[1024];
   double acc = 0.0;
-  for (int64_t q = threadIdx.x; q < np; q += blockDim.x) acc += partial[q];
+  for (int q = threadIdx.x; q < np; q += blockDim.x) acc += partial[q];
   red[threadIdx.x] = acc;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -406,6 +547,8 @@ int grid_for(int64_t n) {
   return (int)(g < 152 * 16 ? (g > 0 ? g : 1) : 152 * 16);
 }
 
+int blocks_for_warps(int64_t nw) { return (int)((nw + kWarps - 1) / kWarps); }
+
 }  // namespace
 
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s) {
@@ -413,16 +556,16 @@ int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStre
 }
 
 int launch_index_enumerate(int w, int64_t* out, cudaStream_t s) {
-  index_enumerate_kernel<<<w, kBlock, 0, s>>>(w, out);
+  index_enumerate_kernel<<<blocks_for_warps(ntri32(w)), kBlock, 0, s>>>(w, out);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
 
 int launch_interface_dump(const LevelDev& L, int64_t* out, cudaStream_t s) {
-  if (L.n_prims == 0) return HG_OK;
-  interface_dump_kernel<<<L.n_prims, kBlock, 0, s>>>(L.n, L.w, L.cell_stride, L.prims, L.n_prims,
-                                                     L.prim_point_base, L.copies, L.max_copies,
-                                                     out);
+  if (L.n_items == 0) return HG_OK;
+  interface_dump_kernel<<<blocks_for_warps(L.n_items), kBlock, 0, s>>>(
+      L.n, L.w, L.items, L.n_items, L.item_prim, L.prims, L.prim_point_base, L.copies,
+      L.max_copies, out);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
@@ -455,15 +598,13 @@ int launch_from_canonical(const LevelDev& L, int dtype, const void* can, void* s
 template <typename T>
 static int run_restrict(const LevelDev& F, const LevelDev& C, const void* rf, void* rc,
                         cudaStream_t s) {
-  restrict_kernel<T><<<C.ncells * C.w, kBlock, 0, s>>>(F.n, F.cell_stride, F.cls_flags, C.n,
-                                                      C.cell_stride, (const T*)rf, (T*)rc);
+  const int n_rows = C.ncells * ntri32(C.w);
+  const int nb_items = blocks_for_warps(C.n_items);
+  const int grid = nb_items + blocks_for_warps(n_rows);
+  restrict_kernel<T><<<grid, kBlock, 0, s>>>(F.n, F.cell_stride, C.n, C.cell_stride, F.cls_flags,
+                                             C.items, C.n_items, nb_items, C.copies, n_rows,
+                                             (const T*)rf, (T*)rc);
   HG_CUDA(cudaGetLastError());
-  if (C.n_prims_inner > 0) {
-    LevelArgs<T> la = level_args<T>(C);
-    p1_iface_kernel<T, OP_APPLY><<<C.n_prims_inner, kBlock, 0, s>>>(
-        la, C.prims, C.copies, nullptr, nullptr, (T*)rc, nullptr, T(0));
-    HG_CUDA(cudaGetLastError());
-  }
   return HG_OK;
 }
 
@@ -475,32 +616,32 @@ int launch_restrict_p1(const LevelDev& F, const LevelDev& C, int dtype, const vo
 
 int launch_prolong_p1(const LevelDev& F, const LevelDev& C, int dtype, const void* ec, void* xf,
                       cudaStream_t s) {
-  const int grid = F.ncells * F.w;
+  const int n_rows = F.ncells * ntri32(F.w);
+  const int grid = blocks_for_warps(n_rows);
   if (dtype == HG_F64)
-    prolong_kernel<double><<<grid, kBlock, 0, s>>>(F.n, F.cell_stride, F.cls_flags, C.cell_stride,
-                                                   (const double*)ec, (double*)xf);
+    prolong_kernel<double><<<grid, kBlock, 0, s>>>(F.n, F.cell_stride, C.cell_stride, F.cls_flags,
+                                                   n_rows, (const double*)ec, (double*)xf);
   else
-    prolong_kernel<float><<<grid, kBlock, 0, s>>>(F.n, F.cell_stride, F.cls_flags, C.cell_stride,
-                                                  (const float*)ec, (float*)xf);
+    prolong_kernel<float><<<grid, kBlock, 0, s>>>(F.n, F.cell_stride, C.cell_stride, F.cls_flags,
+                                                  n_rows, (const float*)ec, (float*)xf);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
 
-int64_t dot_scratch_len(const LevelDev& L) { return (int64_t)L.ncells * L.w; }
+int64_t dot_scratch_len(const LevelDev&) { return kDotBlocks; }
 
 int launch_dot(const LevelDev& L, int dtype, const void* x, const void* y, int mask,
                double* scratch, double* result_dev, cudaStream_t s) {
-  const int grid = L.ncells * L.w;
+  const int n_rows = L.ncells * ntri32(L.w);
   if (dtype == HG_F64)
-    dot_partial_kernel<double><<<grid, kBlock, 0, s>>>(L.n, L.cell_stride, L.cls_flags,
-                                                       (const double*)x, (const double*)y, mask,
-                                                       scratch);
+    dot_partial_kernel<double><<<kDotBlocks, kBlock, 0, s>>>(
+        L.n, L.cell_stride, L.cls_flags, n_rows, (const double*)x, (const double*)y, mask,
+        scratch);
   else
-    dot_partial_kernel<float><<<grid, kBlock, 0, s>>>(L.n, L.cell_stride, L.cls_flags,
-                                                      (const float*)x, (const float*)y, mask,
-                                                      scratch);
+    dot_partial_kernel<float><<<kDotBlocks, kBlock, 0, s>>>(
+        L.n, L.cell_stride, L.cls_flags, n_rows, (const float*)x, (const float*)y, mask, scratch);
   HG_CUDA(cudaGetLastError());
-  sum_partials_kernel<<<1, 1024, 0, s>>>(scratch, grid, result_dev);
+  sum_partials_kernel<<<1, 1024, 0, s>>>(scratch, kDotBlocks, result_dev);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
