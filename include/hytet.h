@@ -191,6 +191,25 @@ int hg_prolong_add(const hg_hier* hier, int space, int fine_level, int dtype,
 int hg_dot(const hg_hier* hier, int space, int level, int dtype, const void* x, const void* y,
            int mask, double* result, void* stream);
 
+/* Same dot product as hg_dot, for callers that cannot allocate device memory
+ * (the paper has no counterpart: this is a deployment variant).  Such
+ * callers are code running inside a memory pool or arena that owns the whole
+ * device, code that must not trigger the implicit synchronisation of
+ * cudaMalloc/cudaFree, or code on paths where allocation is not allowed.
+ * hg_dot_noalloc allocates nothing: its per-block partial sums live in one
+ * fixed 4 KB array in device global memory (512 doubles, kept by every GPU
+ * that loads the library until the process exits), and the result goes to
+ * the caller's device pointer `result` (one double) without synchronising.
+ *   Limit: at most 512 x 256 = 131072 lattice rows per level (rows = cells x
+ *   (n+1)(n+2)/2); larger levels are rejected with HG_ERR_INVALID_ARG.
+ *   The first call on a device looks up the array's device address (with
+ *   that device current); make that first call before any stream capture.
+ *   All calls share the array: calls that overlap on the GPU (other streams
+ *   or host threads) race and give wrong results.  Each call rewrites the
+ *   partials it reads, so nothing has to be cleared between calls. */
+int hg_dot_noalloc(const hg_hier* hier, int space, int level, int dtype, const void* x,
+                   const void* y, int mask, double* result, void* stream);
+
 /* ---------------------------------------------------------- multigrid --
  * Geometric multigrid on the refinement hierarchy (multigrid by design,
  * Sec. 5.1): V(nu1,nu2) cycles with weighted-Jacobi smoothing (Sec. 5.2.1:

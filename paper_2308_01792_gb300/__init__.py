@@ -54,6 +54,7 @@ SIGNATURES = {
     "hg_prolong_add": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "hg_dot": (_I, [_P, _I, _I, _I, _P, _P, _I, _PD, _P]),
     "hg_device_status": (_I, [_P, _P]),
+    "hg_dot_noalloc": (_I, [_P, _I, _I, _I, _P, _P, _I, _P, _P]),
     "hg_gmg_default_params": (None, [_P]),
     "hg_gmg_create": (_I, [_P, _P, ctypes.POINTER(_P)]),
     "hg_gmg_destroy": (None, [_P]),
@@ -217,6 +218,11 @@ class Hierarchy:
         _call("hg_dot", self._h, space, level, _dtype_code(x), _ptr(x), _ptr(y), mask,
               ctypes.byref(r), _stream(stream))
         return r.value
+
+    def dot_noalloc(self, level, x, y, out, mask=HG_MASK_INNER, space=HG_SPACE_P1, stream=None):
+        """hg_dot_noalloc: writes the dot into out[0] (CUDA float64 tensor), no sync."""
+        _call("hg_dot_noalloc", self._h, space, level, _dtype_code(x), _ptr(x), _ptr(y), mask,
+              _ptr(out), _stream(stream))
 
     def device_status(self, stream=None):
         _call("hg_device_status", self._h, _stream(stream))
