@@ -66,9 +66,7 @@ struct Gmg {
     a.mode = HG_REPLACE;
     a.mask = HG_MASK_INNER;
     a.omega = prm.omega;
-    a.sten = dt == HG_F64 ? (const void*)op->sten64[l - hier->lmin]
-                          : (const void*)op->sten32[l - hier->lmin];
-    return launch_p1_const(L(l), dt, a, s);
+    return op->launch(l, dt, a, s);
   }
 
   int smooth(int l, int dt, void* x, const void* b, int nu, cudaStream_t s) {

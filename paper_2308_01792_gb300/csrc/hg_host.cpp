@@ -327,6 +327,7 @@ int Hier::build_level(int l) {
     H.canon = canon;
     H.canon_rep = rep;
     H.dirichlet = dir;
+    H.canon_keys = uniq;
     H.canon_xyz.resize(3 * L.n_unique);
     const double den = (double)mesh->grid_denom * n;
     for (int64_t u = 0; u < L.n_unique; ++u) {
@@ -526,11 +527,11 @@ void p1_cell_stencils(const Mesh& m, int64_t c, int n, int kind, double S[16][16
 int Op::build(const Hier* h, int kind_, const double* coeff) {
   hier = h;
   kind = kind_;
+  if (kind == HG_OP_P1_DIVKGRAD) return build_divkgrad(coeff);
   if (kind != HG_OP_P1_LAPLACE && kind != HG_OP_P1_MASS) {
     set_error("operator kind %d not available in this build", kind);
     return HG_ERR_UNSUPPORTED;
   }
-  (void)coeff;
   sten64.resize(h->lmax - h->lmin + 1, nullptr);
   sten32.resize(h->lmax - h->lmin + 1, nullptr);
   for (int l = h->lmin; l <= h->lmax; ++l) {
@@ -551,9 +552,116 @@ int Op::build(const Hier* h, int kind_, const double* coeff) {
   return HG_OK;
 }
 
+// -div(k grad) with k at the vertices: per level the coefficient is the
+// finest-level value at the same lattice point (injection), the element
+// matrices of the six micro-cell types are computed per macro cell, and
+// 1/diag(A) comes from the operator's own diagonal kernel.
+int Op::build_divkgrad(const double* coeff) {
+  const Hier* h = hier;
+  if (!coeff) {
+    set_error("HG_OP_P1_DIVKGRAD needs the coefficient at the finest-level vertices");
+    return HG_ERR_INVALID_ARG;
+  }
+  if (!h->mesh->grid_denom) {
+    set_error("HG_OP_P1_DIVKGRAD needs vertex coordinates on an exact lattice");
+    return HG_ERR_UNSUPPORTED;
+  }
+  const int nl = h->lmax - h->lmin + 1;
+  for (int dt = 0; dt < 2; ++dt) {
+    vk[dt].assign(nl, nullptr);
+    vK[dt].assign(nl, nullptr);
+    vinv[dt].assign(nl, nullptr);
+  }
+  const LevelHost& F = h->lv[h->lmax - h->lmin];
+  const int64_t off = 1 << 20, m21 = (1 << 21) - 1;
+  for (int l = h->lmin; l <= h->lmax; ++l) {
+    const LevelHost& H = h->lv[l - h->lmin];
+    const LevelDev& L = H.dev;
+    const int shift = h->lmax - l;
+    // coefficient at this level's canonical vertices, then at every stored copy
+    std::vector<double> kc(L.n_unique), ks(L.n_stored, 0.0);
+    for (int64_t u = 0; u < L.n_unique; ++u) {
+      const int64_t key = H.canon_keys[u];
+      const int64_t X = ((key & m21) - off) << shift, Y = (((key >> 21) & m21) - off) << shift,
+                    Z = ((key >> 42) - off) << shift;
+      const int64_t fk = ((Z + off) << 42) | ((Y + off) << 21) | (X + off);
+      auto it = std::lower_bound(F.canon_keys.begin(), F.canon_keys.end(), fk);
+      if (it == F.canon_keys.end() || *it != fk) {
+        set_error("internal: level %d vertex not found on the finest level", l);
+        return HG_ERR_INVALID_ARG;
+      }
+      kc[u] = coeff[it - F.canon_keys.begin()];
+    }
+    for (int64_t q = 0; q < L.n_stored; ++q)
+      if (H.canon[q] >= 0) ks[q] = kc[H.canon[q]];
+    // element-matrix rows of the 24 incidences (type t, corner a): row a of K_t
+    const int n = 1 << l;
+    std::vector<double> K(96 * h->mesh->nc);
+    for (int64_t c = 0; c < h->mesh->nc; ++c)
+      for (int t = 0; t < 6; ++t) {
+        double X[4][3], Ke[4][4];
+        micro_cell_coords(*h->mesh, c, n, t, X);
+        p1_element_matrix(HG_OP_P1_LAPLACE, X, Ke);
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) K[96 * c + 16 * t + 4 * a + b] = Ke[a][b];
+      }
+    std::vector<float> ks32(ks.begin(), ks.end()), K32(K.begin(), K.end());
+    double* d = nullptr;
+    float* f = nullptr;
+    if (int r = upload(&d, ks)) return r;
+    vk[HG_F64][l - h->lmin] = d;
+    if (int r = upload(&d, K)) return r;
+    vK[HG_F64][l - h->lmin] = d;
+    if (int r = upload(&f, ks32)) return r;
+    vk[HG_F32][l - h->lmin] = f;
+    if (int r = upload(&f, K32)) return r;
+    vK[HG_F32][l - h->lmin] = f;
+    // diagonal (all DoFs, FP64) -> 1/diag where nonzero
+    double* diag = nullptr;
+    HG_CUDA(cudaMalloc(&diag, L.n_stored * sizeof(double)));
+    HG_CUDA(cudaMemset(diag, 0, L.n_stored * sizeof(double)));
+    StencilArgs a{};
+    a.x = diag;  // unused by the diagonal mode, must be non-null
+    a.out = diag;
+    a.op = OP_DIAG;
+    a.mask = HG_MASK_ALL;
+    VarCoef vc{vk[HG_F64][l - h->lmin], vK[HG_F64][l - h->lmin], nullptr};
+    if (int r = launch_p1_divkgrad(L, HG_F64, a, vc, 0)) return r;
+    std::vector<double> dh(L.n_stored);
+    HG_CUDA(cudaMemcpy(dh.data(), diag, L.n_stored * sizeof(double), cudaMemcpyDeviceToHost));
+    cudaFree(diag);
+    std::vector<double> inv(L.n_stored, 0.0);
+    std::vector<float> inv32(L.n_stored, 0.0f);
+    for (int64_t q = 0; q < L.n_stored; ++q)
+      if (dh[q] != 0.0) {
+        inv[q] = 1.0 / dh[q];
+        inv32[q] = (float)inv[q];
+      }
+    if (int r = upload(&d, inv)) return r;
+    vinv[HG_F64][l - h->lmin] = d;
+    if (int r = upload(&f, inv32)) return r;
+    vinv[HG_F32][l - h->lmin] = f;
+  }
+  return HG_OK;
+}
+
+int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
+  const int li = level - hier->lmin;
+  const LevelDev& L = hier->lv[li].dev;
+  if (kind == HG_OP_P1_DIVKGRAD) {
+    VarCoef vc{vk[dtype][li], vK[dtype][li], vinv[dtype][li]};
+    return launch_p1_divkgrad(L, dtype, a, vc, s);
+  }
+  a.sten = dtype == HG_F64 ? (const void*)sten64[li] : (const void*)sten32[li];
+  return launch_p1_const(L, dtype, a, s);
+}
+
 Op::~Op() {
   for (auto p : sten64) cudaFree(p);
   for (auto p : sten32) cudaFree(p);
+  for (int dt = 0; dt < 2; ++dt)
+    for (auto* v : {&vk[dt], &vK[dt], &vinv[dt]})
+      for (void* p : *v) cudaFree(p);
 }
 
 }  // namespace hg
@@ -729,9 +837,7 @@ static int run_cell_op(const hg_op* op, int level, int dtype, StencilArgs a, cud
            "input and output must be distinct non-null device pointers");
   HG_CHECK(((uintptr_t)a.x & 15) == 0, HG_ERR_INVALID_ARG,
            "input vector must be 16-byte aligned");
-  a.sten = dtype == HG_F64 ? (const void*)op->sten64[level - op->hier->lmin]
-                           : (const void*)op->sten32[level - op->hier->lmin];
-  return launch_p1_const(*L, dtype, a, s);
+  return op->launch(level, dtype, a, s);
 }
 
 int hg_apply(const hg_op* op, int level, int dtype, const void* x, void* y, int mode, int mask,

@@ -50,6 +50,7 @@ struct LevelHost {
   std::vector<int64_t> canon_rep;
   std::vector<uint8_t> dirichlet;
   std::vector<double> canon_xyz;
+  std::vector<int64_t> canon_keys;  // packed (z,y,x) lattice keys, ascending
 };
 
 struct Hier {
@@ -73,10 +74,15 @@ struct Hier {
 struct Op {
   const Hier* hier = nullptr;
   int kind = 0;
-  std::vector<double*> sten64;  // per level [ncells][16][16]
+  std::vector<double*> sten64;  // per level [ncells][16][16] (constant-coefficient kinds)
   std::vector<float*> sten32;
+  // variable-coefficient P1 (per level): k at stored vertices, element rows, 1/diag
+  std::vector<void*> vk[2], vK[2], vinv[2];
 
   int build(const Hier* h, int kind, const double* coeff);
+  int build_divkgrad(const double* coeff);
+  // One cell operation (apply / residual / Jacobi / diagonal) of this operator.
+  int launch(int level, int dtype, StencilArgs a, cudaStream_t s) const;
   ~Op();
 };
 

@@ -154,7 +154,7 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // ------------------------------------------------------------ launchers
 // Operation of the cell kernel + interface kernel pair.
-enum CellOp : int { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2 };
+enum CellOp : int { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_DIAG = 3 };
 
 struct StencilArgs {
   const void* x;        // input
@@ -166,6 +166,15 @@ struct StencilArgs {
 };
 
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);
+
+// Variable-coefficient P1 operator data of one level and dtype.
+struct VarCoef {
+  const void* k;        // coefficient at stored vertices
+  const void* K;        // [ncells][24][4] element-matrix rows of the incidences
+  const void* invdiag;  // stored 1/diag(A) (non-Dirichlet DoFs)
+};
+int launch_p1_divkgrad(const LevelDev& L, int dtype, const StencilArgs& a, const VarCoef& vc,
+                       cudaStream_t s);
 int launch_index_enumerate(int w, int64_t* out, cudaStream_t s);
 int launch_interface_dump(const LevelDev& L, int64_t* out, cudaStream_t s);
 int launch_to_canonical(const LevelDev& L, int dtype, const void* st, void* can, cudaStream_t s);

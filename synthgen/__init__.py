@@ -112,6 +112,19 @@ def rff_eval(params, xyz: np.ndarray) -> np.ndarray:
     return np.exp(out)
 
 
+def rff_eval_torch(params, xyz, device="cuda"):
+    """rff_eval with torch on a device, for large point sets (same formula, FP64)."""
+    import torch
+    omega, beta, amp = params
+    om = torch.tensor(omega, dtype=torch.float64, device=device)
+    be = torch.tensor(beta, dtype=torch.float64, device=device)
+    X = torch.as_tensor(np.asarray(xyz, dtype=np.float64), device=device)
+    out = torch.empty(len(X), dtype=torch.float64, device=device)
+    for s in range(0, len(X), 1 << 18):
+        out[s:s + (1 << 18)] = amp * torch.cos(X[s:s + (1 << 18)] @ om.T + be).sum(dim=1)
+    return torch.exp(out).cpu().numpy()
+
+
 def batched_problem_draw(seed: int = 42, count: int = 512):
     """Per-problem (m, level) of the batched workload: m in {1,2,3}, level in {3..6}."""
     rng = np.random.Generator(np.random.PCG64(seed))
