@@ -150,6 +150,59 @@ def cpu_baseline_spmv(seconds=10.0):
                       f"{SAMPLE_LEVEL} ({rm.n_vertices} DoFs), {reps} reps in {dt:.1f} s"}
 
 
+GMG_WORKLOAD = "cube384_L6_p1_lognormal_gmg_to_1e-8"
+WEIGHTS = os.path.join(ROOT, "paper_2308_01792_gb300", "weights", "learned_smoother_cube384.npy")
+
+
+def gmg_comparison(stream):
+    """Time to 1e-8 relative residual on the 4x4x4 Kuhn cube (384 macro cells),
+    level 6 (17 M DoFs), P1 -div(k grad), k = exp(g) log-normal (seed 1000),
+    seeded U[-1,1] right-hand side: plain FP64 V(3,3) cycles vs FP32 V-cycles
+    in FP64 refinement, without and with the learned smoother."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    from paper_2308_01792_gb300 import learned
+    macro = sg.kuhn_cube(4)
+    t0 = time.perf_counter()
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 0, 6)
+    _, xyz, dirich = H.canonical_info(6)
+    k = sg.rff_eval_torch(sg.rff_params(1000), xyz, dtype=torch.float32)
+    op = hg.Operator(H, hg.HG_OP_P1_DIVKGRAD, coeff=k)
+    bc = sg.uniform_vector(9, len(xyz))
+    bc[dirich] = 0.0
+    b = H.from_canonical(6, torch.tensor(bc, device="cuda"))
+    setup_s = time.perf_counter() - t0
+    if os.path.exists(WEIGHTS):
+        net, trained = hg.MLP(np.load(WEIGHTS)), "loaded " + os.path.relpath(WEIGHTS, ROOT)
+    else:
+        X, t, npairs = learned.make_noise_pairs(macro, 0, 4, range(1, 25), 4, 2)
+        net, loss = learned.train(X, t, steps=3000, batch=65536, lr=1e-3)
+        trained = f"trained in bench: {npairs} noise pairs, loss {loss:.4g}"
+    out = {"workload": GMG_WORKLOAD, "unique_dofs": int(len(xyz)), "tol": 1e-8,
+           "setup_s": setup_s, "weights": trained}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for name, prec, use in (("plain_f64", hg.HG_PREC_F64, False),
+                            ("mixed_f32_ir", hg.HG_PREC_MIXED, False),
+                            ("learned_mixed", hg.HG_PREC_MIXED, True)):
+        G = hg.GMG(op)
+        G.set_learned(net if use else None)
+        x = H.zeros(6, torch.float64)
+        G.solve(x, b, tol=1e-8, max_iter=200, precision=prec, stream=stream)   # warm-up
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it, rel = G.solve(x, b, tol=1e-8, max_iter=200, precision=prec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel}
+        if use:
+            out[name]["fallbacks"] = G.learned_fallbacks()
+        del G
+    out["learned_vs_plain_f64_speedup"] = out["plain_f64"]["s"] / out["learned_mixed"]["s"]
+    out["learned_vs_mixed_speedup"] = out["mixed_f32_ir"]["s"] / out["learned_mixed"]["s"]
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -192,6 +245,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-gmg", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -296,6 +350,8 @@ def main():
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_gmg:
+        out["gmg"] = gmg_comparison(stream)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_spmv()
     if rank == 0:

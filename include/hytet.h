@@ -258,6 +258,50 @@ int hg_solve(hg_gmg* g, int precision, double* x, const double* b, double rel_to
  * count, at most cap values are written to out (host). */
 int hg_gmg_history(const hg_gmg* g, double* out, int cap, int* n);
 
+/* ------------------------------------------------- learned local smoother --
+ * A small network N (16 -> 32 -> 32 -> 1, ReLU, no biases, so N(a s) =
+ * a N(s) for a > 0) maps the 15-point neighbourhood of s = D^-1 (b - A x) at
+ * a DoF to a correction; the learned smoothing step is
+ *   x <- x + omega s + N(s)  (macro-cell-interior DoFs),  x + omega s  (others).
+ * The paper has no learned component; this extends its matvec+diagonal
+ * smoothers.  Evaluated and trained with BF16 tensor-core kernels that
+ * accumulate in FP32.  Parameters: 1568 floats = W1 (32x16, row = output) |
+ * W2 (32x32) | w3 (32). */
+typedef struct hg_mlp hg_mlp;
+
+/* New network with zero weights (N = 0) on the current device. */
+int hg_mlp_create(hg_mlp** out);
+void hg_mlp_destroy(hg_mlp* mlp);
+/* Host copies of the 1568 FP32 parameters; set also resets the optimiser. */
+int hg_mlp_set_params(hg_mlp* mlp, const float* params);
+int hg_mlp_get_params(const hg_mlp* mlp, float* params);
+/* out[b] = N(X[b]) for n rows of 16 FP32 features (device, rounded to bf16). */
+int hg_mlp_forward(const hg_mlp* mlp, const float* X, int64_t n, float* out, void* stream);
+/* Gradient of L = mean_b (N(X_b) - t_b)^2 over n samples: X device bf16
+ * [n][16] (16-byte aligned), t device FP32 [n].  grad (host, 1568 floats)
+ * and loss (host) may be NULL.  Synchronises `stream`. */
+int hg_mlp_grad(hg_mlp* mlp, const void* X, const float* t, int64_t n, float* grad,
+                double* loss, void* stream);
+/* `steps` Adam steps (lr, beta 0.9/0.999) on consecutive minibatches of
+ * `batch` samples (wrapping); *final_loss (if not NULL) = L over all n. */
+int hg_mlp_train(hg_mlp* mlp, const void* X, const float* t, int64_t n, int steps,
+                 int64_t batch, double lr, double* final_loss, void* stream);
+/* Training pairs from one residual/error state on `level` (FP32 stored
+ * vectors r = b - A x, the converged solution xstar and the iterate x):
+ * every stride-th macro-cell-interior DoF (interior rank % stride == offset)
+ * gives the features s(15 neighbours) / |s-neighbourhood| (bf16 [16], last 0)
+ * and the target (xstar - x - omega s) / |s-neighbourhood|.  With X == NULL
+ * only *count is returned. */
+int hg_learn_samples(const hg_op* op, int level, const float* r, const float* xstar,
+                     const float* x, double omega, int stride, int offset, void* X, float* t,
+                     int64_t* count, void* stream);
+/* Use `mlp` (NULL: none) for the smoothing steps on the finest level of
+ * FP32 V-cycles (hg_vcycle with HG_F32, hg_solve with HG_PREC_MIXED).  In a
+ * solve, a refinement step that increases the FP64 residual switches the
+ * rest of the solve back to the plain smoother (counted). */
+int hg_gmg_set_learned(hg_gmg* g, const hg_mlp* mlp);
+int hg_gmg_learned_fallbacks(const hg_gmg* g, int* n);
+
 #ifdef __cplusplus
 }
 #endif

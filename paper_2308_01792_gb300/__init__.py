@@ -61,6 +61,16 @@ SIGNATURES = {
     "hg_vcycle": (_I, [_P, _I, _I, _P, _P, _P]),
     "hg_solve": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(ctypes.c_int), _PD, _P]),
     "hg_gmg_history": (_I, [_P, _PD, _I, ctypes.POINTER(ctypes.c_int)]),
+    "hg_mlp_create": (_I, [ctypes.POINTER(_P)]),
+    "hg_mlp_destroy": (None, [_P]),
+    "hg_mlp_set_params": (_I, [_P, _P]),
+    "hg_mlp_get_params": (_I, [_P, _P]),
+    "hg_mlp_forward": (_I, [_P, _P, _L, _P, _P]),
+    "hg_mlp_grad": (_I, [_P, _P, _P, _L, _P, _PD, _P]),
+    "hg_mlp_train": (_I, [_P, _P, _P, _L, _I, _L, _D, _PD, _P]),
+    "hg_learn_samples": (_I, [_P, _I, _P, _P, _P, _D, _I, _I, _P, _P, _PL, _P]),
+    "hg_gmg_set_learned": (_I, [_P, _P]),
+    "hg_gmg_learned_fallbacks": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
 }
 
 HG_PREC_F64, HG_PREC_MIXED = 0, 1
@@ -290,6 +300,15 @@ class GMG:
             raise HGError("hg_solve", r, lib().hg_last_error().decode())
         return it.value, rel.value
 
+    def set_learned(self, mlp=None):
+        _call("hg_gmg_set_learned", self._h, mlp._h if mlp is not None else None)
+        self.mlp = mlp
+
+    def learned_fallbacks(self):
+        n = ctypes.c_int()
+        _call("hg_gmg_learned_fallbacks", self._h, ctypes.byref(n))
+        return n.value
+
     def history(self):
         n = ctypes.c_int()
         _call("hg_gmg_history", self._h, None, 0, ctypes.byref(n))
@@ -301,6 +320,69 @@ class GMG:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hg_gmg_destroy(self._h)
             self._h = None
+
+
+N_MLP_PARAMS = 512 + 1024 + 32
+
+
+class MLP:
+    """The learned local smoother network (BF16 tensor-core kernels)."""
+
+    def __init__(self, params=None):
+        h = _P()
+        _call("hg_mlp_create", ctypes.byref(h))
+        self._h = h
+        if params is not None:
+            self.set_params(params)
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32).reshape(-1)
+        if p.size != N_MLP_PARAMS:
+            raise ValueError(f"need {N_MLP_PARAMS} parameters")
+        _call("hg_mlp_set_params", self._h, p.ctypes.data_as(_P))
+
+    def params(self):
+        p = np.empty(N_MLP_PARAMS, dtype=np.float32)
+        _call("hg_mlp_get_params", self._h, p.ctypes.data_as(_P))
+        return p
+
+    def forward(self, X, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        _call("hg_mlp_forward", self._h, _ptr(X), X.shape[0], _ptr(out), _stream(stream))
+        return out
+
+    def grad(self, X, t, stream=None):
+        g = np.empty(N_MLP_PARAMS, dtype=np.float32)
+        loss = ctypes.c_double()
+        _call("hg_mlp_grad", self._h, _ptr(X), _ptr(t), X.shape[0], g.ctypes.data_as(_P),
+              ctypes.byref(loss), _stream(stream))
+        return loss.value, g
+
+    def train(self, X, t, steps, batch, lr, stream=None):
+        loss = ctypes.c_double()
+        _call("hg_mlp_train", self._h, _ptr(X), _ptr(t), X.shape[0], steps, batch, lr,
+              ctypes.byref(loss), _stream(stream))
+        return loss.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hg_mlp_destroy(self._h)
+            self._h = None
+
+
+def learn_samples(op, level, r, xstar, x, omega, stride, offset, stream=None):
+    """Training pairs (X bf16 [count,16], t float32 [count]) from one state."""
+    import torch
+    cnt = ctypes.c_int64()
+    _call("hg_learn_samples", op._h, level, None, None, None, omega, stride, offset, None, None,
+          ctypes.byref(cnt), _stream(stream))
+    X = torch.empty((cnt.value, 16), dtype=torch.bfloat16, device="cuda")
+    t = torch.empty(cnt.value, dtype=torch.float32, device="cuda")
+    _call("hg_learn_samples", op._h, level, _ptr(r), _ptr(xstar), _ptr(x), omega, stride, offset,
+          _ptr(X), _ptr(t), ctypes.byref(cnt), _stream(stream))
+    return X, t
 
 
 def index_tw(w, i, j, k):

@@ -29,6 +29,9 @@ struct Gmg {
   double* dot_dev = nullptr;
   double* dot_host = nullptr;
   std::vector<double> history;
+  const Mlp* learned = nullptr;   // learned smoothing on the finest FP32 level
+  bool learned_active = false;
+  int learned_fallbacks = 0;
 
   const LevelDev& L(int l) const { return hier->lv[l - hier->lmin].dev; }
   size_t bytes(int l, int dt) const { return L(l).n_stored * (dt == HG_F64 ? 8 : 4); }
@@ -71,10 +74,21 @@ struct Gmg {
 
   int smooth(int l, int dt, void* x, const void* b, int nu, cudaStream_t s) {
     void* t = W(dt, WT, l);
+    const bool learn = learned_active && dt == HG_F32 && l == lmax;
     for (int q = 0; q < nu; ++q) {
       const void* src = (q % 2 == 0) ? x : t;
       void* dst = (q % 2 == 0) ? t : x;
-      if (int r = cell_op(l, dt, OP_JACOBI, src, b, dst, s)) return r;
+      if (learn) {
+        // x' = x + omega s + N(s), s = D^-1 (b - A x)
+        void* res = W(dt, WR, l);
+        if (int r = cell_op(l, dt, OP_RESID, src, b, res, s)) return r;
+        if (int r = launch_learned_step(L(l), (const float*)src, (const float*)res,
+                                        (const float*)op->vinv[HG_F32][l - hier->lmin],
+                                        (float)prm.omega, learned->params, (float*)dst, s))
+          return r;
+      } else {
+        if (int r = cell_op(l, dt, OP_JACOBI, src, b, dst, s)) return r;
+      }
     }
     if (nu % 2) HG_CUDA(cudaMemcpyAsync(x, t, bytes(l, dt), cudaMemcpyDeviceToDevice, s));
     return HG_OK;
@@ -209,6 +223,9 @@ int Gmg::solve(int precision, double* x, const double* b, double tol, int max_it
   const double nb = std::sqrt(bb);
   int it = 0;
   double rel = 0.0;
+  learned_active = learned != nullptr;
+  learned_fallbacks = 0;
+  double prev = 1.0;
   if (nb == 0.0) {
     history.push_back(0.0);
   } else {
@@ -222,6 +239,13 @@ int Gmg::solve(int precision, double* x, const double* b, double tol, int max_it
       const double rn = std::sqrt(rr);
       rel = rn / nb;
       history.push_back(rel);
+      // safeguard: if a learned cycle increased the residual, continue with the
+      // plain smoother
+      if (learned_active && rel > prev) {
+        learned_active = false;
+        ++learned_fallbacks;
+      }
+      prev = rel;
       if (rel <= tol || it >= max_iter) break;
       if (precision == HG_PREC_F64) {
         if (int r = vcycle(l, HG_F64, x, b, s)) return r;
@@ -267,6 +291,7 @@ using namespace hg;
 
 struct hg_gmg : Gmg {};
 struct hg_op : Op {};
+struct hg_mlp : Mlp {};
 
 extern "C" {
 
@@ -337,6 +362,7 @@ int hg_vcycle(hg_gmg* g, int level, int dtype, void* x, const void* b, void* str
     return HG_ERR_INVALID_ARG;
   }
   if (int r = g->alloc_work(dtype)) return r;
+  g->learned_active = g->learned != nullptr;
   return g->vcycle(level, dtype, x, b, (cudaStream_t)stream);
 }
 
@@ -351,6 +377,28 @@ int hg_solve(hg_gmg* g, int precision, double* x, const double* b, double rel_to
     return HG_ERR_INVALID_ARG;
   }
   return g->solve(precision, x, b, rel_tol, max_iter, iters, rel_res, (cudaStream_t)stream);
+}
+
+int hg_gmg_set_learned(hg_gmg* g, const hg_mlp* mlp) {
+  if (!g) {
+    set_error("hg_gmg_set_learned: null handle");
+    return HG_ERR_INVALID_ARG;
+  }
+  if (mlp && g->op->vinv[HG_F32].empty()) {
+    set_error("learned smoothing needs the operator's stored diagonal (exact lattice)");
+    return HG_ERR_UNSUPPORTED;
+  }
+  g->learned = mlp;
+  return HG_OK;
+}
+
+int hg_gmg_learned_fallbacks(const hg_gmg* g, int* n) {
+  if (!g || !n) {
+    set_error("hg_gmg_learned_fallbacks: null argument");
+    return HG_ERR_INVALID_ARG;
+  }
+  *n = g->learned_fallbacks;
+  return HG_OK;
 }
 
 int hg_gmg_history(const hg_gmg* g, double* out, int cap, int* n) {

@@ -548,6 +548,36 @@ int Op::build(const Hier* h, int kind_, const double* coeff) {
     }
     if (int r = upload(&sten64[l - h->lmin], s64)) return r;
     if (int r = upload(&sten32[l - h->lmin], s32)) return r;
+    // 1/diag(A) at every stored copy (sum of the copies' stencil centres)
+    const LevelHost& H = h->lv[l - h->lmin];
+    const LevelDev& L = H.dev;
+    if (h->mesh->grid_denom) {
+      std::vector<double> du(L.n_unique, 0.0);
+      for (int64_t c = 0; c < h->mesh->nc; ++c)
+        for (int k = 0; k <= n; ++k)
+          for (int j = 0; j + k <= n; ++j)
+            for (int i = 0; i + j + k <= n; ++i) {
+              const int64_t q = c * L.cell_stride + tw(n + 1, i, j, k);
+              du[H.canon[q]] += s64[256 * c + 16 * point_class(n, i, j, k)];
+            }
+      std::vector<double> inv(L.n_stored, 0.0);
+      std::vector<float> inv32(L.n_stored, 0.0f);
+      for (int64_t q = 0; q < L.n_stored; ++q)
+        if (H.canon[q] >= 0 && du[H.canon[q]] != 0.0) {
+          inv[q] = 1.0 / du[H.canon[q]];
+          inv32[q] = (float)inv[q];
+        }
+      if (vinv[0].empty()) {
+        vinv[0].assign(h->lmax - h->lmin + 1, nullptr);
+        vinv[1].assign(h->lmax - h->lmin + 1, nullptr);
+      }
+      double* d = nullptr;
+      float* f = nullptr;
+      if (int r = upload(&d, inv)) return r;
+      if (int r = upload(&f, inv32)) return r;
+      vinv[HG_F64][l - h->lmin] = d;
+      vinv[HG_F32][l - h->lmin] = f;
+    }
   }
   return HG_OK;
 }

@@ -86,6 +86,22 @@ struct Op {
   ~Op();
 };
 
+// Parameters and optimiser state of the learned smoother network (device).
+struct Mlp {
+  float* params = nullptr;   // kMlpParams
+  float* grad = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* partial = nullptr;  // [blocks][kMlpParams] gradient partials
+  double* lpart = nullptr;
+  double* loss = nullptr;
+  double* loss_host = nullptr;
+  int partial_blocks = 0;
+  int step = 0;
+  int build();
+  ~Mlp();
+};
+
 void micro_cell_coords(const Mesh& m, int64_t c, int n, int type, double X[4][3]);
 void bary_gradients(const double X[4][3], double G[4][3], double* vol);
 void p1_cell_stencils(const Mesh& m, int64_t c, int n, int kind, double S[16][16]);

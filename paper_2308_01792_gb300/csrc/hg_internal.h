@@ -191,6 +191,22 @@ int launch_dot(const LevelDev& L, int dtype, const void* x, const void* y, int m
 int launch_coarse_solve(const LevelDev& L, const CoarseDev& C, int dtype, const void* b, void* x,
                         cudaStream_t s);
 int launch_demote_scaled(int64_t n, const double* r, double scale, float* out, cudaStream_t s);
+// Learned smoother network (params: W1 32x16 | W2 32x32 | w3 32, FP32 master).
+constexpr int kMlpParams = 512 + 1024 + 32;
+int launch_mlp_forward(const float* X, int64_t N, const float* W1, const float* W2,
+                       const float* w3, float* out, cudaStream_t s);
+int mlp_grad_blocks(int64_t count);
+int launch_mlp_grad(const void* Xs, const float* ts, int64_t N, int64_t first, int64_t count,
+                    const float* W1, const float* W2, const float* w3, float* partial,
+                    double* lpart, float* grad, double* loss, cudaStream_t s);
+int launch_mlp_adam(float* p, const float* grad, float* m, float* v, float lr, int step,
+                    cudaStream_t s);
+int launch_learned_step(const LevelDev& L, const float* x, const float* r, const float* inv,
+                        float omega, const float* params, float* xo, cudaStream_t s);
+int64_t learned_sample_count(const LevelDev& L, int sstride, int soff);
+int launch_learned_sample(const LevelDev& L, const float* r, const float* inv, const float* xstar,
+                          const float* x, float omega, int sstride, int soff, void* X, float* t,
+                          cudaStream_t s);
 int launch_promote_axpy(int64_t n, double alpha, const float* d, double* x, cudaStream_t s);
 
 }  // namespace hg

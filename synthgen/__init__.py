@@ -112,17 +112,19 @@ def rff_eval(params, xyz: np.ndarray) -> np.ndarray:
     return np.exp(out)
 
 
-def rff_eval_torch(params, xyz, device="cuda"):
-    """rff_eval with torch on a device, for large point sets (same formula, FP64)."""
+def rff_eval_torch(params, xyz, device="cuda", dtype=None):
+    """rff_eval with torch on a device, for large point sets (same formula;
+    FP64 by default, FP32 on request for speed)."""
     import torch
+    dtype = dtype or torch.float64
     omega, beta, amp = params
-    om = torch.tensor(omega, dtype=torch.float64, device=device)
-    be = torch.tensor(beta, dtype=torch.float64, device=device)
-    X = torch.as_tensor(np.asarray(xyz, dtype=np.float64), device=device)
-    out = torch.empty(len(X), dtype=torch.float64, device=device)
+    om = torch.tensor(omega, dtype=dtype, device=device)
+    be = torch.tensor(beta, dtype=dtype, device=device)
+    X = torch.as_tensor(np.asarray(xyz, dtype=np.float64), device=device).to(dtype)
+    out = torch.empty(len(X), dtype=dtype, device=device)
     for s in range(0, len(X), 1 << 18):
         out[s:s + (1 << 18)] = amp * torch.cos(X[s:s + (1 << 18)] @ om.T + be).sum(dim=1)
-    return torch.exp(out).cpu().numpy()
+    return torch.exp(out).double().cpu().numpy()
 
 
 def batched_problem_draw(seed: int = 42, count: int = 512):
