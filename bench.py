@@ -203,6 +203,78 @@ def gmg_comparison(stream):
     return out
 
 
+BATCH_WORKLOAD = "batch512_p1_poisson_to_1e-8"
+
+
+def batch_comparison(stream, count=512):
+    """512 independent P1 Poisson problems (unit cube as m^3 sub-cubes x 6
+    Kuhn tetrahedra, m in {1,2,3}, level in {3..6}, drawn with seed 42),
+    seeded U[-1,1] right-hand sides, each solved to 1e-8 relative residual:
+    one batched solve (a persistent launch per V-cycle stage over all
+    problems, CUDA-graph replay, autotuned variant) against the same problems
+    solved one after another."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    draw = sg.batched_problem_draw(42, count)
+    t0 = time.perf_counter()
+    shared = {}
+    Gs, xs, bs = [], [], []
+    dofs = 0
+    for p, (m, L) in enumerate(draw):
+        if (m, L) not in shared:
+            macro = sg.kuhn_cube(m)
+            H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 0, L)
+            op = hg.Operator(H)
+            _, xyz, dirich = H.canonical_info(L)
+            shared[(m, L)] = [H, op, hg.GMG(op), False, len(xyz), dirich]
+        H, op, G0, used, nu, dirich = shared[(m, L)]
+        Gs.append(G0.clone() if used else G0)
+        shared[(m, L)][3] = True
+        bc = sg.uniform_vector(1000 + p, nu)
+        bc[dirich] = 0.0
+        bs.append(H.from_canonical(L, torch.tensor(bc, device="cuda")))
+        xs.append(H.zeros(L, torch.float64))
+        dofs += nu
+    B = hg.Batch(Gs, xs, bs, graph=True, autotune=True)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    B.solve(tol=1e-8, max_iter=100, stream=stream)        # warm-up
+    times = []
+    for _ in range(3):
+        e0.record(stream)
+        it, rel = B.solve(tol=1e-8, max_iter=100, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    rows, gf, us = B.tuning()
+    t_batch = float(np.median(times))
+    # the same problems, one solve at a time (same kernels, no batching)
+    x1 = [torch.zeros_like(v) for v in xs]
+    Gs[0].solve(x1[0], bs[0], tol=1e-8, max_iter=100, precision=hg.HG_PREC_MIXED, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    its1 = []
+    for p in range(count):
+        i1, _ = Gs[p].solve(x1[p], bs[p], tol=1e-8, max_iter=100, precision=hg.HG_PREC_MIXED,
+                            stream=stream)
+        its1.append(i1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    return {"workload": BATCH_WORKLOAD, "problems": count, "unique_dofs_total": int(dofs),
+            "hierarchies": len(shared), "tol": 1e-8, "setup_s": setup_s,
+            "batched": {"s": t_batch, "s_all": times, "iters_max": int(it.max()),
+                        "iters_mean": float(it.mean()), "rel_res_max": float(rel.max()),
+                        "gdof_per_s_solved": dofs / t_batch / 1e9,
+                        "tuned_rows": rows, "tuned_grid_blocks_per_sm": 4 * gf,
+                        "tuned_stage_us": us},
+            "one_at_a_time": {"s": t_seq, "iters_max": int(max(its1)),
+                              "iters_equal": bool(np.array_equal(np.array(its1), it))},
+            "batched_vs_one_at_a_time_speedup": t_seq / t_batch}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -246,6 +318,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gmg", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -352,6 +425,8 @@ def main():
     }
     if rank == 0 and not args.no_gmg:
         out["gmg"] = gmg_comparison(stream)
+    if rank == 0 and not args.no_batch:
+        out["batch"] = batch_comparison(stream)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_spmv()
     if rank == 0:

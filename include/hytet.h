@@ -258,6 +258,46 @@ int hg_solve(hg_gmg* g, int precision, double* x, const double* b, double rel_to
  * count, at most cap values are written to out (host). */
 int hg_gmg_history(const hg_gmg* g, double* out, int cap, int* n);
 
+/* New GMG for the same operator and parameters with its own work vectors
+ * (the coarse inverse is copied, not rebuilt); for batches of problems that
+ * share a hierarchy. */
+int hg_gmg_clone(const hg_gmg* src, hg_gmg** out);
+
+/* --------------------------------------------------------- batched solves --
+ * A batch solves `count` independent problems A_p x_p = b_p (each a GMG over
+ * its own hierarchy and constant-stencil operator; x_p, b_p FP64 stored
+ * vectors of its finest level, device pointers fixed for the batch's life)
+ * with FP32 V-cycles inside FP64 iterative refinement (Sec. 5.1 multigrid,
+ * many problems at once).  Each V-cycle stage (a smoothing sweep, the
+ * residual, a restriction, the coarse solves, a prolongation) and each
+ * refinement step is ONE persistent launch over the work of all problems
+ * taking part; problems with fewer levels are aligned by the distance from
+ * their finest level.
+ *   flags: HG_BATCH_GRAPH    capture the stage sequence as two CUDA graphs
+ *                            (residual + norms; correction) and replay them,
+ *          HG_BATCH_AUTOTUNE time the stage-kernel variants (register-window
+ *                            rows 2/4/8 x 1/2/4 x 4 blocks per SM) at
+ *                            creation and keep the fastest.
+ * Every problem needs its own hg_gmg (hg_gmg_clone) with the same
+ * nu1/nu2/inner_cycles; a problem may not appear twice.  The batch holds
+ * the problems' handles: destroy it before them. */
+typedef struct hg_batch hg_batch;
+enum { HG_BATCH_GRAPH = 1, HG_BATCH_AUTOTUNE = 2 };
+int hg_batch_create(hg_gmg* const* problems, int count, double* const* x, const double* const* b,
+                    int flags, hg_batch** out);
+void hg_batch_destroy(hg_batch* batch);
+/* Zero every x_p, then iterate until every problem has met rel_tol (or
+ * max_iter).  iters[p]: the step at which problem p first met rel_tol;
+ * rel_res[p]: its relative residual then (or at exit).  A converged problem
+ * keeps its iterate unchanged while the others continue.  Ordered after
+ * `stream`'s prior work, synchronises it.  Errors: HG_ERR_NOT_CONVERGED
+ * (results still written), HG_ERR_INVALID_ARG. */
+int hg_batch_solve(hg_batch* batch, double rel_tol, int max_iter, int* iters, double* rel_res,
+                   void* stream);
+/* The stage-kernel variant in use: register-window rows, blocks per SM / 4,
+ * and (after autotuning) the fastest finest-stage time in microseconds. */
+int hg_batch_tuning(const hg_batch* batch, int* rows, int* grid_factor, double* stage_us);
+
 /* ------------------------------------------------- learned local smoother --
  * A small network N (16 -> 32 -> 32 -> 1, ReLU, no biases, so N(a s) =
  * a N(s) for a > 0) maps the 15-point neighbourhood of s = D^-1 (b - A x) at

@@ -71,7 +71,14 @@ SIGNATURES = {
     "hg_learn_samples": (_I, [_P, _I, _P, _P, _P, _D, _I, _I, _P, _P, _PL, _P]),
     "hg_gmg_set_learned": (_I, [_P, _P]),
     "hg_gmg_learned_fallbacks": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "hg_gmg_clone": (_I, [_P, ctypes.POINTER(_P)]),
+    "hg_batch_create": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(_P)]),
+    "hg_batch_destroy": (None, [_P]),
+    "hg_batch_solve": (_I, [_P, _D, _I, _P, _P, _P]),
+    "hg_batch_tuning": (_I, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _PD]),
 }
+
+HG_BATCH_GRAPH, HG_BATCH_AUTOTUNE = 1, 2
 
 HG_PREC_F64, HG_PREC_MIXED = 0, 1
 
@@ -316,9 +323,63 @@ class GMG:
         _call("hg_gmg_history", self._h, out, n.value, ctypes.byref(n))
         return list(out)[:n.value]
 
+    def clone(self):
+        """A GMG for the same operator/parameters with its own work vectors."""
+        h = _P()
+        _call("hg_gmg_clone", self._h, ctypes.byref(h))
+        g = GMG.__new__(GMG)
+        g._h = h
+        g.op = self.op
+        return g
+
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hg_gmg_destroy(self._h)
+            self._h = None
+
+
+class Batch:
+    """Many independent GMG problems solved together by persistent stage
+    launches (optionally replayed as CUDA graphs, with autotuned variants).
+    ``problems``: distinct GMG objects; ``x``/``b``: FP64 finest-level stored
+    vectors, one per problem, kept alive by the batch."""
+
+    def __init__(self, problems, x, b, graph=True, autotune=True):
+        import torch
+        n = len(problems)
+        if not (n == len(x) == len(b)) or n == 0:
+            raise ValueError("problems, x and b need the same nonzero length")
+        for v in list(x) + list(b):
+            if v.dtype != torch.float64 or not v.is_cuda or not v.is_contiguous():
+                raise ValueError("x and b must be contiguous FP64 CUDA tensors")
+        hs = (_P * n)(*[g._h.value for g in problems])
+        xs = (_P * n)(*[v.data_ptr() for v in x])
+        bs = (_P * n)(*[v.data_ptr() for v in b])
+        flags = (HG_BATCH_GRAPH if graph else 0) | (HG_BATCH_AUTOTUNE if autotune else 0)
+        h = _P()
+        _call("hg_batch_create", hs, n, xs, bs, flags, ctypes.byref(h))
+        self._h = h
+        self._keep = (list(problems), list(x), list(b))
+        self.count = n
+
+    def solve(self, tol=1e-8, max_iter=100, stream=None, check=True):
+        """Returns (iters, rel_res) as numpy arrays (per problem)."""
+        it = np.zeros(self.count, dtype=np.int32)
+        rel = np.zeros(self.count, dtype=np.float64)
+        r = lib().hg_batch_solve(self._h, tol, max_iter, it.ctypes.data_as(_P),
+                                 rel.ctypes.data_as(_P), _stream(stream))
+        if r != 0 and (check or r != -5):
+            raise HGError("hg_batch_solve", r, lib().hg_last_error().decode())
+        return it, rel
+
+    def tuning(self):
+        rows, gf, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _call("hg_batch_tuning", self._h, ctypes.byref(rows), ctypes.byref(gf), ctypes.byref(us))
+        return rows.value, gf.value, us.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hg_batch_destroy(self._h)
             self._h = None
 
 

@@ -413,3 +413,622 @@ int hg_gmg_history(const hg_gmg* g, double* out, int cap, int* n) {
 }
 
 }  // extern "C"
+
+// ======================================================= batched solves
+// Many independent problems (each with its own hierarchy/operator/GMG) are
+// solved together: every stage of the FP32 V-cycle (a smoothing sweep, the
+// residual, a restriction, the coarse solves, a prolongation) and every step
+// of the FP64 refinement loop is ONE persistent launch over the work units of
+// all problems that take part in it.  V-cycles of problems with different
+// depths are aligned by the distance from their finest level.  The stage
+// sequence is captured once as two CUDA graphs (residual + norms, correction)
+// and replayed; an autotuner picks the register-window rows and the
+// persistent grid size of the cell stages.
+namespace hg {
+
+namespace {
+
+enum StageKind { ST_CELL, ST_RESTRICT, ST_PROLONG, ST_EW, ST_DOT, ST_COARSE };
+
+struct Stage {
+  int kind = 0, dtype = 0, op = 0, nprob = 0;
+  void* descs = nullptr;
+  int* base = nullptr;
+  int* base2 = nullptr;
+  double* scratch = nullptr;  // per-unit partials of a dot stage
+  int units = 0, units2 = 0;
+};
+
+struct Batch {
+  std::vector<Gmg*> P;
+  std::vector<double*> x;
+  std::vector<const double*> b;
+  std::vector<Stage> init, g1, g2;
+  double *rr = nullptr, *rs = nullptr, *nb = nullptr;
+  double *rr_host = nullptr, *rs_host = nullptr;
+  std::vector<double> nbh;
+  double tune_us = 0.0;
+  int rows = 8, gfac = 2, sms = 152;
+  cudaStream_t cs = nullptr;
+  cudaGraphExec_t e1 = nullptr, e2 = nullptr;
+
+  ~Batch() {
+    for (auto* L : {&init, &g1, &g2})
+      for (Stage& s : *L) {
+        cudaFree(s.descs);
+        cudaFree(s.base);
+        cudaFree(s.base2);
+        cudaFree(s.scratch);
+      }
+    cudaFree(rr);
+    cudaFree(rs);
+    cudaFree(nb);
+    if (rr_host) cudaFreeHost(rr_host);
+    if (rs_host) cudaFreeHost(rs_host);
+    if (e1) cudaGraphExecDestroy(e1);
+    if (e2) cudaGraphExecDestroy(e2);
+    if (cs) cudaStreamDestroy(cs);
+  }
+
+  int grid() const { return gfac * sms * 4; }
+
+  int finish(Stage& st, const std::vector<char>& host, const std::vector<int>& base,
+             const std::vector<int>* base2 = nullptr) {
+    st.nprob = (int)base.size() - 1;
+    st.units = base.back();
+    HG_CUDA(cudaMalloc(&st.descs, std::max<size_t>(host.size(), 16)));
+    if (!host.empty()) HG_CUDA(cudaMemcpy(st.descs, host.data(), host.size(), cudaMemcpyHostToDevice));
+    HG_CUDA(cudaMalloc(&st.base, base.size() * sizeof(int)));
+    HG_CUDA(cudaMemcpy(st.base, base.data(), base.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (base2) {
+      st.units2 = base2->back();
+      HG_CUDA(cudaMalloc(&st.base2, base2->size() * sizeof(int)));
+      HG_CUDA(cudaMemcpy(st.base2, base2->data(), base2->size() * sizeof(int),
+                         cudaMemcpyHostToDevice));
+    }
+    return HG_OK;
+  }
+
+  struct CellItem {
+    int p, l;
+    const void *x, *b;
+    void* out;
+  };
+  int add_cell(std::vector<Stage>& L, int dt, int op, const std::vector<CellItem>& items) {
+    if (items.empty()) return HG_OK;
+    Stage st;
+    st.kind = ST_CELL;
+    st.dtype = dt;
+    st.op = op;
+    const size_t sz = p1_desc_bytes(dt);
+    std::vector<char> host(sz * items.size());
+    std::vector<int> base(1, 0);
+    for (size_t q = 0; q < items.size(); ++q) {
+      const Gmg* G = P[items[q].p];
+      StencilArgs a{};
+      a.x = items[q].x;
+      a.b = items[q].b;
+      a.out = items[q].out;
+      a.op = op;
+      a.mode = HG_REPLACE;
+      a.mask = HG_MASK_INNER;
+      a.omega = G->prm.omega;
+      const int li = items[q].l - G->hier->lmin;
+      a.sten = dt == HG_F64 ? (const void*)G->op->sten64[li] : (const void*)G->op->sten32[li];
+      int u = 0;
+      p1_make_desc(G->L(items[q].l), dt, a, host.data() + q * sz, &u);
+      base.push_back(base.back() + u);
+    }
+    if (int r = finish(st, host, base)) return r;
+    L.push_back(st);
+    return HG_OK;
+  }
+
+  struct XferItem {
+    int p, lf;
+    const void* src;
+    void* dst;
+  };
+  int add_xfer(std::vector<Stage>& L, int kind, int dt, const std::vector<XferItem>& items) {
+    if (items.empty()) return HG_OK;
+    Stage st;
+    st.kind = kind;
+    st.dtype = dt;
+    const size_t sz = kind == ST_RESTRICT ? restrict_desc_bytes(dt) : prolong_desc_bytes(dt);
+    std::vector<char> host(sz * items.size());
+    std::vector<int> base(1, 0);
+    for (size_t q = 0; q < items.size(); ++q) {
+      const Gmg* G = P[items[q].p];
+      const LevelDev& F = G->L(items[q].lf);
+      const LevelDev& C = G->L(items[q].lf - 1);
+      int u = 0;
+      if (kind == ST_RESTRICT)
+        restrict_make_desc(F, C, dt, items[q].src, items[q].dst, host.data() + q * sz, &u);
+      else
+        prolong_make_desc(F, C, dt, items[q].src, items[q].dst, host.data() + q * sz, &u);
+      base.push_back(base.back() + u);
+    }
+    if (int r = finish(st, host, base)) return r;
+    L.push_back(st);
+    return HG_OK;
+  }
+
+  int add_ew(std::vector<Stage>& L, int op, const std::vector<EwDesc>& d) {
+    if (d.empty()) return HG_OK;
+    Stage st;
+    st.kind = ST_EW;
+    st.op = op;
+    std::vector<char> host(sizeof(EwDesc) * d.size());
+    memcpy(host.data(), d.data(), host.size());
+    std::vector<int> base(1, 0);
+    for (const EwDesc& e : d) base.push_back(base.back() + (int)ew_units(e.n));
+    if (int r = finish(st, host, base)) return r;
+    L.push_back(st);
+    return HG_OK;
+  }
+
+  int add_dot(std::vector<Stage>& L, int dt, const std::vector<DotDesc>& d) {
+    Stage st;
+    st.kind = ST_DOT;
+    st.dtype = dt;
+    std::vector<char> host(sizeof(DotDesc) * d.size());
+    memcpy(host.data(), d.data(), host.size());
+    std::vector<int> base(1, 0);
+    for (const DotDesc& e : d) base.push_back(base.back() + (int)dot_units(e.n_rows));
+    if (int r = finish(st, host, base)) return r;
+    HG_CUDA(cudaMalloc(&st.scratch, std::max(st.units, 1) * sizeof(double)));
+    L.push_back(st);
+    return HG_OK;
+  }
+
+  int add_coarse(std::vector<Stage>& L, const std::vector<CoarseBDesc>& d) {
+    Stage st;
+    st.kind = ST_COARSE;
+    st.dtype = HG_F32;
+    std::vector<char> host(sizeof(CoarseBDesc) * d.size());
+    memcpy(host.data(), d.data(), host.size());
+    std::vector<int> b1(1, 0), b2(1, 0);
+    for (const CoarseBDesc& c : d) {
+      b1.push_back(b1.back() + (int)coarse_units_mv(c.nint));
+      b2.push_back(b2.back() + (int)coarse_units_sc(c.n_stored));
+    }
+    if (int r = finish(st, host, b1, &b2)) return r;
+    L.push_back(st);
+    return HG_OK;
+  }
+
+  int run(const Stage& st, cudaStream_t s, double* rr_out) const {
+    switch (st.kind) {
+      case ST_CELL:
+        return launch_p1_batched(st.dtype, st.op, rows, st.descs, st.base, st.nprob,
+                                 std::min(grid(), std::max(st.units, 1)), s);
+      case ST_RESTRICT:
+        return launch_restrict_batched(st.dtype, st.descs, st.base, st.nprob,
+                                       std::min(grid(), std::max(st.units, 1)), s);
+      case ST_PROLONG:
+        return launch_prolong_batched(st.dtype, st.descs, st.base, st.nprob,
+                                      std::min(grid(), std::max(st.units, 1)), s);
+      case ST_EW:
+        return launch_batched_ew(st.op, (const EwDesc*)st.descs, st.base, st.nprob,
+                                 std::min(sms * 8, std::max(st.units, 1)), s);
+      case ST_DOT:
+        return launch_batched_dot(st.dtype, (const DotDesc*)st.descs, st.base, st.nprob,
+                                  std::min(sms * 8, std::max(st.units, 1)), st.scratch, rr_out, s);
+      case ST_COARSE:
+        return launch_batched_coarse(st.dtype, (const CoarseBDesc*)st.descs, st.base, st.base2,
+                                     st.nprob,
+                                     std::min(sms * 8, std::max(std::max(st.units, st.units2), 1)),
+                                     s);
+    }
+    return HG_OK;
+  }
+
+  int run_list(const std::vector<Stage>& L, cudaStream_t s, double* rr_out) const {
+    for (const Stage& st : L)
+      if (int r = run(st, s, rr_out)) return r;
+    return HG_OK;
+  }
+
+  int build();
+  int capture(const std::vector<Stage>& L, double* rr_out, cudaGraphExec_t* out);
+  int autotune(double* best_us);
+};
+
+DotDesc dot_desc(const LevelDev& L, const void* x, const void* y) {
+  DotDesc d;
+  d.n = L.n;
+  d.stride = L.cell_stride;
+  d.flags = L.cls_flags;
+  d.n_rows = L.ncells * ntri32(L.w);
+  d.x = x;
+  d.y = y;
+  return d;
+}
+
+int Batch::build() {
+  const int np = (int)P.size();
+  HG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0));
+  HG_CUDA(cudaMalloc(&rr, np * sizeof(double)));
+  HG_CUDA(cudaMalloc(&rs, np * sizeof(double)));
+  HG_CUDA(cudaMemset(rs, 0, np * sizeof(double)));
+  HG_CUDA(cudaMallocHost(&rs_host, np * sizeof(double)));
+  HG_CUDA(cudaMalloc(&nb, np * sizeof(double)));
+  HG_CUDA(cudaMallocHost(&rr_host, np * sizeof(double)));
+  for (Gmg* G : P)
+    if (int r = G->alloc_work(HG_F32)) return r;
+  // init: x = 0, |b|^2 -> nb
+  {
+    std::vector<EwDesc> z;
+    std::vector<DotDesc> d;
+    for (int p = 0; p < np; ++p) {
+      const LevelDev& L = P[p]->L(P[p]->lmax);
+      z.push_back({L.n_stored, x[p], nullptr, nullptr, HG_F64});
+      d.push_back(dot_desc(L, b[p], b[p]));
+    }
+    if (int r = add_ew(init, EW_ZERO, z)) return r;
+    if (int r = add_dot(init, HG_F64, d)) return r;
+  }
+  // g1: r64 = b - A x (FP64), |r64|^2 -> rr
+  {
+    std::vector<CellItem> c;
+    std::vector<DotDesc> d;
+    for (int p = 0; p < np; ++p) {
+      c.push_back({p, P[p]->lmax, x[p], b[p], P[p]->r64});
+      d.push_back(dot_desc(P[p]->L(P[p]->lmax), P[p]->r64, P[p]->r64));
+    }
+    if (int r = add_cell(g1, HG_F64, OP_RESID, c)) return r;
+    if (int r = add_dot(g1, HG_F64, d)) return r;
+  }
+  // g2: b32 = r64/|r|, d32 = 0, FP32 V-cycle(s) on (d32, b32), x += |r| d32,
+  // with |r|^2 taken from rs (zero for a problem that has converged, which
+  // then keeps its iterate unchanged)
+  {
+    std::vector<EwDesc> dm, zd, pr;
+    for (int p = 0; p < np; ++p) {
+      const int64_t n = P[p]->L(P[p]->lmax).n_stored;
+      dm.push_back({n, P[p]->b32, P[p]->r64, rs + p, HG_F32});
+      zd.push_back({n, P[p]->d32, nullptr, nullptr, HG_F32});
+      pr.push_back({n, x[p], P[p]->d32, rs + p, HG_F64});
+    }
+    if (int r = add_ew(g2, EW_DEMOTE, dm)) return r;
+    if (int r = add_ew(g2, EW_ZERO, zd)) return r;
+    const int nu1 = P[0]->prm.nu1, nu2 = P[0]->prm.nu2;
+    int dmax = 0;
+    for (Gmg* G : P) dmax = std::max(dmax, G->lmax - G->lmin);
+    auto X = [&](int p, int d) -> void* {
+      return d == 0 ? (void*)P[p]->d32 : P[p]->W(HG_F32, Gmg::WX, P[p]->lmax - d);
+    };
+    auto B = [&](int p, int d) -> void* {
+      return d == 0 ? (void*)P[p]->b32 : P[p]->W(HG_F32, Gmg::WB, P[p]->lmax - d);
+    };
+    auto smooth = [&](int d, int nu) -> int {
+      for (int q = 0; q < nu; ++q) {
+        std::vector<CellItem> c;
+        for (int p = 0; p < np; ++p) {
+          if (d >= P[p]->lmax - P[p]->lmin) continue;
+          const int l = P[p]->lmax - d;
+          void* t = P[p]->W(HG_F32, Gmg::WT, l);
+          c.push_back({p, l, q % 2 == 0 ? X(p, d) : t, B(p, d), q % 2 == 0 ? t : X(p, d)});
+        }
+        if (int r = add_cell(g2, HG_F32, OP_JACOBI, c)) return r;
+      }
+      if (nu % 2) {
+        std::vector<EwDesc> cp;
+        for (int p = 0; p < np; ++p) {
+          if (d >= P[p]->lmax - P[p]->lmin) continue;
+          const int l = P[p]->lmax - d;
+          cp.push_back({P[p]->L(l).n_stored, X(p, d), P[p]->W(HG_F32, Gmg::WT, l), nullptr, HG_F32});
+        }
+        if (int r = add_ew(g2, EW_COPY, cp)) return r;
+      }
+      return HG_OK;
+    };
+    for (int cyc = 0; cyc < std::max(P[0]->prm.inner_cycles, 1); ++cyc) {
+    for (int d = 0; d < dmax; ++d) {
+      if (int r = smooth(d, nu1)) return r;
+      std::vector<CellItem> res;
+      std::vector<XferItem> rs;
+      std::vector<EwDesc> zc;
+      for (int p = 0; p < np; ++p) {
+        if (d >= P[p]->lmax - P[p]->lmin) continue;
+        const int l = P[p]->lmax - d;
+        void* rv = P[p]->W(HG_F32, Gmg::WR, l);
+        res.push_back({p, l, X(p, d), B(p, d), rv});
+        rs.push_back({p, l, rv, B(p, d + 1)});
+        zc.push_back({P[p]->L(l - 1).n_stored, X(p, d + 1), nullptr, nullptr, HG_F32});
+      }
+      if (int r = add_cell(g2, HG_F32, OP_RESID, res)) return r;
+      if (int r = add_xfer(g2, ST_RESTRICT, HG_F32, rs)) return r;
+      if (int r = add_ew(g2, EW_ZERO, zc)) return r;
+    }
+    std::vector<CoarseBDesc> co;
+    for (int p = 0; p < np; ++p) {
+      const Gmg* G = P[p];
+      const int d = G->lmax - G->lmin;
+      const LevelDev& L = G->L(G->lmin);
+      co.push_back({G->coarse.n, G->coarse.ainv, G->coarse.stored_rep, B(p, d), G->coarse.xint,
+                    L.n_stored, L.canon, G->coarse.int_of_canon, X(p, d)});
+    }
+    if (int r = add_coarse(g2, co)) return r;
+    for (int d = dmax - 1; d >= 0; --d) {
+      std::vector<XferItem> pl;
+      for (int p = 0; p < np; ++p) {
+        if (d >= P[p]->lmax - P[p]->lmin) continue;
+        pl.push_back({p, P[p]->lmax - d, X(p, d + 1), X(p, d)});
+      }
+      if (int r = add_xfer(g2, ST_PROLONG, HG_F32, pl)) return r;
+      if (int r = smooth(d, nu2)) return r;
+    }
+    }
+    if (int r = add_ew(g2, EW_PROMOTE, pr)) return r;
+  }
+  HG_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  return HG_OK;
+}
+
+int Batch::capture(const std::vector<Stage>& L, double* rr_out, cudaGraphExec_t* out) {
+  if (*out) {
+    cudaGraphExecDestroy(*out);
+    *out = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  HG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const int r = run_list(L, cs, rr_out);
+  const cudaError_t e = cudaStreamEndCapture(cs, &g);
+  if (r) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  const cudaError_t ei = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
+  return HG_OK;
+}
+
+// Time the first finest-level smoothing stage for each (rows, grid factor).
+int Batch::autotune(double* best_us) {
+  const Stage* st = nullptr;
+  for (const Stage& s : g2)
+    if (s.kind == ST_CELL) {
+      st = &s;
+      break;
+    }
+  if (!st) return HG_OK;
+  cudaEvent_t a, z;
+  HG_CUDA(cudaEventCreate(&a));
+  HG_CUDA(cudaEventCreate(&z));
+  double best = 1e30;
+  int br = rows, bg = gfac;
+  for (int R : {2, 4, 8})
+    for (int gf : {1, 2, 4}) {
+      rows = R;
+      gfac = gf;
+      if (int r = run(*st, cs, rr)) return r;  // warm-up
+      HG_CUDA(cudaEventRecord(a, cs));
+      for (int q = 0; q < 3; ++q)
+        if (int r = run(*st, cs, rr)) return r;
+      HG_CUDA(cudaEventRecord(z, cs));
+      HG_CUDA(cudaEventSynchronize(z));
+      float ms = 0.f;
+      HG_CUDA(cudaEventElapsedTime(&ms, a, z));
+      if (ms / 3 < best) {
+        best = ms / 3;
+        br = R;
+        bg = gf;
+      }
+    }
+  rows = br;
+  gfac = bg;
+  cudaEventDestroy(a);
+  cudaEventDestroy(z);
+  if (best_us) *best_us = best * 1e3;
+  return HG_OK;
+}
+
+}  // namespace
+}  // namespace hg
+
+struct hg_batch : hg::Batch {};
+
+extern "C" {
+
+int hg_gmg_clone(const hg_gmg* src, hg_gmg** out) {
+  if (!src || !out) {
+    set_error("hg_gmg_clone: null argument");
+    return HG_ERR_INVALID_ARG;
+  }
+  auto g = std::make_unique<hg_gmg>();
+  g->op = src->op;
+  g->hier = src->hier;
+  g->prm = src->prm;
+  g->lmin = src->lmin;
+  g->lmax = src->lmax;
+  g->learned = src->learned;
+  if (int r = g->alloc_work(HG_F64)) return r;
+  const size_t nl = g->L(g->lmax).n_stored;
+  HG_CUDA(cudaMalloc(&g->r64, nl * sizeof(double)));
+  HG_CUDA(cudaMalloc(&g->b32, nl * sizeof(float)));
+  HG_CUDA(cudaMalloc(&g->d32, nl * sizeof(float)));
+  HG_CUDA(cudaMemset(g->r64, 0, nl * sizeof(double)));
+  HG_CUDA(cudaMemset(g->b32, 0, nl * sizeof(float)));
+  HG_CUDA(cudaMemset(g->d32, 0, nl * sizeof(float)));
+  HG_CUDA(cudaMalloc(&g->dot_scratch, dot_scratch_len(g->L(g->lmax)) * sizeof(double)));
+  HG_CUDA(cudaMalloc(&g->dot_dev, sizeof(double)));
+  HG_CUDA(cudaMallocHost(&g->dot_host, sizeof(double)));
+  // coarse solver: copies of the source's tables
+  g->coarse.n = src->coarse.n;
+  const LevelDev& Lc = g->L(g->lmin);
+  HG_CUDA(cudaMalloc(&g->coarse.int_of_canon, std::max<int64_t>(Lc.n_unique, 1) * sizeof(int32_t)));
+  HG_CUDA(cudaMemcpy(g->coarse.int_of_canon, src->coarse.int_of_canon,
+                     Lc.n_unique * sizeof(int32_t), cudaMemcpyDeviceToDevice));
+  const int n = src->coarse.n;
+  if (n > 0) {
+    HG_CUDA(cudaMalloc(&g->coarse.stored_rep, n * sizeof(int64_t)));
+    HG_CUDA(cudaMalloc(&g->coarse.xint, n * sizeof(double)));
+    HG_CUDA(cudaMalloc(&g->coarse.ainv, (size_t)n * n * sizeof(double)));
+    HG_CUDA(cudaMemcpy(g->coarse.stored_rep, src->coarse.stored_rep, n * sizeof(int64_t),
+                       cudaMemcpyDeviceToDevice));
+    HG_CUDA(cudaMemcpy(g->coarse.ainv, src->coarse.ainv, (size_t)n * n * sizeof(double),
+                       cudaMemcpyDeviceToDevice));
+  }
+  *out = g.release();
+  return HG_OK;
+}
+
+int hg_batch_create(hg_gmg* const* problems, int count, double* const* x, const double* const* b,
+                    int flags, hg_batch** out) {
+  if (!problems || !x || !b || count < 1 || !out) {
+    set_error("hg_batch_create: bad argument");
+    return HG_ERR_INVALID_ARG;
+  }
+  auto B = std::make_unique<hg_batch>();
+  for (int p = 0; p < count; ++p) {
+    Gmg* G = problems[p];
+    if (!G || !x[p] || !b[p] || (const void*)x[p] == (const void*)b[p]) {
+      set_error("hg_batch_create: null problem or vector %d", p);
+      return HG_ERR_INVALID_ARG;
+    }
+    if (G->op->kind != HG_OP_P1_LAPLACE && G->op->kind != HG_OP_P1_MASS) {
+      set_error("hg_batch_create: problem %d: batched solves take constant-stencil operators", p);
+      return HG_ERR_UNSUPPORTED;
+    }
+    if (G->prm.nu1 != problems[0]->prm.nu1 || G->prm.nu2 != problems[0]->prm.nu2 ||
+        G->prm.inner_cycles != problems[0]->prm.inner_cycles) {
+      set_error("hg_batch_create: all problems need the same nu1/nu2/inner_cycles");
+      return HG_ERR_INVALID_ARG;
+    }
+    B->P.push_back(G);
+    B->x.push_back(x[p]);
+    B->b.push_back(b[p]);
+  }
+  {
+    std::vector<Gmg*> sorted(B->P);
+    std::sort(sorted.begin(), sorted.end());
+    if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+      set_error("hg_batch_create: a problem appears twice (each needs its own work vectors)");
+      return HG_ERR_INVALID_ARG;
+    }
+  }
+  if (int r = B->build()) return r;
+  if (flags & HG_BATCH_AUTOTUNE) {
+    if (int r = B->autotune(&B->tune_us)) return r;
+  }
+  if (flags & HG_BATCH_GRAPH) {
+    if (int r = B->capture(B->g1, B->rr, &B->e1)) return r;
+    if (int r = B->capture(B->g2, B->rr, &B->e2)) return r;
+  }
+  HG_CUDA(cudaStreamSynchronize(B->cs));
+  *out = B.release();
+  return HG_OK;
+}
+
+void hg_batch_destroy(hg_batch* B) { delete B; }
+
+int hg_batch_tuning(const hg_batch* B, int* rows, int* grid_factor, double* stage_us) {
+  if (!B) {
+    set_error("hg_batch_tuning: null handle");
+    return HG_ERR_INVALID_ARG;
+  }
+  if (rows) *rows = B->rows;
+  if (grid_factor) *grid_factor = B->gfac;
+  if (stage_us) *stage_us = B->tune_us;
+  return HG_OK;
+}
+
+int hg_batch_solve(hg_batch* B, double rel_tol, int max_iter, int* iters, double* rel_res,
+                   void* stream) {
+  if (!B || max_iter < 0 || !iters || !rel_res) {
+    set_error("hg_batch_solve: bad argument");
+    return HG_ERR_INVALID_ARG;
+  }
+  const int count = (int)B->P.size();
+  cudaStream_t us = (cudaStream_t)stream;
+  // the work runs on the batch's own stream, ordered after the caller's stream
+  cudaEvent_t ev;
+  HG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  HG_CUDA(cudaEventRecord(ev, us));
+  HG_CUDA(cudaStreamWaitEvent(B->cs, ev, 0));
+  const bool graph = B->e1 != nullptr;
+  int rc = HG_OK;
+  bool all = false;
+  B->nbh.assign(count, 0.0);
+  if ((rc = B->run_list(B->init, B->cs, B->nb))) goto done;
+  if (cudaMemcpyAsync(B->rr_host, B->nb, count * sizeof(double), cudaMemcpyDeviceToHost, B->cs) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(B->cs) != cudaSuccess) {
+    rc = cuda_fail(cudaGetLastError(), "hg_batch_solve: norm of b");
+    goto done;
+  }
+  for (int p = 0; p < count; ++p) {
+    B->nbh[p] = std::sqrt(B->rr_host[p]);
+    iters[p] = -1;
+    rel_res[p] = 1.0;
+  }
+  for (int it = 0; it <= max_iter; ++it) {
+    if (graph) {
+      if (cudaGraphLaunch(B->e1, B->cs) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "cudaGraphLaunch");
+        goto done;
+      }
+    } else if ((rc = B->run_list(B->g1, B->cs, B->rr))) {
+      goto done;
+    }
+    if (cudaMemcpyAsync(B->rr_host, B->rr, count * sizeof(double), cudaMemcpyDeviceToHost,
+                        B->cs) != cudaSuccess ||
+        cudaStreamSynchronize(B->cs) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "hg_batch_solve: residual norms");
+      goto done;
+    }
+    all = true;
+    for (int p = 0; p < count; ++p) {
+      const double rel = B->nbh[p] > 0 ? std::sqrt(B->rr_host[p]) / B->nbh[p] : 0.0;
+      if (iters[p] < 0) {
+        rel_res[p] = rel;
+        if (rel <= rel_tol) iters[p] = it;
+      }
+      // a converged problem gets a zero correction from here on
+      B->rs_host[p] = iters[p] < 0 ? B->rr_host[p] : 0.0;
+      if (iters[p] < 0) all = false;
+    }
+    if (all || it == max_iter) break;
+    if (cudaMemcpyAsync(B->rs, B->rs_host, count * sizeof(double), cudaMemcpyHostToDevice,
+                        B->cs) != cudaSuccess) {
+      rc = cuda_fail(cudaGetLastError(), "hg_batch_solve: scales");
+      goto done;
+    }
+    if (graph) {
+      if (cudaGraphLaunch(B->e2, B->cs) != cudaSuccess) {
+        rc = cuda_fail(cudaGetLastError(), "cudaGraphLaunch");
+        goto done;
+      }
+    } else if ((rc = B->run_list(B->g2, B->cs, B->rr))) {
+      goto done;
+    }
+  }
+  for (int p = 0; p < count; ++p)
+    if (iters[p] < 0) iters[p] = max_iter;
+done:
+  cudaEventRecord(ev, B->cs);
+  cudaStreamWaitEvent(us, ev, 0);
+  cudaStreamSynchronize(B->cs);
+  cudaEventDestroy(ev);
+  if (rc) return rc;
+  {
+    std::vector<const Hier*> hs;
+    for (Gmg* G : B->P)
+      if (std::find(hs.begin(), hs.end(), G->hier) == hs.end()) hs.push_back(G->hier);
+    for (const Hier* h : hs) {
+      if (int r = h->fetch_error(B->cs)) return r;
+      HG_CUDA(cudaStreamSynchronize(B->cs));
+      if (int r = h->check_error()) return r;
+    }
+  }
+  if (!all) {
+    set_error("hg_batch_solve: not all problems reached %.1e in %d iterations", rel_tol, max_iter);
+    return HG_ERR_NOT_CONVERGED;
+  }
+  return HG_OK;
+}
+
+}  // extern "C"

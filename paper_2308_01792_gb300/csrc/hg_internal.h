@@ -209,4 +209,60 @@ int launch_learned_sample(const LevelDev& L, const float* r, const float* inv, c
                           cudaStream_t s);
 int launch_promote_axpy(int64_t n, double alpha, const float* d, double* x, cudaStream_t s);
 
+// ------------------------------------------------------------ batched stages
+// Many independent problems in one persistent launch: each problem
+// contributes `units` blocks; base[p] = sum of the units of problems < p.
+enum BatchEw : int { EW_ZERO = 0, EW_COPY = 1, EW_DEMOTE = 2, EW_PROMOTE = 3 };
+struct EwDesc {         // element-wise stage on one problem's stored vector
+  int64_t n;
+  void* a;              // ZERO a=0 | COPY a=b | DEMOTE a(f32)=b(f64)/|r| | PROMOTE a(f64)+=|r| b(f32)
+  const void* b;
+  const double* rr;     // |r|^2 of the problem (DEMOTE/PROMOTE)
+  int dtype;            // ZERO/COPY element type
+};
+struct DotDesc {        // FP64 dot over owned non-Dirichlet DoFs of one problem
+  int n;
+  int64_t stride;
+  const uint8_t* flags;
+  int n_rows;
+  const void* x;
+  const void* y;
+};
+struct CoarseBDesc {    // dense coarse solve of one problem
+  int nint;
+  const double* ainv;
+  const int64_t* rep;
+  const void* b;
+  double* xint;
+  int64_t n_stored;
+  const int32_t* canon;
+  const int32_t* ioc;
+  void* x;
+};
+constexpr int kDotRowsPerUnit = 128;  // lattice rows per unit of the batched dot
+int64_t dot_units(int n_rows);
+int64_t ew_units(int64_t n);
+int launch_batched_ew(int op, const EwDesc* d, const int* base, int nprob, int grid, cudaStream_t s);
+int launch_batched_dot(int dtype, const DotDesc* d, const int* base, int nprob, int grid,
+                       double* partial, double* rr, cudaStream_t s);
+int launch_batched_coarse(int dtype, const CoarseBDesc* d, const int* base_mv, const int* base_sc,
+                          int nprob, int grid, cudaStream_t s);
+int64_t coarse_units_mv(int nint);
+int64_t coarse_units_sc(int64_t n_stored);
+// descriptors of the cell/transfer stages (built on the host, raw bytes)
+size_t p1_desc_bytes(int dtype);
+int p1_make_desc(const LevelDev& L, int dtype, const StencilArgs& a, void* dst, int* units);
+size_t restrict_desc_bytes(int dtype);
+int restrict_make_desc(const LevelDev& F, const LevelDev& C, int dtype, const void* rf, void* rc,
+                       void* dst, int* units);
+size_t prolong_desc_bytes(int dtype);
+int prolong_make_desc(const LevelDev& F, const LevelDev& C, int dtype, const void* ec, void* xf,
+                      void* dst, int* units);
+int launch_p1_batched(int dtype, int op, int rows, const void* descs, const int* base, int nprob,
+                      int grid, cudaStream_t s);
+int launch_restrict_batched(int dtype, const void* descs, const int* base, int nprob, int grid,
+                            cudaStream_t s);
+int launch_prolong_batched(int dtype, const void* descs, const int* base, int nprob, int grid,
+                           cudaStream_t s);
+
 }  // namespace hg

@@ -23,6 +23,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include "hg_internal.h"
 
@@ -167,9 +168,8 @@ __device__ void interface_point(const FusedArgs<T>& A, int item, int lane) {
 // Interior tile (see the file comment).  Row starts move by row lengths:
 // rs(j+1,k) = rs(j,k) + (w-k-j).
 template <typename T, int OP, int R>
-__device__ void interior_tile(const FusedArgs<T>& A, int t, int lane) {
-  const int4 tl = A.tiles[t];
-  const int cell = tl.x, k = tl.y, i0 = tl.z, j0 = tl.w & 0xffff, nr = (tl.w >> 16) - j0;
+__device__ void interior_tile_rows(const FusedArgs<T>& A, int cell, int k, int i0, int j0, int nr,
+                                   int lane) {
   const int w = A.w;
   const int64_t base = (int64_t)cell * A.stride;
   const T* __restrict__ x = A.x + base;
@@ -239,15 +239,66 @@ __device__ void interior_tile(const FusedArgs<T>& A, int t, int lane) {
   }
 }
 
-template <typename T, int OP>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) p1_fused_kernel(FusedArgs<T> A) {
+// A table tile (up to kTileRows rows) in register-window chunks of R rows.
+template <typename T, int OP, int R>
+__device__ __forceinline__ void interior_tile(const FusedArgs<T>& A, int t, int lane) {
+  const int4 tl = A.tiles[t];
+  const int j0 = tl.w & 0xffff, j1 = tl.w >> 16;
+  for (int jc = j0; jc < j1; jc += R)
+    interior_tile_rows<T, OP, R>(A, tl.x, tl.y, tl.z, jc, min(R, j1 - jc), lane);
+}
+
+// Block `blk` of one operator application: interface items first, then tiles.
+template <typename T, int OP, int R>
+__device__ __forceinline__ void p1_block(const FusedArgs<T>& A, int blk) {
   const int lane = threadIdx.x & 31;
-  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if ((int)blockIdx.x < A.nb_items) {
+  const int wg = blk * kWarps + (threadIdx.x >> 5);
+  if (blk < A.nb_items) {
     if (wg < A.n_items) interface_point<T, OP>(A, wg, lane);
   } else {
     const int t = wg - A.nb_items * kWarps;
-    if (t < A.n_tiles) interior_tile<T, OP, kTileRows>(A, t, lane);
+    if (t < A.n_tiles) interior_tile<T, OP, R>(A, t, lane);
+  }
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) p1_fused_kernel(FusedArgs<T> A) {
+  p1_block<T, OP, kTileRows>(A, blockIdx.x);
+}
+
+// Index of the problem owning unit u: base[p] <= u < base[p+1].
+__device__ __forceinline__ int unit_problem(const int* __restrict__ base, int nprob, int u) {
+  int lo = 0, hi = nprob - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (__ldg(base + mid) <= u) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// A problem's descriptor copied into shared memory for the block's current
+// unit (read there, it cannot alias the global stores of the stage, so the
+// compiler need not reload it after each one).  Called by every thread.
+template <typename D>
+__device__ __forceinline__ const D& stage_desc(const D* __restrict__ src, unsigned char* dst) {
+  static_assert(sizeof(D) % 4 == 0, "descriptor size");
+  __syncthreads();  // the previous unit is done with dst
+  for (int q = threadIdx.x; q < (int)(sizeof(D) / 4); q += blockDim.x)
+    reinterpret_cast<int*>(dst)[q] = __ldg(reinterpret_cast<const int*>(src) + q);
+  __syncthreads();
+  return *reinterpret_cast<const D*>(dst);
+}
+
+// Batched persistent form: units u (one per block of each problem's grid,
+// problems concatenated) are taken in a grid-stride loop.
+template <typename T, int OP, int R>
+__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) p1_batched_kernel(
+    const FusedArgs<T>* __restrict__ descs, const int* __restrict__ base, int nprob) {
+  __shared__ __align__(16) unsigned char sd[sizeof(FusedArgs<T>)];
+  const int total = __ldg(base + nprob);
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = unit_problem(base, nprob, u);
+    p1_block<T, OP, R>(stage_desc(descs + p, sd), u - __ldg(base + p));
   }
 }
 
@@ -397,18 +448,29 @@ __device__ __forceinline__ T restrict_partial(const T* __restrict__ rf, const ui
   return acc;
 }
 
-// Blocks [0, nb_items) take coarse interface items, the rest coarse rows.
+// Restriction of one fine/coarse level pair (blocks [0, nb_items) take coarse
+// interface items, the rest coarse rows).
 template <typename T>
-__global__ void __launch_bounds__(kBlock) restrict_kernel(
-    int nf, int64_t fstride, int nc, int64_t cstride, const uint8_t* flags, const int4* items,
-    int n_items, int nb_items, const IfaceCopy* copies, int n_rows,
-    const T* __restrict__ RF, T* __restrict__ RC) {
+struct RestrictDesc {
+  int nf, nc;
+  int64_t fstride, cstride;
+  const uint8_t* flags;
+  const int4* items;
+  int n_items, nb_items;
+  const IfaceCopy* copies;
+  int n_rows;
+  const T* rf;
+  T* rc;
+};
+
+template <typename T>
+__device__ __forceinline__ void restrict_block(const RestrictDesc<T>& D, int blk) {
   const int lane = threadIdx.x & 31;
-  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int wc = nc + 1;
-  if ((int)blockIdx.x < nb_items) {
-    if (wg >= n_items) return;
-    const int4 it = items[wg];
+  const int wg = blk * kWarps + (threadIdx.x >> 5);
+  const int nf = D.nf, nc = D.nc, wc = nc + 1;
+  if (blk < D.nb_items) {
+    if (wg >= D.n_items) return;
+    const int4 it = D.items[wg];
     IfacePrim P;
     P.dim = it.z & 15;
     P.ncopies = (it.z >> 4) & 255;
@@ -417,30 +479,30 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(
     if (p >= prim_points(P.dim, nc)) return;
     int wts[3];
     prim_weights(P.dim, nc, p, wts);
-    const IfaceCopy* cp = copies + it.x;
+    const IfaceCopy* cp = D.copies + it.x;
     T v = T(0);
     if (!P.dirichlet) {
       for (int q = 0; q < P.ncopies; ++q) {
         int I, J, K;
         copy_local_ijk(cp[q], P.dim, wts, I, J, K);
-        v += restrict_partial<T>(RF + (int64_t)cp[q].cell * fstride, flags + cp[q].cell * 16, nf,
-                                 I, J, K);
+        v += restrict_partial<T>(D.rf + (int64_t)cp[q].cell * D.fstride, D.flags + cp[q].cell * 16,
+                                 nf, I, J, K);
       }
     }
     for (int q = 0; q < P.ncopies; ++q) {
       int I, J, K;
       copy_local_ijk(cp[q], P.dim, wts, I, J, K);
-      RC[(int64_t)cp[q].cell * cstride + tw32(wc, I, J, K)] = v;
+      D.rc[(int64_t)cp[q].cell * D.cstride + tw32(wc, I, J, K)] = v;
     }
     return;
   }
-  const int r = wg - nb_items * kWarps;
-  if (r >= n_rows) return;
+  const int r = wg - D.nb_items * kWarps;
+  if (r >= D.n_rows) return;
   int cell, J, K;
   row_item(wc, r, cell, J, K);
-  const T* rf = RF + (int64_t)cell * fstride;
-  T* rc = RC + (int64_t)cell * cstride;
-  const uint8_t* fl = flags + cell * 16;
+  const T* rf = D.rf + (int64_t)cell * D.fstride;
+  T* rc = D.rc + (int64_t)cell * D.cstride;
+  const uint8_t* fl = D.flags + cell * 16;
   const int r0 = row_start(wc, J, K);
   for (int I = lane; I + J + K <= nc; I += 32) {
     if (point_class(nc, I, J, K) != 0) continue;  // interface points: items above
@@ -448,22 +510,34 @@ __global__ void __launch_bounds__(kBlock) restrict_kernel(
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kBlock) restrict_kernel(RestrictDesc<T> D) {
+  restrict_block<T>(D, blockIdx.x);
+}
+
 // Prolongation x_f += P e_c: fine points with even coordinates copy the coarse
 // value; the others are midpoints of the coarse edge picked by the parity.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) prolong_kernel(int nf, int64_t fstride, int64_t cstride,
-                                                         const uint8_t* flags, int n_rows,
-                                                         const T* __restrict__ EC,
-                                                         T* __restrict__ XF) {
+struct ProlongDesc {
+  int nf;
+  int64_t fstride, cstride;
+  const uint8_t* flags;
+  int n_rows;
+  const T* ec;
+  T* xf;
+};
+
+template <typename T>
+__device__ __forceinline__ void prolong_block(const ProlongDesc<T>& D, int blk) {
   const int lane = threadIdx.x & 31;
-  const int r = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  const int wf = nf + 1, wc = nf / 2 + 1;
-  if (r >= n_rows) return;
+  const int r = blk * kWarps + (threadIdx.x >> 5);
+  const int nf = D.nf, wf = nf + 1, wc = nf / 2 + 1;
+  if (r >= D.n_rows) return;
   int cell, j, k;
   row_item(wf, r, cell, j, k);
-  const T* ec = EC + (int64_t)cell * cstride;
-  T* xf = XF + (int64_t)cell * fstride;
-  const uint8_t* fl = flags + cell * 16;
+  const T* ec = D.ec + (int64_t)cell * D.cstride;
+  T* xf = D.xf + (int64_t)cell * D.fstride;
+  const uint8_t* fl = D.flags + cell * 16;
   const int r0 = row_start(wf, j, k);
   for (int i = lane; i + j + k <= nf; i += 32) {
     if (fl[point_class(nf, i, j, k)] & CF_DIRICHLET) continue;
@@ -487,6 +561,33 @@ __global__ void __launch_bounds__(kBlock) prolong_kernel(int nf, int64_t fstride
       v = T(0.5) * (a + b);
     }
     xf[r0 + i] += v;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) prolong_kernel(ProlongDesc<T> D) {
+  prolong_block<T>(D, blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) restrict_batched_kernel(
+    const RestrictDesc<T>* __restrict__ descs, const int* __restrict__ base, int nprob) {
+  __shared__ __align__(16) unsigned char sd[sizeof(RestrictDesc<T>)];
+  const int total = __ldg(base + nprob);
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = unit_problem(base, nprob, u);
+    restrict_block<T>(stage_desc(descs + p, sd), u - __ldg(base + p));
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) prolong_batched_kernel(
+    const ProlongDesc<T>* __restrict__ descs, const int* __restrict__ base, int nprob) {
+  __shared__ __align__(16) unsigned char sd[sizeof(ProlongDesc<T>)];
+  const int total = __ldg(base + nprob);
+  for (int u = blockIdx.x; u < total; u += gridDim.x) {
+    const int p = unit_problem(base, nprob, u);
+    prolong_block<T>(stage_desc(descs + p, sd), u - __ldg(base + p));
   }
 }
 
@@ -596,14 +697,41 @@ int launch_from_canonical(const LevelDev& L, int dtype, const void* can, void* s
 }
 
 template <typename T>
+RestrictDesc<T> restrict_desc(const LevelDev& F, const LevelDev& C, const void* rf, void* rc) {
+  RestrictDesc<T> D;
+  D.nf = F.n;
+  D.nc = C.n;
+  D.fstride = F.cell_stride;
+  D.cstride = C.cell_stride;
+  D.flags = F.cls_flags;
+  D.items = C.items;
+  D.n_items = C.n_items;
+  D.nb_items = blocks_for_warps(C.n_items);
+  D.copies = C.copies;
+  D.n_rows = C.ncells * ntri32(C.w);
+  D.rf = (const T*)rf;
+  D.rc = (T*)rc;
+  return D;
+}
+
+template <typename T>
+ProlongDesc<T> prolong_desc(const LevelDev& F, const LevelDev& C, const void* ec, void* xf) {
+  ProlongDesc<T> D;
+  D.nf = F.n;
+  D.fstride = F.cell_stride;
+  D.cstride = C.cell_stride;
+  D.flags = F.cls_flags;
+  D.n_rows = F.ncells * ntri32(F.w);
+  D.ec = (const T*)ec;
+  D.xf = (T*)xf;
+  return D;
+}
+
+template <typename T>
 static int run_restrict(const LevelDev& F, const LevelDev& C, const void* rf, void* rc,
                         cudaStream_t s) {
-  const int n_rows = C.ncells * ntri32(C.w);
-  const int nb_items = blocks_for_warps(C.n_items);
-  const int grid = nb_items + blocks_for_warps(n_rows);
-  restrict_kernel<T><<<grid, kBlock, 0, s>>>(F.n, F.cell_stride, C.n, C.cell_stride, F.cls_flags,
-                                             C.items, C.n_items, nb_items, C.copies, n_rows,
-                                             (const T*)rf, (T*)rc);
+  const RestrictDesc<T> D = restrict_desc<T>(F, C, rf, rc);
+  restrict_kernel<T><<<D.nb_items + blocks_for_warps(D.n_rows), kBlock, 0, s>>>(D);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
@@ -616,14 +744,122 @@ int launch_restrict_p1(const LevelDev& F, const LevelDev& C, int dtype, const vo
 
 int launch_prolong_p1(const LevelDev& F, const LevelDev& C, int dtype, const void* ec, void* xf,
                       cudaStream_t s) {
-  const int n_rows = F.ncells * ntri32(F.w);
-  const int grid = blocks_for_warps(n_rows);
-  if (dtype == HG_F64)
-    prolong_kernel<double><<<grid, kBlock, 0, s>>>(F.n, F.cell_stride, C.cell_stride, F.cls_flags,
-                                                   n_rows, (const double*)ec, (double*)xf);
+  if (dtype == HG_F64) {
+    const ProlongDesc<double> D = prolong_desc<double>(F, C, ec, xf);
+    prolong_kernel<double><<<blocks_for_warps(D.n_rows), kBlock, 0, s>>>(D);
+  } else {
+    const ProlongDesc<float> D = prolong_desc<float>(F, C, ec, xf);
+    prolong_kernel<float><<<blocks_for_warps(D.n_rows), kBlock, 0, s>>>(D);
+  }
+  HG_CUDA(cudaGetLastError());
+  return HG_OK;
+}
+
+// ------------------------------------------------------ batched descriptors
+size_t p1_desc_bytes(int dtype) {
+  return dtype == HG_F64 ? sizeof(FusedArgs<double>) : sizeof(FusedArgs<float>);
+}
+
+int p1_make_desc(const LevelDev& L, int dtype, const StencilArgs& a, void* dst, int* units) {
+  const int n_items = (a.op == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_items_inner : L.n_items;
+  if (dtype == HG_F64) {
+    const FusedArgs<double> A = fused_args<double>(L, a, n_items);
+    memcpy(dst, &A, sizeof A);
+    *units = A.nb_items + (L.n_tiles + kWarps - 1) / kWarps;
+  } else {
+    const FusedArgs<float> A = fused_args<float>(L, a, n_items);
+    memcpy(dst, &A, sizeof A);
+    *units = A.nb_items + (L.n_tiles + kWarps - 1) / kWarps;
+  }
+  return HG_OK;
+}
+
+size_t restrict_desc_bytes(int dtype) {
+  return dtype == HG_F64 ? sizeof(RestrictDesc<double>) : sizeof(RestrictDesc<float>);
+}
+
+int restrict_make_desc(const LevelDev& F, const LevelDev& C, int dtype, const void* rf, void* rc,
+                       void* dst, int* units) {
+  if (dtype == HG_F64) {
+    const RestrictDesc<double> D = restrict_desc<double>(F, C, rf, rc);
+    memcpy(dst, &D, sizeof D);
+    *units = D.nb_items + blocks_for_warps(D.n_rows);
+  } else {
+    const RestrictDesc<float> D = restrict_desc<float>(F, C, rf, rc);
+    memcpy(dst, &D, sizeof D);
+    *units = D.nb_items + blocks_for_warps(D.n_rows);
+  }
+  return HG_OK;
+}
+
+size_t prolong_desc_bytes(int dtype) {
+  return dtype == HG_F64 ? sizeof(ProlongDesc<double>) : sizeof(ProlongDesc<float>);
+}
+
+int prolong_make_desc(const LevelDev& F, const LevelDev& C, int dtype, const void* ec, void* xf,
+                      void* dst, int* units) {
+  if (dtype == HG_F64) {
+    const ProlongDesc<double> D = prolong_desc<double>(F, C, ec, xf);
+    memcpy(dst, &D, sizeof D);
+    *units = blocks_for_warps(D.n_rows);
+  } else {
+    const ProlongDesc<float> D = prolong_desc<float>(F, C, ec, xf);
+    memcpy(dst, &D, sizeof D);
+    *units = blocks_for_warps(D.n_rows);
+  }
+  return HG_OK;
+}
+
+template <typename T, int OP>
+static void p1_batched_rows(int rows, const void* d, const int* base, int nprob, int grid,
+                            cudaStream_t s) {
+  const FusedArgs<T>* D = (const FusedArgs<T>*)d;
+  if (rows <= 2)
+    p1_batched_kernel<T, OP, 2><<<grid, kBlock, 0, s>>>(D, base, nprob);
+  else if (rows <= 4)
+    p1_batched_kernel<T, OP, 4><<<grid, kBlock, 0, s>>>(D, base, nprob);
   else
-    prolong_kernel<float><<<grid, kBlock, 0, s>>>(F.n, F.cell_stride, C.cell_stride, F.cls_flags,
-                                                  n_rows, (const float*)ec, (float*)xf);
+    p1_batched_kernel<T, OP, 8><<<grid, kBlock, 0, s>>>(D, base, nprob);
+}
+
+int launch_p1_batched(int dtype, int op, int rows, const void* descs, const int* base, int nprob,
+                      int grid, cudaStream_t s) {
+  if (nprob <= 0) return HG_OK;
+  if (dtype == HG_F64) {
+    if (op == OP_APPLY) p1_batched_rows<double, OP_APPLY>(rows, descs, base, nprob, grid, s);
+    else if (op == OP_RESID) p1_batched_rows<double, OP_RESID>(rows, descs, base, nprob, grid, s);
+    else p1_batched_rows<double, OP_JACOBI>(rows, descs, base, nprob, grid, s);
+  } else {
+    if (op == OP_APPLY) p1_batched_rows<float, OP_APPLY>(rows, descs, base, nprob, grid, s);
+    else if (op == OP_RESID) p1_batched_rows<float, OP_RESID>(rows, descs, base, nprob, grid, s);
+    else p1_batched_rows<float, OP_JACOBI>(rows, descs, base, nprob, grid, s);
+  }
+  HG_CUDA(cudaGetLastError());
+  return HG_OK;
+}
+
+int launch_restrict_batched(int dtype, const void* descs, const int* base, int nprob, int grid,
+                            cudaStream_t s) {
+  if (nprob <= 0) return HG_OK;
+  if (dtype == HG_F64)
+    restrict_batched_kernel<double><<<grid, kBlock, 0, s>>>((const RestrictDesc<double>*)descs,
+                                                            base, nprob);
+  else
+    restrict_batched_kernel<float><<<grid, kBlock, 0, s>>>((const RestrictDesc<float>*)descs,
+                                                           base, nprob);
+  HG_CUDA(cudaGetLastError());
+  return HG_OK;
+}
+
+int launch_prolong_batched(int dtype, const void* descs, const int* base, int nprob, int grid,
+                           cudaStream_t s) {
+  if (nprob <= 0) return HG_OK;
+  if (dtype == HG_F64)
+    prolong_batched_kernel<double><<<grid, kBlock, 0, s>>>((const ProlongDesc<double>*)descs,
+                                                           base, nprob);
+  else
+    prolong_batched_kernel<float><<<grid, kBlock, 0, s>>>((const ProlongDesc<float>*)descs, base,
+                                                          nprob);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
