@@ -160,6 +160,12 @@ int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
  * (Sec. 5.2: constant-coefficient stencils precomputed per macro primitive,
  * element matrices on the fly for variable coefficients). */
 int hg_op_create(const hg_hier* hier, int kind, const double* coeff, hg_op** out);
+
+/* The quadrature rule of the P2 element matrices: the symmetric 14-point,
+ * degree-5, positive-weight rule (orbits 4+4+6), derived by the library from
+ * its moment equations.  Host outputs: bary 14x4 barycentric coordinates,
+ * weights 14 (sum 1), *npoints = 14; any may be NULL.  Needs no GPU. */
+int hg_quadrature_rule(double* bary, double* weights, int* npoints);
 void hg_op_destroy(hg_op* op);
 
 /* y = A x (HG_REPLACE) or y += A x (HG_ADD) on one level; the ghost-layer
@@ -275,9 +281,9 @@ int hg_gmg_clone(const hg_gmg* src, hg_gmg** out);
  * their finest level.
  *   flags: HG_BATCH_GRAPH    capture the stage sequence as two CUDA graphs
  *                            (residual + norms; correction) and replay them,
- *          HG_BATCH_AUTOTUNE time the stage-kernel variants (register-window
- *                            rows 2/4/8 x 1/2/4 x 4 blocks per SM) at
- *                            creation and keep the fastest.
+ *          HG_BATCH_AUTOTUNE time the stage-kernel variants (plane-window
+ *                            prefetch depth 0/1/2 x 1/2/4 x 4 blocks per SM)
+ *                            at creation and keep the fastest.
  * Every problem needs its own hg_gmg (hg_gmg_clone) with the same
  * nu1/nu2/inner_cycles; a problem may not appear twice.  The batch holds
  * the problems' handles: destroy it before them. */
@@ -294,7 +300,7 @@ void hg_batch_destroy(hg_batch* batch);
  * (results still written), HG_ERR_INVALID_ARG. */
 int hg_batch_solve(hg_batch* batch, double rel_tol, int max_iter, int* iters, double* rel_res,
                    void* stream);
-/* The stage-kernel variant in use: register-window rows, blocks per SM / 4,
+/* The stage-kernel variant in use: plane-window prefetch depth, blocks per SM / 4,
  * and (after autotuning) the fastest finest-stage time in microseconds. */
 int hg_batch_tuning(const hg_batch* batch, int* rows, int* grid_factor, double* stage_us);
 

@@ -72,6 +72,7 @@ SIGNATURES = {
     "hg_gmg_set_learned": (_I, [_P, _P]),
     "hg_gmg_learned_fallbacks": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "hg_gmg_clone": (_I, [_P, ctypes.POINTER(_P)]),
+    "hg_quadrature_rule": (_I, [_P, _P, ctypes.POINTER(ctypes.c_int)]),
     "hg_batch_create": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(_P)]),
     "hg_batch_destroy": (None, [_P]),
     "hg_batch_solve": (_I, [_P, _D, _I, _P, _P, _P]),
@@ -444,6 +445,15 @@ def learn_samples(op, level, r, xstar, x, omega, stride, offset, stream=None):
     _call("hg_learn_samples", op._h, level, _ptr(r), _ptr(xstar), _ptr(x), omega, stride, offset,
           _ptr(X), _ptr(t), ctypes.byref(cnt), _stream(stream))
     return X, t
+
+
+def quadrature_rule():
+    """(bary (14,4), weights (14,)) of the library's P2 quadrature rule (host)."""
+    b = np.zeros((14, 4))
+    w = np.zeros(14)
+    n = ctypes.c_int()
+    _call("hg_quadrature_rule", b.ctypes.data_as(_P), w.ctypes.data_as(_P), ctypes.byref(n))
+    return b[:n.value], w[:n.value]
 
 
 def index_tw(w, i, j, k):

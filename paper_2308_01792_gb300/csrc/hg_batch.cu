@@ -54,20 +54,6 @@ __global__ void __launch_bounds__(kB) ew_batched_kernel(const EwDesc* __restrict
   }
 }
 
-// Row item r -> (cell, j, k) of a level's lattice (plane k has w-k rows).
-__device__ __forceinline__ void batch_row(int w, int r, int& cell, int& j, int& k) {
-  const int per = ntri32(w);
-  cell = r / per;
-  const int rr = r - cell * per;
-  const float q = 2.0f * w + 1.0f;
-  int kk = (int)floorf((q - sqrtf(fmaxf(q * q - 8.0f * rr, 0.0f))) * 0.5f);
-  if (kk < 0) kk = 0;
-  while ((kk + 1) * (2 * w - kk) / 2 <= rr) ++kk;
-  while (kk * (2 * w - kk + 1) / 2 > rr) --kk;
-  k = kk;
-  j = rr - kk * (2 * w - kk + 1) / 2;
-}
-
 // Unit u of problem p covers lattice rows [b*kDotRowsPerUnit, +kDotRowsPerUnit)
 // of that problem (b = u - base[p]), one warp per row in turn; each unit
 // writes one partial and a second kernel adds each problem's partials in
@@ -88,7 +74,7 @@ __global__ void __launch_bounds__(kB) dot_batched_kernel(const DotDesc* __restri
     double acc = 0.0;
     for (int r = r0 + warp; r < r1; r += kB / 32) {
       int cell, j, k;
-      batch_row(w, r, cell, j, k);
+      row_item(w, r, cell, j, k);
       const int64_t rs = (int64_t)cell * D.stride + row_start(w, j, k);
       const uint8_t* fl = D.flags + cell * 16;
       for (int i = lane; i + j + k <= D.n; i += 32) {

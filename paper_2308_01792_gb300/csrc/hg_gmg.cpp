@@ -33,7 +33,7 @@ struct Gmg {
   bool learned_active = false;
   int learned_fallbacks = 0;
 
-  const LevelDev& L(int l) const { return hier->lv[l - hier->lmin].dev; }
+  const LevelDev& L(int l) const { return op->dev(l); }
   size_t bytes(int l, int dt) const { return L(l).n_stored * (dt == HG_F64 ? 8 : 4); }
 
   int alloc_work(int dt) {
@@ -101,10 +101,14 @@ struct Gmg {
     if (int r = cell_op(l, dt, OP_RESID, x, b, res, s)) return r;
     void* bc = W(dt, WB, l - 1);
     void* xc = W(dt, WX, l - 1);
-    if (int r = launch_restrict_p1(L(l), L(l - 1), dt, res, bc, s)) return r;
+    if (int r = op->space == HG_SPACE_P2 ? launch_restrict_p2(L(l), L(l - 1), dt, res, bc, s)
+                                         : launch_restrict_p1(L(l), L(l - 1), dt, res, bc, s))
+      return r;
     HG_CUDA(cudaMemsetAsync(xc, 0, bytes(l - 1, dt), s));
     if (int r = vcycle(l - 1, dt, xc, bc, s)) return r;
-    if (int r = launch_prolong_p1(L(l), L(l - 1), dt, xc, x, s)) return r;
+    if (int r = op->space == HG_SPACE_P2 ? launch_prolong_p2(L(l), L(l - 1), dt, xc, x, s)
+                                         : launch_prolong_p1(L(l), L(l - 1), dt, xc, x, s))
+      return r;
     return smooth(l, dt, x, b, prm.nu2, s);
   }
 
@@ -118,7 +122,7 @@ struct Gmg {
 // Cholesky factorisation and the explicit inverse (the coarse problem has at
 // most a few thousand unknowns).
 int Gmg::build_coarse() {
-  const LevelHost& H = hier->lv[lmin - hier->lmin];
+  const LevelHost& H = op->host(lmin);
   const LevelDev& Lc = H.dev;
   if (!hier->mesh->grid_denom) {
     set_error("the coarse solver needs vertex coordinates on an exact lattice");
@@ -318,11 +322,11 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
   } else {
     hg_gmg_default_params(&g->prm);
   }
-  const Hier* h = op->hier;
-  g->lmax = h->lmax;
-  g->lmin = g->prm.lmin < 0 ? h->lmin : g->prm.lmin;
-  if (g->lmin < h->lmin || g->lmin > h->lmax) {
-    set_error("coarsest level %d outside the hierarchy %d..%d", g->lmin, h->lmin, h->lmax);
+  g->lmax = op->lmax;
+  g->lmin = g->prm.lmin < 0 ? op->lmin : g->prm.lmin;
+  if (g->lmin < op->lmin || g->lmin > op->lmax) {
+    set_error("coarsest level %d outside the operator's levels %d..%d", g->lmin, op->lmin,
+              op->lmax);
     return HG_ERR_LEVEL_RANGE;
   }
   if (g->prm.nu1 < 0 || g->prm.nu2 < 0 || !(g->prm.omega > 0.0)) {
@@ -384,7 +388,7 @@ int hg_gmg_set_learned(hg_gmg* g, const hg_mlp* mlp) {
     set_error("hg_gmg_set_learned: null handle");
     return HG_ERR_INVALID_ARG;
   }
-  if (mlp && g->op->vinv[HG_F32].empty()) {
+  if (mlp && (g->op->space != HG_SPACE_P1 || g->op->vinv[HG_F32].empty())) {
     set_error("learned smoothing needs the operator's stored diagonal (exact lattice)");
     return HG_ERR_UNSUPPORTED;
   }
@@ -422,7 +426,7 @@ int hg_gmg_history(const hg_gmg* g, double* out, int cap, int* n) {
 // all problems that take part in it.  V-cycles of problems with different
 // depths are aligned by the distance from their finest level.  The stage
 // sequence is captured once as two CUDA graphs (residual + norms, correction)
-// and replayed; an autotuner picks the register-window rows and the
+// and replayed; an autotuner picks the plane-window prefetch depth and the
 // persistent grid size of the cell stages.
 namespace hg {
 
@@ -448,7 +452,7 @@ struct Batch {
   double *rr_host = nullptr, *rs_host = nullptr;
   std::vector<double> nbh;
   double tune_us = 0.0;
-  int rows = 8, gfac = 2, sms = 152;
+  int rows = 1, gfac = 2, sms = 152;
   cudaStream_t cs = nullptr;
   cudaGraphExec_t e1 = nullptr, e2 = nullptr;
 
@@ -800,7 +804,7 @@ int Batch::autotune(double* best_us) {
   HG_CUDA(cudaEventCreate(&z));
   double best = 1e30;
   int br = rows, bg = gfac;
-  for (int R : {2, 4, 8})
+  for (int R : {0, 1, 2})
     for (int gf : {1, 2, 4}) {
       rows = R;
       gfac = gf;

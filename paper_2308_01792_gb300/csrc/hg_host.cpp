@@ -210,9 +210,10 @@ int Hier::build_level(int l) {
   L.n = 1 << l;
   L.w = L.n + 1;
   L.ncells = (int)mesh->nc;
-  // padded to 32 elements with at least 4 spare: 16-byte staging copies may read
-  // up to 12 bytes past the last element they need
-  L.cell_stride = (ntet(L.w) + 4 + 31) / 32 * 32;
+  // padded to a multiple of 32 elements with at least 32 spare: the interior
+  // tiles' window loads of lanes past a row's end reach up to 25 elements
+  // beyond the cell's last lattice point
+  L.cell_stride = (ntet(L.w) + 32 + 31) / 32 * 32;
   L.n_stored = L.cell_stride * mesh->nc;
   const int n = L.n, w = L.w;
   // class flags
@@ -273,6 +274,37 @@ int Hier::build_level(int l) {
   L.n_items = (int)items.size();
   if (int r = upload(&L.items, items)) return r;
   if (int r = upload(&L.item_prim, item_prim)) return r;
+  // apply items: floor(32 / ncopies) points of one primitive, one lane per
+  // (point, copy); primitives with more than 32 copies keep 32 points per item
+  // (one lane per point)
+  std::vector<int4> citems;
+  for (int q = 0; q < (int)prims.size(); ++q) {
+    const IfacePrim& P = prims[q];
+    const int meta = P.dim | (P.ncopies << 4) | (P.dirichlet << 12);
+    const int per = P.ncopies <= 32 ? 32 / P.ncopies : 32;
+    const int np = prim_points(P.dim, n);
+    for (int p0 = 0; p0 < np; p0 += per) citems.push_back({P.first_copy, p0, meta, std::min(per, np - p0)});
+    if (q + 1 == L.n_prims_inner) L.n_citems_inner = (int)citems.size();
+  }
+  L.n_citems = (int)citems.size();
+  if (int r = upload(&L.citems, citems)) return r;
+  // plane-window tiles: in plane k (1..n-3) the interior points lie in the
+  // cell-local offset range [rs(1,k)+1, rs(n-k-2,k)+1]; a window covers 30
+  // consecutive offsets (lanes 1..30, halo lanes 0 and 31), a tile up to
+  // kPlaneSteps windows; (j0, i0) is the lattice row/column of lane 0's offset
+  std::vector<int4> ptiles;
+  for (int k = 1; k <= n - 3; ++k) {
+    const int ga = (int)row_start(w, 1, k) + 1, gb = (int)row_start(w, n - k - 2, k) + 1;
+    const int nwin = (gb - ga + 1 + 29) / 30;
+    for (int t0 = 0; t0 < nwin; t0 += kPlaneSteps) {
+      const int z = ga - 1 + 30 * t0;
+      int j = 0, r = z - (int)row_start(w, 0, k), len = w - k;
+      while (r >= len) { r -= len; --len; ++j; }
+      ptiles.push_back({k | (std::min(kPlaneSteps, nwin - t0) << 16), z, (j << 16) | r, 0});
+    }
+  }
+  L.n_ptiles_cell = (int)ptiles.size();
+  if (int r = upload(&L.ptiles, ptiles)) return r;
   // interior tiles: plane k, 30 outputs i0..i0+29, rows j0..j1-1 of at most
   // kTileRows (interior points 1 <= i,j,k and i+j+k <= n-1)
   std::vector<int4> tiles;
@@ -354,6 +386,7 @@ int Hier::build_level(int l) {
   // every table a kernel reads must be on the device
   if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
       (L.n_items && (!L.items || !L.item_prim)) || (L.n_tiles && !L.tiles) ||
+      (L.n_citems && !L.citems) || (L.n_ptiles_cell && !L.ptiles) ||
       (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
     set_error("internal: level %d device tables incomplete", l);
     return HG_ERR_CUDA;
@@ -406,6 +439,8 @@ Hier::~Hier() {
     cudaFree(L.copies);
     cudaFree(L.prim_point_base);
     cudaFree(L.tiles);
+    cudaFree(L.citems);
+    cudaFree(L.ptiles);
     cudaFree(L.items);
     cudaFree(L.item_prim);
   }
@@ -524,9 +559,20 @@ void p1_cell_stencils(const Mesh& m, int64_t c, int n, int kind, double S[16][16
   }
 }
 
+int lattice_index(const Hier* h, int space, int level) {
+  const int lat = space == HG_SPACE_P2 ? level + 1 : level;
+  if (space != HG_SPACE_P1 && space != HG_SPACE_P2) return -1;
+  if (level < 0 || lat < h->lmin || lat > h->lmax) return -1;
+  return lat - h->lmin;
+}
+
 int Op::build(const Hier* h, int kind_, const double* coeff) {
   hier = h;
   kind = kind_;
+  lmin = h->lmin;
+  lmax = h->lmax;
+  if (kind == HG_OP_P2_LAPLACE || kind == HG_OP_P2_MASS || kind == HG_OP_P2_DIVKGRAD)
+    return build_p2(coeff);
   if (kind == HG_OP_P1_DIVKGRAD) return build_divkgrad(coeff);
   if (kind != HG_OP_P1_LAPLACE && kind != HG_OP_P1_MASS) {
     set_error("operator kind %d not available in this build", kind);
@@ -676,6 +722,19 @@ int Op::build_divkgrad(const double* coeff) {
 }
 
 int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
+  if (space == HG_SPACE_P2) {
+    const int li = level - lmin;
+    P2Args P;
+    P.n = 1 << level;
+    P.ncells = (int)hier->mesh->nc;
+    P.cells = p2cells[dtype][li];
+    P.anchors = p2anchors[li];
+    for (int c = 0; c < 9; ++c) P.anchor_off[c] = p2off[li][c];
+    P.mode = p2mode;
+    P.acc = p2acc[dtype][li];
+    P.invdiag = p2inv[dtype][li];
+    return launch_p2(dev(level), dtype, a, P, s);
+  }
   const int li = level - hier->lmin;
   const LevelDev& L = hier->lv[li].dev;
   if (kind == HG_OP_P1_DIVKGRAD) {
@@ -687,6 +746,10 @@ int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
 }
 
 Op::~Op() {
+  for (int dt = 0; dt < 2; ++dt)
+    for (auto* v : {&p2cells[dt], &p2acc[dt], &p2inv[dt]})
+      for (void* p : *v) cudaFree(p);
+  for (auto p : p2anchors) cudaFree(p);
   for (auto p : sten64) cudaFree(p);
   for (auto p : sten32) cudaFree(p);
   for (int dt = 0; dt < 2; ++dt)
@@ -754,10 +817,12 @@ void hg_hier_destroy(hg_hier* h) { delete h; }
 int hg_function_size(const hg_hier* h, int space, int level, int64_t* n_stored,
                      int64_t* n_unique, int64_t* n_inner, int64_t* cell_stride) {
   HG_CHECK(h, HG_ERR_INVALID_ARG, "hg_function_size: null hierarchy");
-  HG_CHECK(space == HG_SPACE_P1, HG_ERR_UNSUPPORTED, "space %d not available", space);
-  HG_CHECK(level >= h->lmin && level <= h->lmax, HG_ERR_LEVEL_RANGE, "level %d outside %d..%d",
-           level, h->lmin, h->lmax);
-  const LevelDev& L = h->lv[level - h->lmin].dev;
+  HG_CHECK(space == HG_SPACE_P1 || space == HG_SPACE_P2, HG_ERR_UNSUPPORTED,
+           "space %d not available", space);
+  const int li = lattice_index(h, space, level);
+  HG_CHECK(li >= 0, HG_ERR_LEVEL_RANGE, "level %d of space %d outside the hierarchy %d..%d",
+           level, space, h->lmin, h->lmax);
+  const LevelDev& L = h->lv[li].dev;
   if (n_stored) *n_stored = L.n_stored;
   if (n_unique) *n_unique = L.n_unique;
   if (n_inner) *n_inner = L.n_inner;
@@ -768,11 +833,13 @@ int hg_function_size(const hg_hier* h, int space, int level, int64_t* n_stored,
 int hg_canonical_info(const hg_hier* h, int space, int level, int64_t* s2c, double* xyz,
                       uint8_t* dirichlet) {
   HG_CHECK(h, HG_ERR_INVALID_ARG, "hg_canonical_info: null hierarchy");
-  HG_CHECK(space == HG_SPACE_P1, HG_ERR_UNSUPPORTED, "space %d not available", space);
-  HG_CHECK(level >= h->lmin && level <= h->lmax, HG_ERR_LEVEL_RANGE, "level out of range");
+  HG_CHECK(space == HG_SPACE_P1 || space == HG_SPACE_P2, HG_ERR_UNSUPPORTED,
+           "space %d not available", space);
+  const int li = lattice_index(h, space, level);
+  HG_CHECK(li >= 0, HG_ERR_LEVEL_RANGE, "level out of range");
   HG_CHECK(h->mesh->grid_denom, HG_ERR_UNSUPPORTED,
            "canonical order needs vertex coordinates on a lattice of spacing 1/D, D <= 64");
-  const LevelHost& H = h->lv[level - h->lmin];
+  const LevelHost& H = h->lv[li];
   if (s2c)
     for (size_t q = 0; q < H.canon.size(); ++q) s2c[q] = H.canon[q];
   if (xyz) std::copy(H.canon_xyz.begin(), H.canon_xyz.end(), xyz);
@@ -785,15 +852,17 @@ static const LevelDev* level_of(const Hier* h, int space, int level) {
     set_error("null hierarchy");
     return nullptr;
   }
-  if (space != HG_SPACE_P1) {
+  if (space != HG_SPACE_P1 && space != HG_SPACE_P2) {
     set_error("space %d not available", space);
     return nullptr;
   }
-  if (level < h->lmin || level > h->lmax) {
-    set_error("level %d outside %d..%d", level, h->lmin, h->lmax);
+  const int li = lattice_index(h, space, level);
+  if (li < 0) {
+    set_error("level %d of space %d outside the hierarchy %d..%d", level, space, h->lmin,
+              h->lmax);
     return nullptr;
   }
-  return &h->lv[level - h->lmin].dev;
+  return &h->lv[li].dev;
 }
 
 int hg_to_canonical(const hg_hier* h, int space, int level, int dtype, const void* st,
@@ -860,8 +929,8 @@ void hg_op_destroy(hg_op* op) { delete op; }
 
 static int run_cell_op(const hg_op* op, int level, int dtype, StencilArgs a, cudaStream_t s) {
   HG_CHECK(op, HG_ERR_INVALID_ARG, "null operator");
-  const LevelDev* L = level_of(op->hier, HG_SPACE_P1, level);
-  if (!L) return HG_ERR_LEVEL_RANGE;
+  const LevelDev* L = level_of(op->hier, op->space, level);
+  if (!L || level < op->lmin || level > op->lmax) return HG_ERR_LEVEL_RANGE;
   HG_CHECK(dtype == HG_F32 || dtype == HG_F64, HG_ERR_INVALID_ARG, "bad dtype %d", dtype);
   HG_CHECK(a.x && a.out && a.x != a.out, HG_ERR_INVALID_ARG,
            "input and output must be distinct non-null device pointers");
@@ -914,6 +983,7 @@ int hg_restrict(const hg_hier* h, int space, int fine_level, int dtype, const vo
   const LevelDev* C = level_of(h, space, fine_level - 1);
   if (!F || !C) return HG_ERR_LEVEL_RANGE;
   HG_CHECK(rf && rc && rf != rc, HG_ERR_INVALID_ARG, "hg_restrict: bad pointers");
+  if (space == HG_SPACE_P2) return launch_restrict_p2(*F, *C, dtype, rf, rc, (cudaStream_t)stream);
   return launch_restrict_p1(*F, *C, dtype, rf, rc, (cudaStream_t)stream);
 }
 
@@ -923,6 +993,7 @@ int hg_prolong_add(const hg_hier* h, int space, int fine_level, int dtype, const
   const LevelDev* C = level_of(h, space, fine_level - 1);
   if (!F || !C) return HG_ERR_LEVEL_RANGE;
   HG_CHECK(ec && xf && ec != xf, HG_ERR_INVALID_ARG, "hg_prolong_add: bad pointers");
+  if (space == HG_SPACE_P2) return launch_prolong_p2(*F, *C, dtype, ec, xf, (cudaStream_t)stream);
   return launch_prolong_p1(*F, *C, dtype, ec, xf, (cudaStream_t)stream);
 }
 

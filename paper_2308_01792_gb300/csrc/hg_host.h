@@ -71,9 +71,24 @@ struct Hier {
   ~Hier();
 };
 
+// Index into Hier::lv of the lattice that stores `space` on `level` (P2 on
+// level l uses the lattice of level l+1), or -1 if the hierarchy lacks it.
+int lattice_index(const Hier* h, int space, int level);
+
 struct Op {
   const Hier* hier = nullptr;
   int kind = 0;
+  int space = HG_SPACE_P1;
+  int lmin = 0, lmax = 0;       // levels of the operator's space
+  // P2 (per P2 level): element data per cell (P2Cell<T>), anchors by colour,
+  // accumulation vector and inverse assembled diagonal per dtype
+  std::vector<void*> p2cells[2], p2acc[2], p2inv[2];
+  std::vector<uint32_t*> p2anchors;
+  std::vector<std::vector<int>> p2off;
+  int p2mode = 0;
+  const LevelHost& host(int l) const { return hier->lv[lattice_index(hier, space, l)]; }
+  const LevelDev& dev(int l) const { return host(l).dev; }
+  int build_p2(const double* coeff);
   std::vector<double*> sten64;  // per level [ncells][16][16] (constant-coefficient kinds)
   std::vector<float*> sten32;
   // variable-coefficient P1 (per level): k at stored vertices, element rows, 1/diag
@@ -103,6 +118,9 @@ struct Mlp {
 };
 
 void micro_cell_coords(const Mesh& m, int64_t c, int n, int type, double X[4][3]);
+// Symmetric 14-point degree-5 rule on the tetrahedron (barycentric points,
+// weights summing to 1), derived once from its moment equations.
+int sym14_rule(double bary[14][4], double w[14]);
 void bary_gradients(const double X[4][3], double G[4][3], double* vol);
 void p1_cell_stencils(const Mesh& m, int64_t c, int n, int kind, double S[16][16]);
 

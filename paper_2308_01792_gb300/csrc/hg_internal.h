@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 
 #include <string>
@@ -55,6 +56,22 @@ inline void dir_offset(int d, int& di, int& dj, int& dk) {
 
 // Boundary class of a cell-local point: bit0 on face opposite v0
 // (i+j+k = n), bit1 on i = 0 (opposite v1), bit2 on j = 0, bit3 on k = 0.
+// Row item r -> (cell, j, k) of a lattice with w points per macro edge
+// (cells of ntri(w) rows each; plane k has w-k rows).
+HG_HD void row_item(int w, int r, int& cell, int& j, int& k) {
+  const int per = (int)ntri(w);
+  cell = r / per;
+  const int rr = r - cell * per;
+  const float q = 2.0f * w + 1.0f;
+  const float disc = q * q - 8.0f * rr;
+  int kk = (int)floorf((q - sqrtf(disc > 0.0f ? disc : 0.0f)) * 0.5f);
+  if (kk < 0) kk = 0;
+  while ((kk + 1) * (2 * w - kk) / 2 <= rr) ++kk;
+  while (kk * (2 * w - kk + 1) / 2 > rr) --kk;
+  k = kk;
+  j = rr - kk * (2 * w - kk + 1) / 2;
+}
+
 HG_HD int point_class(int n, int i, int j, int k) {
   return (i + j + k == n ? 1 : 0) | (i == 0 ? 2 : 0) | (j == 0 ? 4 : 0) | (k == 0 ? 8 : 0);
 }
@@ -129,10 +146,18 @@ struct LevelDev {
   int4* items;               // interface items (first_copy, p0, dim|ncopies<<4|dirichlet<<12, 0),
   int32_t* item_prim;        //   32 consecutive points of one primitive; item -> primitive
   int n_items, n_items_inner;
+  // operator-application work items
+  int4* citems;              // interface items of the apply: (first_copy, p0, meta as above,
+  int n_citems, n_citems_inner;  //   points); points = floor(32 / ncopies), one lane per copy
+  int4* ptiles;              // plane-window tiles of ONE cell (the same for every cell):
+  int n_ptiles_cell;         //   (k | windows << 16, lane-0 offset z, j0 << 16 | i0, 0)
 };
 
-// Output rows per interior tile of the fused apply kernel.
+// Output rows per interior tile of the variable-coefficient kernel.
 constexpr int kTileRows = 8;
+// Windows of 30 consecutive lattice offsets per plane-window tile of the
+// constant-stencil kernels.
+constexpr int kPlaneSteps = 16;
 
 // Dense FP64 coarse-grid solver data.
 struct CoarseDev {
@@ -166,6 +191,58 @@ struct StencilArgs {
 };
 
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);
+
+// ------------------------------------------------------------------- P2
+// A P2 function on level l (vertex and edge DoFs of the level-l micro-cells)
+// is stored on the vertex lattice of level l+1: the micro-vertices are the
+// even points of the doubled lattice and every other point is the midpoint
+// of exactly one level-l micro-edge.  The level-(l+1) P1 tables (copies,
+// interface items, canonical keys, Dirichlet flags) therefore serve P2.
+//
+// Element data of one macro cell on one P2 level for the element-wise
+// kernels: the element matrix of a micro-cell of type t is
+//   K = sum_q kq C_q H_t C_q^T,  kq = w_q |T| k(x_q),
+// with C_q the P2 gradient coefficients at quadrature point q (functions of
+// its barycentric coordinates only) and H_t = G G^T of the type's
+// barycentric gradients.  k(x) = a + b sin(2 pi x) sin(2 pi y) sin(2 pi z)
+// is evaluated separably: x_q = x_p + d_{t,q} (anchor position x_p), so
+// sin(2 pi x_q) = sin(2 pi x_p) cos(2 pi d) + cos(2 pi x_p) sin(2 pi d).
+template <typename T>
+struct P2Cell {
+  T H[6][10];        // G G^T per type: 00 01 02 03 11 12 13 22 23 33
+  T kA[14], kB[14];  // w_q |T| a, w_q |T| b
+  T sc[6][14][6];    // per type and point: sin, cos of 2 pi d per axis
+  T x0[3];           // anchor (i,j,k) sits at x0 + i e[0] + j e[1] + k e[2]
+  T e[3][3];
+  T vol;             // micro-cell volume (mass element matrix = vol * M_ref)
+  T pad;
+};
+enum { P2_STIFF = 0, P2_MASS = 1, P2_DIAG = 2 };
+// Apply of one P2 level: 8 colour phases accumulate the element products
+// into acc (zeroed first), a finish pass sums interface copies and forms the
+// operation (apply / residual / Jacobi with invdiag / 1 / diagonal).
+struct P2Args {
+  int n;                     // micro-intervals per macro edge on the P2 level
+  int ncells;
+  const void* cells;         // P2Cell<T>[ncells]
+  const uint32_t* anchors;   // device: packed (i | j << 10 | k << 20) per colour, concatenated
+  int anchor_off[9];         // host: colour offsets into anchors
+  int mode;                  // P2_STIFF / P2_MASS
+  void* acc;                 // work vector of the level (stored layout)
+  const void* invdiag;
+};
+constexpr int OP_INVDIAG = 4;  // finish pass writing 1 / (assembled diagonal)
+int p2_upload_constants(const double qbary[14][4], const double qw[14], const double mass[10][10]);
+int launch_p2(const LevelDev& L, int dtype, const StencilArgs& a, const P2Args& P, cudaStream_t s);
+int launch_p2_diag(const LevelDev& L, int dtype, const P2Args& P, void* invdiag, cudaStream_t s);
+// P2 transfers between P2 levels l-1 and l, given the lattices F (level l+1)
+// and C (level l) that store them: x_f += P e_c (quadratic interpolation) and
+// r_c = P^T r_f.
+int launch_prolong_p2(const LevelDev& F, const LevelDev& C, int dtype, const void* ec, void* xf,
+                      cudaStream_t s);
+int launch_restrict_p2(const LevelDev& F, const LevelDev& C, int dtype, const void* rf, void* rc,
+                       cudaStream_t s);
+
 
 // Variable-coefficient P1 operator data of one level and dtype.
 struct VarCoef {

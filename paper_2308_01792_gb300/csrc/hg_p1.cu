@@ -7,18 +7,24 @@
 // An operator application (Sec. 5.2 apply(), stencil-based pattern with
 // constant stencils precomputed per macro cell) is ONE launch of warp-sized
 // work items of two kinds:
-//  * interface items (first in the grid): one lane per point of a macro
-//    face/edge/vertex (the ghost-layer exchange of Sec. 2 as an on-device
-//    gather).  The lane sums the per-cell partial stencils of every copy, in
-//    ascending cell order, straight from x (all 30 weights and values of a
-//    copy are loaded before the sum), and writes the sum to every copy, so
-//    copies stay bit-identical and no second pass is needed;
-//  * interior tiles: a warp owns lanes i = i0-1 .. i0+30 (30 outputs, one
-//    halo lane each side) of one plane k of one macro cell and kTileRows rows
-//    j0..; it first issues every row load the 15-point stencil needs (plane k
-//    rows j0-1..j0+R, plane k+1 rows j0-1..j0+R-1, plane k-1 rows j0..j0+R:
-//    3R+4 coalesced loads in flight at once), then forms the R output rows
-//    from registers, with warp shuffles for the i+-1 neighbours.
+//  * interface items (first in the grid): points of a macro face/edge/vertex
+//    (the ghost-layer exchange of Sec. 2 as an on-device gather).  Each lane
+//    takes one (point, copy) pair, floor(32 / copies) points per item, and
+//    loads its copy's partial stencil; the partials of a point are summed in
+//    ascending cell order by lane exchanges and the sum is written to every
+//    copy, so copies stay bit-identical and no second pass is needed;
+//  * plane-window tiles: rows are contiguous in t_w order, so the points of
+//    plane k form one run of offsets, and the i-1 / i+1 neighbours of an
+//    interior point are the offsets g-1 / g+1 even where a window spans
+//    several rows.  A warp takes 32 consecutive offsets (outputs at lanes
+//    1..30) of one plane; relative to g, the other neighbour rows sit at
+//    +len, -(len+1) (rows j+-1), +T(w-k-1)+len, +T(w-k-1) (plane k+1, rows
+//    j, j-1), -(T(w-k)+len+1), -T(w-k) (plane k-1, rows j, j+1), with len the
+//    lane's row length: seven coalesced loads per window, shuffles for the
+//    shifted neighbours, no lanes lost to short rows beyond the halo lanes
+//    and the boundary points.  A tile is a strip of up to kPlaneSteps
+//    windows, software-pipelined: the next windows' loads are in flight
+//    while one window is computed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -39,9 +45,10 @@ struct FusedArgs {
   int n, w;
   int64_t stride;
   const uint8_t* flags;
-  const int4* tiles;  // interior tiles (cell, k, i0, j0 | j1 << 16)
-  int n_tiles;
-  const int4* items;  // interface items (first_copy, p0, dim | ncopies<<4 | dirichlet<<12, -)
+  const int4* tiles;  // plane-window tiles of one cell (same for every cell)
+  int n_tiles_cell;
+  int n_tiles;        // all cells
+  const int4* items;  // apply items (first_copy, p0, dim | ncopies<<4 | dirichlet<<12, points)
   int n_items;
   int nb_items;       // blocks holding interface items (first in the grid)
   const IfacePrim* prims;
@@ -110,21 +117,26 @@ __device__ __forceinline__ void cell_partial_load(const T* __restrict__ x, const
   }
 }
 
+// 15-term dot in three independent chains (plane k, k+1, k-1 terms) for
+// instruction-level parallelism; the order is fixed, so every caller with the
+// same operands gets the same bits.
 template <typename T>
 __device__ __forceinline__ T dot15(const T sv[kNDir], const T xv[kNDir]) {
-  T acc = T(0);
-#pragma unroll
-  for (int d = 0; d < kNDir; ++d) acc += sv[d] * xv[d];
-  return acc;
+  const T a0 = sv[0] * xv[0] + sv[1] * xv[1] + sv[2] * xv[2] + sv[3] * xv[3] + sv[4] * xv[4] +
+               sv[7] * xv[7] + sv[8] * xv[8];
+  const T a1 = sv[5] * xv[5] + sv[9] * xv[9] + sv[11] * xv[11] + sv[13] * xv[13];
+  const T a2 = sv[6] * xv[6] + sv[10] * xv[10] + sv[12] * xv[12] + sv[14] * xv[14];
+  return a0 + (a1 + a2);
 }
 
+// Item of a primitive with more than 32 copies: one lane per point, copies
+// in turn.
 template <typename T, int OP>
-__device__ void interface_point(const FusedArgs<T>& A, int item, int lane) {
-  const int4 it = A.items[item];
+__device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, int lane) {
   const int dim = it.z & 15, ncopies = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
   const int n = A.n, w = A.w;
   const int p = it.y + lane;
-  if (p >= prim_points(dim, n)) return;
+  if (lane >= it.w) return;
   int wts[3];
   prim_weights(dim, n, p, wts);
   const IfaceCopy* cp = A.copies + it.x;
@@ -165,87 +177,178 @@ __device__ void interface_point(const FusedArgs<T>& A, int item, int lane) {
   }
 }
 
-// Interior tile (see the file comment).  Row starts move by row lengths:
-// rs(j+1,k) = rs(j,k) + (w-k-j).
-template <typename T, int OP, int R>
-__device__ void interior_tile_rows(const FusedArgs<T>& A, int cell, int k, int i0, int j0, int nr,
-                                   int lane) {
-  const int w = A.w;
-  const int64_t base = (int64_t)cell * A.stride;
-  const T* __restrict__ x = A.x + base;
-  T* __restrict__ y = A.y + base;
-  const T* __restrict__ S = A.sten + (int64_t)cell * 256;
-  const int i = i0 - 1 + lane;
-  const int lk = w - k, lkp = w - k - 1, lkm = w - k + 1;  // row length = l - j
-  T K[R + 2], Kp[R + 1], Km[R + 1];
-  {
-    int r = row_start(w, j0 - 1, k);
-#pragma unroll
-    for (int q = 0; q < R + 2; ++q) {
-      const int len = lk - (j0 - 1 + q);
-      K[q] = (q < nr + 2 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
-      r += len;
+// Apply item: lane = pt * C + c takes copy c of point pt (C copies, C <= 32).
+template <typename T, int OP>
+__device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
+  const int4 it = A.items[item];
+  const int dim = it.z & 15, C = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
+  if (C > 32) {
+    interface_point_serial<T, OP>(A, it, lane);
+    return;
+  }
+  const int n = A.n, w = A.w;
+  const int pt = lane / C, c = lane - pt * C;
+  const bool act = pt < it.w;
+  int wts[3];
+  prim_weights(dim, n, it.y + (act ? pt : 0), wts);
+  const IfaceCopy cpy = A.copies[it.x + (act ? c : 0)];
+  int i, j, k;
+  copy_local_ijk(cpy, dim, wts, i, j, k);
+  const int64_t cbase = (int64_t)cpy.cell * A.stride;
+  const int64_t g = cbase + tw32(w, i, j, k);
+  T v;
+  if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
+    v = OP == OP_JACOBI ? A.x[g] : T(0);
+  } else {
+    T sv[kNDir], xv[kNDir];
+    cell_partial_load<T>(A.x + cbase, A.sten + (int64_t)cpy.cell * 256 + point_class(n, i, j, k) * 16,
+                         n, w, i, j, k, sv, xv);
+    const T part = dot15<T>(sv, xv);
+    // partials of the point's C lanes, ascending copy (= cell) order
+    T sum = T(0), diag = T(0);
+    const int g0 = pt * C;
+    for (int q = 0; q < C; ++q) {
+      sum += __shfl_sync(0xffffffffu, part, (g0 + q) & 31);
+      if (OP == OP_JACOBI) diag += __shfl_sync(0xffffffffu, sv[0], (g0 + q) & 31);
     }
-    r = row_start(w, j0 - 1, k + 1);
-#pragma unroll
-    for (int q = 0; q < R + 1; ++q) {
-      const int len = lkp - (j0 - 1 + q);
-      Kp[q] = (q < nr + 1 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
-      r += len;
-    }
-    r = row_start(w, j0, k - 1);
-#pragma unroll
-    for (int q = 0; q < R + 1; ++q) {
-      const int len = lkm - (j0 + q);
-      Km[q] = (q < nr + 1 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
-      r += len;
+    if (OP == OP_APPLY) {
+      v = A.mode == HG_ADD ? A.y[g] + sum : sum;
+    } else if (OP == OP_RESID) {
+      v = A.b[g] - sum;
+    } else {
+      v = A.x[g] + A.omega * (A.b[g] - sum) / diag;
     }
   }
-  T s[kNDir];
-#pragma unroll
-  for (int d = 0; d < kNDir; ++d) s[d] = __ldg(S + d);
-  const T wd = OP == OP_JACOBI ? A.omega / s[0] : T(0);
-  const bool out_lane = lane >= 1 && lane <= 30;
-  int ry = row_start(w, j0, k);
-#pragma unroll
-  for (int q = 0; q < R; ++q) {
-    if (q < nr) {
-      const int j = j0 + q;
-      const T c = K[q + 1], up = K[q + 2], dn = K[q];
-      const T cm = __shfl_up_sync(0xffffffffu, c, 1), cp = __shfl_down_sync(0xffffffffu, c, 1);
-      const T upm = __shfl_up_sync(0xffffffffu, up, 1);
-      const T dnp = __shfl_down_sync(0xffffffffu, dn, 1);
-      const T p1c = Kp[q + 1], p1m = Kp[q];
-      const T p1cm = __shfl_up_sync(0xffffffffu, p1c, 1);
-      const T p1mp = __shfl_down_sync(0xffffffffu, p1m, 1);
-      const T m1c = Km[q], m1p = Km[q + 1];
-      const T m1cp = __shfl_down_sync(0xffffffffu, m1c, 1);
-      const T m1pm = __shfl_up_sync(0xffffffffu, m1p, 1);
-      const T acc = s[0] * c + s[1] * cp + s[2] * cm + s[3] * up + s[4] * dn + s[5] * p1c +
-                    s[6] * m1c + s[7] * upm + s[8] * dnp + s[9] * p1cm + s[10] * m1cp +
-                    s[11] * p1m + s[12] * m1p + s[13] * p1mp + s[14] * m1pm;
-      if (out_lane && i < lk - j - 1) {
-        const int idx = ry + i;
-        if (OP == OP_APPLY) {
-          y[idx] = A.mode == HG_ADD ? y[idx] + acc : acc;
-        } else if (OP == OP_RESID) {
-          y[idx] = A.b[base + idx] - acc;
-        } else {
-          y[idx] = c + (A.b[base + idx] - acc) * wd;
-        }
-      }
-      ry += lk - j;
+  if (act) A.y[g] = v;
+}
+
+// One window of a plane tile in registers: the seven row values of the lane's
+// point, its offset and whether it is an output.
+template <typename T>
+struct PlaneWin {
+  T c, up, dn, p1c, p1m, m1c, m1p;
+  int g;
+  bool ok;
+};
+
+// Lane position inside a plane: offset g, row j, column r, row length len.
+struct PlanePos {
+  int g, r, len, j;
+};
+
+// Advance the lane by one window (30 offsets) and issue its seven loads.
+// Lanes are placed up to gb+1 (the row end after the last interior point,
+// whose values the last output takes by shuffle); the row walk stays inside
+// the plane and lanes past gb+1 load at gb+1 (row length 3): in bounds, never
+// stored.
+template <typename T>
+__device__ __forceinline__ void plane_load(PlaneWin<T>& W, const T* __restrict__ x, PlanePos& P,
+                                           bool advance, int gb, int Tp, int Tm, bool halo) {
+  if (advance) {
+    P.g += 30;
+    P.r += 30;
+    while (P.r >= P.len && P.g <= gb + 1) { P.r -= P.len; --P.len; ++P.j; }
+  }
+  const bool in = P.g <= gb + 1;
+  const int gq = in ? P.g : gb + 1, lq = in ? P.len : 3;
+  W.ok = in && P.g <= gb && !halo && P.r >= 1 && P.r <= P.len - 2;
+  W.g = gq;
+  W.c = __ldg(x + gq);
+  W.up = __ldg(x + gq + lq);
+  W.dn = __ldg(x + gq - lq - 1);
+  W.p1c = __ldg(x + gq + Tp + lq);
+  W.p1m = __ldg(x + gq + Tp);
+  W.m1c = __ldg(x + gq - Tm - lq - 1);
+  W.m1p = __ldg(x + gq - Tm);
+}
+
+// The 15-point stencil of one window from registers and shuffles, stored.
+template <typename T, int OP>
+__device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const PlaneWin<T>& W,
+                                              const T s[kNDir], T wd, int64_t base,
+                                              T* __restrict__ y) {
+  const T cm = __shfl_up_sync(0xffffffffu, W.c, 1), cp = __shfl_down_sync(0xffffffffu, W.c, 1);
+  const T upm = __shfl_up_sync(0xffffffffu, W.up, 1);
+  const T dnp = __shfl_down_sync(0xffffffffu, W.dn, 1);
+  const T p1cm = __shfl_up_sync(0xffffffffu, W.p1c, 1);
+  const T p1mp = __shfl_down_sync(0xffffffffu, W.p1m, 1);
+  const T m1cp = __shfl_down_sync(0xffffffffu, W.m1c, 1);
+  const T m1pm = __shfl_up_sync(0xffffffffu, W.m1p, 1);
+  const T a0 = s[0] * W.c + s[1] * cp + s[2] * cm + s[3] * W.up + s[4] * W.dn + s[7] * upm +
+               s[8] * dnp;
+  const T a1 = s[5] * W.p1c + s[9] * p1cm + s[11] * W.p1m + s[13] * p1mp;
+  const T a2 = s[6] * W.m1c + s[10] * m1cp + s[12] * W.m1p + s[14] * m1pm;
+  const T acc = a0 + (a1 + a2);
+  if (W.ok) {
+    const int idx = W.g;
+    if (OP == OP_APPLY) {
+      y[idx] = A.mode == HG_ADD ? y[idx] + acc : acc;
+    } else if (OP == OP_RESID) {
+      y[idx] = A.b[base + idx] - acc;
+    } else {
+      y[idx] = W.c + (A.b[base + idx] - acc) * wd;
     }
   }
 }
 
-// A table tile (up to kTileRows rows) in register-window chunks of R rows.
-template <typename T, int OP, int R>
-__device__ __forceinline__ void interior_tile(const FusedArgs<T>& A, int t, int lane) {
-  const int4 tl = A.tiles[t];
-  const int j0 = tl.w & 0xffff, j1 = tl.w >> 16;
-  for (int jc = j0; jc < j1; jc += R)
-    interior_tile_rows<T, OP, R>(A, tl.x, tl.y, tl.z, jc, min(R, j1 - jc), lane);
+// Plane-window tile t (see the file comment): its windows in order, the loads
+// of the next D windows in flight while one is computed (D = 0, 1 or 2;
+// three rotating register sets for D = 2).
+template <typename T, int OP, int D>
+__device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lane) {
+  const int cell = t / A.n_tiles_cell;
+  const int4 tl = A.tiles[t - cell * A.n_tiles_cell];
+  const int k = tl.x & 0xffff, nwin = tl.x >> 16;
+  const int w = A.w, n = A.n;
+  const int64_t base = (int64_t)cell * A.stride;
+  const T* __restrict__ x = A.x + base;
+  T* __restrict__ y = A.y + base;
+  const T* __restrict__ S = A.sten + (int64_t)cell * 256;
+  const int Tp = ntri32(w - k - 1), Tm = ntri32(w - k);
+  const int gb = row_start(w, n - k - 2, k) + 1;  // last interior offset of the plane
+  T s[kNDir];
+#pragma unroll
+  for (int d = 0; d < kNDir; ++d) s[d] = __ldg(S + d);
+  const T wd = OP == OP_JACOBI ? A.omega / s[0] : T(0);
+  const bool halo = lane == 0 || lane == 31;
+  PlanePos P;
+  P.j = tl.z >> 16;
+  P.r = (tl.z & 0xffff) + lane;
+  P.len = w - k - P.j;
+  P.g = tl.y + lane;
+  while (P.r >= P.len && P.g <= gb + 1) { P.r -= P.len; --P.len; ++P.j; }
+  PlaneWin<T> W0, W1, W2;
+  if (D == 0) {
+    for (int q = 0; q < nwin; ++q) {
+      plane_load<T>(W0, x, P, q > 0, gb, Tp, Tm, halo);
+      plane_compute<T, OP>(A, W0, s, wd, base, y);
+    }
+  } else if (D == 1) {
+    plane_load<T>(W0, x, P, false, gb, Tp, Tm, halo);
+    for (int q = 0; q < nwin; q += 2) {
+      if (q + 1 < nwin) plane_load<T>(W1, x, P, true, gb, Tp, Tm, halo);
+      plane_compute<T, OP>(A, W0, s, wd, base, y);
+      if (q + 1 < nwin) {
+        if (q + 2 < nwin) plane_load<T>(W0, x, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP>(A, W1, s, wd, base, y);
+      }
+    }
+  } else {
+    plane_load<T>(W0, x, P, false, gb, Tp, Tm, halo);
+    if (nwin > 1) plane_load<T>(W1, x, P, true, gb, Tp, Tm, halo);
+    for (int q = 0; q < nwin; q += 3) {
+      if (q + 2 < nwin) plane_load<T>(W2, x, P, true, gb, Tp, Tm, halo);
+      plane_compute<T, OP>(A, W0, s, wd, base, y);
+      if (q + 1 < nwin) {
+        if (q + 3 < nwin) plane_load<T>(W0, x, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP>(A, W1, s, wd, base, y);
+      }
+      if (q + 2 < nwin) {
+        if (q + 4 < nwin) plane_load<T>(W1, x, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP>(A, W2, s, wd, base, y);
+      }
+    }
+  }
 }
 
 // Block `blk` of one operator application: interface items first, then tiles.
@@ -254,16 +357,23 @@ __device__ __forceinline__ void p1_block(const FusedArgs<T>& A, int blk) {
   const int lane = threadIdx.x & 31;
   const int wg = blk * kWarps + (threadIdx.x >> 5);
   if (blk < A.nb_items) {
-    if (wg < A.n_items) interface_point<T, OP>(A, wg, lane);
+    if (wg < A.n_items) interface_item<T, OP>(A, wg, lane);
   } else {
     const int t = wg - A.nb_items * kWarps;
-    if (t < A.n_tiles) interior_tile<T, OP, R>(A, t, lane);
+    if (t < A.n_tiles) plane_tile<T, OP, R>(A, t, lane);
   }
 }
 
+// Windows of a plane tile whose loads are in flight while one is computed.
+constexpr int kPlanePrefetch = 1;
+
+// Resident blocks per SM the register budget is sized for (FP32 / FP64).
+template <typename T>
+constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
+
 template <typename T, int OP>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) p1_fused_kernel(FusedArgs<T> A) {
-  p1_block<T, OP, kTileRows>(A, blockIdx.x);
+__global__ void __launch_bounds__(kBlock, min_blocks<T>()) p1_fused_kernel(FusedArgs<T> A) {
+  p1_block<T, OP, kPlanePrefetch>(A, blockIdx.x);
 }
 
 // Index of the problem owning unit u: base[p] <= u < base[p+1].
@@ -276,29 +386,15 @@ __device__ __forceinline__ int unit_problem(const int* __restrict__ base, int np
   return lo;
 }
 
-// A problem's descriptor copied into shared memory for the block's current
-// unit (read there, it cannot alias the global stores of the stage, so the
-// compiler need not reload it after each one).  Called by every thread.
-template <typename D>
-__device__ __forceinline__ const D& stage_desc(const D* __restrict__ src, unsigned char* dst) {
-  static_assert(sizeof(D) % 4 == 0, "descriptor size");
-  __syncthreads();  // the previous unit is done with dst
-  for (int q = threadIdx.x; q < (int)(sizeof(D) / 4); q += blockDim.x)
-    reinterpret_cast<int*>(dst)[q] = __ldg(reinterpret_cast<const int*>(src) + q);
-  __syncthreads();
-  return *reinterpret_cast<const D*>(dst);
-}
-
 // Batched persistent form: units u (one per block of each problem's grid,
 // problems concatenated) are taken in a grid-stride loop.
 template <typename T, int OP, int R>
-__global__ void __launch_bounds__(kBlock, sizeof(T) == 4 ? 4 : 2) p1_batched_kernel(
+__global__ void __launch_bounds__(kBlock, min_blocks<T>()) p1_batched_kernel(
     const FusedArgs<T>* __restrict__ descs, const int* __restrict__ base, int nprob) {
-  __shared__ __align__(16) unsigned char sd[sizeof(FusedArgs<T>)];
   const int total = __ldg(base + nprob);
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = unit_problem(base, nprob, u);
-    p1_block<T, OP, R>(stage_desc(descs + p, sd), u - __ldg(base + p));
+    p1_block<T, OP, R>(descs[p], u - __ldg(base + p));
   }
 }
 
@@ -309,9 +405,10 @@ FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
   A.w = L.w;
   A.stride = L.cell_stride;
   A.flags = L.cls_flags;
-  A.tiles = L.tiles;
-  A.n_tiles = L.n_tiles;
-  A.items = L.items;
+  A.tiles = L.ptiles;
+  A.n_tiles_cell = L.n_ptiles_cell;
+  A.n_tiles = L.n_ptiles_cell * L.ncells;
+  A.items = L.citems;
   A.n_items = n_items;
   A.nb_items = (n_items + kWarps - 1) / kWarps;
   A.prims = L.prims;
@@ -329,9 +426,9 @@ FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
 
 template <typename T, int OP>
 int run_p1(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
-  const int n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_items_inner : L.n_items;
+  const int n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_citems_inner : L.n_citems;
   FusedArgs<T> A = fused_args<T>(L, a, n_items);
-  const int grid = A.nb_items + (L.n_tiles + kWarps - 1) / kWarps;
+  const int grid = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   if (grid == 0) return HG_OK;
   p1_fused_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
   HG_CUDA(cudaGetLastError());
@@ -352,18 +449,6 @@ int run_p1_op(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
 // ------------------------------------------------------------ row items
 // Row item r of a level: cell = r / ntri(w), then plane k and row j of the
 // cell's lattice.  Plane k has w-k rows; R(k) = k(2w-k+1)/2 rows precede it.
-__device__ __forceinline__ void row_item(int w, int r, int& cell, int& j, int& k) {
-  const int per = ntri32(w);
-  cell = r / per;
-  const int rr = r - cell * per;
-  const float q = 2.0f * w + 1.0f;
-  int kk = (int)floorf((q - sqrtf(fmaxf(q * q - 8.0f * rr, 0.0f))) * 0.5f);
-  if (kk < 0) kk = 0;
-  while ((kk + 1) * (2 * w - kk) / 2 <= rr) ++kk;
-  while (kk * (2 * w - kk + 1) / 2 > rr) --kk;
-  k = kk;
-  j = rr - kk * (2 * w - kk + 1) / 2;
-}
 
 // ------------------------------------------------------------ maps / dumps
 __global__ void index_enumerate_kernel(int w, int64_t* out) {
@@ -572,22 +657,20 @@ __global__ void __launch_bounds__(kBlock) prolong_kernel(ProlongDesc<T> D) {
 template <typename T>
 __global__ void __launch_bounds__(kBlock) restrict_batched_kernel(
     const RestrictDesc<T>* __restrict__ descs, const int* __restrict__ base, int nprob) {
-  __shared__ __align__(16) unsigned char sd[sizeof(RestrictDesc<T>)];
   const int total = __ldg(base + nprob);
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = unit_problem(base, nprob, u);
-    restrict_block<T>(stage_desc(descs + p, sd), u - __ldg(base + p));
+    restrict_block<T>(descs[p], u - __ldg(base + p));
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) prolong_batched_kernel(
     const ProlongDesc<T>* __restrict__ descs, const int* __restrict__ base, int nprob) {
-  __shared__ __align__(16) unsigned char sd[sizeof(ProlongDesc<T>)];
   const int total = __ldg(base + nprob);
   for (int u = blockIdx.x; u < total; u += gridDim.x) {
     const int p = unit_problem(base, nprob, u);
-    prolong_block<T>(stage_desc(descs + p, sd), u - __ldg(base + p));
+    prolong_block<T>(descs[p], u - __ldg(base + p));
   }
 }
 
@@ -761,15 +844,15 @@ size_t p1_desc_bytes(int dtype) {
 }
 
 int p1_make_desc(const LevelDev& L, int dtype, const StencilArgs& a, void* dst, int* units) {
-  const int n_items = (a.op == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_items_inner : L.n_items;
+  const int n_items = (a.op == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_citems_inner : L.n_citems;
   if (dtype == HG_F64) {
     const FusedArgs<double> A = fused_args<double>(L, a, n_items);
     memcpy(dst, &A, sizeof A);
-    *units = A.nb_items + (L.n_tiles + kWarps - 1) / kWarps;
+    *units = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   } else {
     const FusedArgs<float> A = fused_args<float>(L, a, n_items);
     memcpy(dst, &A, sizeof A);
-    *units = A.nb_items + (L.n_tiles + kWarps - 1) / kWarps;
+    *units = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   }
   return HG_OK;
 }
@@ -814,12 +897,12 @@ template <typename T, int OP>
 static void p1_batched_rows(int rows, const void* d, const int* base, int nprob, int grid,
                             cudaStream_t s) {
   const FusedArgs<T>* D = (const FusedArgs<T>*)d;
-  if (rows <= 2)
-    p1_batched_kernel<T, OP, 2><<<grid, kBlock, 0, s>>>(D, base, nprob);
-  else if (rows <= 4)
-    p1_batched_kernel<T, OP, 4><<<grid, kBlock, 0, s>>>(D, base, nprob);
+  if (rows <= 0)
+    p1_batched_kernel<T, OP, 0><<<grid, kBlock, 0, s>>>(D, base, nprob);
+  else if (rows <= 1)
+    p1_batched_kernel<T, OP, 1><<<grid, kBlock, 0, s>>>(D, base, nprob);
   else
-    p1_batched_kernel<T, OP, 8><<<grid, kBlock, 0, s>>>(D, base, nprob);
+    p1_batched_kernel<T, OP, 2><<<grid, kBlock, 0, s>>>(D, base, nprob);
 }
 
 int launch_p1_batched(int dtype, int op, int rows, const void* descs, const int* base, int nprob,

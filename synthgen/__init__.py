@@ -21,6 +21,7 @@ import numpy as np
 __all__ = [
     "MacroMesh", "reference_tet", "kuhn_cube", "uniform_vector",
     "rff_params", "rff_eval", "batched_problem_draw", "WORKLOADS",
+    "SINPROD_AB", "sinprod_coefficient", "sinprod_manufactured",
 ]
 
 
@@ -125,6 +126,35 @@ def rff_eval_torch(params, xyz, device="cuda", dtype=None):
     for s in range(0, len(X), 1 << 18):
         out[s:s + (1 << 18)] = amp * torch.cos(X[s:s + (1 << 18)] @ om.T + be).sum(dim=1)
     return torch.exp(out).double().cpu().numpy()
+
+
+# The smooth coefficient of the P2 workload, k(x) = a + b sin(2 pi x) sin(2 pi y)
+# sin(2 pi z), as (a, b).
+SINPROD_AB = (1.0, 0.5)
+
+
+def sinprod_coefficient(a: float = SINPROD_AB[0], b: float = SINPROD_AB[1]):
+    """k(x) = a + b sin(2 pi x) sin(2 pi y) sin(2 pi z) as a callable on (N,3) points."""
+    def k(X):
+        X = np.asarray(X, dtype=np.float64)
+        return a + b * np.prod(np.sin(2.0 * np.pi * X), axis=1)
+    return k
+
+
+def sinprod_manufactured(xyz, a: float = SINPROD_AB[0], b: float = SINPROD_AB[1]):
+    """u = sin(pi x) sin(pi y) sin(pi z) and f = -div(k grad u) for the sinprod k,
+    in closed form (f = 3 pi^2 k u - grad k . grad u), at points (N,3)."""
+    X = np.asarray(xyz, dtype=np.float64)
+    s1, c1 = np.sin(np.pi * X), np.cos(np.pi * X)
+    s2, c2 = np.sin(2 * np.pi * X), np.cos(2 * np.pi * X)
+    u = np.prod(s1, axis=1)
+    k = a + b * np.prod(s2, axis=1)
+    gu = np.pi * np.stack([c1[:, 0] * s1[:, 1] * s1[:, 2], s1[:, 0] * c1[:, 1] * s1[:, 2],
+                           s1[:, 0] * s1[:, 1] * c1[:, 2]], axis=1)
+    gk = 2 * np.pi * b * np.stack([c2[:, 0] * s2[:, 1] * s2[:, 2], s2[:, 0] * c2[:, 1] * s2[:, 2],
+                                   s2[:, 0] * s2[:, 1] * c2[:, 2]], axis=1)
+    f = 3 * np.pi ** 2 * k * u - np.sum(gk * gu, axis=1)
+    return u, f
 
 
 def batched_problem_draw(seed: int = 42, count: int = 512):

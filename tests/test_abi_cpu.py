@@ -73,3 +73,25 @@ def test_bad_meshes_are_rejected(built):
     xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0, 0, -1], [1, 1, 1]], float)
     with pytest.raises(hg.HGError):
         hg.Mesh(xyz, np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]]))
+
+
+def test_quadrature_rule_exact_to_degree_five():
+    """The library derives its P2 rule from the moment equations: positive
+    weights summing to 1, points inside the tetrahedron, every barycentric
+    monomial of degree <= 5 integrated exactly (closed form 3! prod a_i! /
+    (|a|+3)!), and degree 6 not (so the rule is the degree-5 one)."""
+    import itertools
+    import math
+    b, w = hg.quadrature_rule()
+    assert b.shape == (14, 4) and np.all(w > 0) and abs(w.sum() - 1) < 1e-15
+    assert np.all(b >= 0) and np.allclose(b.sum(axis=1), 1, atol=1e-15)
+    worst = {}
+    for al in itertools.product(range(7), repeat=4):
+        d = sum(al)
+        if d > 6:
+            continue
+        ex = 6 * math.prod(math.factorial(a) for a in al) / math.factorial(d + 3)
+        got = float(np.sum(w * np.prod(b ** np.array(al), axis=1)))
+        worst[d] = max(worst.get(d, 0.0), abs(got - ex))
+    assert max(worst[d] for d in range(6)) < 1e-15
+    assert worst[6] > 1e-6

@@ -60,7 +60,7 @@ def test_batch_converges_and_equals_single_solves(batch):
     it, rel = B.solve(tol=TOL, max_iter=60)
     rows, gf, us = B.tuning()
     print("batch:", draw, "iters", it.tolist(), "tuned rows", rows, "grid factor", gf, us, "us")
-    assert rows in (2, 4, 8) and gf in (1, 2, 4) and us > 0
+    assert rows in (0, 1, 2) and gf in (1, 2, 4) and us > 0
     assert np.all(rel <= TOL) and np.all(it > 0)
     for p, G in enumerate(Gs):
         H = shared[keys[p]][0]
