@@ -275,6 +275,83 @@ def batch_comparison(stream, count=512):
             "batched_vs_one_at_a_time_speedup": t_seq / t_batch}
 
 
+P2_WORKLOAD = "cube48_L6_p2_sinprod"
+# FP32 operations per micro-cell of the P2 stiffness apply: per quadrature point
+# 6 (k: three separable sines) + 2 (kq) + 8 (C_q factors) + 16 (u = C^T x)
+# + 20 (v = kq H u) + 16 (y += C v) multiply-add pairs or singles, counted as
+# flops: 2 per FMA.
+P2_FLOPS_PER_CELL = 14 * 2 * (3 + 1 + 4 + 16 + 20 + 16)
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x max SM clock
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def p2_comparison(stream, level=6):
+    """P2 -div(k grad), k = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z), on the
+    unit cube as 2x2x2 sub-cubes x 6 Kuhn tetrahedra (48 macro cells), P2
+    level 6 (257^3 DoFs): FP32 element-wise apply (on-the-fly quadrature), and
+    the manufactured problem u = sin(pi x) sin(pi y) sin(pi z) solved to 1e-10
+    by FP32 V-cycles in FP64 refinement and by FP64 V-cycles."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    P2 = hg.HG_SPACE_P2
+    macro = sg.kuhn_cube(2)
+    t0 = time.perf_counter()
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 0, level + 1)
+    stiff = hg.Operator(H, hg.HG_OP_P2_DIVKGRAD, coeff=sg.SINPROD_AB)
+    mass = hg.Operator(H, hg.HG_OP_P2_MASS)
+    ns, nu, ni, _ = H.size(level, space=P2)
+    _, xyz, dirich = H.canonical_info(level, space=P2)
+    setup_s = time.perf_counter() - t0
+    n_cells_micro = len(macro.cells) * 8 ** level
+    # apply throughput, 4 rotating pairs (4 x 2 x 70 MB > L2)
+    xs = [H.from_canonical(level, torch.tensor(sg.uniform_vector(300 + q, nu), dtype=torch.float32,
+                                               device="cuda"), space=P2) for q in range(4)]
+    ys = [torch.zeros_like(v) for v in xs]
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for q in range(3):
+        stiff.apply(level, xs[q % 4], ys[q % 4], stream=stream)
+    torch.cuda.synchronize()
+    K = 20
+    e0.record(stream)
+    for q in range(K):
+        stiff.apply(level, xs[q % 4], ys[q % 4], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_apply = e0.elapsed_time(e1) / K * 1e-3
+    tflops = P2_FLOPS_PER_CELL * n_cells_micro / t_apply / 1e12
+    out = {"workload": P2_WORKLOAD, "unique_dofs": int(nu), "interior_dofs": int(ni),
+           "micro_cells": int(n_cells_micro), "setup_s": setup_s,
+           "apply_f32": {"us": t_apply * 1e6, "gdof_per_s": nu / t_apply / 1e9,
+                         "tflops": tflops, "roofline": {"bound": "alu", "achieved": tflops,
+                                                        "peak": FP32_PEAK_TFLOPS,
+                                                        "unit": "TFLOP/s",
+                                                        "frac": tflops / FP32_PEAK_TFLOPS}}}
+    del xs, ys
+    u, f = sg.sinprod_manufactured(xyz, *sg.SINPROD_AB)
+    b = H.zeros(level, torch.float64, space=P2)
+    mass.apply(level, H.from_canonical(level, torch.tensor(f, device="cuda"), space=P2), b,
+               stream=stream)
+    sol = {}
+    for name, prec in (("mixed_f32_ir", hg.HG_PREC_MIXED), ("plain_f64", hg.HG_PREC_F64)):
+        G = hg.GMG(stiff, lmin=0)
+        x = H.zeros(level, torch.float64, space=P2)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it, rel = G.solve(x, b, tol=1e-10, max_iter=100, precision=prec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        xc = H.to_canonical(level, x, space=P2).cpu().numpy()
+        sol[name] = xc
+        out[name] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel,
+                     "max_err_vs_u": float(np.max(np.abs(xc - u)))}
+        del G
+    out["mixed_vs_f64_rel_diff"] = float(np.linalg.norm(sol["mixed_f32_ir"] - sol["plain_f64"]) /
+                                         np.linalg.norm(sol["plain_f64"]))
+    out["mixed_vs_f64_speedup"] = out["plain_f64"]["s"] / out["mixed_f32_ir"]["s"]
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -319,6 +396,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gmg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-p2", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -427,6 +505,8 @@ def main():
         out["gmg"] = gmg_comparison(stream)
     if rank == 0 and not args.no_batch:
         out["batch"] = batch_comparison(stream)
+    if rank == 0 and not args.no_p2:
+        out["p2"] = p2_comparison(stream)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_spmv()
     if rank == 0:
