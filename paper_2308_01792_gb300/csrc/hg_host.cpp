@@ -305,20 +305,6 @@ int Hier::build_level(int l) {
   }
   L.n_ptiles_cell = (int)ptiles.size();
   if (int r = upload(&L.ptiles, ptiles)) return r;
-  // interior tiles: plane k, 30 outputs i0..i0+29, rows j0..j1-1 of at most
-  // kTileRows (interior points 1 <= i,j,k and i+j+k <= n-1)
-  std::vector<int4> tiles;
-  for (int64_t c = 0; c < mesh->nc; ++c)
-    for (int k = 1; k <= n - 3; ++k)
-      for (int i0 = 1; i0 <= n - 2 - k; i0 += 30) {
-        const int jlast = n - 1 - k - i0;
-        for (int j0 = 1; j0 <= jlast; j0 += kTileRows) {
-          const int j1 = std::min(j0 + kTileRows, jlast + 1);
-          tiles.push_back({(int)c, k, i0, j0 | (j1 << 16)});
-        }
-      }
-  L.n_tiles = (int)tiles.size();
-  if (int r = upload(&L.tiles, tiles)) return r;
   // canonical numbering by exact lattice coordinates
   if (mesh->grid_denom) {
     std::vector<int64_t> keys(L.n_stored, -1);
@@ -385,7 +371,7 @@ int Hier::build_level(int l) {
   }
   // every table a kernel reads must be on the device
   if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
-      (L.n_items && (!L.items || !L.item_prim)) || (L.n_tiles && !L.tiles) ||
+      (L.n_items && (!L.items || !L.item_prim)) ||
       (L.n_citems && !L.citems) || (L.n_ptiles_cell && !L.ptiles) ||
       (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
     set_error("internal: level %d device tables incomplete", l);
@@ -438,7 +424,6 @@ Hier::~Hier() {
     cudaFree(L.prims);
     cudaFree(L.copies);
     cudaFree(L.prim_point_base);
-    cudaFree(L.tiles);
     cudaFree(L.citems);
     cudaFree(L.ptiles);
     cudaFree(L.items);

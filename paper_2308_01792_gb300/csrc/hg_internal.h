@@ -140,8 +140,6 @@ struct LevelDev {
   int n_prims, n_prims_inner, max_copies;
   int32_t* prim_point_base;  // [n_prims+1] prefix sums of prim_points
   // work items of the fused kernels
-  int4* tiles;               // interior tiles (cell, k, i0, j0 | j1 << 16)
-  int n_tiles;
   int* err;                  // device error word shared by the hierarchy's kernels
   int4* items;               // interface items (first_copy, p0, dim|ncopies<<4|dirichlet<<12, 0),
   int32_t* item_prim;        //   32 consecutive points of one primitive; item -> primitive
@@ -153,8 +151,6 @@ struct LevelDev {
   int n_ptiles_cell;         //   (k | windows << 16, lane-0 offset z, j0 << 16 | i0, 0)
 };
 
-// Output rows per interior tile of the variable-coefficient kernel.
-constexpr int kTileRows = 8;
 // Windows of 30 consecutive lattice offsets per plane-window tile of the
 // constant-stencil kernels.
 constexpr int kPlaneSteps = 16;

@@ -12,8 +12,11 @@
 // sums over the copies in ascending cell order (as for constant stencils).
 //
 // Same launch structure as the constant-stencil kernel: interface items
-// first, then interior tiles whose warps hold register windows of the 7 rows
-// of x and of k that the 15-point neighbourhood touches.
+// first, then plane-window tiles (30 consecutive t_w offsets of one plane per
+// warp window, 16-window strips; see hg_p1.cu) that load the 7 neighbour
+// rows of x and of k per window and take the shifted neighbours by shuffle.
+// The cell's 24 x 4 element rows sit in a per-warp shared-memory copy and
+// are read as 16-byte vectors (every lane of a warp reads the same row).
 #include <cuda_runtime.h>
 
 #include "hg_internal.h"
@@ -24,7 +27,6 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
-constexpr int kVarRows = 4;  // output rows per interior tile
 
 // Incidence q = 4*type + corner: direction index (see dir_offset) of the
 // element's vertex b seen from the output vertex (corner) v.
@@ -71,11 +73,40 @@ __device__ __forceinline__ T divkgrad_point(const T xv[kNDir], const T kv[kNDir]
   return acc;
 }
 
+// Vector of one 4-entry element row.
+template <typename T>
+struct Row4;
+template <>
+struct Row4<float> {
+  using type = float4;
+};
+template <>
+struct Row4<double> {
+  using type = double4;
+};
+
+// Interior point (all 24 incidences), element rows from shared memory.
+template <typename T>
+__device__ __forceinline__ T divkgrad_point_sm(const T xv[kNDir], const T kv[kNDir],
+                                               const typename Row4<T>::type* __restrict__ Ks) {
+  T acc = T(0);
+#pragma unroll
+  for (int q = 0; q < 24; ++q) {
+    const typename Row4<T>::type Kr = Ks[q];
+    const T kT = T(0.25) * (kv[kInc[q][0]] + kv[kInc[q][1]] + kv[kInc[q][2]] + kv[kInc[q][3]]);
+    const T r = Kr.x * xv[kInc[q][0]] + Kr.y * xv[kInc[q][1]] + Kr.z * xv[kInc[q][2]] +
+                Kr.w * xv[kInc[q][3]];
+    acc += kT * r;
+  }
+  return acc;
+}
+
 template <typename T>
 struct VarArgs {
   int n, w;
   int64_t stride;
-  const int4* tiles;
+  const int4* tiles;  // plane-window tiles of one cell (same for every cell)
+  int n_tiles_cell;
   int n_tiles;
   const int4* items;
   int n_items, nb_items;
@@ -110,13 +141,20 @@ __device__ __forceinline__ void gather15(const T* __restrict__ x, int n, int w, 
   }
 }
 
+// Apply item (lane = pt * C + c takes copy c of point pt, C <= 32 copies):
+// each lane gathers its copy's partial, the point's C partials are summed in
+// ascending cell order by lane exchange and written to every copy.
 template <typename T, int OP>
-__device__ void var_interface_point(const VarArgs<T>& A, int item, int lane) {
-  const int4 it = A.items[item];
+__device__ void var_interface_item(const VarArgs<T>& A, int item, int lane);
+
+// Item of a primitive with more than 32 copies: one lane per point, copies
+// in turn.
+template <typename T, int OP>
+__device__ void var_interface_point(const VarArgs<T>& A, const int4& it, int lane) {
   const int dim = it.z & 15, ncopies = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
   const int n = A.n, w = A.w;
   const int p = it.y + lane;
-  if (p >= prim_points(dim, n)) return;
+  if (lane >= it.w) return;
   int wts[3];
   // face points: rows b = 1..n-2 of n-1-b points (same order as the items)
   if (dim == 2) {
@@ -178,111 +216,163 @@ __device__ void var_interface_point(const VarArgs<T>& A, int item, int lane) {
   }
 }
 
-// Register window of one lattice row set (see the constant-stencil tiles):
-// plane k rows j0-1..j0+R, plane k+1 rows j0-1..j0+R-1, plane k-1 rows j0..j0+R.
-template <typename T, int R>
-struct Window {
-  T K[R + 2], Kp[R + 1], Km[R + 1];
-  __device__ __forceinline__ void load(const T* __restrict__ x, int w, int i, int j0, int k,
-                                       int nr) {
-    const int lk = w - k, lkp = w - k - 1, lkm = w - k + 1;
-    int r = row_start(w, j0 - 1, k);
-#pragma unroll
-    for (int q = 0; q < R + 2; ++q) {
-      const int len = lk - (j0 - 1 + q);
-      K[q] = (q < nr + 2 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
-      r += len;
-    }
-    r = row_start(w, j0 - 1, k + 1);
-#pragma unroll
-    for (int q = 0; q < R + 1; ++q) {
-      const int len = lkp - (j0 - 1 + q);
-      Kp[q] = (q < nr + 1 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
-      r += len;
-    }
-    r = row_start(w, j0, k - 1);
-#pragma unroll
-    for (int q = 0; q < R + 1; ++q) {
-      const int len = lkm - (j0 + q);
-      Km[q] = (q < nr + 1 && i >= 0 && i < len) ? __ldg(x + r + i) : T(0);
-      r += len;
-    }
-  }
-  // 15 values of output row q in direction order (all lanes shuffle)
-  __device__ __forceinline__ void neighbours(int q, T v[kNDir]) const {
-    const unsigned F = 0xffffffffu;
-    v[0] = K[q + 1];
-    v[1] = __shfl_down_sync(F, K[q + 1], 1);
-    v[2] = __shfl_up_sync(F, K[q + 1], 1);
-    v[3] = K[q + 2];
-    v[4] = K[q];
-    v[5] = Kp[q + 1];
-    v[6] = Km[q];
-    v[7] = __shfl_up_sync(F, K[q + 2], 1);
-    v[8] = __shfl_down_sync(F, K[q], 1);
-    v[9] = __shfl_up_sync(F, Kp[q + 1], 1);
-    v[10] = __shfl_down_sync(F, Km[q], 1);
-    v[11] = Kp[q];
-    v[12] = Km[q + 1];
-    v[13] = __shfl_down_sync(F, Kp[q], 1);
-    v[14] = __shfl_up_sync(F, Km[q + 1], 1);
-  }
-};
-
 template <typename T, int OP>
-__device__ void var_interior_tile(const VarArgs<T>& A, int t, int lane) {
-  const int4 tl = A.tiles[t];
-  const int cell = tl.x, k = tl.y, i0 = tl.z, j0 = tl.w & 0xffff, j1 = tl.w >> 16;
-  const int w = A.w;
+__device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
+  const int4 it = A.items[item];
+  const int dim = it.z & 15, C = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
+  if (C > 32) {
+    // one lane per point, copies in turn (32-point item)
+    var_interface_point<T, OP>(A, it, lane);
+    return;
+  }
+  const int n = A.n, w = A.w;
+  const int pt = lane / C, c = lane - pt * C;
+  const bool act = pt < it.w;
+  int wts[3];
+  prim_point_weights(dim, n, it.y + (act ? pt : 0), wts);
+  const IfaceCopy cpy = A.copies[it.x + (act ? c : 0)];
+  int i, j, k;
+  copy_local_ijk(cpy, dim, wts, i, j, k);
+  const int64_t cbase = (int64_t)cpy.cell * A.stride;
+  const int64_t g = cbase + tw32(w, i, j, k);
+  T v;
+  if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER) && OP != OP_DIAG) {
+    v = OP == OP_JACOBI ? A.x[g] : T(0);
+  } else {
+    T xv[kNDir], kv[kNDir];
+    if (OP == OP_DIAG) {
+#pragma unroll
+      for (int d = 0; d < kNDir; ++d) xv[d] = d == 0 ? T(1) : T(0);
+    } else {
+      gather15<T>(A.x + cbase, n, w, i, j, k, xv);
+    }
+    gather15<T>(A.kc + cbase, n, w, i, j, k, kv);
+    const T part = divkgrad_point<T, false>(xv, kv, A.K + (int64_t)cpy.cell * 96,
+                                            incidence_mask(point_class(n, i, j, k)));
+    T sum = T(0);
+    const int g0 = pt * C;
+    for (int q = 0; q < C; ++q) sum += __shfl_sync(0xffffffffu, part, (g0 + q) & 31);
+    if (OP == OP_APPLY || OP == OP_DIAG) {
+      v = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[g] + sum : sum;
+    } else if (OP == OP_RESID) {
+      v = A.b[g] - sum;
+    } else {
+      v = A.x[g] + A.omega * (A.b[g] - sum) * A.invdiag[g];
+    }
+  }
+  if (act) A.y[g] = v;
+}
+
+// Plane-window tile t of the variable-coefficient operator (offsets and row
+// walk as in the constant-stencil kernel of hg_p1.cu): per window the lane
+// loads the 7 rows of x and of k, takes the 8 shifted neighbours of each by
+// shuffle, and gathers the 24 incidences.  Ks: this warp's shared copy of
+// the cell's element rows.
+template <typename T, int OP>
+__device__ void var_plane_tile(const VarArgs<T>& A, int t, int lane,
+                               typename Row4<T>::type* __restrict__ Ks) {
+  const int cell = t / A.n_tiles_cell;
+  const int4 tl = A.tiles[t - cell * A.n_tiles_cell];
+  const int k = tl.x & 0xffff, nwin = tl.x >> 16;
+  const int w = A.w, n = A.n;
   const int64_t base = (int64_t)cell * A.stride;
-  const int i = i0 - 1 + lane;
-  const bool out_lane = lane >= 1 && lane <= 30;
-  const T* __restrict__ K = A.K + (int64_t)cell * 96;
-  // the tile table is built for kTileRows rows; process it in chunks of kVarRows
-  for (int jc = j0; jc < j1; jc += kVarRows) {
-    const int nr = min(kVarRows, j1 - jc);
-    Window<T, kVarRows> wx, wk;
-    if (OP != OP_DIAG) wx.load(A.x + base, w, i, jc, k, nr);
-    wk.load(A.kc + base, w, i, jc, k, nr);
-    int ry = row_start(w, jc, k);
+  const T* __restrict__ x = A.x + base;
+  const T* __restrict__ kc = A.kc + base;
+  {
+    const T* __restrict__ K = A.K + (int64_t)cell * 96;
+    T* ks = reinterpret_cast<T*>(Ks);
+    for (int q = lane; q < 96; q += 32) ks[q] = __ldg(K + q);
+    __syncwarp();
+  }
+  const int Tp = ntri32(w - k - 1), Tm = ntri32(w - k);
+  const int gb = row_start(w, n - k - 2, k) + 1;
+  const bool halo = lane == 0 || lane == 31;
+  int j = tl.z >> 16, r = (tl.z & 0xffff) + lane, len = w - k - j;
+  int g = tl.y + lane;
+  // lanes are placed up to gb+1; the walk stays inside the plane and lanes
+  // past gb+1 read at gb+1 (row length 3), never stored
+  while (r >= len && g <= gb + 1) { r -= len; --len; ++j; }
+  const unsigned F = 0xffffffffu;
+  for (int q = 0; q < nwin; ++q) {
+    if (q > 0) {
+      g += 30;
+      r += 30;
+      while (r >= len && g <= gb + 1) { r -= len; --len; ++j; }
+    }
+    const bool in = g <= gb + 1;
+    const int gq = in ? g : gb + 1, lq = in ? len : 3;
+    const bool ok = in && g <= gb && !halo && r >= 1 && r <= len - 2;
+    const int o[7] = {gq, gq + lq, gq - lq - 1, gq + Tp + lq, gq + Tp, gq - Tm - lq - 1, gq - Tm};
+    T xr[7], kr[7];
 #pragma unroll
-    for (int q = 0; q < kVarRows; ++q) {
-      if (q < nr) {
-        const int j = jc + q;
-        T xv[kNDir], kv[kNDir];
-        if (OP == OP_DIAG) {
+    for (int m = 0; m < 7; ++m) {
+      xr[m] = OP == OP_DIAG ? T(0) : __ldg(x + o[m]);
+      kr[m] = __ldg(kc + o[m]);
+    }
+    // direction order: 0 c, 1 +i, 2 -i, 3 +j, 4 -j, 5 +k, 6 -k, 7 (-1,1,0),
+    // 8 (1,-1,0), 9 (-1,0,1), 10 (1,0,-1), 11 (0,-1,1), 12 (0,1,-1),
+    // 13 (1,-1,1), 14 (-1,1,-1); rows o: c, up, dn, p1c, p1m, m1c, m1p
+    T xv[kNDir], kv[kNDir];
+    kv[0] = kr[0];
+    kv[1] = __shfl_down_sync(F, kr[0], 1);
+    kv[2] = __shfl_up_sync(F, kr[0], 1);
+    kv[3] = kr[1];
+    kv[4] = kr[2];
+    kv[5] = kr[3];
+    kv[6] = kr[5];
+    kv[7] = __shfl_up_sync(F, kr[1], 1);
+    kv[8] = __shfl_down_sync(F, kr[2], 1);
+    kv[9] = __shfl_up_sync(F, kr[3], 1);
+    kv[10] = __shfl_down_sync(F, kr[5], 1);
+    kv[11] = kr[4];
+    kv[12] = kr[6];
+    kv[13] = __shfl_down_sync(F, kr[4], 1);
+    kv[14] = __shfl_up_sync(F, kr[6], 1);
+    if (OP == OP_DIAG) {
 #pragma unroll
-          for (int d = 0; d < kNDir; ++d) xv[d] = d == 0 ? T(1) : T(0);
-        } else {
-          wx.neighbours(q, xv);
-        }
-        wk.neighbours(q, kv);
-        const T acc = divkgrad_point<T, true>(xv, kv, K, 0u);
-        if (out_lane && i < (w - k) - j - 1) {
-          const int64_t idx = base + ry + i;
-          if (OP == OP_APPLY || OP == OP_DIAG) {
-            A.y[idx] = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[idx] + acc : acc;
-          } else if (OP == OP_RESID) {
-            A.y[idx] = A.b[idx] - acc;
-          } else {
-            A.y[idx] = xv[0] + A.omega * (A.b[idx] - acc) * A.invdiag[idx];
-          }
-        }
-        ry += (w - k) - j;
+      for (int d = 0; d < kNDir; ++d) xv[d] = d == 0 ? T(1) : T(0);
+    } else {
+      xv[0] = xr[0];
+      xv[1] = __shfl_down_sync(F, xr[0], 1);
+      xv[2] = __shfl_up_sync(F, xr[0], 1);
+      xv[3] = xr[1];
+      xv[4] = xr[2];
+      xv[5] = xr[3];
+      xv[6] = xr[5];
+      xv[7] = __shfl_up_sync(F, xr[1], 1);
+      xv[8] = __shfl_down_sync(F, xr[2], 1);
+      xv[9] = __shfl_up_sync(F, xr[3], 1);
+      xv[10] = __shfl_down_sync(F, xr[5], 1);
+      xv[11] = xr[4];
+      xv[12] = xr[6];
+      xv[13] = __shfl_down_sync(F, xr[4], 1);
+      xv[14] = __shfl_up_sync(F, xr[6], 1);
+    }
+    const T acc = divkgrad_point_sm<T>(xv, kv, Ks);
+    if (ok) {
+      const int64_t idx = base + gq;
+      if (OP == OP_APPLY || OP == OP_DIAG) {
+        A.y[idx] = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[idx] + acc : acc;
+      } else if (OP == OP_RESID) {
+        A.y[idx] = A.b[idx] - acc;
+      } else {
+        A.y[idx] = xr[0] + A.omega * (A.b[idx] - acc) * A.invdiag[idx];
       }
     }
   }
+  __syncwarp();
 }
 
 template <typename T, int OP>
 __global__ void __launch_bounds__(kBlock) p1var_kernel(VarArgs<T> A) {
+  __shared__ typename Row4<T>::type Ks[kWarps][24];
   const int lane = threadIdx.x & 31;
   const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if ((int)blockIdx.x < A.nb_items) {
-    if (wg < A.n_items) var_interface_point<T, OP>(A, wg, lane);
+    if (wg < A.n_items) var_interface_item<T, OP>(A, wg, lane);
   } else {
     const int t = wg - A.nb_items * kWarps;
-    if (t < A.n_tiles) var_interior_tile<T, OP>(A, t, lane);
+    if (t < A.n_tiles) var_plane_tile<T, OP>(A, t, lane, Ks[threadIdx.x >> 5]);
   }
 }
 
@@ -292,10 +382,11 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.n = L.n;
   A.w = L.w;
   A.stride = L.cell_stride;
-  A.tiles = L.tiles;
-  A.n_tiles = L.n_tiles;
-  A.items = L.items;
-  A.n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_items_inner : L.n_items;
+  A.tiles = L.ptiles;
+  A.n_tiles_cell = L.n_ptiles_cell;
+  A.n_tiles = L.n_ptiles_cell * L.ncells;
+  A.items = L.citems;
+  A.n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_citems_inner : L.n_citems;
   A.nb_items = (A.n_items + kWarps - 1) / kWarps;
   A.copies = L.copies;
   A.x = (const T*)a.x;
@@ -308,7 +399,7 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.op = a.op;
   A.mode = a.mode;
   A.mask = a.mask;
-  const int grid = A.nb_items + (L.n_tiles + kWarps - 1) / kWarps;
+  const int grid = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   if (grid == 0) return HG_OK;
   p1var_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
   HG_CUDA(cudaGetLastError());
