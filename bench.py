@@ -151,6 +151,11 @@ def cpu_baseline_spmv(seconds=10.0):
 
 
 GMG_WORKLOAD = "cube384_L6_p1_lognormal_gmg_to_1e-8"
+# FP32 V-cycles per FP64 refinement step of the mixed solves (one FP64
+# residual per step; measured on GB300: 3 beats 1 and 2 for both the P1
+# div-k-grad and the P2 problem, whose FP64 residuals cost 8 ms and 26 ms).
+# Plain FP64 solves do one V-cycle per residual as before.
+INNER_CYCLES = 3
 WEIGHTS = os.path.join(ROOT, "paper_2308_01792_gb300", "weights", "learned_smoother_cube384.npy")
 
 
@@ -179,13 +184,13 @@ def gmg_comparison(stream):
         net, loss = learned.train(X, t, steps=3000, batch=65536, lr=1e-3)
         trained = f"trained in bench: {npairs} noise pairs, loss {loss:.4g}"
     out = {"workload": GMG_WORKLOAD, "unique_dofs": int(len(xyz)), "tol": 1e-8,
-           "setup_s": setup_s, "weights": trained}
+           "setup_s": setup_s, "weights": trained, "fp32_cycles_per_refinement_step": INNER_CYCLES}
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for name, prec, use in (("plain_f64", hg.HG_PREC_F64, False),
                             ("mixed_f32_ir", hg.HG_PREC_MIXED, False),
                             ("learned_mixed", hg.HG_PREC_MIXED, True)):
-        G = hg.GMG(op)
+        G = hg.GMG(op, inner_cycles=INNER_CYCLES)
         G.set_learned(net if use else None)
         x = H.zeros(6, torch.float64)
         G.solve(x, b, tol=1e-8, max_iter=200, precision=prec, stream=stream)   # warm-up
@@ -321,6 +326,7 @@ def p2_comparison(stream, level=6):
     t_apply = e0.elapsed_time(e1) / K * 1e-3
     tflops = P2_FLOPS_PER_CELL * n_cells_micro / t_apply / 1e12
     out = {"workload": P2_WORKLOAD, "unique_dofs": int(nu), "interior_dofs": int(ni),
+           "fp32_cycles_per_refinement_step": INNER_CYCLES,
            "micro_cells": int(n_cells_micro), "setup_s": setup_s,
            "apply_f32": {"us": t_apply * 1e6, "gdof_per_s": nu / t_apply / 1e9,
                          "tflops": tflops, "roofline": {"bound": "alu", "achieved": tflops,
@@ -334,7 +340,7 @@ def p2_comparison(stream, level=6):
                stream=stream)
     sol = {}
     for name, prec in (("mixed_f32_ir", hg.HG_PREC_MIXED), ("plain_f64", hg.HG_PREC_F64)):
-        G = hg.GMG(stiff, lmin=0)
+        G = hg.GMG(stiff, lmin=0, inner_cycles=INNER_CYCLES)
         x = H.zeros(level, torch.float64, space=P2)
         torch.cuda.synchronize()
         e0.record(stream)
@@ -397,6 +403,8 @@ def main():
     ap.add_argument("--no-gmg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-p2", action="store_true")
+    ap.add_argument("--p2-level", type=int, default=6,
+                    help="P2 level of the P2 leg (6 = the 17 M DoF workload; smaller for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -506,7 +514,7 @@ def main():
     if rank == 0 and not args.no_batch:
         out["batch"] = batch_comparison(stream)
     if rank == 0 and not args.no_p2:
-        out["p2"] = p2_comparison(stream)
+        out["p2"] = p2_comparison(stream, args.p2_level)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_spmv()
     if rank == 0:

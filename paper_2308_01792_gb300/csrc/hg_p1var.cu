@@ -73,16 +73,14 @@ __device__ __forceinline__ T divkgrad_point(const T xv[kNDir], const T kv[kNDir]
   return acc;
 }
 
-// Vector of one 4-entry element row.
+// One 4-entry element row, aligned for a single vector shared-memory read.
 template <typename T>
-struct Row4;
-template <>
-struct Row4<float> {
-  using type = float4;
+struct alignas(4 * sizeof(T)) Row4Vec {
+  T x, y, z, w;
 };
-template <>
-struct Row4<double> {
-  using type = double4;
+template <typename T>
+struct Row4 {
+  using type = Row4Vec<T>;
 };
 
 // Interior point (all 24 incidences), element rows from shared memory.

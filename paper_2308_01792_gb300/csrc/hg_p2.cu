@@ -136,8 +136,15 @@ __device__ __forceinline__ void p2_element(const P2Cell<T>& C, int t, const T sx
 }
 
 // One colour phase: thread = anchor of colour `col` in cell blockIdx.y.
+// Resident blocks per SM the register budget is sized for (FP32 / FP64;
+// FP32 measured best at 6 against 1..5 on the 48-cell cube at P2 level 6).
+template <typename T>
+struct P2MinBlocks {
+  static constexpr int value = sizeof(T) == 4 ? 6 : 1;
+};
+
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kP2Block) p2_phase_kernel(const P2Cell<T>* __restrict__ cells,
+__global__ void __launch_bounds__(kP2Block, P2MinBlocks<T>::value) p2_phase_kernel(const P2Cell<T>* __restrict__ cells,
                                                             const uint32_t* __restrict__ anchors,
                                                             int n_anchors, int n, int64_t stride,
                                                             const T* __restrict__ x,
