@@ -19,10 +19,14 @@
  *   "stored" vectors: macro cell c occupies elements
  *   [c*cell_stride, (c+1)*cell_stride).  Inside a cell the micro-vertex
  *   (i,j,k), i+j+k <= n (n = 2^level), is at t_{n+1}(i,j,k) (Sec. 4,
- *   linearisation t_w).  For P2 the cell block holds the vertex array
- *   followed by the edge subgroups x,y,z,xy,xz,yz (width n) and xyz
- *   (width n-1), each in t_w order of its anchors (Sec. 5.1, P2 composition).
- *   Tail padding of each cell block is zero and never written.
+ *   linearisation t_w).  A P2 function on level l (vertex and edge DoFs of
+ *   the level-l micro-cells, Sec. 5.1) is stored as the vertex lattice of
+ *   level l+1: micro-vertices are its even points and every other point is
+ *   the midpoint of exactly one level-l micro-edge (the seven parity classes
+ *   are the seven edge directions), so P2 on level l uses the layout, copies
+ *   and canonical order of lattice level l+1; a hierarchy built to lmax
+ *   serves P2 levels up to lmax-1.
+ *   Tail padding of each cell block is never written by the library.
  *   Micro-vertices on macro faces/edges/vertices are stored once per macro
  *   cell that contains them; every library call leaves all copies equal.
  * - The library never frees caller memory.  It allocates its own device
@@ -104,7 +108,9 @@ void hg_hier_destroy(hg_hier* hier);
 
 /* Sizes of a stored vector (n_stored, including per-cell copies and padding),
  * the number of unique DoFs (n_unique) and of non-Dirichlet unique DoFs
- * (n_inner), and the per-cell stride.  Any output may be NULL. */
+ * (n_inner), and the per-cell stride (a multiple of 32 elements with at least
+ * 32 spare; the kernels may read, never write, the spare elements).  Any
+ * output may be NULL.  space: HG_SPACE_P1 or HG_SPACE_P2. */
 int hg_function_size(const hg_hier* hier, int space, int level, int64_t* n_stored,
                      int64_t* n_unique, int64_t* n_inner, int64_t* cell_stride);
 
@@ -156,6 +162,12 @@ int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
  * kind: HG_OP_*.  coeff: for HG_OP_P1_DIVKGRAD, host array of k at the
  * unique vertices of level lmax in canonical order (injected to coarser
  * levels); for HG_OP_P2_DIVKGRAD, host {a, b}; otherwise NULL.
+ * P2 operators (levels max(0, lmin-1) .. lmax-1 of the hierarchy) are
+ * element-wise: per micro-cell the 10x10 element matrix acts on the fly by
+ * the 14-point rule of hg_quadrature_rule, with k evaluated exactly at every
+ * quadrature point; Jacobi uses the assembled diagonal.  P2 applies use an
+ * operator-owned accumulation vector per level and dtype: calls on the same
+ * operator, level and dtype must not run concurrently on different streams.
  * Element matrices/stencils are computed per macro cell and level in FP64
  * (Sec. 5.2: constant-coefficient stencils precomputed per macro primitive,
  * element matrices on the fly for variable coefficients). */
