@@ -128,6 +128,22 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate_replicas(ms, units_per_rank, steps, pg=None, device="cuda"):
+    """Whole-job figures of N independent replicas: the timed region is the
+    maximum over ranks (all_reduce MAX of each rank's CUDA-event time, ms) and
+    every rank processed units_per_rank per step.  Returns (ms per step,
+    units per second in units of 1e9)."""
+    import torch
+    ws = 1
+    if pg is not None:
+        t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+        ws = pg.get_world_size()
+    ms_step = ms / steps
+    return ms_step, units_per_rank * ws / (ms_step * 1e-3) / 1e9
+
+
 def cpu_baseline_spmv(seconds=10.0):
     """Oracle CSR SpMV (SciPy, single thread) on the same mesh at SAMPLE_LEVEL."""
     from oracle import fem
@@ -456,12 +472,7 @@ def main():
         pg.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
-    if pg:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_step = ms / args.steps
-    value = nu * ws / (ms_step * 1e-3) / 1e9
+    ms_step, value = aggregate_replicas(ms, nu, args.steps, pg, "cuda")
 
     # end to end: canonical host vector -> device -> apply -> host, pinned buffers
     xh = torch.tensor(sg.uniform_vector(7, nu), dtype=dt).pin_memory()
