@@ -7,10 +7,11 @@
 // the level-l points p (Sec. 3.2): all six lie in the unit cube [p, p+1]^3,
 // whose doubled-lattice points (2p + {0,1,2}^3) hold their 10 DoFs each.
 // Anchors of equal parity (i, j, k mod 2) have disjoint closed cubes, so the
-// apply is 8 colour phases; in a phase one thread takes one anchor and adds
-// the products of its micro-cells' element matrices into the accumulation
-// vector with plain read-modify-write (no two threads touch a DoF, the order
-// of contributions to every DoF is fixed: colour, then type).
+// apply is 8 colour phases; in a phase one thread takes one anchor, loads the
+// 27 cube points once, sums the products of its micro-cells' element
+// matrices in registers and adds them into the accumulation vector with one
+// plain read-modify-write per point (no two threads touch a DoF; the order of
+// contributions to every DoF is fixed: colour, then type).
 //
 // Element matrices are never stored: for type t and quadrature point q the
 // gradients of the 10 basis functions are C_q (barycentric gradients), with
@@ -137,10 +138,10 @@ __device__ __forceinline__ void p2_element(const P2Cell<T>& C, int t, const T sx
 
 // One colour phase: thread = anchor of colour `col` in cell blockIdx.y.
 // Resident blocks per SM the register budget is sized for (FP32 / FP64;
-// FP32 measured best at 6 against 1..5 on the 48-cell cube at P2 level 6).
+// FP32 measured best at 5 against 4 and 6 on the 48-cell cube at P2 level 6).
 template <typename T>
 struct P2MinBlocks {
-  static constexpr int value = sizeof(T) == 4 ? 6 : 1;
+  static constexpr int value = sizeof(T) == 4 ? 5 : 1;
 };
 
 template <typename T, int MODE>
@@ -181,29 +182,44 @@ __global__ void __launch_bounds__(kP2Block, P2MinBlocks<T>::value) p2_phase_kern
     sincos_2pi(py, &sxyz[2], &sxyz[3]);
     sincos_2pi(pz, &sxyz[4], &sxyz[5]);
   }
+  // the 27 doubled-lattice points 2p + (dx, dy, dz) of the anchor's cube are
+  // loaded once (those inside the macro cell), the six micro-cells accumulate
+  // into registers, every point is written back once
+  T X[27], Y[27];
+#pragma unroll
+  for (int c = 0; c < 27; ++c) {
+    const int dx = c % 3, dy = (c / 3) % 3, dz = c / 9;
+    const bool in = 2 * s + dx + dy + dz <= 2 * n;
+    X[c] = (MODE == P2_DIAG || !in) ? T(0) : xc[rs[dy][dz] + 2 * i + dx];
+    Y[c] = T(0);
+  }
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
     if (s > n - 1 - kDelta[t]) continue;
-    int idx[10];
+    int cid[10];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int dx = 2 * kToff[t][v][0], dy = 2 * kToff[t][v][1], dz = 2 * kToff[t][v][2];
-      idx[v] = rs[dy][dz] + 2 * i + dx;
-    }
+    for (int v = 0; v < 4; ++v)
+      cid[v] = 2 * kToff[t][v][0] + 6 * kToff[t][v][1] + 18 * kToff[t][v][2];
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
       const int va = kEdge[e][0], vb = kEdge[e][1];
-      const int dx = kToff[t][va][0] + kToff[t][vb][0];
-      const int dy = kToff[t][va][1] + kToff[t][vb][1];
-      const int dz = kToff[t][va][2] + kToff[t][vb][2];
-      idx[4 + e] = rs[dy][dz] + 2 * i + dx;
+      cid[4 + e] = (kToff[t][va][0] + kToff[t][vb][0]) + 3 * (kToff[t][va][1] + kToff[t][vb][1]) +
+                   9 * (kToff[t][va][2] + kToff[t][vb][2]);
     }
     T xv[10], yv[10];
 #pragma unroll
-    for (int v = 0; v < 10; ++v) xv[v] = MODE == P2_DIAG ? T(0) : xc[idx[v]];
+    for (int v = 0; v < 10; ++v) xv[v] = X[cid[v]];
     p2_element<T, MODE>(C, t, sxyz, xv, yv);
 #pragma unroll
-    for (int v = 0; v < 10; ++v) yc[idx[v]] += yv[v];
+    for (int v = 0; v < 10; ++v) Y[cid[v]] += yv[v];
+  }
+#pragma unroll
+  for (int c = 0; c < 27; ++c) {
+    const int dx = c % 3, dy = (c / 3) % 3, dz = c / 9;
+    if (2 * s + dx + dy + dz <= 2 * n) {
+      const int q = rs[dy][dz] + 2 * i + dx;
+      yc[q] += Y[c];
+    }
   }
 }
 
