@@ -306,7 +306,7 @@ P2_FLOPS_PER_CELL = 14 * 2 * (3 + 1 + 4 + 16 + 20 + 16)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def p2_comparison(stream, level=6):
+def p2_comparison(stream, level=6, solve=True):
     """P2 -div(k grad), k = 1 + 0.5 sin(2 pi x) sin(2 pi y) sin(2 pi z), on the
     unit cube as 2x2x2 sub-cubes x 6 Kuhn tetrahedra (48 macro cells), P2
     level 6 (257^3 DoFs): FP32 element-wise apply (on-the-fly quadrature), and
@@ -350,6 +350,8 @@ def p2_comparison(stream, level=6):
                                                         "unit": "TFLOP/s",
                                                         "frac": tflops / FP32_PEAK_TFLOPS}}}
     del xs, ys
+    if not solve:
+        return out
     u, f = sg.sinprod_manufactured(xyz, *sg.SINPROD_AB)
     b = H.zeros(level, torch.float64, space=P2)
     mass.apply(level, H.from_canonical(level, torch.tensor(f, device="cuda"), space=P2), b,
@@ -419,6 +421,8 @@ def main():
     ap.add_argument("--no-gmg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-p2", action="store_true")
+    ap.add_argument("--no-p2-solve", action="store_true",
+                    help="P2 leg: apply only (for profiling)")
     ap.add_argument("--p2-level", type=int, default=6,
                     help="P2 level of the P2 leg (6 = the 17 M DoF workload; smaller for profiling)")
     args = ap.parse_args()
@@ -474,30 +478,56 @@ def main():
     clk = clocks.stop()
     ms_step, value = aggregate_replicas(ms, nu, args.steps, pg, "cuda")
 
-    # end to end: canonical host vector -> device -> apply -> host, pinned buffers
-    xh = torch.tensor(sg.uniform_vector(7, nu), dtype=dt).pin_memory()
-    xh[torch.from_numpy(dirich.astype(bool))] = 0
-    yh = torch.empty(nu, dtype=dt).pin_memory()
-    xd = torch.empty(nu, dtype=dt, device="cuda")
-    xst, yst = H.zeros(LEVEL, dt), H.zeros(LEVEL, dt)
-    e2e_steps = max(10, args.steps // 4)
+    # end to end through the public API: every step copies its canonical input
+    # from pinned host memory, scatters it to the stored layout, applies the
+    # operator, gathers the result and copies it to pinned host memory.  Steps
+    # are pipelined over three buffer sets and three streams (H2D, compute,
+    # D2H), so one step's copies overlap the neighbouring steps' kernels.
+    NB = 3
+    s_in, s_c, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+    x0h = torch.tensor(sg.uniform_vector(7, nu), dtype=dt)
+    x0h[torch.from_numpy(dirich.astype(bool))] = 0
+    bufs = []
+    for _ in range(NB):
+        bufs.append({"xh": x0h.clone().pin_memory(), "yh": torch.empty(nu, dtype=dt).pin_memory(),
+                     "xd": torch.empty(nu, dtype=dt, device="cuda"),
+                     "yd": torch.empty(nu, dtype=dt, device="cuda"),
+                     "xs": H.zeros(LEVEL, dt), "ys": H.zeros(LEVEL, dt),
+                     "ein": torch.cuda.Event(), "eout": torch.cuda.Event(),
+                     "efree": torch.cuda.Event()})
+    for b in bufs:
+        b["efree"].record(s_out)
+    e2e_steps = max(12, args.steps // 4)
 
-    def e2e_step():
-        xd.copy_(xh, non_blocking=True)
-        H.from_canonical(LEVEL, xd, out=xst, stream=stream)
-        op.apply(LEVEL, xst, yst, stream=stream)
-        yd = H.to_canonical(LEVEL, yst, stream=stream)
-        yh.copy_(yd, non_blocking=True)
+    def e2e_step(q):
+        b = bufs[q % NB]
+        s_in.wait_event(b["efree"])
+        with torch.cuda.stream(s_in):
+            b["xd"].copy_(b["xh"], non_blocking=True)
+        b["ein"].record(s_in)
+        s_c.wait_event(b["ein"])
+        H.from_canonical(LEVEL, b["xd"], out=b["xs"], stream=s_c)
+        op.apply(LEVEL, b["xs"], b["ys"], stream=s_c)
+        H.to_canonical(LEVEL, b["ys"], stream=s_c, out=b["yd"])
+        b["eout"].record(s_c)
+        s_out.wait_event(b["eout"])
+        with torch.cuda.stream(s_out):
+            b["yh"].copy_(b["yd"], non_blocking=True)
+        b["efree"].record(s_out)
 
-    for _ in range(3):
-        e2e_step()
+    for q in range(2 * NB):
+        e2e_step(q)
     torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
-    e1.record(stream)
+    e0.record(s_in)
+    for q in range(e2e_steps):
+        e2e_step(q)
+    e1.record(s_out)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    ref_y = torch.zeros(nu, dtype=dt, device="cuda")
+    H.to_canonical(LEVEL, bufs[0]["ys"], out=ref_y)
+    if not torch.equal(bufs[0]["yh"], ref_y.cpu()):
+        raise RuntimeError("e2e: host result differs from the device result")
 
     peak, peak_kind = _peaks()
     achieved = BYTES_PER_DOF * nu / (ms_step * 1e-3) / 1e9
@@ -525,7 +555,7 @@ def main():
     if rank == 0 and not args.no_batch:
         out["batch"] = batch_comparison(stream)
     if rank == 0 and not args.no_p2:
-        out["p2"] = p2_comparison(stream, args.p2_level)
+        out["p2"] = p2_comparison(stream, args.p2_level, solve=not args.no_p2_solve)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_spmv()
     if rank == 0:

@@ -195,12 +195,13 @@ class Hierarchy:
         import torch
         return torch.zeros(self.size(level, space)[0], dtype=dtype, device="cuda")
 
-    def to_canonical(self, level, x, space=HG_SPACE_P1, stream=None):
+    def to_canonical(self, level, x, space=HG_SPACE_P1, stream=None, out=None):
         import torch
         ns, nu, _, _ = self.size(level, space)
-        out = torch.empty(nu, dtype=x.dtype, device=x.device)
+        if out is None:
+            out = torch.empty(nu, dtype=x.dtype, device=x.device)
         _call("hg_to_canonical", self._h, space, level, _dtype_code(x), _ptr(x, ns),
-              _ptr(out), _stream(stream))
+              _ptr(out, nu), _stream(stream))
         return out
 
     def from_canonical(self, level, c, out=None, space=HG_SPACE_P1, stream=None):
