@@ -247,7 +247,8 @@ def batch_comparison(stream, count=512):
             H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 0, L)
             op = hg.Operator(H)
             _, xyz, dirich = H.canonical_info(L)
-            shared[(m, L)] = [H, op, hg.GMG(op), False, len(xyz), dirich]
+            shared[(m, L)] = [H, op, hg.GMG(op, inner_cycles=INNER_CYCLES), False, len(xyz),
+                              dirich]
         H, op, G0, used, nu, dirich = shared[(m, L)]
         Gs.append(G0.clone() if used else G0)
         shared[(m, L)][3] = True
@@ -285,6 +286,7 @@ def batch_comparison(stream, count=512):
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1) / 1e3
     return {"workload": BATCH_WORKLOAD, "problems": count, "unique_dofs_total": int(dofs),
+            "fp32_cycles_per_refinement_step": INNER_CYCLES,
             "hierarchies": len(shared), "tol": 1e-8, "setup_s": setup_s,
             "batched": {"s": t_batch, "s_all": times, "iters_max": int(it.max()),
                         "iters_mean": float(it.mean()), "rel_res_max": float(rel.max()),
