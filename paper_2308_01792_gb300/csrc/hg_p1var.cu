@@ -35,42 +35,47 @@ __device__ constexpr int kInc[24][4] = {
     {10, 8, 0, 1},  {6, 4, 2, 0},   {0, 13, 8, 11}, {14, 0, 6, 2},   {7, 5, 0, 9},   {12, 1, 10, 0},
     {0, 13, 11, 5}, {14, 0, 2, 7},  {12, 1, 0, 3},  {6, 8, 4, 0},    {0, 13, 5, 1},  {14, 0, 7, 12},
     {6, 8, 0, 10},  {2, 11, 9, 0},  {0, 13, 1, 8},  {14, 0, 12, 6},  {2, 11, 0, 4},  {7, 5, 3, 0}};
-// Vertex offsets of the six subgroups and their width deficit (w = n - delta).
-__device__ constexpr int kOff[6][4][3] = {
-    {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}},
-    {{0, 1, 0}, {1, 0, 1}, {1, 0, 0}, {0, 0, 1}}, {{0, 1, 0}, {1, 0, 1}, {0, 0, 1}, {0, 1, 1}},
-    {{0, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 0}}, {{0, 1, 0}, {1, 0, 1}, {1, 1, 0}, {1, 0, 0}}};
-__device__ constexpr int kDelta[6] = {0, 2, 1, 1, 1, 1};
 
 // Mask of the incidences whose micro-cell lies inside the macro cell for a
-// point of boundary class cls (bit f: on the face opposite local vertex f).
-__device__ __forceinline__ unsigned incidence_mask(int cls) {
+// point of boundary class cls (bit f: on the face opposite local vertex f),
+// one entry per class, fixed at compile time.
+__host__ __device__ constexpr unsigned incidence_mask_of(int cls) {
+  constexpr int off[6][4][3] = {
+      {{0, 0, 0}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}}, {{1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}},
+      {{0, 1, 0}, {1, 0, 1}, {1, 0, 0}, {0, 0, 1}}, {{0, 1, 0}, {1, 0, 1}, {0, 0, 1}, {0, 1, 1}},
+      {{0, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 0}}, {{0, 1, 0}, {1, 0, 1}, {1, 1, 0}, {1, 0, 0}}};
+  constexpr int delta[6] = {0, 2, 1, 1, 1, 1};
   unsigned m = 0;
-#pragma unroll
   for (int q = 0; q < 24; ++q) {
     const int t = q / 4, a = q % 4;
-    const int* o = kOff[t][a];
+    const int* o = off[t][a];
     bool in = !((o[0] && (cls & 2)) || (o[1] && (cls & 4)) || (o[2] && (cls & 8)));
-    if (o[0] + o[1] + o[2] == kDelta[t] && (cls & 1)) in = false;
+    if (o[0] + o[1] + o[2] == delta[t] && (cls & 1)) in = false;
     m |= in ? (1u << q) : 0u;
   }
   return m;
 }
+__device__ constexpr unsigned kIncMask[16] = {
+    incidence_mask_of(0),  incidence_mask_of(1),  incidence_mask_of(2),  incidence_mask_of(3),
+    incidence_mask_of(4),  incidence_mask_of(5),  incidence_mask_of(6),  incidence_mask_of(7),
+    incidence_mask_of(8),  incidence_mask_of(9),  incidence_mask_of(10), incidence_mask_of(11),
+    incidence_mask_of(12), incidence_mask_of(13), incidence_mask_of(14), incidence_mask_of(15)};
+__device__ __forceinline__ unsigned incidence_mask(int cls) { return kIncMask[cls & 15]; }
 
 // sum over incidences in `mask` of k_T * (K row . x_T); K: 24 x 4 of the cell.
 template <typename T, bool FULL>
 __device__ __forceinline__ T divkgrad_point(const T xv[kNDir], const T kv[kNDir],
                                             const T* __restrict__ K, unsigned mask) {
-  T acc = T(0);
+  T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
   for (int q = 0; q < 24; ++q) {
     if (!FULL && !((mask >> q) & 1u)) continue;
     const T kT = T(0.25) * (kv[kInc[q][0]] + kv[kInc[q][1]] + kv[kInc[q][2]] + kv[kInc[q][3]]);
     const T r = __ldg(K + 4 * q) * xv[kInc[q][0]] + __ldg(K + 4 * q + 1) * xv[kInc[q][1]] +
                 __ldg(K + 4 * q + 2) * xv[kInc[q][2]] + __ldg(K + 4 * q + 3) * xv[kInc[q][3]];
-    acc += kT * r;
+    acc[q & 3] += kT * r;
   }
-  return acc;
+  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 // One 4-entry element row, aligned for a single vector shared-memory read.
@@ -87,16 +92,17 @@ struct Row4 {
 template <typename T>
 __device__ __forceinline__ T divkgrad_point_sm(const T xv[kNDir], const T kv[kNDir],
                                                const typename Row4<T>::type* __restrict__ Ks) {
-  T acc = T(0);
+  // four partial sums (incidences q mod 4) shorten the dependent chain
+  T acc[4] = {T(0), T(0), T(0), T(0)};
 #pragma unroll
   for (int q = 0; q < 24; ++q) {
     const typename Row4<T>::type Kr = Ks[q];
     const T kT = T(0.25) * (kv[kInc[q][0]] + kv[kInc[q][1]] + kv[kInc[q][2]] + kv[kInc[q][3]]);
     const T r = Kr.x * xv[kInc[q][0]] + Kr.y * xv[kInc[q][1]] + Kr.z * xv[kInc[q][2]] +
                 Kr.w * xv[kInc[q][3]];
-    acc += kT * r;
+    acc[q & 3] += kT * r;
   }
-  return acc;
+  return (acc[0] + acc[1]) + (acc[2] + acc[3]);
 }
 
 template <typename T>
