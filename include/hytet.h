@@ -195,6 +195,21 @@ int hg_residual(const hg_op* op, int level, int dtype, const void* x, const void
 int hg_jacobi(const hg_op* op, int level, int dtype, double omega, const void* x,
               const void* b, void* x_out, void* stream);
 
+/* One colour sub-sweep of 4-colour Gauss-Seidel, out of place: x_out = x
+ * with the DoFs of `colour` (0..3) replaced by x + D^-1 (b - A x), every
+ * other DoF copied.  Colours 0,1,2,3 in turn (ping-ponging x and x_out) are
+ * one sweep.  The colour of a lattice point is (a X + b Y + c Z) mod 4 of its
+ * exact integer coordinates, with (a, b, c) chosen by the hierarchy so that
+ * no micro-edge joins two points of one colour.  P1 operators only; x and
+ * x_out must not alias.  Errors: HG_ERR_UNSUPPORTED (P2 operator, or no
+ * such colouring for this mesh), HG_ERR_INVALID_ARG. */
+int hg_gauss_seidel(const hg_op* op, int level, int dtype, int colour, const void* x,
+                    const void* b, void* x_out, void* stream);
+
+/* The Gauss-Seidel colours of a P1 level in canonical DoF order (host,
+ * n_unique bytes).  HG_ERR_UNSUPPORTED if the mesh admits no colouring. */
+int hg_gs_colours(const hg_hier* hier, int level, uint8_t* colours);
+
 /* Grid transfers between level and level-1 (nodal interpolation P and its
  * transpose): r_coarse = P^T r_fine (Dirichlet DoFs of r_coarse set to 0);
  * x_fine += P e_coarse (Dirichlet DoFs of x_fine untouched). */
@@ -231,11 +246,12 @@ int hg_dot_noalloc(const hg_hier* hier, int space, int level, int dtype, const v
 /* ---------------------------------------------------------- multigrid --
  * Geometric multigrid on the refinement hierarchy (multigrid by design,
  * Sec. 5.1): V(nu1,nu2) cycles with weighted-Jacobi smoothing (Sec. 5.2.1:
- * smoothers that need only the matrix-vector product and the diagonal),
+ * smoothers that need only the matrix-vector product and the diagonal) or
+ * 4-colour Gauss-Seidel (P1 operators),
  * restriction P^T and prolongation P (nodal interpolation), and an exact
  * FP64 solve on the coarsest level (dense Cholesky inverse, <= 2048
  * unknowns; built at creation by applying the operator to unit vectors).
- * Only HG_OP_P1_LAPLACE / HG_OP_P1_MASS operators are accepted so far. */
+ * Every P1 and P2 operator kind is accepted. */
 enum { HG_PREC_F64 = 0,   /* plain FP64 V-cycles                                  */
        HG_PREC_MIXED = 1  /* FP32 V-cycles inside FP64 iterative refinement: the
                              outer residual, norms and coarse solve stay FP64   */
@@ -246,7 +262,10 @@ typedef struct {
   double omega;        /* Jacobi weight (default 2/3)                            */
   int lmin;            /* coarsest level; -1 = the hierarchy's lmin              */
   int inner_cycles;    /* FP32 V-cycles per refinement step (default 1)          */
+  int smoother;        /* HG_SMOOTH_JACOBI (default) or HG_SMOOTH_GS: one step =
+                          one 4-colour Gauss-Seidel sweep (P1 operators)          */
 } hg_gmg_params;
+enum { HG_SMOOTH_JACOBI = 0, HG_SMOOTH_GS = 1 };
 
 /* Fill *p with the defaults above. */
 void hg_gmg_default_params(hg_gmg_params* p);

@@ -73,6 +73,8 @@ SIGNATURES = {
     "hg_gmg_learned_fallbacks": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "hg_gmg_clone": (_I, [_P, ctypes.POINTER(_P)]),
     "hg_quadrature_rule": (_I, [_P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "hg_gauss_seidel": (_I, [_P, _I, _I, _I, _P, _P, _P, _P]),
+    "hg_gs_colours": (_I, [_P, _I, _P]),
     "hg_batch_create": (_I, [_P, _I, _P, _P, _I, ctypes.POINTER(_P)]),
     "hg_batch_destroy": (None, [_P]),
     "hg_batch_solve": (_I, [_P, _D, _I, _P, _P, _P]),
@@ -82,11 +84,12 @@ SIGNATURES = {
 HG_BATCH_GRAPH, HG_BATCH_AUTOTUNE = 1, 2
 
 HG_PREC_F64, HG_PREC_MIXED = 0, 1
+HG_SMOOTH_JACOBI, HG_SMOOTH_GS = 0, 1
 
 
 class GmgParams(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
-                ("lmin", ctypes.c_int), ("inner_cycles", ctypes.c_int)]
+                ("lmin", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("smoother", ctypes.c_int)]
 
 _lib = None
 
@@ -243,6 +246,13 @@ class Hierarchy:
         _call("hg_dot_noalloc", self._h, space, level, _dtype_code(x), _ptr(x), _ptr(y), mask,
               _ptr(out), _stream(stream))
 
+    def gs_colours(self, level):
+        """Gauss-Seidel colour (0..3) of every unique DoF, canonical order (host)."""
+        nu = self.size(level)[1]
+        out = np.zeros(nu, dtype=np.uint8)
+        _call("hg_gs_colours", self._h, level, out.ctypes.data_as(_P))
+        return out
+
     def device_status(self, stream=None):
         _call("hg_device_status", self._h, _stream(stream))
 
@@ -274,6 +284,11 @@ class Operator:
         _call("hg_residual", self._h, level, _dtype_code(x), _ptr(x), _ptr(b), _ptr(r),
               _stream(stream))
 
+    def gauss_seidel(self, level, x, b, x_out, colour, stream=None):
+        """One colour sub-sweep (out of place) of 4-colour Gauss-Seidel."""
+        _call("hg_gauss_seidel", self._h, level, _dtype_code(x), int(colour), _ptr(x), _ptr(b),
+              _ptr(x_out), _stream(stream))
+
     def jacobi(self, level, x, b, x_out, omega=2.0 / 3.0, stream=None):
         _call("hg_jacobi", self._h, level, _dtype_code(x), float(omega), _ptr(x), _ptr(b),
               _ptr(x_out), _stream(stream))
@@ -287,10 +302,12 @@ class Operator:
 class GMG:
     """Geometric multigrid (V-cycles) for an operator on its hierarchy."""
 
-    def __init__(self, op: Operator, nu1=3, nu2=3, omega=2.0 / 3.0, lmin=-1, inner_cycles=1):
+    def __init__(self, op: Operator, nu1=3, nu2=3, omega=2.0 / 3.0, lmin=-1, inner_cycles=1,
+                 smoother=HG_SMOOTH_JACOBI):
         p = GmgParams()
         lib().hg_gmg_default_params(ctypes.byref(p))
         p.nu1, p.nu2, p.omega, p.lmin, p.inner_cycles = nu1, nu2, omega, lmin, inner_cycles
+        p.smoother = smoother
         h = _P()
         _call("hg_gmg_create", op._h, ctypes.byref(p), ctypes.byref(h))
         self._h = h

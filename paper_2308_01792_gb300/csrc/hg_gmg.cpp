@@ -60,7 +60,8 @@ struct Gmg {
     return hier->check_error();
   }
 
-  int cell_op(int l, int dt, int opk, const void* x, const void* b, void* out, cudaStream_t s) {
+  int cell_op(int l, int dt, int opk, const void* x, const void* b, void* out, cudaStream_t s,
+              int colour = 0) {
     StencilArgs a{};
     a.x = x;
     a.b = b;
@@ -69,12 +70,23 @@ struct Gmg {
     a.mode = HG_REPLACE;
     a.mask = HG_MASK_INNER;
     a.omega = prm.omega;
+    a.colour = colour;
     return op->launch(l, dt, a, s);
   }
 
   int smooth(int l, int dt, void* x, const void* b, int nu, cudaStream_t s) {
     void* t = W(dt, WT, l);
     const bool learn = learned_active && dt == HG_F32 && l == lmax;
+    if (prm.smoother == HG_SMOOTH_GS && !learn) {
+      // nu 4-colour sweeps; 4 nu sub-sweeps ping-pong x and t and end in x
+      for (int q = 0; q < nu; ++q)
+        for (int c = 0; c < 4; ++c) {
+          const void* src = (c % 2 == 0) ? x : t;
+          void* dst = (c % 2 == 0) ? t : x;
+          if (int r = cell_op(l, dt, OP_GS, src, b, dst, s, c)) return r;
+        }
+      return HG_OK;
+    }
     for (int q = 0; q < nu; ++q) {
       const void* src = (q % 2 == 0) ? x : t;
       void* dst = (q % 2 == 0) ? t : x;
@@ -307,6 +319,7 @@ void hg_gmg_default_params(hg_gmg_params* p) {
   p->omega = 2.0 / 3.0;
   p->lmin = -1;
   p->inner_cycles = 1;
+  p->smoother = HG_SMOOTH_JACOBI;
 }
 
 int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
@@ -328,6 +341,21 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
     set_error("coarsest level %d outside the operator's levels %d..%d", g->lmin, op->lmin,
               op->lmax);
     return HG_ERR_LEVEL_RANGE;
+  }
+  if (g->prm.smoother != HG_SMOOTH_JACOBI && g->prm.smoother != HG_SMOOTH_GS) {
+    set_error("unknown smoother %d", g->prm.smoother);
+    return HG_ERR_INVALID_ARG;
+  }
+  if (g->prm.smoother == HG_SMOOTH_GS) {
+    if (op->space != HG_SPACE_P1) {
+      set_error("Gauss-Seidel smoothing: P1 operators only");
+      return HG_ERR_UNSUPPORTED;
+    }
+    for (int l = g->lmin; l <= g->lmax; ++l)
+      if (!g->L(l).colour) {
+        set_error("Gauss-Seidel smoothing: this mesh admits no 4-colouring of the lattice");
+        return HG_ERR_UNSUPPORTED;
+      }
   }
   if (g->prm.nu1 < 0 || g->prm.nu2 < 0 || !(g->prm.omega > 0.0)) {
     set_error("bad smoother parameters nu1=%d nu2=%d omega=%g", g->prm.nu1, g->prm.nu2,
@@ -895,6 +923,10 @@ int hg_batch_create(hg_gmg* const* problems, int count, double* const* x, const 
     }
     if (G->op->kind != HG_OP_P1_LAPLACE && G->op->kind != HG_OP_P1_MASS) {
       set_error("hg_batch_create: problem %d: batched solves take constant-stencil operators", p);
+      return HG_ERR_UNSUPPORTED;
+    }
+    if (G->prm.smoother != HG_SMOOTH_JACOBI) {
+      set_error("hg_batch_create: problem %d: batched solves smooth with weighted Jacobi", p);
       return HG_ERR_UNSUPPORTED;
     }
     if (G->prm.nu1 != problems[0]->prm.nu1 || G->prm.nu2 != problems[0]->prm.nu2 ||

@@ -344,6 +344,27 @@ int Hier::build_level(int l) {
           }
     H.canon = canon;
     H.canon_rep = rep;
+    // Gauss-Seidel colours of the exact lattice points
+    if (mesh->gs_abc[0] >= 0) {
+      const int a = mesh->gs_abc[0], b = mesh->gs_abc[1], cc = mesh->gs_abc[2];
+      std::vector<uint8_t> col(L.n_stored, 0);
+      for (int64_t c = 0; c < mesh->nc; ++c) {
+        const int64_t* X[4];
+        for (int m = 0; m < 4; ++m) X[m] = &mesh->ixyz[3 * mesh->cells[c][m]];
+        for (int k = 0; k <= n; ++k)
+          for (int j = 0; j + k <= n; ++j)
+            for (int i = 0; i + j + k <= n; ++i) {
+              int64_t P[3];
+              for (int r = 0; r < 3; ++r)
+                P[r] = X[0][r] * n + i * (X[1][r] - X[0][r]) + j * (X[2][r] - X[0][r]) +
+                       k * (X[3][r] - X[0][r]);
+              const int64_t v = a * P[0] + b * P[1] + cc * P[2];
+              col[c * L.cell_stride + tw(w, i, j, k)] = (uint8_t)(((v % 4) + 4) % 4);
+            }
+      }
+      H.colour = col;
+      if (int r = upload(&L.colour, col)) return r;
+    }
     H.dirichlet = dir;
     H.canon_keys = uniq;
     H.canon_xyz.resize(3 * L.n_unique);
@@ -380,8 +401,39 @@ int Hier::build_level(int l) {
   return HG_OK;
 }
 
+void Mesh::find_colouring() {
+  gs_abc[0] = -1;
+  if (!grid_denom) return;
+  static const int dirs[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {-1, 1, 0},
+                                 {-1, 0, 1}, {0, -1, 1}, {1, -1, 1}};
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c < 4; ++c) {
+        bool ok = true;
+        for (int64_t e = 0; e < nc && ok; ++e) {
+          const int64_t* X[4];
+          for (int m = 0; m < 4; ++m) X[m] = &ixyz[3 * cells[e][m]];
+          for (int d = 0; d < 7 && ok; ++d) {
+            int64_t g[3];
+            for (int r = 0; r < 3; ++r)
+              g[r] = dirs[d][0] * (X[1][r] - X[0][r]) + dirs[d][1] * (X[2][r] - X[0][r]) +
+                     dirs[d][2] * (X[3][r] - X[0][r]);
+            const int64_t v = a * g[0] + b * g[1] + c * g[2];
+            if (((v % 4) + 4) % 4 == 0) ok = false;
+          }
+        }
+        if (ok) {
+          gs_abc[0] = a;
+          gs_abc[1] = b;
+          gs_abc[2] = c;
+          return;
+        }
+      }
+}
+
 int Hier::build(const Mesh* m, int lmin_, int lmax_) {
   mesh = m;
+  const_cast<Mesh*>(m)->find_colouring();
   lmin = lmin_;
   lmax = lmax_;
   lv.resize(lmax - lmin + 1);
@@ -425,6 +477,7 @@ Hier::~Hier() {
     cudaFree(L.copies);
     cudaFree(L.prim_point_base);
     cudaFree(L.citems);
+    cudaFree(L.colour);
     cudaFree(L.ptiles);
     cudaFree(L.items);
     cudaFree(L.item_prim);
@@ -960,6 +1013,36 @@ int hg_jacobi(const hg_op* op, int level, int dtype, double omega, const void* x
   a.op = OP_JACOBI;
   a.mask = HG_MASK_INNER;
   return run_cell_op(op, level, dtype, a, (cudaStream_t)stream);
+}
+
+int hg_gauss_seidel(const hg_op* op, int level, int dtype, int colour, const void* x,
+                    const void* b, void* x_out, void* stream) {
+  HG_CHECK(op, HG_ERR_INVALID_ARG, "hg_gauss_seidel: null operator");
+  HG_CHECK(op->space == HG_SPACE_P1, HG_ERR_UNSUPPORTED,
+           "hg_gauss_seidel: P1 operators only (the colouring is of the P1 lattice coupling)");
+  HG_CHECK(colour >= 0 && colour < 4, HG_ERR_INVALID_ARG, "hg_gauss_seidel: colour %d", colour);
+  HG_CHECK(b && b != x_out, HG_ERR_INVALID_ARG, "hg_gauss_seidel: b must be distinct from x_out");
+  const LevelDev* L = level_of(op->hier, op->space, level);
+  HG_CHECK(L && L->colour, HG_ERR_UNSUPPORTED,
+           "hg_gauss_seidel: this mesh admits no 4-colouring of the lattice");
+  StencilArgs a{};
+  a.x = x;
+  a.b = b;
+  a.out = x_out;
+  a.op = OP_GS;
+  a.mask = HG_MASK_INNER;
+  a.colour = colour;
+  return run_cell_op(op, level, dtype, a, (cudaStream_t)stream);
+}
+
+int hg_gs_colours(const hg_hier* h, int level, uint8_t* colours) {
+  HG_CHECK(h && colours, HG_ERR_INVALID_ARG, "hg_gs_colours: null argument");
+  const int li = lattice_index(h, HG_SPACE_P1, level);
+  HG_CHECK(li >= 0, HG_ERR_LEVEL_RANGE, "hg_gs_colours: level %d", level);
+  const LevelHost& H = h->lv[li];
+  HG_CHECK(!H.colour.empty(), HG_ERR_UNSUPPORTED, "hg_gs_colours: no 4-colouring for this mesh");
+  for (int64_t u = 0; u < H.dev.n_unique; ++u) colours[u] = H.colour[H.canon_rep[u]];
+  return HG_OK;
 }
 
 int hg_restrict(const hg_hier* h, int space, int fine_level, int dtype, const void* rf, void* rc,

@@ -33,6 +33,11 @@ struct Mesh {
   int64_t n_boundary_faces = 0;
   int grid_denom = 0;                         // D with integer xyz*D, 0 if none
   std::vector<int64_t> ixyz;
+  // 4-colouring of every level's lattice: colour = (a X + b Y + c Z) mod 4 of
+  // the exact lattice point, with (a, b, c) such that no micro-edge joins two
+  // points of one colour; gs_abc[0] < 0 if no such triple exists
+  int gs_abc[3] = {-1, 0, 0};
+  void find_colouring();
 
   int build(const double* xyz, int64_t nv, const int64_t* cells, int64_t nc);
   void cell_jacobian(int64_t c, double J[9]) const;
@@ -51,6 +56,7 @@ struct LevelHost {
   std::vector<uint8_t> dirichlet;
   std::vector<double> canon_xyz;
   std::vector<int64_t> canon_keys;  // packed (z,y,x) lattice keys, ascending
+  std::vector<uint8_t> colour;      // 4-colouring per stored point (empty if none)
 };
 
 struct Hier {

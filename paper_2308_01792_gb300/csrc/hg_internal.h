@@ -149,6 +149,7 @@ struct LevelDev {
   int n_citems, n_citems_inner;  //   points); points = floor(32 / ncopies), one lane per copy
   int4* ptiles;              // plane-window tiles of ONE cell (the same for every cell):
   int n_ptiles_cell;         //   (k | windows << 16, lane-0 offset z, j0 << 16 | i0, 0)
+  uint8_t* colour;           // Gauss-Seidel colour (0..3) per stored point, or null
 };
 
 // Windows of 30 consecutive lattice offsets per plane-window tile of the
@@ -175,7 +176,9 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // ------------------------------------------------------------ launchers
 // Operation of the cell kernel + interface kernel pair.
-enum CellOp : int { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_DIAG = 3 };
+// OP_GS: one colour sub-sweep of Gauss-Seidel, out of place (points of other
+// colours copied)
+enum CellOp : int { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_DIAG = 3, OP_GS = 6 };
 
 struct StencilArgs {
   const void* x;        // input
@@ -184,6 +187,7 @@ struct StencilArgs {
   const void* sten;     // [ncells][16][16] T (class, direction)
   double omega;
   int op, mode, mask;
+  int colour;           // OP_GS: the colour updated
 };
 
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);

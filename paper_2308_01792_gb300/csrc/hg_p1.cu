@@ -59,6 +59,8 @@ struct FusedArgs {
   const T* sten;
   T omega;
   int mode, mask;
+  const uint8_t* colour;  // OP_GS: colour per stored point
+  int gs_colour;          // OP_GS: the colour updated
   int* err;            // device error word (bounded waits record HG_ERR_TIMEOUT)
 };
 
@@ -148,7 +150,7 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
   }
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
-    v = OP == OP_JACOBI ? A.x[idx0] : T(0);
+    v = (OP == OP_JACOBI || OP == OP_GS) ? A.x[idx0] : T(0);
   } else {
     T sum = T(0), diag = T(0);
     for (int q = 0; q < ncopies; ++q) {
@@ -160,12 +162,14 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
                            A.sten + (int64_t)cell * 256 + point_class(n, i, j, k) * 16, n, w, i,
                            j, k, sv, xv);
       sum += dot15<T>(sv, xv);
-      if (OP == OP_JACOBI) diag += sv[0];
+      if (OP == OP_JACOBI || OP == OP_GS) diag += sv[0];
     }
     if (OP == OP_APPLY) {
       v = A.mode == HG_ADD ? A.y[idx0] + sum : sum;
     } else if (OP == OP_RESID) {
       v = A.b[idx0] - sum;
+    } else if (OP == OP_GS) {
+      v = A.colour[idx0] == A.gs_colour ? A.x[idx0] + (A.b[idx0] - sum) / diag : A.x[idx0];
     } else {
       v = A.x[idx0] + A.omega * (A.b[idx0] - sum) / diag;
     }
@@ -198,7 +202,7 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
   const int64_t g = cbase + tw32(w, i, j, k);
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
-    v = OP == OP_JACOBI ? A.x[g] : T(0);
+    v = (OP == OP_JACOBI || OP == OP_GS) ? A.x[g] : T(0);
   } else {
     T sv[kNDir], xv[kNDir];
     cell_partial_load<T>(A.x + cbase, A.sten + (int64_t)cpy.cell * 256 + point_class(n, i, j, k) * 16,
@@ -209,12 +213,14 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
     const int g0 = pt * C;
     for (int q = 0; q < C; ++q) {
       sum += __shfl_sync(0xffffffffu, part, (g0 + q) & 31);
-      if (OP == OP_JACOBI) diag += __shfl_sync(0xffffffffu, sv[0], (g0 + q) & 31);
+      if (OP == OP_JACOBI || OP == OP_GS) diag += __shfl_sync(0xffffffffu, sv[0], (g0 + q) & 31);
     }
     if (OP == OP_APPLY) {
       v = A.mode == HG_ADD ? A.y[g] + sum : sum;
     } else if (OP == OP_RESID) {
       v = A.b[g] - sum;
+    } else if (OP == OP_GS) {
+      v = A.colour[g] == A.gs_colour ? A.x[g] + (A.b[g] - sum) / diag : A.x[g];
     } else {
       v = A.x[g] + A.omega * (A.b[g] - sum) / diag;
     }
@@ -285,6 +291,8 @@ __device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const Plane
       y[idx] = A.mode == HG_ADD ? y[idx] + acc : acc;
     } else if (OP == OP_RESID) {
       y[idx] = A.b[base + idx] - acc;
+    } else if (OP == OP_GS) {
+      y[idx] = A.colour[base + idx] == A.gs_colour ? W.c + (A.b[base + idx] - acc) * wd : W.c;
     } else {
       y[idx] = W.c + (A.b[base + idx] - acc) * wd;
     }
@@ -309,7 +317,7 @@ __device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lan
   T s[kNDir];
 #pragma unroll
   for (int d = 0; d < kNDir; ++d) s[d] = __ldg(S + d);
-  const T wd = OP == OP_JACOBI ? A.omega / s[0] : T(0);
+  const T wd = OP == OP_JACOBI ? A.omega / s[0] : OP == OP_GS ? T(1) / s[0] : T(0);
   const bool halo = lane == 0 || lane == 31;
   PlanePos P;
   P.j = tl.z >> 16;
@@ -420,6 +428,8 @@ FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
   A.omega = (T)a.omega;
   A.mode = a.mode;
   A.mask = a.mask;
+  A.colour = L.colour;
+  A.gs_colour = a.colour;
   A.err = L.err;
   return A;
 }
@@ -441,6 +451,7 @@ int run_p1_op(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
     case OP_APPLY: return run_p1<T, OP_APPLY>(L, a, s);
     case OP_RESID: return run_p1<T, OP_RESID>(L, a, s);
     case OP_JACOBI: return run_p1<T, OP_JACOBI>(L, a, s);
+    case OP_GS: return run_p1<T, OP_GS>(L, a, s);
   }
   set_error("unknown cell operation %d", a.op);
   return HG_ERR_INVALID_ARG;

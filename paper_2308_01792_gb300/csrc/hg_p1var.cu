@@ -123,6 +123,8 @@ struct VarArgs {
   const T* invdiag;  // stored 1/diag (Jacobi)
   T omega;
   int op, mode, mask;
+  const uint8_t* colour;  // OP_GS: colour per stored point
+  int gs_colour;
 };
 
 // 15-point neighbourhood of a cell-local point from global memory (values
@@ -187,7 +189,7 @@ __device__ void var_interface_point(const VarArgs<T>& A, const int4& it, int lan
   }
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER) && OP != OP_DIAG) {
-    v = OP == OP_JACOBI ? A.x[idx0] : T(0);
+    v = (OP == OP_JACOBI || OP == OP_GS) ? A.x[idx0] : T(0);
   } else {
     T sum = T(0);
     for (int q = 0; q < ncopies; ++q) {
@@ -209,6 +211,9 @@ __device__ void var_interface_point(const VarArgs<T>& A, const int4& it, int lan
       v = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[idx0] + sum : sum;
     } else if (OP == OP_RESID) {
       v = A.b[idx0] - sum;
+    } else if (OP == OP_GS) {
+      v = A.colour[idx0] == A.gs_colour ? A.x[idx0] + (A.b[idx0] - sum) * A.invdiag[idx0]
+                                        : A.x[idx0];
     } else {
       v = A.x[idx0] + A.omega * (A.b[idx0] - sum) * A.invdiag[idx0];
     }
@@ -241,7 +246,7 @@ __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
   const int64_t g = cbase + tw32(w, i, j, k);
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER) && OP != OP_DIAG) {
-    v = OP == OP_JACOBI ? A.x[g] : T(0);
+    v = (OP == OP_JACOBI || OP == OP_GS) ? A.x[g] : T(0);
   } else {
     T xv[kNDir], kv[kNDir];
     if (OP == OP_DIAG) {
@@ -260,6 +265,8 @@ __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
       v = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[g] + sum : sum;
     } else if (OP == OP_RESID) {
       v = A.b[g] - sum;
+    } else if (OP == OP_GS) {
+      v = A.colour[g] == A.gs_colour ? A.x[g] + (A.b[g] - sum) * A.invdiag[g] : A.x[g];
     } else {
       v = A.x[g] + A.omega * (A.b[g] - sum) * A.invdiag[g];
     }
@@ -359,6 +366,8 @@ __device__ void var_plane_tile(const VarArgs<T>& A, int t, int lane,
         A.y[idx] = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[idx] + acc : acc;
       } else if (OP == OP_RESID) {
         A.y[idx] = A.b[idx] - acc;
+      } else if (OP == OP_GS) {
+        A.y[idx] = A.colour[idx] == A.gs_colour ? xr[0] + (A.b[idx] - acc) * A.invdiag[idx] : xr[0];
       } else {
         A.y[idx] = xr[0] + A.omega * (A.b[idx] - acc) * A.invdiag[idx];
       }
@@ -403,6 +412,8 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.op = a.op;
   A.mode = a.mode;
   A.mask = a.mask;
+  A.colour = L.colour;
+  A.gs_colour = a.colour;
   const int grid = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   if (grid == 0) return HG_OK;
   p1var_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
@@ -417,6 +428,7 @@ int run_var_op(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaS
     case OP_RESID: return run_var<T, OP_RESID>(L, a, vc, s);
     case OP_JACOBI: return run_var<T, OP_JACOBI>(L, a, vc, s);
     case OP_DIAG: return run_var<T, OP_DIAG>(L, a, vc, s);
+    case OP_GS: return run_var<T, OP_GS>(L, a, vc, s);
   }
   set_error("unknown cell operation %d", a.op);
   return HG_ERR_INVALID_ARG;
