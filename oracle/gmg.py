@@ -11,14 +11,24 @@ standard algorithm written out on SciPy CSR matrices:
   coarse quadratics evaluated at the fine DoF points).  R_l = P_l^T.
 * Coarse operators by rediscretisation on the coarse mesh.
 * Smoothers: weighted Jacobi x += w D^-1 (b - A x) (the paper names
-  matvec+diagonal smoothers, Sec. 5.2.1) or 4-colour Gauss-Seidel.
+  matvec+diagonal smoothers, Sec. 5.2.1), 4-colour Gauss-Seidel, or
+  Chebyshev-accelerated Jacobi (Sec. 5.2.1 and the FMG solver of Sec. 6:
+  Chebyshev smoothers of order 2 after Adams et al. 2003): the Chebyshev
+  semi-iteration for D^-1 A on [0.1, 1.1] * lambda_max, lambda_max from a
+  fixed power iteration on D^-1 A.
+* ``fmg``: full multigrid (nested iteration, Sec. 6: five V(1,1) cycles per
+  level): the right-hand side is restricted to every level, the coarsest is
+  solved exactly, and each finer level starts from the prolongated coarser
+  solution and runs a fixed number of V-cycles.
 * V(nu1,nu2) recursion with a dense Cholesky solve on the coarsest level.
 * ``solve``: x0 = 0, one V-cycle per iteration, stop when
   ||b - A x||_2 <= tol ||b||_2 on the interior DoFs.
 
 Parity: pinned by contraction-rate and O(h^2) convergence tests, by the
-Galerkin identity P^T A_f P = A_c for the P1 Laplacian, and by exact
-solutions of the coarse problem.
+Galerkin identity P^T A_f P = A_c for the P1 Laplacian, by exact solutions of
+the coarse problem, by the closed-form Chebyshev error polynomial on a
+diagonal matrix, by the power-iteration limit, and by FMG reaching an
+algebraic error below the discretization error.
 """
 from __future__ import annotations
 
@@ -182,3 +192,50 @@ def solve(H: Hierarchy, b, tol=1e-10, max_iter=100, **kw):
         it += 1
         hist.append(np.linalg.norm(b - A @ x) / nb)
     return x, it, hist
+
+
+def power_lambda_max(A, D, v0, iters=20):
+    """Largest eigenvalue of D^-1 A by a fixed power iteration from v0:
+    w = D^-1 A v, lambda = ||w|| / ||v||, v = w / ||w||; returns the last lambda."""
+    v = v0 / np.linalg.norm(v0)
+    lam = 0.0
+    for _ in range(iters):
+        w = (A @ v) / D
+        nw = np.linalg.norm(w)
+        lam = nw
+        v = w / nw
+    return lam
+
+
+def chebyshev(A, D, x, b, lam_max, order=2, lo=0.1, hi=1.1):
+    """Chebyshev semi-iteration (Saad, Iterative Methods, Alg. 12.1) for
+    D^-1 A on the interval [lo, hi] * lam_max: `order` residual evaluations."""
+    a, c = lo * lam_max, hi * lam_max
+    theta, delta = 0.5 * (c + a), 0.5 * (c - a)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    r = b - A @ x
+    d = r / (D * theta)
+    x = x + d
+    for _ in range(order - 1):
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        r = b - A @ x
+        d = rho_new * rho * d + (2.0 * rho_new / delta) * (r / D)
+        x = x + d
+        rho = rho_new
+    return x
+
+
+def fmg(H: Hierarchy, b, cycles=5, nu1=1, nu2=1, smoother=None, **kw):
+    """Full multigrid for the finest-level right-hand side b (interior DoFs):
+    b restricted to every level (b_{l-1} = P_l^T b_l), exact coarsest solve,
+    then on each finer level x_l = P_l x_{l-1} followed by `cycles` V-cycles."""
+    bs = {H.lmax: b}
+    for l in range(H.lmax, H.lmin, -1):
+        bs[l - 1] = H.P[l].T @ bs[l]
+    x = vcycle(H, H.lmin, np.zeros_like(bs[H.lmin]), bs[H.lmin])
+    for l in range(H.lmin + 1, H.lmax + 1):
+        x = H.P[l] @ x
+        for _ in range(cycles):
+            x = vcycle(H, l, x, bs[l], nu1, nu2, smoother=smoother, **kw)
+    return x

@@ -100,3 +100,67 @@ def test_gauss_seidel_colouring_is_conflict_free_and_converges():
     for _ in range(20):
         x = gmg.gauss_seidel_colours(lev.A, lev.D, x, b, colour)
     assert np.linalg.norm(b - lev.A @ x) < r0
+
+
+def test_chebyshev_error_polynomial_on_diagonal_matrix():
+    """For A = diag(lam) and D = I the Chebyshev step with b = 0 multiplies each
+    error component by the scaled Chebyshev polynomial T_k((theta - lam)/delta) /
+    T_k(theta/delta) (closed form), k = order."""
+    import scipy.sparse as sp
+    lam = np.linspace(0.05, 2.0, 37)
+    A = sp.diags(lam).tocsr()
+    D = np.ones_like(lam)
+    e0 = np.ones_like(lam)
+    lmax = 2.0
+    for order in (1, 2, 3):
+        e = gmg.chebyshev(A, D, e0.copy(), np.zeros_like(lam), lmax, order=order)
+        a, c = 0.1 * lmax, 1.1 * lmax
+        theta, delta = (a + c) / 2, (c - a) / 2
+        Tk = np.polynomial.chebyshev.Chebyshev.basis(order)
+        assert np.allclose(e, Tk((theta - lam) / delta) / Tk(theta / delta), rtol=1e-12, atol=1e-14)
+
+
+def test_chebyshev_order_one_is_weighted_jacobi():
+    H = gmg.Hierarchy(sg.kuhn_cube(1), 1, 3)
+    lev = H.levels[3]
+    x = sg.uniform_vector(3, len(lev.interior))
+    b = sg.uniform_vector(4, len(lev.interior))
+    lmax = 1.7
+    theta = 0.6 * lmax
+    assert np.allclose(gmg.chebyshev(lev.A, lev.D, x, b, lmax, order=1),
+                       gmg.jacobi(lev.A, lev.D, x, b, 1.0 / theta), rtol=1e-14, atol=1e-14)
+
+
+def test_power_iteration_finds_the_largest_eigenvalue():
+    import scipy.sparse as sp
+    lam = np.array([0.3, 1.0, 2.5, 0.7])
+    A = sp.diags(lam).tocsr()
+    got = gmg.power_lambda_max(A, np.ones(4), np.ones(4), iters=200)
+    assert abs(got - 2.5) < 1e-12
+    H = gmg.Hierarchy(sg.kuhn_cube(1), 2, 3)
+    lev = H.levels[3]
+    dense = np.linalg.eigvals(np.diag(1 / lev.D) @ lev.A.toarray()).real.max()
+    est = gmg.power_lambda_max(lev.A, lev.D, sg.uniform_vector(9, len(lev.interior)), iters=400)
+    assert abs(est - dense) < 1e-3 * dense and est <= dense * (1 + 1e-12)
+
+
+def test_fmg_reaches_discretization_accuracy():
+    """FMG with 5 V(1,1) Chebyshev-smoothed cycles per level on the manufactured
+    Poisson problem (u = sin pi x sin pi y sin pi z on the unit cube): the
+    algebraic error ||x - x_h|| is far below the discretization error ||x_h - u||."""
+    import scipy.sparse.linalg as spla
+    H = gmg.Hierarchy(sg.kuhn_cube(1), 1, 4)
+    lev = H.levels[4]
+    f = 3 * np.pi ** 2 * np.prod(np.sin(np.pi * lev.xyz), axis=1)
+    b = (lev.M_full @ f)[lev.interior]
+    lam = {len(H.levels[l].interior): gmg.power_lambda_max(
+        H.levels[l].A, H.levels[l].D, sg.uniform_vector(11, len(H.levels[l].interior)))
+        for l in range(2, 5)}
+
+    def cheb(A, D, x, bb):
+        return gmg.chebyshev(A, D, x, bb, lam[len(x)])
+
+    x = gmg.fmg(H, b, cycles=5, nu1=1, nu2=1, smoother=cheb)
+    xh = spla.spsolve(lev.A.tocsc(), b)
+    u = np.prod(np.sin(np.pi * lev.xyz), axis=1)[lev.interior]
+    assert np.linalg.norm(x - xh) < 0.05 * np.linalg.norm(xh - u)
