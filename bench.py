@@ -221,6 +221,32 @@ def gmg_comparison(stream):
         del G
     out["learned_vs_plain_f64_speedup"] = out["plain_f64"]["s"] / out["learned_mixed"]["s"]
     out["learned_vs_mixed_speedup"] = out["mixed_f32_ir"]["s"] / out["learned_mixed"]["s"]
+    # Chebyshev-accelerated Jacobi of order 2, V(1,1), FP32 cycles in FP64
+    # refinement; then full multigrid with 5 V(1,1) Chebyshev cycles per level
+    G = hg.GMG(op, nu1=1, nu2=1, inner_cycles=INNER_CYCLES, smoother=hg.HG_SMOOTH_CHEB)
+    x = H.zeros(6, torch.float64)
+    G.solve(x, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    it, rel = G.solve(x, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["cheb2_v11_mixed_f32_ir"] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel}
+    bb = H.dot(6, b, b)
+    for name, dt in (("fmg_f32", torch.float32), ("fmg_f64", torch.float64)):
+        xf = H.zeros(6, dt)
+        bf = b.to(dt)
+        G.fmg(6, xf, bf, cycles=5, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        G.fmg(6, xf, bf, cycles=5, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        r = H.zeros(6, torch.float64)
+        op.residual(6, xf.double(), b, r)
+        out[name] = {"s": e0.elapsed_time(e1) / 1e3, "cycles_per_level": 5,
+                     "rel_res": float(np.sqrt(H.dot(6, r, r) / bb))}
+    del G
     return out
 
 

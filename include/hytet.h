@@ -246,8 +246,9 @@ int hg_dot_noalloc(const hg_hier* hier, int space, int level, int dtype, const v
 /* ---------------------------------------------------------- multigrid --
  * Geometric multigrid on the refinement hierarchy (multigrid by design,
  * Sec. 5.1): V(nu1,nu2) cycles with weighted-Jacobi smoothing (Sec. 5.2.1:
- * smoothers that need only the matrix-vector product and the diagonal) or
- * 4-colour Gauss-Seidel (P1 operators),
+ * smoothers that need only the matrix-vector product and the diagonal),
+ * Chebyshev-accelerated Jacobi (Sec. 5.2.1; order 2 in the FMG solver of
+ * Sec. 6) or 4-colour Gauss-Seidel (P1 operators),
  * restriction P^T and prolongation P (nodal interpolation), and an exact
  * FP64 solve on the coarsest level (dense Cholesky inverse, <= 2048
  * unknowns; built at creation by applying the operator to unit vectors).
@@ -262,10 +263,18 @@ typedef struct {
   double omega;        /* Jacobi weight (default 2/3)                            */
   int lmin;            /* coarsest level; -1 = the hierarchy's lmin              */
   int inner_cycles;    /* FP32 V-cycles per refinement step (default 1)          */
-  int smoother;        /* HG_SMOOTH_JACOBI (default) or HG_SMOOTH_GS: one step =
-                          one 4-colour Gauss-Seidel sweep (P1 operators)          */
+  int smoother;        /* HG_SMOOTH_JACOBI (default); HG_SMOOTH_GS: one step =
+                          one 4-colour Gauss-Seidel sweep (P1 operators);
+                          HG_SMOOTH_CHEB: one step = cheb_order steps of the
+                          Chebyshev semi-iteration for D^-1 A on the interval
+                          [cheb_lo, cheb_hi] * lambda_max (any operator kind)    */
+  int cheb_order;      /* Chebyshev: matrix-vector products per step (default 2) */
+  int cheb_iters;      /* Chebyshev: power iterations per level for lambda_max at
+                          creation (default 20)                                  */
+  double cheb_lo, cheb_hi; /* Chebyshev interval in units of lambda_max
+                          (default 0.1, 1.1)                                     */
 } hg_gmg_params;
-enum { HG_SMOOTH_JACOBI = 0, HG_SMOOTH_GS = 1 };
+enum { HG_SMOOTH_JACOBI = 0, HG_SMOOTH_GS = 1, HG_SMOOTH_CHEB = 2 };
 
 /* Fill *p with the defaults above. */
 void hg_gmg_default_params(hg_gmg_params* p);
@@ -294,6 +303,33 @@ int hg_solve(hg_gmg* g, int precision, double* x, const double* b, double rel_to
 /* Relative residuals of the last solve (entry 0 = 1 for x = 0); *n gets the
  * count, at most cap values are written to out (host). */
 int hg_gmg_history(const hg_gmg* g, double* out, int cap, int* n);
+
+/* Chebyshev smoothing needs lambda_max(D^-1 A) on every smoothed level
+ * (lmin < level <= lmax).  hg_gmg_create estimates it with cheb_iters steps
+ * of the power iteration from a fixed pseudo-random start vector (SplitMix64
+ * of the canonical DoF index, in [-1, 1), 0 on Dirichlet DoFs).
+ * hg_gmg_lambda reads the value in use, hg_gmg_set_lambda replaces it
+ * (lam > 0, finite).  hg_gmg_power_lambda runs the power iteration from a
+ * caller's start vector v0 (FP64 stored vector of the level, device; its
+ * Dirichlet entries are ignored): v = v0 / ||v0||, then `iters` times
+ * w = D^-1 A v, lambda = ||w||, v = w / ||w||, 2-norms over the unique
+ * non-Dirichlet DoFs; *lam gets the last lambda (the value in use is not
+ * changed).  It uses the level's FP64 work vectors and synchronises `stream`
+ * once per step.  Errors: HG_ERR_LEVEL_RANGE, HG_ERR_INVALID_ARG (iters
+ * outside 1..10000, v0 zero on the non-Dirichlet DoFs). */
+int hg_gmg_lambda(const hg_gmg* g, int level, double* lam);
+int hg_gmg_set_lambda(hg_gmg* g, int level, double lam);
+int hg_gmg_power_lambda(hg_gmg* g, int level, const double* v0, int iters, double* lam,
+                        void* stream);
+
+/* Full multigrid (nested iteration; the paper's solver in Sec. 6 runs five
+ * V(1,1) cycles per level): b (stored vector of dtype on `level`) is
+ * restricted to every coarser level (b_{l-1} = P^T b_l), the coarsest level
+ * is solved exactly, and on each finer level l the prolongated solution of
+ * level l-1 starts `cycles` V-cycles.  x (stored vector of dtype on `level`)
+ * receives the result; its input is ignored.  Stream-ordered, no host
+ * synchronisation.  Uses the work vectors of the levels below `level`. */
+int hg_fmg(hg_gmg* g, int level, int dtype, void* x, const void* b, int cycles, void* stream);
 
 /* New GMG for the same operator and parameters with its own work vectors
  * (the coarse inverse is copied, not rebuilt); for batches of problems that

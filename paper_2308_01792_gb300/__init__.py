@@ -79,17 +79,23 @@ SIGNATURES = {
     "hg_batch_destroy": (None, [_P]),
     "hg_batch_solve": (_I, [_P, _D, _I, _P, _P, _P]),
     "hg_batch_tuning": (_I, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _PD]),
+    "hg_gmg_lambda": (_I, [_P, _I, _PD]),
+    "hg_gmg_set_lambda": (_I, [_P, _I, _D]),
+    "hg_gmg_power_lambda": (_I, [_P, _I, _P, _I, _PD, _P]),
+    "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
 }
 
 HG_BATCH_GRAPH, HG_BATCH_AUTOTUNE = 1, 2
 
 HG_PREC_F64, HG_PREC_MIXED = 0, 1
-HG_SMOOTH_JACOBI, HG_SMOOTH_GS = 0, 1
+HG_SMOOTH_JACOBI, HG_SMOOTH_GS, HG_SMOOTH_CHEB = 0, 1, 2
 
 
 class GmgParams(ctypes.Structure):
     _fields_ = [("nu1", ctypes.c_int), ("nu2", ctypes.c_int), ("omega", ctypes.c_double),
-                ("lmin", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("smoother", ctypes.c_int)]
+                ("lmin", ctypes.c_int), ("inner_cycles", ctypes.c_int), ("smoother", ctypes.c_int),
+                ("cheb_order", ctypes.c_int), ("cheb_iters", ctypes.c_int),
+                ("cheb_lo", ctypes.c_double), ("cheb_hi", ctypes.c_double)]
 
 _lib = None
 
@@ -303,11 +309,13 @@ class GMG:
     """Geometric multigrid (V-cycles) for an operator on its hierarchy."""
 
     def __init__(self, op: Operator, nu1=3, nu2=3, omega=2.0 / 3.0, lmin=-1, inner_cycles=1,
-                 smoother=HG_SMOOTH_JACOBI):
+                 smoother=HG_SMOOTH_JACOBI, cheb_order=2, cheb_iters=20, cheb_interval=(0.1, 1.1)):
         p = GmgParams()
         lib().hg_gmg_default_params(ctypes.byref(p))
         p.nu1, p.nu2, p.omega, p.lmin, p.inner_cycles = nu1, nu2, omega, lmin, inner_cycles
         p.smoother = smoother
+        p.cheb_order, p.cheb_iters = cheb_order, cheb_iters
+        p.cheb_lo, p.cheb_hi = cheb_interval
         h = _P()
         _call("hg_gmg_create", op._h, ctypes.byref(p), ctypes.byref(h))
         self._h = h
@@ -315,6 +323,26 @@ class GMG:
 
     def vcycle(self, level, x, b, stream=None):
         _call("hg_vcycle", self._h, level, _dtype_code(x), _ptr(x), _ptr(b), _stream(stream))
+
+    def fmg(self, level, x, b, cycles=5, stream=None):
+        """Full multigrid to `level`: x <- FMG(b) with `cycles` V-cycles per level."""
+        _call("hg_fmg", self._h, level, _dtype_code(x), _ptr(x), _ptr(b), cycles, _stream(stream))
+
+    def lam(self, level):
+        """lambda_max(D^-1 A) the Chebyshev smoother uses on `level`."""
+        v = ctypes.c_double()
+        _call("hg_gmg_lambda", self._h, level, ctypes.byref(v))
+        return v.value
+
+    def set_lam(self, level, lam):
+        _call("hg_gmg_set_lambda", self._h, level, float(lam))
+
+    def power_lambda(self, level, v0, iters=20, stream=None):
+        """Power-iteration estimate of lambda_max(D^-1 A) from the FP64 stored vector v0."""
+        v = ctypes.c_double()
+        _call("hg_gmg_power_lambda", self._h, level, _ptr(v0), iters, ctypes.byref(v),
+              _stream(stream))
+        return v.value
 
     def solve(self, x, b, tol=1e-8, max_iter=100, precision=HG_PREC_F64, stream=None,
               check=True):

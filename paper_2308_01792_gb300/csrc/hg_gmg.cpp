@@ -20,8 +20,11 @@ struct Gmg {
   hg_gmg_params prm{};
   int lmin = 0, lmax = 0;
   CoarseDev coarse{};
-  enum { WX = 0, WB = 1, WR = 2, WT = 3 };
-  std::vector<void*> work[2][4];  // [dtype][kind][level - lmin]
+  // work vectors per level: coarse correction, coarse rhs, residual,
+  // smoother partner, Chebyshev direction, FMG right-hand side
+  enum { WX = 0, WB = 1, WR = 2, WT = 3, WD = 4, WF = 5, NWORK = 6 };
+  std::vector<void*> work[2][NWORK];  // [dtype][kind][level - lmin]
+  std::vector<double> lam;         // Chebyshev: lambda_max(D^-1 A) per level - lmin
   double* r64 = nullptr;          // FP64 residual at lmax
   float* b32 = nullptr;           // scaled FP32 residual at lmax
   float* d32 = nullptr;           // FP32 correction at lmax
@@ -38,7 +41,7 @@ struct Gmg {
 
   int alloc_work(int dt) {
     if (!work[dt][0].empty()) return HG_OK;
-    for (int kind = 0; kind < 4; ++kind) {
+    for (int kind = 0; kind < NWORK; ++kind) {
       work[dt][kind].assign(lmax - lmin + 1, nullptr);
       for (int l = lmin; l <= lmax; ++l) {
         void* p = nullptr;
@@ -74,9 +77,144 @@ struct Gmg {
     return op->launch(l, dt, a, s);
   }
 
+  // One Chebyshev step: d = a d + beta D^-1 (b - A x), out = x + d.
+  int cheb_op(int l, int dt, const void* x, const void* b, void* out, void* d, double a,
+              double beta, cudaStream_t s) {
+    StencilArgs st{};
+    st.x = x;
+    st.b = b;
+    st.out = out;
+    st.op = OP_CHEB;
+    st.mode = HG_REPLACE;
+    st.mask = HG_MASK_INNER;
+    st.omega = beta;
+    st.dvec = d;
+    st.cheb_a = a;
+    return op->launch(l, dt, st, s);
+  }
+
+  // Power iteration for lambda_max(D^-1 A) on level l (FP64): v = masked v0,
+  // then `iters` times w = D^-1 A v / ||v||, lambda = ||w||, v = w.  The
+  // normalisation rides in the step's residual weight (b = 0, beta = -1/||v||).
+  int power_lambda(int l, const double* v0, int iters, double* out, cudaStream_t s) {
+    if (int r = alloc_work(HG_F64)) return r;
+    double* zero = (double*)W(HG_F64, WB, l);
+    double* v = (double*)W(HG_F64, WX, l);
+    double* w = (double*)W(HG_F64, WD, l);
+    double* scratch = (double*)W(HG_F64, WT, l);
+    HG_CUDA(cudaMemsetAsync(zero, 0, bytes(l, HG_F64), s));
+    HG_CUDA(cudaMemsetAsync(w, 0, bytes(l, HG_F64), s));
+    // v = v0 on the non-Dirichlet DoFs, 0 elsewhere (residual of x = 0)
+    if (int r = cell_op(l, HG_F64, OP_RESID, zero, v0, v, s)) return r;
+    double vv;
+    if (int r = dot(l, HG_F64, v, v, &vv, s)) return r;
+    if (!(vv > 0.0)) {
+      set_error("power iteration: start vector is zero on the non-Dirichlet DoFs");
+      return HG_ERR_INVALID_ARG;
+    }
+    double lam_k = 0.0;
+    for (int k = 0; k < iters; ++k) {
+      if (int r = cheb_op(l, HG_F64, v, zero, scratch, w, 0.0, -1.0 / std::sqrt(vv), s)) return r;
+      if (int r = dot(l, HG_F64, w, w, &vv, s)) return r;
+      lam_k = std::sqrt(vv);
+      if (!(vv > 0.0)) break;
+      std::swap(v, w);
+    }
+    *out = lam_k;
+    return HG_OK;
+  }
+
+  // Default start vector of the power iteration: SplitMix64 (Steele, Lea and
+  // Flood 2014) of the canonical DoF index, mapped to [-1, 1).
+  int estimate_lambdas(cudaStream_t s) {
+    lam.assign(lmax - lmin + 1, 0.0);
+    for (int l = lmin + 1; l <= lmax; ++l) {
+      const LevelHost& H = op->host(l);
+      std::vector<double> v(H.dev.n_stored, 0.0);
+      for (int64_t q = 0; q < H.dev.n_stored; ++q) {
+        const int64_t u = H.canon[q];
+        if (u < 0 || H.dirichlet[u]) continue;
+        uint64_t z = (uint64_t)u * 0x9e3779b97f4a7c15ull + 0x9e3779b97f4a7c15ull;
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        v[q] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+      }
+      double* dv = nullptr;
+      HG_CUDA(cudaMalloc(&dv, v.size() * sizeof(double)));
+      cudaError_t e = cudaMemcpy(dv, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
+      int r = e == cudaSuccess ? power_lambda(l, dv, prm.cheb_iters, &lam[l - lmin], s)
+                               : cuda_fail(e, "cudaMemcpy(power start vector)");
+      cudaError_t e2 = cudaStreamSynchronize(s);
+      cudaFree(dv);
+      if (r) return r;
+      HG_CUDA(e2);
+    }
+    return HG_OK;
+  }
+
+  // nu Chebyshev polynomials of degree cheb_order in D^-1 A on
+  // [cheb_lo, cheb_hi] lambda_max (Chebyshev semi-iteration, three-term
+  // recurrence of the directions); the steps ping-pong x and t.
+  int smooth_cheb(int l, int dt, void* x, const void* b, int nu, cudaStream_t s) {
+    void* t = W(dt, WT, l);
+    void* d = W(dt, WD, l);
+    const double lm = lam[l - lmin];
+    const double theta = 0.5 * (prm.cheb_hi + prm.cheb_lo) * lm;
+    const double delta = 0.5 * (prm.cheb_hi - prm.cheb_lo) * lm;
+    const double sigma = theta / delta;
+    int steps = 0;
+    for (int q = 0; q < nu; ++q) {
+      double rho = 1.0 / sigma;
+      for (int k = 0; k < prm.cheb_order; ++k, ++steps) {
+        const void* src = (steps % 2 == 0) ? x : t;
+        void* dst = (steps % 2 == 0) ? t : x;
+        double a = 0.0, beta = 1.0 / theta;
+        if (k > 0) {
+          const double rho_new = 1.0 / (2.0 * sigma - rho);
+          a = rho_new * rho;
+          beta = 2.0 * rho_new / delta;
+          rho = rho_new;
+        }
+        if (int r = cheb_op(l, dt, src, b, dst, d, a, beta, s)) return r;
+      }
+    }
+    if (steps % 2) HG_CUDA(cudaMemcpyAsync(x, t, bytes(l, dt), cudaMemcpyDeviceToDevice, s));
+    return HG_OK;
+  }
+
+  // Full multigrid (nested iteration) to `level`: rhs restricted to every
+  // level, exact coarsest solve, then per finer level the prolongated
+  // coarser solution followed by `cycles` V-cycles.  Level-l iterates and
+  // rhs below `level` live in the WX / WF work vectors, which the V-cycle on
+  // level l does not touch (it uses the vectors of level l-1 and below).
+  int fmg(int level, int dt, void* x, const void* b, int cycles, cudaStream_t s) {
+    auto X = [&](int l) { return l == level ? x : W(dt, WX, l); };
+    auto B = [&](int l) { return l == level ? b : (const void*)W(dt, WF, l); };
+    for (int l = level; l > lmin; --l) {
+      const int r = op->space == HG_SPACE_P2
+                        ? launch_restrict_p2(L(l), L(l - 1), dt, B(l), W(dt, WF, l - 1), s)
+                        : launch_restrict_p1(L(l), L(l - 1), dt, B(l), W(dt, WF, l - 1), s);
+      if (r) return r;
+    }
+    HG_CUDA(cudaMemsetAsync(X(lmin), 0, bytes(lmin, dt), s));
+    if (int r = launch_coarse_solve(L(lmin), coarse, dt, B(lmin), X(lmin), s)) return r;
+    for (int l = lmin + 1; l <= level; ++l) {
+      HG_CUDA(cudaMemsetAsync(X(l), 0, bytes(l, dt), s));
+      const int r = op->space == HG_SPACE_P2
+                        ? launch_prolong_p2(L(l), L(l - 1), dt, X(l - 1), X(l), s)
+                        : launch_prolong_p1(L(l), L(l - 1), dt, X(l - 1), X(l), s);
+      if (r) return r;
+      for (int c = 0; c < cycles; ++c)
+        if (int r2 = vcycle(l, dt, X(l), B(l), s)) return r2;
+    }
+    return HG_OK;
+  }
+
   int smooth(int l, int dt, void* x, const void* b, int nu, cudaStream_t s) {
     void* t = W(dt, WT, l);
     const bool learn = learned_active && dt == HG_F32 && l == lmax;
+    if (prm.smoother == HG_SMOOTH_CHEB && !learn) return smooth_cheb(l, dt, x, b, nu, s);
     if (prm.smoother == HG_SMOOTH_GS && !learn) {
       // nu 4-colour sweeps; 4 nu sub-sweeps ping-pong x and t and end in x
       for (int q = 0; q < nu; ++q)
@@ -320,6 +458,10 @@ void hg_gmg_default_params(hg_gmg_params* p) {
   p->lmin = -1;
   p->inner_cycles = 1;
   p->smoother = HG_SMOOTH_JACOBI;
+  p->cheb_order = 2;
+  p->cheb_iters = 20;
+  p->cheb_lo = 0.1;
+  p->cheb_hi = 1.1;
 }
 
 int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
@@ -342,7 +484,8 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
               op->lmax);
     return HG_ERR_LEVEL_RANGE;
   }
-  if (g->prm.smoother != HG_SMOOTH_JACOBI && g->prm.smoother != HG_SMOOTH_GS) {
+  if (g->prm.smoother != HG_SMOOTH_JACOBI && g->prm.smoother != HG_SMOOTH_GS &&
+      g->prm.smoother != HG_SMOOTH_CHEB) {
     set_error("unknown smoother %d", g->prm.smoother);
     return HG_ERR_INVALID_ARG;
   }
@@ -362,6 +505,14 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
               g->prm.omega);
     return HG_ERR_INVALID_ARG;
   }
+  if (g->prm.smoother == HG_SMOOTH_CHEB &&
+      (g->prm.cheb_order < 1 || g->prm.cheb_order > 64 || g->prm.cheb_iters < 1 ||
+       g->prm.cheb_iters > 10000 || !(g->prm.cheb_lo > 0.0) ||
+       !(g->prm.cheb_hi > g->prm.cheb_lo))) {
+    set_error("bad Chebyshev parameters order=%d iters=%d interval [%g, %g]", g->prm.cheb_order,
+              g->prm.cheb_iters, g->prm.cheb_lo, g->prm.cheb_hi);
+    return HG_ERR_INVALID_ARG;
+  }
   if (int r = g->alloc_work(HG_F64)) return r;
   const size_t nl = g->L(g->lmax).n_stored;
   HG_CUDA(cudaMalloc(&g->r64, nl * sizeof(double)));
@@ -374,6 +525,11 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
   HG_CUDA(cudaMalloc(&g->dot_dev, sizeof(double)));
   HG_CUDA(cudaMallocHost(&g->dot_host, sizeof(double)));
   if (int r = g->build_coarse()) return r;
+  if (g->prm.smoother == HG_SMOOTH_CHEB) {
+    if (int r = g->estimate_lambdas(0)) return r;
+  } else {
+    g->lam.assign(g->lmax - g->lmin + 1, 0.0);
+  }
   *out = g.release();
   return HG_OK;
 }
@@ -442,6 +598,66 @@ int hg_gmg_history(const hg_gmg* g, double* out, int cap, int* n) {
   if (out)
     for (int q = 0; q < cap && q < (int)g->history.size(); ++q) out[q] = g->history[q];
   return HG_OK;
+}
+
+static int smoothed_level(const hg_gmg* g, int level, const char* fn) {
+  if (!g) {
+    set_error("%s: null handle", fn);
+    return HG_ERR_INVALID_ARG;
+  }
+  if (level <= g->lmin || level > g->lmax) {
+    set_error("%s: level %d outside the smoothed levels %d..%d", fn, level, g->lmin + 1, g->lmax);
+    return HG_ERR_LEVEL_RANGE;
+  }
+  return HG_OK;
+}
+
+int hg_gmg_lambda(const hg_gmg* g, int level, double* lam) {
+  if (int r = smoothed_level(g, level, "hg_gmg_lambda")) return r;
+  if (!lam) {
+    set_error("hg_gmg_lambda: null output");
+    return HG_ERR_INVALID_ARG;
+  }
+  *lam = g->lam[level - g->lmin];
+  return HG_OK;
+}
+
+int hg_gmg_set_lambda(hg_gmg* g, int level, double lam) {
+  if (int r = smoothed_level(g, level, "hg_gmg_set_lambda")) return r;
+  if (!(lam > 0.0) || !std::isfinite(lam)) {
+    set_error("hg_gmg_set_lambda: lambda %g must be positive and finite", lam);
+    return HG_ERR_INVALID_ARG;
+  }
+  g->lam[level - g->lmin] = lam;
+  return HG_OK;
+}
+
+int hg_gmg_power_lambda(hg_gmg* g, int level, const double* v0, int iters, double* lam,
+                        void* stream) {
+  if (int r = smoothed_level(g, level, "hg_gmg_power_lambda")) return r;
+  if (!v0 || !lam || iters < 1 || iters > 10000) {
+    set_error("hg_gmg_power_lambda: bad argument");
+    return HG_ERR_INVALID_ARG;
+  }
+  return g->power_lambda(level, v0, iters, lam, (cudaStream_t)stream);
+}
+
+int hg_fmg(hg_gmg* g, int level, int dtype, void* x, const void* b, int cycles, void* stream) {
+  if (!g || !x || !b || x == b || cycles < 0) {
+    set_error("hg_fmg: bad argument");
+    return HG_ERR_INVALID_ARG;
+  }
+  if (level < g->lmin || level > g->lmax) {
+    set_error("level %d outside %d..%d", level, g->lmin, g->lmax);
+    return HG_ERR_LEVEL_RANGE;
+  }
+  if (dtype != HG_F32 && dtype != HG_F64) {
+    set_error("bad dtype %d", dtype);
+    return HG_ERR_INVALID_ARG;
+  }
+  if (int r = g->alloc_work(dtype)) return r;
+  g->learned_active = g->learned != nullptr;
+  return g->fmg(level, dtype, x, b, cycles, (cudaStream_t)stream);
 }
 
 }  // extern "C"
@@ -877,6 +1093,7 @@ int hg_gmg_clone(const hg_gmg* src, hg_gmg** out) {
   g->lmin = src->lmin;
   g->lmax = src->lmax;
   g->learned = src->learned;
+  g->lam = src->lam;
   if (int r = g->alloc_work(HG_F64)) return r;
   const size_t nl = g->L(g->lmax).n_stored;
   HG_CUDA(cudaMalloc(&g->r64, nl * sizeof(double)));

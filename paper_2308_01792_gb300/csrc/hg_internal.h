@@ -178,16 +178,25 @@ int cuda_fail(cudaError_t e, const char* what);
 // Operation of the cell kernel + interface kernel pair.
 // OP_GS: one colour sub-sweep of Gauss-Seidel, out of place (points of other
 // colours copied)
-enum CellOp : int { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_DIAG = 3, OP_GS = 6 };
+// OP_CHEB: one step of the Chebyshev semi-iteration for D^-1 A (Sec. 5.2.1,
+// Chebyshev-accelerated Jacobi): d' = cheb_a d + omega D^-1 (b - A x),
+// out = x + d', d <- d' in place (cheb_a == 0: d is not read).  Dirichlet
+// DoFs: out = x, d untouched.
+enum CellOp : int { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_DIAG = 3, OP_GS = 6, OP_CHEB = 7 };
+
+// True for the operations that scale the residual by the inverse diagonal.
+HG_HD constexpr bool op_scaled(int op) { return op == OP_JACOBI || op == OP_GS || op == OP_CHEB; }
 
 struct StencilArgs {
   const void* x;        // input
   const void* b;        // rhs (RESID/JACOBI)
   void* out;            // output
   const void* sten;     // [ncells][16][16] T (class, direction)
-  double omega;
+  double omega;         // JACOBI: weight; CHEB: beta of the residual term
   int op, mode, mask;
   int colour;           // OP_GS: the colour updated
+  void* dvec;           // OP_CHEB: Chebyshev direction d (read if cheb_a != 0, written)
+  double cheb_a;        // OP_CHEB: weight of the previous direction
 };
 
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);

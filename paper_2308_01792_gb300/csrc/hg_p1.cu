@@ -61,6 +61,8 @@ struct FusedArgs {
   int mode, mask;
   const uint8_t* colour;  // OP_GS: colour per stored point
   int gs_colour;          // OP_GS: the colour updated
+  T* dvec;                // OP_CHEB: direction, updated in place
+  T cheb_a;               // OP_CHEB: weight of the previous direction
   int* err;            // device error word (bounded waits record HG_ERR_TIMEOUT)
 };
 
@@ -150,7 +152,7 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
   }
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
-    v = (OP == OP_JACOBI || OP == OP_GS) ? A.x[idx0] : T(0);
+    v = op_scaled(OP) ? A.x[idx0] : T(0);
   } else {
     T sum = T(0), diag = T(0);
     for (int q = 0; q < ncopies; ++q) {
@@ -162,7 +164,7 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
                            A.sten + (int64_t)cell * 256 + point_class(n, i, j, k) * 16, n, w, i,
                            j, k, sv, xv);
       sum += dot15<T>(sv, xv);
-      if (OP == OP_JACOBI || OP == OP_GS) diag += sv[0];
+      if (op_scaled(OP)) diag += sv[0];
     }
     if (OP == OP_APPLY) {
       v = A.mode == HG_ADD ? A.y[idx0] + sum : sum;
@@ -170,6 +172,15 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
       v = A.b[idx0] - sum;
     } else if (OP == OP_GS) {
       v = A.colour[idx0] == A.gs_colour ? A.x[idx0] + (A.b[idx0] - sum) / diag : A.x[idx0];
+    } else if (OP == OP_CHEB) {
+      T dn = A.omega * (A.b[idx0] - sum) / diag;
+      if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[idx0];
+      for (int q = 0; q < ncopies; ++q) {
+        int i, j, k;
+        copy_local_ijk(cp[q], dim, wts, i, j, k);
+        A.dvec[(int64_t)cp[q].cell * A.stride + tw32(w, i, j, k)] = dn;
+      }
+      v = A.x[idx0] + dn;
     } else {
       v = A.x[idx0] + A.omega * (A.b[idx0] - sum) / diag;
     }
@@ -202,7 +213,7 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
   const int64_t g = cbase + tw32(w, i, j, k);
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
-    v = (OP == OP_JACOBI || OP == OP_GS) ? A.x[g] : T(0);
+    v = op_scaled(OP) ? A.x[g] : T(0);
   } else {
     T sv[kNDir], xv[kNDir];
     cell_partial_load<T>(A.x + cbase, A.sten + (int64_t)cpy.cell * 256 + point_class(n, i, j, k) * 16,
@@ -213,7 +224,7 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
     const int g0 = pt * C;
     for (int q = 0; q < C; ++q) {
       sum += __shfl_sync(0xffffffffu, part, (g0 + q) & 31);
-      if (OP == OP_JACOBI || OP == OP_GS) diag += __shfl_sync(0xffffffffu, sv[0], (g0 + q) & 31);
+      if (op_scaled(OP)) diag += __shfl_sync(0xffffffffu, sv[0], (g0 + q) & 31);
     }
     if (OP == OP_APPLY) {
       v = A.mode == HG_ADD ? A.y[g] + sum : sum;
@@ -221,6 +232,12 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
       v = A.b[g] - sum;
     } else if (OP == OP_GS) {
       v = A.colour[g] == A.gs_colour ? A.x[g] + (A.b[g] - sum) / diag : A.x[g];
+    } else if (OP == OP_CHEB) {
+      // every copy's lane reads and writes its own copy of d
+      T dn = A.omega * (A.b[g] - sum) / diag;
+      if (A.cheb_a != T(0) && act) dn += A.cheb_a * A.dvec[g];
+      if (act) A.dvec[g] = dn;
+      v = A.x[g] + dn;
     } else {
       v = A.x[g] + A.omega * (A.b[g] - sum) / diag;
     }
@@ -293,6 +310,11 @@ __device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const Plane
       y[idx] = A.b[base + idx] - acc;
     } else if (OP == OP_GS) {
       y[idx] = A.colour[base + idx] == A.gs_colour ? W.c + (A.b[base + idx] - acc) * wd : W.c;
+    } else if (OP == OP_CHEB) {
+      T dn = (A.b[base + idx] - acc) * wd;
+      if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[base + idx];
+      A.dvec[base + idx] = dn;
+      y[idx] = W.c + dn;
     } else {
       y[idx] = W.c + (A.b[base + idx] - acc) * wd;
     }
@@ -317,7 +339,7 @@ __device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lan
   T s[kNDir];
 #pragma unroll
   for (int d = 0; d < kNDir; ++d) s[d] = __ldg(S + d);
-  const T wd = OP == OP_JACOBI ? A.omega / s[0] : OP == OP_GS ? T(1) / s[0] : T(0);
+  const T wd = (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / s[0] : OP == OP_GS ? T(1) / s[0] : T(0);
   const bool halo = lane == 0 || lane == 31;
   PlanePos P;
   P.j = tl.z >> 16;
@@ -430,6 +452,8 @@ FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
   A.mask = a.mask;
   A.colour = L.colour;
   A.gs_colour = a.colour;
+  A.dvec = (T*)a.dvec;
+  A.cheb_a = (T)a.cheb_a;
   A.err = L.err;
   return A;
 }
@@ -452,6 +476,7 @@ int run_p1_op(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
     case OP_RESID: return run_p1<T, OP_RESID>(L, a, s);
     case OP_JACOBI: return run_p1<T, OP_JACOBI>(L, a, s);
     case OP_GS: return run_p1<T, OP_GS>(L, a, s);
+    case OP_CHEB: return run_p1<T, OP_CHEB>(L, a, s);
   }
   set_error("unknown cell operation %d", a.op);
   return HG_ERR_INVALID_ARG;

@@ -125,6 +125,8 @@ struct VarArgs {
   int op, mode, mask;
   const uint8_t* colour;  // OP_GS: colour per stored point
   int gs_colour;
+  T* dvec;                // OP_CHEB: direction, updated in place
+  T cheb_a;               // OP_CHEB: weight of the previous direction
 };
 
 // 15-point neighbourhood of a cell-local point from global memory (values
@@ -189,7 +191,7 @@ __device__ void var_interface_point(const VarArgs<T>& A, const int4& it, int lan
   }
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER) && OP != OP_DIAG) {
-    v = (OP == OP_JACOBI || OP == OP_GS) ? A.x[idx0] : T(0);
+    v = op_scaled(OP) ? A.x[idx0] : T(0);
   } else {
     T sum = T(0);
     for (int q = 0; q < ncopies; ++q) {
@@ -214,6 +216,15 @@ __device__ void var_interface_point(const VarArgs<T>& A, const int4& it, int lan
     } else if (OP == OP_GS) {
       v = A.colour[idx0] == A.gs_colour ? A.x[idx0] + (A.b[idx0] - sum) * A.invdiag[idx0]
                                         : A.x[idx0];
+    } else if (OP == OP_CHEB) {
+      T dn = A.omega * (A.b[idx0] - sum) * A.invdiag[idx0];
+      if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[idx0];
+      for (int q = 0; q < ncopies; ++q) {
+        int i, j, k;
+        copy_local_ijk(cp[q], dim, wts, i, j, k);
+        A.dvec[(int64_t)cp[q].cell * A.stride + tw32(w, i, j, k)] = dn;
+      }
+      v = A.x[idx0] + dn;
     } else {
       v = A.x[idx0] + A.omega * (A.b[idx0] - sum) * A.invdiag[idx0];
     }
@@ -246,7 +257,7 @@ __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
   const int64_t g = cbase + tw32(w, i, j, k);
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER) && OP != OP_DIAG) {
-    v = (OP == OP_JACOBI || OP == OP_GS) ? A.x[g] : T(0);
+    v = op_scaled(OP) ? A.x[g] : T(0);
   } else {
     T xv[kNDir], kv[kNDir];
     if (OP == OP_DIAG) {
@@ -267,6 +278,12 @@ __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
       v = A.b[g] - sum;
     } else if (OP == OP_GS) {
       v = A.colour[g] == A.gs_colour ? A.x[g] + (A.b[g] - sum) * A.invdiag[g] : A.x[g];
+    } else if (OP == OP_CHEB) {
+      // every copy's lane reads and writes its own copy of d
+      T dn = A.omega * (A.b[g] - sum) * A.invdiag[g];
+      if (A.cheb_a != T(0) && act) dn += A.cheb_a * A.dvec[g];
+      if (act) A.dvec[g] = dn;
+      v = A.x[g] + dn;
     } else {
       v = A.x[g] + A.omega * (A.b[g] - sum) * A.invdiag[g];
     }
@@ -368,6 +385,11 @@ __device__ void var_plane_tile(const VarArgs<T>& A, int t, int lane,
         A.y[idx] = A.b[idx] - acc;
       } else if (OP == OP_GS) {
         A.y[idx] = A.colour[idx] == A.gs_colour ? xr[0] + (A.b[idx] - acc) * A.invdiag[idx] : xr[0];
+      } else if (OP == OP_CHEB) {
+        T dn = A.omega * (A.b[idx] - acc) * A.invdiag[idx];
+        if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[idx];
+        A.dvec[idx] = dn;
+        A.y[idx] = xr[0] + dn;
       } else {
         A.y[idx] = xr[0] + A.omega * (A.b[idx] - acc) * A.invdiag[idx];
       }
@@ -414,6 +436,8 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.mask = a.mask;
   A.colour = L.colour;
   A.gs_colour = a.colour;
+  A.dvec = (T*)a.dvec;
+  A.cheb_a = (T)a.cheb_a;
   const int grid = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   if (grid == 0) return HG_OK;
   p1var_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
@@ -429,6 +453,7 @@ int run_var_op(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaS
     case OP_JACOBI: return run_var<T, OP_JACOBI>(L, a, vc, s);
     case OP_DIAG: return run_var<T, OP_DIAG>(L, a, vc, s);
     case OP_GS: return run_var<T, OP_GS>(L, a, vc, s);
+    case OP_CHEB: return run_var<T, OP_CHEB>(L, a, vc, s);
   }
   set_error("unknown cell operation %d", a.op);
   return HG_ERR_INVALID_ARG;

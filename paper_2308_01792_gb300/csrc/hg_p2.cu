@@ -240,13 +240,25 @@ struct P2Fin {
   const T* invdiag;
   T omega;
   int mode, mask;
+  T* dvec;   // OP_CHEB: direction, updated in place
+  T cheb_a;  // OP_CHEB: weight of the previous direction
 };
 
+// Result at stored position g from the summed product v; `own`: this thread
+// is the one that writes position g (OP_CHEB also updates d there).
 template <typename T, int OP>
-__device__ __forceinline__ T p2_result(const P2Fin<T>& F, int64_t g, T v) {
+__device__ __forceinline__ T p2_result(const P2Fin<T>& F, int64_t g, T v, bool own = true) {
   if (OP == OP_APPLY) return F.mode == HG_ADD ? F.y[g] + v : v;
   if (OP == OP_RESID) return F.b[g] - v;
   if (OP == OP_JACOBI) return F.x[g] + F.omega * F.invdiag[g] * (F.b[g] - v);
+  if (OP == OP_CHEB) {
+    T dn = F.omega * F.invdiag[g] * (F.b[g] - v);
+    if (own) {
+      if (F.cheb_a != T(0)) dn += F.cheb_a * F.dvec[g];
+      F.dvec[g] = dn;
+    }
+    return F.x[g] + dn;
+  }
   return v != T(0) ? T(1) / v : T(0);  // OP_INVDIAG
 }
 
@@ -277,7 +289,7 @@ __global__ void __launch_bounds__(kFinBlock) p2_finish_kernel(P2Fin<T> F) {
         const int64_t g = (int64_t)F.copies[it.x + q].cell * F.stride + tw32(w, i, j, k);
         T v;
         if (dirichlet && (OP != OP_APPLY || F.mask == HG_MASK_INNER))
-          v = OP == OP_JACOBI ? F.x[g] : T(0);
+          v = op_scaled(OP) ? F.x[g] : T(0);
         else
           v = p2_result<T, OP>(F, g, sum);
         F.y[g] = v;
@@ -298,9 +310,9 @@ __global__ void __launch_bounds__(kFinBlock) p2_finish_kernel(P2Fin<T> F) {
     for (int q = 0; q < C; ++q) sum += __shfl_sync(0xffffffffu, part, (g0 + q) & 31);
     T v;
     if (dirichlet && (OP != OP_APPLY || F.mask == HG_MASK_INNER))
-      v = OP == OP_JACOBI ? F.x[g] : T(0);
+      v = op_scaled(OP) ? F.x[g] : T(0);
     else
-      v = p2_result<T, OP>(F, g, sum);
+      v = p2_result<T, OP>(F, g, sum, act);
     if (act) F.y[g] = v;
     return;
   }
@@ -353,6 +365,8 @@ P2Fin<T> fin_args(const LevelDev& L, const StencilArgs& a, const P2Args& P, int 
   F.omega = (T)a.omega;
   F.mode = a.mode;
   F.mask = a.mask;
+  F.dvec = (T*)a.dvec;
+  F.cheb_a = (T)a.cheb_a;
   return F;
 }
 
@@ -376,6 +390,7 @@ int run_p2(const LevelDev& L, const StencilArgs& a, const P2Args& P, cudaStream_
     case OP_APPLY: return run_finish<T, OP_APPLY>(L, a, P, s);
     case OP_RESID: return run_finish<T, OP_RESID>(L, a, P, s);
     case OP_JACOBI: return run_finish<T, OP_JACOBI>(L, a, P, s);
+    case OP_CHEB: return run_finish<T, OP_CHEB>(L, a, P, s);
   }
   set_error("P2 operator: operation %d not available", a.op);
   return HG_ERR_UNSUPPORTED;
