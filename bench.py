@@ -404,6 +404,77 @@ def p2_comparison(stream, level=6, solve=True):
     return out
 
 
+STENCIL_WORKLOAD = "cube384_L6_p1_lognormal_stored_vs_onthefly"
+
+
+def stencil_comparison(stream, m=4, L=6, solve=True):
+    """P1 -div(k grad) on the 4x4x4 Kuhn cube (384 macro cells), level 6
+    (17 M DoFs), k = exp(g) log-normal (seed 1000): FP32 apply with element
+    matrices on the fly against the stored-stencil form (grid-aware
+    precomputation: 15 weights per stored point streamed from HBM), and the
+    mixed-precision GMG solve to 1e-8 with each."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    macro = sg.kuhn_cube(m)
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 0, L)
+    _, xyz, dirich = H.canonical_info(L)
+    k = sg.rff_eval_torch(sg.rff_params(1000), xyz, dtype=torch.float32)
+    t0 = time.perf_counter()
+    fly = hg.Operator(H, hg.HG_OP_P1_DIVKGRAD, coeff=k)
+    t1 = time.perf_counter()
+    st = hg.Operator(H, hg.HG_OP_P1_DIVKGRAD_STORED, coeff=k)
+    t2 = time.perf_counter()
+    ns, nu, _, _ = H.size(L)
+    n = 1 << L
+    lattice = len(macro.cells) * (n + 1) * (n + 2) * (n + 3) // 6
+    bytes_st = lattice * (15 * 4 + 4 + 4)       # weights, x and y of every stored point
+    x = H.from_canonical(L, torch.tensor(sg.uniform_vector(5, nu), dtype=torch.float32,
+                                         device="cuda"))
+    y = torch.zeros_like(x)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    out = {"workload": STENCIL_WORKLOAD if (m, L) == (4, 6) else f"cube{6 * m ** 3}_L{L}",
+           "unique_dofs": int(nu), "stored_points": int(lattice),
+           "setup_s": {"onthefly": t1 - t0, "stored": t2 - t1},
+           "stored_stencil_gb_per_level_f32": 15 * 4 * ns / 1e9,
+           "l2": "x, y and the 1.1 GB of weights exceed L2; no flush needed"}
+    peak, kind = _peaks()
+    for name, op in (("onthefly", fly), ("stored", st)):
+        for _ in range(5):
+            op.apply(L, x, y, stream=stream)
+        torch.cuda.synchronize()
+        K = 50
+        e0.record(stream)
+        for _ in range(K):
+            op.apply(L, x, y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / K * 1e-3
+        out[name] = {"apply_us": t * 1e6, "gdof_per_s": nu / t / 1e9}
+    ach = bytes_st / (out["stored"]["apply_us"] * 1e-6) / 1e9
+    out["stored"]["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                                 "frac": ach / peak, "peak_source": f"{kind} hbm_gbs",
+                                 "algorithmic_bytes_per_launch": bytes_st}
+    out["stored_vs_onthefly_apply_speedup"] = out["onthefly"]["apply_us"] / out["stored"]["apply_us"]
+    if not solve:
+        return out
+    bc = sg.uniform_vector(9, nu)
+    bc[dirich] = 0.0
+    b = H.from_canonical(L, torch.tensor(bc, device="cuda"))
+    for name, op in (("onthefly", fly), ("stored", st)):
+        G = hg.GMG(op, inner_cycles=INNER_CYCLES)
+        xs = H.zeros(L, torch.float64)
+        G.solve(xs, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        it, rel = G.solve(xs, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name]["mixed_solve"] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel}
+        del G
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -449,6 +520,10 @@ def main():
     ap.add_argument("--no-gmg", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-p2", action="store_true")
+    ap.add_argument("--no-stencil", action="store_true")
+    ap.add_argument("--stencil-case", type=int, nargs=2, default=[4, 6], metavar=("M", "LEVEL"),
+                    help="stencil leg mesh (m^3 sub-cubes x 6 cells) and level (smaller for profiling)")
+    ap.add_argument("--no-stencil-solve", action="store_true")
     ap.add_argument("--no-p2-solve", action="store_true",
                     help="P2 leg: apply only (for profiling)")
     ap.add_argument("--p2-level", type=int, default=6,
@@ -584,6 +659,9 @@ def main():
         out["batch"] = batch_comparison(stream)
     if rank == 0 and not args.no_p2:
         out["p2"] = p2_comparison(stream, args.p2_level, solve=not args.no_p2_solve)
+    if rank == 0 and not args.no_stencil:
+        out["stencil"] = stencil_comparison(stream, *args.stencil_case,
+                                            solve=not args.no_stencil_solve)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_spmv()
     if rank == 0:

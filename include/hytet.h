@@ -69,8 +69,13 @@ enum {
   HG_OP_P1_DIVKGRAD = 2, /* -div(k grad), element-wise, k_T = mean of vertex k   */
   HG_OP_P2_LAPLACE = 3,  /* P2 -div grad, element-wise                           */
   HG_OP_P2_MASS = 4,     /* P2 mass, element-wise                                */
-  HG_OP_P2_DIVKGRAD = 5  /* P2 -div(k grad), k(x) = a + b sin2pix sin2piy sin2piz
+  HG_OP_P2_DIVKGRAD = 5, /* P2 -div(k grad), k(x) = a + b sin2pix sin2piy sin2piz
                             by quadrature on the fly                             */
+  HG_OP_P1_DIVKGRAD_STORED = 6 /* HG_OP_P1_DIVKGRAD with grid-aware precomputation
+                            (Sec. 5.2): the 15-point partial stencil of every
+                            stored point kept in HBM (16 values per stored DoF
+                            and level, one padding, FP64 and FP32 copies) and
+                            streamed by the apply                               */
 };
 
 typedef struct hg_mesh hg_mesh;
@@ -159,7 +164,7 @@ int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
                       int64_t* n_rows, int64_t* max_copies, void* stream);
 
 /* ---------------------------------------------------------- operators --
- * kind: HG_OP_*.  coeff: for HG_OP_P1_DIVKGRAD, host array of k at the
+ * kind: HG_OP_*.  coeff: for HG_OP_P1_DIVKGRAD(_STORED), host array of k at the
  * unique vertices of level lmax in canonical order (injected to coarser
  * levels); for HG_OP_P2_DIVKGRAD, host {a, b}; otherwise NULL.
  * P2 operators (levels max(0, lmin-1) .. lmax-1 of the hierarchy) are

@@ -612,6 +612,10 @@ int Op::build(const Hier* h, int kind_, const double* coeff) {
   if (kind == HG_OP_P2_LAPLACE || kind == HG_OP_P2_MASS || kind == HG_OP_P2_DIVKGRAD)
     return build_p2(coeff);
   if (kind == HG_OP_P1_DIVKGRAD) return build_divkgrad(coeff);
+  if (kind == HG_OP_P1_DIVKGRAD_STORED) {
+    if (int r = build_divkgrad(coeff)) return r;
+    return build_stored();
+  }
   if (kind != HG_OP_P1_LAPLACE && kind != HG_OP_P1_MASS) {
     set_error("operator kind %d not available in this build", kind);
     return HG_ERR_UNSUPPORTED;
@@ -759,6 +763,29 @@ int Op::build_divkgrad(const double* coeff) {
   return HG_OK;
 }
 
+// Grid-aware precomputation (Sec. 5.2): the div-k-grad stencil of every
+// stored point, computed once per level in FP64 by the operator's own point
+// sum and rounded to FP32 for the FP32 copy.
+int Op::build_stored() {
+  const Hier* h = hier;
+  const int nl = h->lmax - h->lmin + 1;
+  for (int dt = 0; dt < 2; ++dt) sst[dt].assign(nl, nullptr);
+  for (int l = h->lmin; l <= h->lmax; ++l) {
+    const int li = l - h->lmin;
+    const LevelDev& L = h->lv[li].dev;
+    const int64_t n = (int64_t)16 * L.n_stored;
+    HG_CUDA(cudaMalloc(&sst[HG_F64][li], n * sizeof(double)));
+    HG_CUDA(cudaMalloc(&sst[HG_F32][li], n * sizeof(float)));
+    VarCoef vc{vk[HG_F64][li], vK[HG_F64][li], nullptr};
+    if (int r = launch_divkgrad_stencil(L, HG_F64, vc, sst[HG_F64][li], 0)) return r;
+    if (int r = launch_demote_scaled(n, (const double*)sst[HG_F64][li], 1.0,
+                                     (float*)sst[HG_F32][li], 0))
+      return r;
+    HG_CUDA(cudaDeviceSynchronize());
+  }
+  return HG_OK;
+}
+
 int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
   if (space == HG_SPACE_P2) {
     const int li = level - lmin;
@@ -779,6 +806,11 @@ int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
     VarCoef vc{vk[dtype][li], vK[dtype][li], vinv[dtype][li]};
     return launch_p1_divkgrad(L, dtype, a, vc, s);
   }
+  if (kind == HG_OP_P1_DIVKGRAD_STORED) {
+    a.sten = nullptr;
+    a.sst = sst[dtype][li];
+    return launch_p1_const(L, dtype, a, s);
+  }
   a.sten = dtype == HG_F64 ? (const void*)sten64[li] : (const void*)sten32[li];
   return launch_p1_const(L, dtype, a, s);
 }
@@ -791,7 +823,7 @@ Op::~Op() {
   for (auto p : sten64) cudaFree(p);
   for (auto p : sten32) cudaFree(p);
   for (int dt = 0; dt < 2; ++dt)
-    for (auto* v : {&vk[dt], &vK[dt], &vinv[dt]})
+    for (auto* v : {&vk[dt], &vK[dt], &vinv[dt], &sst[dt]})
       for (void* p : *v) cudaFree(p);
 }
 

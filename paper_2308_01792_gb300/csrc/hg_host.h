@@ -99,9 +99,12 @@ struct Op {
   std::vector<float*> sten32;
   // variable-coefficient P1 (per level): k at stored vertices, element rows, 1/diag
   std::vector<void*> vk[2], vK[2], vinv[2];
+  // stored-stencil P1 (per level): partial stencils of every stored point, [15][n_stored]
+  std::vector<void*> sst[2];
 
   int build(const Hier* h, int kind, const double* coeff);
   int build_divkgrad(const double* coeff);
+  int build_stored();
   // One cell operation (apply / residual / Jacobi / diagonal) of this operator.
   int launch(int level, int dtype, StencilArgs a, cudaStream_t s) const;
   ~Op();

@@ -57,6 +57,7 @@ struct FusedArgs {
   const T* b;
   T* y;
   const T* sten;
+  const T* sst;           // stored stencils [nst][16] (ST kernels) instead of sten
   T omega;
   int mode, mask;
   const uint8_t* colour;  // OP_GS: colour per stored point
@@ -95,12 +96,33 @@ __device__ __forceinline__ void prim_weights(int dim, int n, int p, int wts[3]) 
   }
 }
 
+// 15 weights of one stored stencil (16 values per point, 16-byte vector loads).
+__device__ __forceinline__ void load_sten16(const float* __restrict__ p, float s[kNDir]) {
+  const float4* q = reinterpret_cast<const float4*>(p);
+  const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
+  s[0] = a.x; s[1] = a.y; s[2] = a.z; s[3] = a.w;
+  s[4] = b.x; s[5] = b.y; s[6] = b.z; s[7] = b.w;
+  s[8] = c.x; s[9] = c.y; s[10] = c.z; s[11] = c.w;
+  s[12] = d.x; s[13] = d.y; s[14] = d.z;
+}
+__device__ __forceinline__ void load_sten16(const double* __restrict__ p, double s[kNDir]) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int v = 0; v < 7; ++v) {
+    const double2 t = __ldg(q + v);
+    s[2 * v] = t.x;
+    s[2 * v + 1] = t.y;
+  }
+  s[14] = __ldg(p + 14);
+}
+
 // Partial stencil of one cell at a cell-local point (any class).  The 7
 // rows touched are found from rs(j,k) by row-length steps:
 //   rs(j+-1,k), rs(j,k+1) = rs + ntri(w-k-1) + L, rs(j,k-1) = rs - ntri(w-k) - (L+1),
 //   rs(j-1,k+1) = rs(j,k+1) - L, rs(j+1,k-1) = rs(j,k-1) + L + 1, L = w-k-j.
 // All 15 weights and values are loaded before the sum so the loads overlap.
-template <typename T>
+// S: the class stencil, or with ST the point's own stored stencil.
+template <typename T, bool ST = false>
 __device__ __forceinline__ void cell_partial_load(const T* __restrict__ x, const T* __restrict__ S,
                                                   int n, int w, int i, int j, int k, T sv[kNDir],
                                                   T xv[kNDir]) {
@@ -110,8 +132,12 @@ __device__ __forceinline__ void cell_partial_load(const T* __restrict__ x, const
   const int rkp = r0 + ntri32(w - k - 1) + L, rkm = r0 - ntri32(w - k) - (L + 1);
   const int rjmkp = rkp - L, rjpkm = rkm + L + 1;
   const int rows[15] = {r0, r0, r0, rjp, rjm, rkp, rkm, rjp, rjm, rkp, rkm, rjmkp, rjpkm, rjmkp, rjpkm};
+  if (ST) {
+    load_sten16(S, sv);
+  } else {
 #pragma unroll
-  for (int d = 0; d < kNDir; ++d) sv[d] = __ldg(S + d);
+    for (int d = 0; d < kNDir; ++d) sv[d] = __ldg(S + d);
+  }
 #pragma unroll
   for (int d = 0; d < kNDir; ++d) {
     int di, dj, dk;
@@ -135,7 +161,7 @@ __device__ __forceinline__ T dot15(const T sv[kNDir], const T xv[kNDir]) {
 
 // Item of a primitive with more than 32 copies: one lane per point, copies
 // in turn.
-template <typename T, int OP>
+template <typename T, int OP, bool ST>
 __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, int lane) {
   const int dim = it.z & 15, ncopies = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
   const int n = A.n, w = A.w;
@@ -160,9 +186,14 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
       int i, j, k;
       copy_local_ijk(cp[q], dim, wts, i, j, k);
       const int cell = cp[q].cell;
-      cell_partial_load<T>(A.x + (int64_t)cell * A.stride,
-                           A.sten + (int64_t)cell * 256 + point_class(n, i, j, k) * 16, n, w, i,
-                           j, k, sv, xv);
+      if (ST)
+        cell_partial_load<T, true>(A.x + (int64_t)cell * A.stride,
+                                   A.sst + 16 * ((int64_t)cell * A.stride + tw32(w, i, j, k)), n,
+                                   w, i, j, k, sv, xv);
+      else
+        cell_partial_load<T>(A.x + (int64_t)cell * A.stride,
+                             A.sten + (int64_t)cell * 256 + point_class(n, i, j, k) * 16, n, w, i,
+                             j, k, sv, xv);
       sum += dot15<T>(sv, xv);
       if (op_scaled(OP)) diag += sv[0];
     }
@@ -193,12 +224,12 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
 }
 
 // Apply item: lane = pt * C + c takes copy c of point pt (C copies, C <= 32).
-template <typename T, int OP>
+template <typename T, int OP, bool ST>
 __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
   const int4 it = A.items[item];
   const int dim = it.z & 15, C = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
   if (C > 32) {
-    interface_point_serial<T, OP>(A, it, lane);
+    interface_point_serial<T, OP, ST>(A, it, lane);
     return;
   }
   const int n = A.n, w = A.w;
@@ -216,8 +247,12 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
     v = op_scaled(OP) ? A.x[g] : T(0);
   } else {
     T sv[kNDir], xv[kNDir];
-    cell_partial_load<T>(A.x + cbase, A.sten + (int64_t)cpy.cell * 256 + point_class(n, i, j, k) * 16,
-                         n, w, i, j, k, sv, xv);
+    if (ST)
+      cell_partial_load<T, true>(A.x + cbase, A.sst + 16 * g, n, w, i, j, k, sv, xv);
+    else
+      cell_partial_load<T>(A.x + cbase,
+                           A.sten + (int64_t)cpy.cell * 256 + point_class(n, i, j, k) * 16, n, w,
+                           i, j, k, sv, xv);
     const T part = dot15<T>(sv, xv);
     // partials of the point's C lanes, ascending copy (= cell) order
     T sum = T(0), diag = T(0);
@@ -246,12 +281,14 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
 }
 
 // One window of a plane tile in registers: the seven row values of the lane's
-// point, its offset and whether it is an output.
-template <typename T>
+// point, its offset and whether it is an output (ST: and the point's own
+// stored stencil).
+template <typename T, bool ST>
 struct PlaneWin {
   T c, up, dn, p1c, p1m, m1c, m1p;
   int g;
   bool ok;
+  T s[ST ? kNDir : 1];
 };
 
 // Lane position inside a plane: offset g, row j, column r, row length len.
@@ -264,9 +301,10 @@ struct PlanePos {
 // whose values the last output takes by shuffle); the row walk stays inside
 // the plane and lanes past gb+1 load at gb+1 (row length 3): in bounds, never
 // stored.
-template <typename T>
-__device__ __forceinline__ void plane_load(PlaneWin<T>& W, const T* __restrict__ x, PlanePos& P,
-                                           bool advance, int gb, int Tp, int Tm, bool halo) {
+template <typename T, bool ST>
+__device__ __forceinline__ void plane_load(PlaneWin<T, ST>& W, const T* __restrict__ x,
+                                           const T* __restrict__ sst, PlanePos& P, bool advance,
+                                           int gb, int Tp, int Tm, bool halo) {
   if (advance) {
     P.g += 30;
     P.r += 30;
@@ -283,13 +321,23 @@ __device__ __forceinline__ void plane_load(PlaneWin<T>& W, const T* __restrict__
   W.p1m = __ldg(x + gq + Tp);
   W.m1c = __ldg(x + gq - Tm - lq - 1);
   W.m1p = __ldg(x + gq - Tm);
+  if (ST) {
+    // only output lanes read weights: 64 B (FP32) per point, contiguous over the window
+    if (W.ok) {
+      load_sten16(sst + 16 * (int64_t)gq, W.s);
+    } else {
+#pragma unroll
+      for (int d = 0; d < kNDir; ++d) W.s[d] = T(0);
+    }
+  }
 }
 
 // The 15-point stencil of one window from registers and shuffles, stored.
-template <typename T, int OP>
-__device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const PlaneWin<T>& W,
-                                              const T s[kNDir], T wd, int64_t base,
+template <typename T, int OP, bool ST>
+__device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const PlaneWin<T, ST>& W,
+                                              const T sc[kNDir], T wdc, int64_t base,
                                               T* __restrict__ y) {
+  const T* s = ST ? W.s : sc;
   const T cm = __shfl_up_sync(0xffffffffu, W.c, 1), cp = __shfl_down_sync(0xffffffffu, W.c, 1);
   const T upm = __shfl_up_sync(0xffffffffu, W.up, 1);
   const T dnp = __shfl_down_sync(0xffffffffu, W.dn, 1);
@@ -304,6 +352,10 @@ __device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const Plane
   const T acc = a0 + (a1 + a2);
   if (W.ok) {
     const int idx = W.g;
+    const T wd = !ST ? wdc
+                     : (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / s[0]
+                     : OP == OP_GS                        ? T(1) / s[0]
+                                                          : T(0);
     if (OP == OP_APPLY) {
       y[idx] = A.mode == HG_ADD ? y[idx] + acc : acc;
     } else if (OP == OP_RESID) {
@@ -324,7 +376,7 @@ __device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const Plane
 // Plane-window tile t (see the file comment): its windows in order, the loads
 // of the next D windows in flight while one is computed (D = 0, 1 or 2;
 // three rotating register sets for D = 2).
-template <typename T, int OP, int D>
+template <typename T, int OP, int D, bool ST>
 __device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lane) {
   const int cell = t / A.n_tiles_cell;
   const int4 tl = A.tiles[t - cell * A.n_tiles_cell];
@@ -333,13 +385,17 @@ __device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lan
   const int64_t base = (int64_t)cell * A.stride;
   const T* __restrict__ x = A.x + base;
   T* __restrict__ y = A.y + base;
-  const T* __restrict__ S = A.sten + (int64_t)cell * 256;
   const int Tp = ntri32(w - k - 1), Tm = ntri32(w - k);
   const int gb = row_start(w, n - k - 2, k) + 1;  // last interior offset of the plane
   T s[kNDir];
+  T wd = T(0);
+  const T* __restrict__ sst = ST ? A.sst + 16 * base : nullptr;
+  if (!ST) {
+    const T* __restrict__ S = A.sten + (int64_t)cell * 256;
 #pragma unroll
-  for (int d = 0; d < kNDir; ++d) s[d] = __ldg(S + d);
-  const T wd = (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / s[0] : OP == OP_GS ? T(1) / s[0] : T(0);
+    for (int d = 0; d < kNDir; ++d) s[d] = __ldg(S + d);
+    wd = (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / s[0] : OP == OP_GS ? T(1) / s[0] : T(0);
+  }
   const bool halo = lane == 0 || lane == 31;
   PlanePos P;
   P.j = tl.z >> 16;
@@ -347,50 +403,50 @@ __device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lan
   P.len = w - k - P.j;
   P.g = tl.y + lane;
   while (P.r >= P.len && P.g <= gb + 1) { P.r -= P.len; --P.len; ++P.j; }
-  PlaneWin<T> W0, W1, W2;
+  PlaneWin<T, ST> W0, W1, W2;
   if (D == 0) {
     for (int q = 0; q < nwin; ++q) {
-      plane_load<T>(W0, x, P, q > 0, gb, Tp, Tm, halo);
-      plane_compute<T, OP>(A, W0, s, wd, base, y);
+      plane_load<T, ST>(W0, x, sst, P, q > 0, gb, Tp, Tm, halo);
+      plane_compute<T, OP, ST>(A, W0, s, wd, base, y);
     }
   } else if (D == 1) {
-    plane_load<T>(W0, x, P, false, gb, Tp, Tm, halo);
+    plane_load<T, ST>(W0, x, sst, P, false, gb, Tp, Tm, halo);
     for (int q = 0; q < nwin; q += 2) {
-      if (q + 1 < nwin) plane_load<T>(W1, x, P, true, gb, Tp, Tm, halo);
-      plane_compute<T, OP>(A, W0, s, wd, base, y);
+      if (q + 1 < nwin) plane_load<T, ST>(W1, x, sst, P, true, gb, Tp, Tm, halo);
+      plane_compute<T, OP, ST>(A, W0, s, wd, base, y);
       if (q + 1 < nwin) {
-        if (q + 2 < nwin) plane_load<T>(W0, x, P, true, gb, Tp, Tm, halo);
-        plane_compute<T, OP>(A, W1, s, wd, base, y);
+        if (q + 2 < nwin) plane_load<T, ST>(W0, x, sst, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP, ST>(A, W1, s, wd, base, y);
       }
     }
   } else {
-    plane_load<T>(W0, x, P, false, gb, Tp, Tm, halo);
-    if (nwin > 1) plane_load<T>(W1, x, P, true, gb, Tp, Tm, halo);
+    plane_load<T, ST>(W0, x, sst, P, false, gb, Tp, Tm, halo);
+    if (nwin > 1) plane_load<T, ST>(W1, x, sst, P, true, gb, Tp, Tm, halo);
     for (int q = 0; q < nwin; q += 3) {
-      if (q + 2 < nwin) plane_load<T>(W2, x, P, true, gb, Tp, Tm, halo);
-      plane_compute<T, OP>(A, W0, s, wd, base, y);
+      if (q + 2 < nwin) plane_load<T, ST>(W2, x, sst, P, true, gb, Tp, Tm, halo);
+      plane_compute<T, OP, ST>(A, W0, s, wd, base, y);
       if (q + 1 < nwin) {
-        if (q + 3 < nwin) plane_load<T>(W0, x, P, true, gb, Tp, Tm, halo);
-        plane_compute<T, OP>(A, W1, s, wd, base, y);
+        if (q + 3 < nwin) plane_load<T, ST>(W0, x, sst, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP, ST>(A, W1, s, wd, base, y);
       }
       if (q + 2 < nwin) {
-        if (q + 4 < nwin) plane_load<T>(W1, x, P, true, gb, Tp, Tm, halo);
-        plane_compute<T, OP>(A, W2, s, wd, base, y);
+        if (q + 4 < nwin) plane_load<T, ST>(W1, x, sst, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP, ST>(A, W2, s, wd, base, y);
       }
     }
   }
 }
 
 // Block `blk` of one operator application: interface items first, then tiles.
-template <typename T, int OP, int R>
+template <typename T, int OP, int R, bool ST = false>
 __device__ __forceinline__ void p1_block(const FusedArgs<T>& A, int blk) {
   const int lane = threadIdx.x & 31;
   const int wg = blk * kWarps + (threadIdx.x >> 5);
   if (blk < A.nb_items) {
-    if (wg < A.n_items) interface_item<T, OP>(A, wg, lane);
+    if (wg < A.n_items) interface_item<T, OP, ST>(A, wg, lane);
   } else {
     const int t = wg - A.nb_items * kWarps;
-    if (t < A.n_tiles) plane_tile<T, OP, R>(A, t, lane);
+    if (t < A.n_tiles) plane_tile<T, OP, R, ST>(A, t, lane);
   }
 }
 
@@ -404,6 +460,22 @@ constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
 template <typename T, int OP>
 __global__ void __launch_bounds__(kBlock, min_blocks<T>()) p1_fused_kernel(FusedArgs<T> A) {
   p1_block<T, OP, kPlanePrefetch>(A, blockIdx.x);
+}
+
+// Stored-stencil form (grid-aware precomputation of a variable-coefficient
+// operator): the 64 B (FP32) stencil of each output point streams from HBM
+// with the window's x rows.  Prefetch depth and resident blocks per SM are
+// tuning constants (the weights' registers set the budget): one window in
+// flight at 3-4 blocks per SM beats two windows at 2 blocks per SM.
+#ifndef HG_STORED_PREFETCH
+#define HG_STORED_PREFETCH 0
+#endif
+#ifndef HG_STORED_MIN_BLOCKS
+#define HG_STORED_MIN_BLOCKS 3
+#endif
+template <typename T, int OP>
+__global__ void __launch_bounds__(kBlock, HG_STORED_MIN_BLOCKS) p1_stored_kernel(FusedArgs<T> A) {
+  p1_block<T, OP, HG_STORED_PREFETCH, true>(A, blockIdx.x);
 }
 
 // Index of the problem owning unit u: base[p] <= u < base[p+1].
@@ -447,6 +519,7 @@ FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
   A.b = (const T*)a.b;
   A.y = (T*)a.out;
   A.sten = (const T*)a.sten;
+  A.sst = (const T*)a.sst;
   A.omega = (T)a.omega;
   A.mode = a.mode;
   A.mask = a.mask;
@@ -464,7 +537,10 @@ int run_p1(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
   FusedArgs<T> A = fused_args<T>(L, a, n_items);
   const int grid = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   if (grid == 0) return HG_OK;
-  p1_fused_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
+  if (a.sst)
+    p1_stored_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
+  else
+    p1_fused_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }

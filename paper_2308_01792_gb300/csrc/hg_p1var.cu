@@ -459,11 +459,54 @@ int run_var_op(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaS
   return HG_ERR_INVALID_ARG;
 }
 
+// Partial stencils of every stored point: one warp per lattice row of a
+// cell, lanes over i; weight d = the operator's point sum applied to the
+// unit vector of direction d (incidences inside the cell only).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) divkgrad_stencil_kernel(int n, int w, int64_t stride,
+                                                                  int n_rows, const T* kc,
+                                                                  const T* K, T* S) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (r >= n_rows) return;
+  int cell, j, k;
+  row_item(w, r, cell, j, k);
+  const int64_t r0 = (int64_t)cell * stride + row_start(w, j, k);
+  for (int i = lane; i + j + k <= n; i += 32) {
+    T kv[kNDir];
+    gather15<T>(kc + (int64_t)cell * stride, n, w, i, j, k, kv);
+    const unsigned mask = incidence_mask(point_class(n, i, j, k));
+#pragma unroll 1
+    for (int d = 0; d < kNDir; ++d) {
+      T xv[kNDir];
+#pragma unroll
+      for (int e = 0; e < kNDir; ++e) xv[e] = e == d ? T(1) : T(0);
+      S[16 * (r0 + i) + d] = divkgrad_point<T, false>(xv, kv, K + (int64_t)cell * 96, mask);
+    }
+  }
+}
+
+template <typename T>
+int run_stencil(const LevelDev& L, const VarCoef& vc, void* S, cudaStream_t s) {
+  HG_CUDA(cudaMemsetAsync(S, 0, (size_t)16 * L.n_stored * sizeof(T), s));
+  const int n_rows = L.ncells * ntri32(L.w);
+  if (n_rows == 0) return HG_OK;
+  divkgrad_stencil_kernel<T><<<(n_rows + kWarps - 1) / kWarps, kBlock, 0, s>>>(
+      L.n, L.w, L.cell_stride, n_rows, (const T*)vc.k, (const T*)vc.K, (T*)S);
+  HG_CUDA(cudaGetLastError());
+  return HG_OK;
+}
+
 }  // namespace
 
 int launch_p1_divkgrad(const LevelDev& L, int dtype, const StencilArgs& a, const VarCoef& vc,
                        cudaStream_t s) {
   return dtype == HG_F64 ? run_var_op<double>(L, a, vc, s) : run_var_op<float>(L, a, vc, s);
+}
+
+int launch_divkgrad_stencil(const LevelDev& L, int dtype, const VarCoef& vc, void* S,
+                            cudaStream_t s) {
+  return dtype == HG_F64 ? run_stencil<double>(L, vc, S, s) : run_stencil<float>(L, vc, S, s);
 }
 
 }  // namespace hg

@@ -1,6 +1,8 @@
 """GPU parity of the variable-coefficient P1 operator -div(k grad) (element-wise,
 k_T = mean of the vertex values) and of multigrid built on it, against the
-oracle's assembled matrices (through the C ABI)."""
+oracle's assembled matrices (through the C ABI).  Every test runs for the
+on-the-fly form and for the stored-stencil form (grid-aware precomputation:
+the partial stencil of every stored point kept in HBM)."""
 import numpy as np
 import pytest
 
@@ -32,12 +34,17 @@ CASES = [(sg.reference_tet(), 2, 4, kfun_smooth), (sg.kuhn_cube(2), 1, 4, kfun_l
 IDS = ["tet_smooth", "cube2_lognormal", "cube1_smooth"]
 
 
-@pytest.fixture(scope="module", params=range(len(CASES)), ids=IDS)
+KINDS = [hg.HG_OP_P1_DIVKGRAD, hg.HG_OP_P1_DIVKGRAD_STORED]
+
+
+@pytest.fixture(scope="module", params=[(c, k) for c in range(len(CASES)) for k in KINDS],
+                ids=[f"{i}-{k}" for i in IDS for k in ("onthefly", "stored")])
 def case(request):
-    macro, lmin, lmax, kf = CASES[request.param]
+    c, kind = request.param
+    macro, lmin, lmax, kf = CASES[c]
     H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), lmin, lmax)
     _, xyz, _ = H.canonical_info(lmax)
-    op = hg.Operator(H, hg.HG_OP_P1_DIVKGRAD, coeff=kf(xyz))
+    op = hg.Operator(H, kind, coeff=kf(xyz))
     return macro, H, op, kf
 
 

@@ -8,7 +8,7 @@ point must agree to 1e-12 of the row's term magnitudes (FP64).  Workloads:
 - P2 -div(k grad), k = 1 + 0.5 sin sin sin, unit cube as 48 Kuhn cells,
   P2 level 6 (16 974 593 DoFs);
 - P1 -div(k grad), log-normal k (seed 1000), 384 Kuhn cells, level 6
-  (16 974 593 DoFs);
+  (16 974 593 DoFs), on-the-fly and stored-stencil forms;
 plus the closed-form 7-point identity of the P1 Laplacian on 384 cells."""
 import numpy as np
 import pytest
@@ -105,7 +105,9 @@ def test_p2_stiffness_full_size_sampled_rows():
         assert abs(got - acc) <= 1e-12 * scale, (s, c, pt, got, acc)
 
 
-def test_p1_divkgrad_full_size_sampled_rows():
+@pytest.mark.parametrize("kind", [hg.HG_OP_P1_DIVKGRAD, hg.HG_OP_P1_DIVKGRAD_STORED],
+                         ids=["onthefly", "stored"])
+def test_p1_divkgrad_full_size_sampled_rows(kind):
     macro, L = sg.kuhn_cube(4), 6
     n = 1 << L
     H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), L, L)
@@ -113,7 +115,7 @@ def test_p1_divkgrad_full_size_sampled_rows():
     ns, nu, _, stride = H.size(L)
     assert nu == 257 ** 3
     k = sg.rff_eval_torch(sg.rff_params(1000), xyz)          # the workload's field, FP64
-    op = hg.Operator(H, hg.HG_OP_P1_DIVKGRAD, coeff=k)
+    op = hg.Operator(H, kind, coeff=k)
     xc = sg.uniform_vector(63, nu)
     x = H.from_canonical(L, torch.tensor(xc, device="cuda"))
     y = H.zeros(L, torch.float64)
