@@ -622,10 +622,12 @@ int Op::build(const Hier* h, int kind_, const double* coeff) {
   }
   sten64.resize(h->lmax - h->lmin + 1, nullptr);
   sten32.resize(h->lmax - h->lmin + 1, nullptr);
+  pattern.assign(h->lmax - h->lmin + 1, 0);
   for (int l = h->lmin; l <= h->lmax; ++l) {
     const int n = 1 << l;
     std::vector<double> s64(256 * h->mesh->nc);
     std::vector<float> s32(256 * h->mesh->nc);
+    bool pat7 = true;
     for (int64_t c = 0; c < h->mesh->nc; ++c) {
       double S[16][16];
       p1_cell_stencils(*h->mesh, c, n, kind, S);
@@ -633,7 +635,11 @@ int Op::build(const Hier* h, int kind_, const double* coeff) {
         s64[256 * c + q] = S[q / 16][q % 16];
         s32[256 * c + q] = (float)S[q / 16][q % 16];
       }
+      // interior stencil (class 0) exactly zero outside the seven-point subset?
+      for (int d = 0; d < kNDir; ++d)
+        if (!((kPat7Mask >> d) & 1u) && S[0][d] != 0.0) pat7 = false;
     }
+    pattern[l - h->lmin] = pat7 ? kPat7 : 0;
     if (int r = upload(&sten64[l - h->lmin], s64)) return r;
     if (int r = upload(&sten32[l - h->lmin], s32)) return r;
     // 1/diag(A) at every stored copy (sum of the copies' stencil centres)
@@ -812,6 +818,7 @@ int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
     return launch_p1_const(L, dtype, a, s);
   }
   a.sten = dtype == HG_F64 ? (const void*)sten64[li] : (const void*)sten32[li];
+  a.pattern = pattern[li];
   return launch_p1_const(L, dtype, a, s);
 }
 

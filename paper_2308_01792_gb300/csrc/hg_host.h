@@ -97,6 +97,7 @@ struct Op {
   int build_p2(const double* coeff);
   std::vector<double*> sten64;  // per level [ncells][16][16] (constant-coefficient kinds)
   std::vector<float*> sten32;
+  std::vector<int> pattern;     // per level: kPat7 when the interior stencils allow it
   // variable-coefficient P1 (per level): k at stored vertices, element rows, 1/diag
   std::vector<void*> vk[2], vK[2], vinv[2];
   // stored-stencil P1 (per level): partial stencils of every stored point, [15][n_stored]

@@ -154,7 +154,10 @@ struct LevelDev {
 
 // Windows of 30 consecutive lattice offsets per plane-window tile of the
 // constant-stencil kernels.
-constexpr int kPlaneSteps = 16;
+#ifndef HG_PLANE_STEPS
+#define HG_PLANE_STEPS 16
+#endif
+constexpr int kPlaneSteps = HG_PLANE_STEPS;
 
 // Dense FP64 coarse-grid solver data.
 struct CoarseDev {
@@ -184,6 +187,12 @@ int cuda_fail(cudaError_t e, const char* what);
 // DoFs: out = x, d untouched.
 enum CellOp : int { OP_APPLY = 0, OP_RESID = 1, OP_JACOBI = 2, OP_DIAG = 3, OP_GS = 6, OP_CHEB = 7 };
 
+// Interior-stencil pattern of a constant-coefficient level: the directions
+// (indices of dir_offset) that may be nonzero under kPat7.
+constexpr int kPat7 = 1;
+constexpr unsigned kPat7Mask = (1u << 0) | (1u << 1) | (1u << 2) | (1u << 7) | (1u << 8) |
+                               (1u << 11) | (1u << 12);
+
 // True for the operations that scale the residual by the inverse diagonal.
 HG_HD constexpr bool op_scaled(int op) { return op == OP_JACOBI || op == OP_GS || op == OP_CHEB; }
 
@@ -197,6 +206,8 @@ struct StencilArgs {
   double omega;         // JACOBI: weight; CHEB: beta of the residual term
   int op, mode, mask;
   int colour;           // OP_GS: the colour updated
+  int pattern;          // constant stencils: 0, or kPat7 when every cell's interior stencil is
+                        // zero outside centre, +-(1,0,0), +-(1,-1,0), +-(0,-1,1)
   void* dvec;           // OP_CHEB: Chebyshev direction d (read if cheb_a != 0, written)
   double cheb_a;        // OP_CHEB: weight of the previous direction
 };

@@ -301,7 +301,10 @@ struct PlanePos {
 // whose values the last output takes by shuffle); the row walk stays inside
 // the plane and lanes past gb+1 load at gb+1 (row length 3): in bounds, never
 // stored.
-template <typename T, bool ST>
+// PAT = kPat7: the cell stencils vanish outside the seven-point subset
+// (centre, +-(1,0,0), +-(1,-1,0), +-(0,-1,1)); the rows without weights are
+// not loaded (planes k+-1 then need only one row each).
+template <typename T, bool ST, int PAT = 0>
 __device__ __forceinline__ void plane_load(PlaneWin<T, ST>& W, const T* __restrict__ x,
                                            const T* __restrict__ sst, PlanePos& P, bool advance,
                                            int gb, int Tp, int Tm, bool halo) {
@@ -317,9 +320,9 @@ __device__ __forceinline__ void plane_load(PlaneWin<T, ST>& W, const T* __restri
   W.c = __ldg(x + gq);
   W.up = __ldg(x + gq + lq);
   W.dn = __ldg(x + gq - lq - 1);
-  W.p1c = __ldg(x + gq + Tp + lq);
+  if (PAT != kPat7) W.p1c = __ldg(x + gq + Tp + lq);
   W.p1m = __ldg(x + gq + Tp);
-  W.m1c = __ldg(x + gq - Tm - lq - 1);
+  if (PAT != kPat7) W.m1c = __ldg(x + gq - Tm - lq - 1);
   W.m1p = __ldg(x + gq - Tm);
   if (ST) {
     // only output lanes read weights: 64 B (FP32) per point, contiguous over the window
@@ -333,7 +336,9 @@ __device__ __forceinline__ void plane_load(PlaneWin<T, ST>& W, const T* __restri
 }
 
 // The 15-point stencil of one window from registers and shuffles, stored.
-template <typename T, int OP, bool ST>
+// With PAT = kPat7 the terms of the eight zero weights are left out; adding
+// an exact zero changes no sum, so the result is the same bits.
+template <typename T, int OP, bool ST, int PAT = 0>
 __device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const PlaneWin<T, ST>& W,
                                               const T sc[kNDir], T wdc, int64_t base,
                                               T* __restrict__ y) {
@@ -341,15 +346,21 @@ __device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const Plane
   const T cm = __shfl_up_sync(0xffffffffu, W.c, 1), cp = __shfl_down_sync(0xffffffffu, W.c, 1);
   const T upm = __shfl_up_sync(0xffffffffu, W.up, 1);
   const T dnp = __shfl_down_sync(0xffffffffu, W.dn, 1);
-  const T p1cm = __shfl_up_sync(0xffffffffu, W.p1c, 1);
-  const T p1mp = __shfl_down_sync(0xffffffffu, W.p1m, 1);
-  const T m1cp = __shfl_down_sync(0xffffffffu, W.m1c, 1);
-  const T m1pm = __shfl_up_sync(0xffffffffu, W.m1p, 1);
-  const T a0 = s[0] * W.c + s[1] * cp + s[2] * cm + s[3] * W.up + s[4] * W.dn + s[7] * upm +
-               s[8] * dnp;
-  const T a1 = s[5] * W.p1c + s[9] * p1cm + s[11] * W.p1m + s[13] * p1mp;
-  const T a2 = s[6] * W.m1c + s[10] * m1cp + s[12] * W.m1p + s[14] * m1pm;
-  const T acc = a0 + (a1 + a2);
+  T acc;
+  if (PAT == kPat7) {
+    const T a0 = s[0] * W.c + s[1] * cp + s[2] * cm + s[7] * upm + s[8] * dnp;
+    acc = a0 + (s[11] * W.p1m + s[12] * W.m1p);
+  } else {
+    const T p1cm = __shfl_up_sync(0xffffffffu, W.p1c, 1);
+    const T p1mp = __shfl_down_sync(0xffffffffu, W.p1m, 1);
+    const T m1cp = __shfl_down_sync(0xffffffffu, W.m1c, 1);
+    const T m1pm = __shfl_up_sync(0xffffffffu, W.m1p, 1);
+    const T a0 = s[0] * W.c + s[1] * cp + s[2] * cm + s[3] * W.up + s[4] * W.dn + s[7] * upm +
+                 s[8] * dnp;
+    const T a1 = s[5] * W.p1c + s[9] * p1cm + s[11] * W.p1m + s[13] * p1mp;
+    const T a2 = s[6] * W.m1c + s[10] * m1cp + s[12] * W.m1p + s[14] * m1pm;
+    acc = a0 + (a1 + a2);
+  }
   if (W.ok) {
     const int idx = W.g;
     const T wd = !ST ? wdc
@@ -376,7 +387,7 @@ __device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const Plane
 // Plane-window tile t (see the file comment): its windows in order, the loads
 // of the next D windows in flight while one is computed (D = 0, 1 or 2;
 // three rotating register sets for D = 2).
-template <typename T, int OP, int D, bool ST>
+template <typename T, int OP, int D, bool ST, int PAT = 0>
 __device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lane) {
   const int cell = t / A.n_tiles_cell;
   const int4 tl = A.tiles[t - cell * A.n_tiles_cell];
@@ -406,39 +417,39 @@ __device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lan
   PlaneWin<T, ST> W0, W1, W2;
   if (D == 0) {
     for (int q = 0; q < nwin; ++q) {
-      plane_load<T, ST>(W0, x, sst, P, q > 0, gb, Tp, Tm, halo);
-      plane_compute<T, OP, ST>(A, W0, s, wd, base, y);
+      plane_load<T, ST, PAT>(W0, x, sst, P, q > 0, gb, Tp, Tm, halo);
+      plane_compute<T, OP, ST, PAT>(A, W0, s, wd, base, y);
     }
   } else if (D == 1) {
-    plane_load<T, ST>(W0, x, sst, P, false, gb, Tp, Tm, halo);
+    plane_load<T, ST, PAT>(W0, x, sst, P, false, gb, Tp, Tm, halo);
     for (int q = 0; q < nwin; q += 2) {
-      if (q + 1 < nwin) plane_load<T, ST>(W1, x, sst, P, true, gb, Tp, Tm, halo);
-      plane_compute<T, OP, ST>(A, W0, s, wd, base, y);
+      if (q + 1 < nwin) plane_load<T, ST, PAT>(W1, x, sst, P, true, gb, Tp, Tm, halo);
+      plane_compute<T, OP, ST, PAT>(A, W0, s, wd, base, y);
       if (q + 1 < nwin) {
-        if (q + 2 < nwin) plane_load<T, ST>(W0, x, sst, P, true, gb, Tp, Tm, halo);
-        plane_compute<T, OP, ST>(A, W1, s, wd, base, y);
+        if (q + 2 < nwin) plane_load<T, ST, PAT>(W0, x, sst, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP, ST, PAT>(A, W1, s, wd, base, y);
       }
     }
   } else {
-    plane_load<T, ST>(W0, x, sst, P, false, gb, Tp, Tm, halo);
-    if (nwin > 1) plane_load<T, ST>(W1, x, sst, P, true, gb, Tp, Tm, halo);
+    plane_load<T, ST, PAT>(W0, x, sst, P, false, gb, Tp, Tm, halo);
+    if (nwin > 1) plane_load<T, ST, PAT>(W1, x, sst, P, true, gb, Tp, Tm, halo);
     for (int q = 0; q < nwin; q += 3) {
-      if (q + 2 < nwin) plane_load<T, ST>(W2, x, sst, P, true, gb, Tp, Tm, halo);
-      plane_compute<T, OP, ST>(A, W0, s, wd, base, y);
+      if (q + 2 < nwin) plane_load<T, ST, PAT>(W2, x, sst, P, true, gb, Tp, Tm, halo);
+      plane_compute<T, OP, ST, PAT>(A, W0, s, wd, base, y);
       if (q + 1 < nwin) {
-        if (q + 3 < nwin) plane_load<T, ST>(W0, x, sst, P, true, gb, Tp, Tm, halo);
-        plane_compute<T, OP, ST>(A, W1, s, wd, base, y);
+        if (q + 3 < nwin) plane_load<T, ST, PAT>(W0, x, sst, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP, ST, PAT>(A, W1, s, wd, base, y);
       }
       if (q + 2 < nwin) {
-        if (q + 4 < nwin) plane_load<T, ST>(W1, x, sst, P, true, gb, Tp, Tm, halo);
-        plane_compute<T, OP, ST>(A, W2, s, wd, base, y);
+        if (q + 4 < nwin) plane_load<T, ST, PAT>(W1, x, sst, P, true, gb, Tp, Tm, halo);
+        plane_compute<T, OP, ST, PAT>(A, W2, s, wd, base, y);
       }
     }
   }
 }
 
 // Block `blk` of one operator application: interface items first, then tiles.
-template <typename T, int OP, int R, bool ST = false>
+template <typename T, int OP, int R, bool ST = false, int PAT = 0>
 __device__ __forceinline__ void p1_block(const FusedArgs<T>& A, int blk) {
   const int lane = threadIdx.x & 31;
   const int wg = blk * kWarps + (threadIdx.x >> 5);
@@ -446,20 +457,26 @@ __device__ __forceinline__ void p1_block(const FusedArgs<T>& A, int blk) {
     if (wg < A.n_items) interface_item<T, OP, ST>(A, wg, lane);
   } else {
     const int t = wg - A.nb_items * kWarps;
-    if (t < A.n_tiles) plane_tile<T, OP, R, ST>(A, t, lane);
+    if (t < A.n_tiles) plane_tile<T, OP, R, ST, PAT>(A, t, lane);
   }
 }
 
 // Windows of a plane tile whose loads are in flight while one is computed.
-constexpr int kPlanePrefetch = 1;
+#ifndef HG_P1_PREFETCH
+#define HG_P1_PREFETCH 1
+#endif
+constexpr int kPlanePrefetch = HG_P1_PREFETCH;
 
 // Resident blocks per SM the register budget is sized for (FP32 / FP64).
+#ifndef HG_P1_MIN_BLOCKS_F32
+#define HG_P1_MIN_BLOCKS_F32 3
+#endif
 template <typename T>
-constexpr int min_blocks() { return sizeof(T) == 4 ? 3 : 2; }
+constexpr int min_blocks() { return sizeof(T) == 4 ? HG_P1_MIN_BLOCKS_F32 : 2; }
 
-template <typename T, int OP>
+template <typename T, int OP, int PAT = 0>
 __global__ void __launch_bounds__(kBlock, min_blocks<T>()) p1_fused_kernel(FusedArgs<T> A) {
-  p1_block<T, OP, kPlanePrefetch>(A, blockIdx.x);
+  p1_block<T, OP, kPlanePrefetch, false, PAT>(A, blockIdx.x);
 }
 
 // Stored-stencil form (grid-aware precomputation of a variable-coefficient
@@ -539,6 +556,8 @@ int run_p1(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
   if (grid == 0) return HG_OK;
   if (a.sst)
     p1_stored_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
+  else if (a.pattern == kPat7)
+    p1_fused_kernel<T, OP, kPat7><<<grid, kBlock, 0, s>>>(A);
   else
     p1_fused_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
   HG_CUDA(cudaGetLastError());
