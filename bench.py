@@ -412,7 +412,8 @@ def stencil_comparison(stream, m=4, L=6, solve=True):
     (17 M DoFs), k = exp(g) log-normal (seed 1000): FP32 apply with element
     matrices on the fly against the stored-stencil form (grid-aware
     precomputation: 15 weights per stored point streamed from HBM), and the
-    mixed-precision GMG solve to 1e-8 with each."""
+    mixed-precision GMG solve to 1e-8 with each (Jacobi V(3,3); the stored form
+    also with Chebyshev(2) V(1,1))."""
     import torch
     import paper_2308_01792_gb300 as hg
     macro = sg.kuhn_cube(m)
@@ -461,8 +462,9 @@ def stencil_comparison(stream, m=4, L=6, solve=True):
     bc = sg.uniform_vector(9, nu)
     bc[dirich] = 0.0
     b = H.from_canonical(L, torch.tensor(bc, device="cuda"))
-    for name, op in (("onthefly", fly), ("stored", st)):
-        G = hg.GMG(op, inner_cycles=INNER_CYCLES)
+    for name, op, cheb in (("onthefly", fly, False), ("stored", st, False), ("stored", st, True)):
+        G = (hg.GMG(op, nu1=1, nu2=1, inner_cycles=INNER_CYCLES, smoother=hg.HG_SMOOTH_CHEB) if cheb
+             else hg.GMG(op, inner_cycles=INNER_CYCLES))
         xs = H.zeros(L, torch.float64)
         G.solve(xs, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
         torch.cuda.synchronize()
@@ -470,7 +472,8 @@ def stencil_comparison(stream, m=4, L=6, solve=True):
         it, rel = G.solve(xs, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
-        out[name]["mixed_solve"] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel}
+        out[name]["mixed_solve_cheb2_v11" if cheb else "mixed_solve"] = {
+            "s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel}
         del G
     return out
 

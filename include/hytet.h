@@ -74,8 +74,8 @@ enum {
   HG_OP_P1_DIVKGRAD_STORED = 6 /* HG_OP_P1_DIVKGRAD with grid-aware precomputation
                             (Sec. 5.2): the 15-point partial stencil of every
                             stored point kept in HBM (16 values per stored DoF
-                            and level, one padding, FP64 and FP32 copies) and
-                            streamed by the apply                               */
+                            and level: 15 weights and the inverse centre weight;
+                            FP64 and FP32 copies) and streamed by the apply     */
 };
 
 typedef struct hg_mesh hg_mesh;

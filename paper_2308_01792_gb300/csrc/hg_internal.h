@@ -202,7 +202,7 @@ struct StencilArgs {
   void* out;            // output
   const void* sten;     // [ncells][16][16] T (class, direction)
   const void* sst;      // or stored stencils [n_stored][16] T: the partial stencil of every
-                        // stored point (its cell's micro-cells), 15 weights + 1 pad
+                        // stored point (its cell's micro-cells), 15 weights + 1/centre
   double omega;         // JACOBI: weight; CHEB: beta of the residual term
   int op, mode, mask;
   int colour;           // OP_GS: the colour updated
@@ -276,7 +276,7 @@ int launch_p1_divkgrad(const LevelDev& L, int dtype, const StencilArgs& a, const
                        cudaStream_t s);
 // Stored stencils of the div-k-grad operator: S[16 q + d] = the weight of
 // direction d in the partial stencil of stored point q (zero outside the
-// lattice and in the pad entry d = 15).
+// lattice); S[16 q + 15] = 1 / S[16 q] for points inside a cell, else 0.
 int launch_divkgrad_stencil(const LevelDev& L, int dtype, const VarCoef& vc, void* S,
                             cudaStream_t s);
 int launch_index_enumerate(int w, int64_t* out, cudaStream_t s);

@@ -96,16 +96,20 @@ __device__ __forceinline__ void prim_weights(int dim, int n, int p, int wts[3]) 
   }
 }
 
-// 15 weights of one stored stencil (16 values per point, 16-byte vector loads).
-__device__ __forceinline__ void load_sten16(const float* __restrict__ p, float s[kNDir]) {
+// One stored stencil: 15 weights and, in the 16th slot, 1/(centre weight)
+// for points inside the cell (16-byte vector loads).
+__device__ __forceinline__ void load_sten16(const float* __restrict__ p, float s[kNDir],
+                                            float& inv) {
   const float4* q = reinterpret_cast<const float4*>(p);
   const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2), d = __ldg(q + 3);
   s[0] = a.x; s[1] = a.y; s[2] = a.z; s[3] = a.w;
   s[4] = b.x; s[5] = b.y; s[6] = b.z; s[7] = b.w;
   s[8] = c.x; s[9] = c.y; s[10] = c.z; s[11] = c.w;
   s[12] = d.x; s[13] = d.y; s[14] = d.z;
+  inv = d.w;
 }
-__device__ __forceinline__ void load_sten16(const double* __restrict__ p, double s[kNDir]) {
+__device__ __forceinline__ void load_sten16(const double* __restrict__ p, double s[kNDir],
+                                            double& inv) {
   const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
   for (int v = 0; v < 7; ++v) {
@@ -113,7 +117,9 @@ __device__ __forceinline__ void load_sten16(const double* __restrict__ p, double
     s[2 * v] = t.x;
     s[2 * v + 1] = t.y;
   }
-  s[14] = __ldg(p + 14);
+  const double2 t = __ldg(q + 7);
+  s[14] = t.x;
+  inv = t.y;
 }
 
 // Partial stencil of one cell at a cell-local point (any class).  The 7
@@ -133,7 +139,8 @@ __device__ __forceinline__ void cell_partial_load(const T* __restrict__ x, const
   const int rjmkp = rkp - L, rjpkm = rkm + L + 1;
   const int rows[15] = {r0, r0, r0, rjp, rjm, rkp, rkm, rjp, rjm, rkp, rkm, rjmkp, rjpkm, rjmkp, rjpkm};
   if (ST) {
-    load_sten16(S, sv);
+    T inv;
+    load_sten16(S, sv, inv);
   } else {
 #pragma unroll
     for (int d = 0; d < kNDir; ++d) sv[d] = __ldg(S + d);
@@ -289,6 +296,7 @@ struct PlaneWin {
   int g;
   bool ok;
   T s[ST ? kNDir : 1];
+  T inv;  // ST: 1 / centre weight
 };
 
 // Lane position inside a plane: offset g, row j, column r, row length len.
@@ -327,10 +335,11 @@ __device__ __forceinline__ void plane_load(PlaneWin<T, ST>& W, const T* __restri
   if (ST) {
     // only output lanes read weights: 64 B (FP32) per point, contiguous over the window
     if (W.ok) {
-      load_sten16(sst + 16 * (int64_t)gq, W.s);
+      load_sten16(sst + 16 * (int64_t)gq, W.s, W.inv);
     } else {
 #pragma unroll
       for (int d = 0; d < kNDir; ++d) W.s[d] = T(0);
+      W.inv = T(0);
     }
   }
 }
@@ -364,8 +373,8 @@ __device__ __forceinline__ void plane_compute(const FusedArgs<T>& A, const Plane
   if (W.ok) {
     const int idx = W.g;
     const T wd = !ST ? wdc
-                     : (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / s[0]
-                     : OP == OP_GS                        ? T(1) / s[0]
+                     : (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega * W.inv
+                     : OP == OP_GS                        ? W.inv
                                                           : T(0);
     if (OP == OP_APPLY) {
       y[idx] = A.mode == HG_ADD ? y[idx] + acc : acc;
@@ -643,6 +652,9 @@ __global__ void scatter_kernel(const T* __restrict__ can, const int32_t* __restr
 }
 
 // ---------------------------------------------------------- grid transfers
+// Lattice rows per warp of the transfer kernels (consecutive in row-item order).
+constexpr int kXferRows = 4;
+
 // Restriction r_c = P^T r_f.  A coarse point I collects the fine points 2I
 // (weight 1) and 2I +- d (weight 1/2, the midpoints of the coarse edges at I)
 // that lie in the cell and are owned by it (each unique fine DoF counted once).
@@ -712,17 +724,27 @@ __device__ __forceinline__ void restrict_block(const RestrictDesc<T>& D, int blk
     }
     return;
   }
-  const int r = wg - D.nb_items * kWarps;
+  const int r = (wg - D.nb_items * kWarps) * kXferRows;
   if (r >= D.n_rows) return;
   int cell, J, K;
   row_item(wc, r, cell, J, K);
-  const T* rf = D.rf + (int64_t)cell * D.fstride;
-  T* rc = D.rc + (int64_t)cell * D.cstride;
-  const uint8_t* fl = D.flags + cell * 16;
-  const int r0 = row_start(wc, J, K);
-  for (int I = lane; I + J + K <= nc; I += 32) {
-    if (point_class(nc, I, J, K) != 0) continue;  // interface points: items above
-    rc[r0 + I] = restrict_partial<T>(rf, fl, nf, I, J, K);
+  // coarse rows r .. r + kXferRows - 1 in row-item order (J inner, then K, then cell)
+  for (int q = 0; q < kXferRows && r + q < D.n_rows; ++q) {
+    const T* rf = D.rf + (int64_t)cell * D.fstride;
+    T* rc = D.rc + (int64_t)cell * D.cstride;
+    const uint8_t* fl = D.flags + cell * 16;
+    const int r0 = row_start(wc, J, K);
+    for (int I = lane; I + J + K <= nc; I += 32) {
+      if (point_class(nc, I, J, K) != 0) continue;  // interface points: items above
+      rc[r0 + I] = restrict_partial<T>(rf, fl, nf, I, J, K);
+    }
+    if (++J == wc - K) {
+      J = 0;
+      if (++K == wc) {
+        K = 0;
+        ++cell;
+      }
+    }
   }
 }
 
@@ -743,40 +765,46 @@ struct ProlongDesc {
   T* xf;
 };
 
+// Coarse-edge direction of a fine point by coordinate parity p = i&1 |
+// (j&1)<<1 | (k&1)<<2, one 2-bit field (offset + 1) per parity: p = 0 maps
+// to (0,0,0), whose two endpoints coincide (0.5 (a + a) = a exactly).
+constexpr unsigned kParDi = (1u << 0) | (2u << 2) | (1u << 4) | (0u << 6) | (1u << 8) | (0u << 10) |
+                            (1u << 12) | (2u << 14);
+constexpr unsigned kParDj = (1u << 0) | (1u << 2) | (2u << 4) | (2u << 6) | (1u << 8) | (1u << 10) |
+                            (0u << 12) | (0u << 14);
+constexpr unsigned kParDk = (1u << 0) | (1u << 2) | (1u << 4) | (1u << 6) | (2u << 8) | (2u << 10) |
+                            (2u << 12) | (2u << 14);
+
 template <typename T>
 __device__ __forceinline__ void prolong_block(const ProlongDesc<T>& D, int blk) {
   const int lane = threadIdx.x & 31;
-  const int r = blk * kWarps + (threadIdx.x >> 5);
+  const int r = (blk * kWarps + (threadIdx.x >> 5)) * kXferRows;
   const int nf = D.nf, wf = nf + 1, wc = nf / 2 + 1;
   if (r >= D.n_rows) return;
   int cell, j, k;
   row_item(wf, r, cell, j, k);
-  const T* ec = D.ec + (int64_t)cell * D.cstride;
-  T* xf = D.xf + (int64_t)cell * D.fstride;
-  const uint8_t* fl = D.flags + cell * 16;
-  const int r0 = row_start(wf, j, k);
-  for (int i = lane; i + j + k <= nf; i += 32) {
-    if (fl[point_class(nf, i, j, k)] & CF_DIRICHLET) continue;
-    const int par = (i & 1) | ((j & 1) << 1) | ((k & 1) << 2);
-    T v;
-    if (par == 0) {
-      v = ec[tw32(wc, i >> 1, j >> 1, k >> 1)];
-    } else {
-      int di = 0, dj = 0, dk = 0;
-      switch (par) {
-        case 1: di = 1; break;
-        case 2: dj = 1; break;
-        case 4: dk = 1; break;
-        case 3: di = -1; dj = 1; break;
-        case 5: di = -1; dk = 1; break;
-        case 6: dj = -1; dk = 1; break;
-        default: di = 1; dj = -1; dk = 1; break;
-      }
+  // rows r .. r + kXferRows - 1 in row-item order (j inner, then k, then cell)
+  for (int q = 0; q < kXferRows && r + q < D.n_rows; ++q) {
+    const T* ec = D.ec + (int64_t)cell * D.cstride;
+    T* xf = D.xf + (int64_t)cell * D.fstride;
+    const uint8_t* fl = D.flags + cell * 16;
+    const int r0 = row_start(wf, j, k);
+    for (int i = lane; i + j + k <= nf; i += 32) {
+      if (fl[point_class(nf, i, j, k)] & CF_DIRICHLET) continue;
+      const int par2 = 2 * ((i & 1) | ((j & 1) << 1) | ((k & 1) << 2));
+      const int di = (int)((kParDi >> par2) & 3u) - 1, dj = (int)((kParDj >> par2) & 3u) - 1,
+                dk = (int)((kParDk >> par2) & 3u) - 1;
       const T a = ec[tw32(wc, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1)];
       const T b = ec[tw32(wc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1)];
-      v = T(0.5) * (a + b);
+      xf[r0 + i] += T(0.5) * (a + b);
     }
-    xf[r0 + i] += v;
+    if (++j == wf - k) {
+      j = 0;
+      if (++k == wf) {
+        k = 0;
+        ++cell;
+      }
+    }
   }
 }
 
@@ -863,6 +891,8 @@ int grid_for(int64_t n) {
 }
 
 int blocks_for_warps(int64_t nw) { return (int)((nw + kWarps - 1) / kWarps); }
+// Warps of the row part of one transfer launch (kXferRows rows each).
+int64_t xfer_warps(int64_t n_rows) { return (n_rows + kXferRows - 1) / kXferRows; }
 
 }  // namespace
 
@@ -945,7 +975,7 @@ template <typename T>
 static int run_restrict(const LevelDev& F, const LevelDev& C, const void* rf, void* rc,
                         cudaStream_t s) {
   const RestrictDesc<T> D = restrict_desc<T>(F, C, rf, rc);
-  restrict_kernel<T><<<D.nb_items + blocks_for_warps(D.n_rows), kBlock, 0, s>>>(D);
+  restrict_kernel<T><<<D.nb_items + blocks_for_warps(xfer_warps(D.n_rows)), kBlock, 0, s>>>(D);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
@@ -960,10 +990,10 @@ int launch_prolong_p1(const LevelDev& F, const LevelDev& C, int dtype, const voi
                       cudaStream_t s) {
   if (dtype == HG_F64) {
     const ProlongDesc<double> D = prolong_desc<double>(F, C, ec, xf);
-    prolong_kernel<double><<<blocks_for_warps(D.n_rows), kBlock, 0, s>>>(D);
+    prolong_kernel<double><<<blocks_for_warps(xfer_warps(D.n_rows)), kBlock, 0, s>>>(D);
   } else {
     const ProlongDesc<float> D = prolong_desc<float>(F, C, ec, xf);
-    prolong_kernel<float><<<blocks_for_warps(D.n_rows), kBlock, 0, s>>>(D);
+    prolong_kernel<float><<<blocks_for_warps(xfer_warps(D.n_rows)), kBlock, 0, s>>>(D);
   }
   HG_CUDA(cudaGetLastError());
   return HG_OK;
@@ -997,11 +1027,11 @@ int restrict_make_desc(const LevelDev& F, const LevelDev& C, int dtype, const vo
   if (dtype == HG_F64) {
     const RestrictDesc<double> D = restrict_desc<double>(F, C, rf, rc);
     memcpy(dst, &D, sizeof D);
-    *units = D.nb_items + blocks_for_warps(D.n_rows);
+    *units = D.nb_items + blocks_for_warps(xfer_warps(D.n_rows));
   } else {
     const RestrictDesc<float> D = restrict_desc<float>(F, C, rf, rc);
     memcpy(dst, &D, sizeof D);
-    *units = D.nb_items + blocks_for_warps(D.n_rows);
+    *units = D.nb_items + blocks_for_warps(xfer_warps(D.n_rows));
   }
   return HG_OK;
 }
@@ -1015,11 +1045,11 @@ int prolong_make_desc(const LevelDev& F, const LevelDev& C, int dtype, const voi
   if (dtype == HG_F64) {
     const ProlongDesc<double> D = prolong_desc<double>(F, C, ec, xf);
     memcpy(dst, &D, sizeof D);
-    *units = blocks_for_warps(D.n_rows);
+    *units = blocks_for_warps(xfer_warps(D.n_rows));
   } else {
     const ProlongDesc<float> D = prolong_desc<float>(F, C, ec, xf);
     memcpy(dst, &D, sizeof D);
-    *units = blocks_for_warps(D.n_rows);
+    *units = blocks_for_warps(xfer_warps(D.n_rows));
   }
   return HG_OK;
 }

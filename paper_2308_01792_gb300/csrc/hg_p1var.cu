@@ -461,7 +461,8 @@ int run_var_op(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaS
 
 // Partial stencils of every stored point: one warp per lattice row of a
 // cell, lanes over i; weight d = the operator's point sum applied to the
-// unit vector of direction d (incidences inside the cell only).
+// unit vector of direction d (incidences inside the cell only); the 16th
+// value is 1 / centre weight for points inside the cell, else 0.
 template <typename T>
 __global__ void __launch_bounds__(kBlock) divkgrad_stencil_kernel(int n, int w, int64_t stride,
                                                                   int n_rows, const T* kc,
@@ -476,13 +477,19 @@ __global__ void __launch_bounds__(kBlock) divkgrad_stencil_kernel(int n, int w, 
     T kv[kNDir];
     gather15<T>(kc + (int64_t)cell * stride, n, w, i, j, k, kv);
     const unsigned mask = incidence_mask(point_class(n, i, j, k));
+    T centre = T(0);
 #pragma unroll 1
     for (int d = 0; d < kNDir; ++d) {
       T xv[kNDir];
 #pragma unroll
       for (int e = 0; e < kNDir; ++e) xv[e] = e == d ? T(1) : T(0);
-      S[16 * (r0 + i) + d] = divkgrad_point<T, false>(xv, kv, K + (int64_t)cell * 96, mask);
+      const T v = divkgrad_point<T, false>(xv, kv, K + (int64_t)cell * 96, mask);
+      S[16 * (r0 + i) + d] = v;
+      if (d == 0) centre = v;
     }
+    // slot 15: inverse diagonal of points inside the cell (their stencil is complete)
+    S[16 * (r0 + i) + 15] =
+        (point_class(n, i, j, k) == 0 && centre != T(0)) ? T(1) / centre : T(0);
   }
 }
 
