@@ -404,6 +404,81 @@ def p2_comparison(stream, level=6, solve=True):
     return out
 
 
+KERNELS_WORKLOAD = "cube384_L6_p1_laplace_kernels"
+
+
+def kernels_comparison(stream):
+    """Every P1 multigrid kernel on its own, HBM-cold: the 4x4x4 Kuhn cube
+    (384 macro cells), level 6 (17 M DoFs, vectors of 70 MB FP32 > L2),
+    constant-coefficient P1 Laplacian; plus the headline apply L2-hot (the
+    6-cell level-7 x and y reused every rep).  Per kernel: CUDA-event time
+    per launch (mean of 20 after 3 warm-up), algorithmic bytes (unique DoFs
+    of the level, the transfers per fine DoF) and the fraction of the measured
+    HBM bandwidth."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    macro = sg.kuhn_cube(4)
+    L = 6
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), L - 1, L)
+    op = hg.Operator(H)
+    ns, nu, _, _ = H.size(L)
+    nuc = H.size(L - 1)[1]
+    peak, kind = _peaks()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def tm(f, K=20):
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K * 1e-3
+
+    out = {"workload": KERNELS_WORKLOAD, "unique_dofs": int(nu), "peak_gbs": peak,
+           "peak_source": f"{kind} hbm_gbs"}
+
+    def rec(name, t, nbytes, note=None):
+        gbs = nbytes / t / 1e9
+        out[name] = {"us": t * 1e6, "gb_per_s": gbs, "frac": gbs / peak, "bytes": int(nbytes)}
+        if note:
+            out[name]["note"] = note
+
+    for dt, w in ((torch.float32, 4), (torch.float64, 8)):
+        tag = "f32" if dt == torch.float32 else "f64"
+        x = H.from_canonical(L, torch.tensor(sg.uniform_vector(21, nu), dtype=dt, device="cuda"))
+        b = H.from_canonical(L, torch.tensor(sg.uniform_vector(22, nu), dtype=dt, device="cuda"))
+        y = torch.zeros_like(x)
+        rec(f"apply_{tag}", tm(lambda: op.apply(L, x, y, stream=stream)), 2 * w * nu,
+            None if w == 4 else "FP64 arithmetic binds on GB300")
+        rec(f"residual_{tag}", tm(lambda: op.residual(L, x, b, y, stream=stream)), 3 * w * nu)
+        rec(f"jacobi_{tag}", tm(lambda: op.jacobi(L, x, b, y, stream=stream)), 3 * w * nu)
+        if w == 4:
+            xc = torch.zeros(H.size(L - 1)[0], dtype=dt, device="cuda")
+            # restriction: fine residual read, coarse written; prolongation: coarse
+            # read, fine read and written
+            rec("restrict_f32", tm(lambda: H.restrict(L, x, xc, stream=stream)), w * (nu + nuc))
+            rec("prolong_f32", tm(lambda: H.prolong_add(L, xc, y, stream=stream)),
+                w * (2 * nu + nuc))
+            rec("dot_f32", tm(lambda: H.dot(L, x, b, stream=stream), 10), 2 * w * nu,
+                "includes the host read of the result")
+        del x, b, y
+    # the headline apply with x and y resident in L2
+    m1 = sg.kuhn_cube(1)
+    H1 = hg.Hierarchy(hg.Mesh(m1.xyz, m1.cells), LEVEL, LEVEL)
+    op1 = hg.Operator(H1)
+    nu1 = H1.size(LEVEL)[1]
+    x = H1.from_canonical(LEVEL, torch.tensor(sg.uniform_vector(23, nu1), dtype=torch.float32,
+                                              device="cuda"))
+    y = torch.zeros_like(x)
+    rec("apply_f32_l2hot_cube6_L7", tm(lambda: op1.apply(LEVEL, x, y, stream=stream), 200),
+        8 * nu1, "x and y (17 MB) stay in L2; not an HBM figure")
+    return out
+
+
 STENCIL_WORKLOAD = "cube384_L6_p1_lognormal_stored_vs_onthefly"
 
 
@@ -524,6 +599,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-p2", action="store_true")
     ap.add_argument("--no-stencil", action="store_true")
+    ap.add_argument("--no-kernels", action="store_true")
     ap.add_argument("--stencil-case", type=int, nargs=2, default=[4, 6], metavar=("M", "LEVEL"),
                     help="stencil leg mesh (m^3 sub-cubes x 6 cells) and level (smaller for profiling)")
     ap.add_argument("--no-stencil-solve", action="store_true")
@@ -662,6 +738,8 @@ def main():
         out["batch"] = batch_comparison(stream)
     if rank == 0 and not args.no_p2:
         out["p2"] = p2_comparison(stream, args.p2_level, solve=not args.no_p2_solve)
+    if rank == 0 and not args.no_kernels:
+        out["kernels"] = kernels_comparison(stream)
     if rank == 0 and not args.no_stencil:
         out["stencil"] = stencil_comparison(stream, *args.stencil_case,
                                             solve=not args.no_stencil_solve)
