@@ -78,6 +78,15 @@ def kuhn_cube(m: int) -> MacroMesh:
     return MacroMesh(verts, np.array(cells, dtype=np.int64), m, f"kuhn_cube_m{m}")
 
 
+def permuted_cells(macro: MacroMesh, seed: int) -> MacroMesh:
+    """The same mesh with every cell's local vertex order permuted by a seeded
+    draw (PCG64): the refinement and all local orientations change, the
+    domain does not."""
+    g = np.random.Generator(np.random.PCG64(seed))
+    cells = np.array([row[g.permutation(4)] for row in macro.cells], dtype=np.int64)
+    return MacroMesh(macro.vertices, cells, macro.scale, f"{macro.name}_perm{seed}")
+
+
 def uniform_vector(seed: int, n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
     """n values U[lo, hi) in FP64 from numpy's PCG64 stream with the given seed.
 
