@@ -19,8 +19,8 @@ pytestmark = pytest.mark.gpu
 import paper_2308_01792_gb300 as hg
 
 CASES = [(sg.reference_tet(), 2, 4), (sg.kuhn_cube(1), 1, 4), (sg.kuhn_cube(2), 1, 3),
-         (sg.kuhn_cube(1), 1, 6)]
-IDS = ["tet_L2-4", "cube1_L1-4", "cube2_L1-3", "cube1_L1-6"]
+         (sg.kuhn_cube(1), 1, 6), (sg.permuted_cells(sg.kuhn_cube(1), 3), 1, 4)]
+IDS = ["tet_L2-4", "cube1_L1-4", "cube2_L1-3", "cube1_L1-6", "cube1perm_L1-4"]
 
 
 @pytest.fixture(scope="module", params=range(len(CASES)), ids=IDS)

@@ -23,9 +23,12 @@ import paper_2308_01792_gb300 as hg
 
 TOL = {torch.float64: 1e-12, torch.float32: 1e-5}
 
+# the permuted meshes list each cell's vertices in a seeded order, so local and
+# global orientations disagree and the refinement's inner diagonals change
 CASES = [(sg.reference_tet(), 2, 4), (sg.reference_tet(), 0, 6), (sg.kuhn_cube(1), 0, 5),
-         (sg.kuhn_cube(2), 1, 4)]
-IDS = ["tet_L2-4", "tet_L0-6", "cube1_L0-5", "cube2_L1-4"]
+         (sg.kuhn_cube(2), 1, 4), (sg.permuted_cells(sg.kuhn_cube(1), 3), 0, 4),
+         (sg.permuted_cells(sg.kuhn_cube(2), 7), 1, 3)]
+IDS = ["tet_L2-4", "tet_L0-6", "cube1_L0-5", "cube2_L1-4", "cube1perm_L0-4", "cube2perm_L1-3"]
 
 
 @pytest.fixture(scope="module", params=range(len(CASES)), ids=IDS)

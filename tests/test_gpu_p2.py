@@ -26,8 +26,9 @@ import paper_2308_01792_gb300 as hg
 P2 = hg.HG_SPACE_P2
 AB = sg.SINPROD_AB
 KFUN = sg.sinprod_coefficient(*AB)
-CASES = [(sg.kuhn_cube(1), 2), (sg.kuhn_cube(1), 3), (sg.kuhn_cube(2), 2), (sg.reference_tet(), 3)]
-IDS = ["cube1_L2", "cube1_L3", "cube2_L2", "tet_L3"]
+CASES = [(sg.kuhn_cube(1), 2), (sg.kuhn_cube(1), 3), (sg.kuhn_cube(2), 2), (sg.reference_tet(), 3),
+         (sg.permuted_cells(sg.kuhn_cube(1), 3), 2)]
+IDS = ["cube1_L2", "cube1_L3", "cube2_L2", "tet_L3", "cube1perm_L2"]
 
 
 @pytest.fixture(scope="module", params=range(len(CASES)), ids=IDS)
