@@ -71,11 +71,19 @@ enum {
   HG_OP_P2_MASS = 4,     /* P2 mass, element-wise                                */
   HG_OP_P2_DIVKGRAD = 5, /* P2 -div(k grad), k(x) = a + b sin2pix sin2piy sin2piz
                             by quadrature on the fly                             */
-  HG_OP_P1_DIVKGRAD_STORED = 6 /* HG_OP_P1_DIVKGRAD with grid-aware precomputation
+  HG_OP_P1_DIVKGRAD_STORED = 6, /* HG_OP_P1_DIVKGRAD with grid-aware precomputation
                             (Sec. 5.2): the 15-point partial stencil of every
                             stored point kept in HBM (16 values per stored DoF
                             and level: 15 weights and the inverse centre weight;
                             FP64 and FP32 copies) and streamed by the apply     */
+  HG_OP_N1_CURLCURL = 7  /* lowest-order Nedelec (first kind) alpha curl curl +
+                            beta I, coeff = {alpha >= 0, beta > 0}: one DoF per
+                            micro-edge (tangential line integral, oriented from
+                            the lower to the higher canonical vertex key),
+                            stored as HG_SPACE_P2 vectors at the edge-midpoint
+                            points (vertex points stay 0); element-wise 6x6
+                            matrices; apply, residual, Jacobi and Chebyshev
+                            steps (no multigrid yet)                           */
 };
 
 typedef struct hg_mesh hg_mesh;
@@ -166,7 +174,8 @@ int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
 /* ---------------------------------------------------------- operators --
  * kind: HG_OP_*.  coeff: for HG_OP_P1_DIVKGRAD(_STORED), host array of k at the
  * unique vertices of level lmax in canonical order (injected to coarser
- * levels); for HG_OP_P2_DIVKGRAD, host {a, b}; otherwise NULL.
+ * levels); for HG_OP_P2_DIVKGRAD, host {a, b}; for HG_OP_N1_CURLCURL, host
+ * {alpha, beta}; otherwise NULL.
  * P2 operators (levels max(0, lmin-1) .. lmax-1 of the hierarchy) are
  * element-wise: per micro-cell the 10x10 element matrix acts on the fly by
  * the 14-point rule of hg_quadrature_rule, with k evaluated exactly at every

@@ -22,6 +22,7 @@ HG_REPLACE, HG_ADD = 0, 1
 HG_MASK_INNER, HG_MASK_ALL = 0, 1
 HG_OP_P1_LAPLACE, HG_OP_P1_MASS, HG_OP_P1_DIVKGRAD = 0, 1, 2
 HG_OP_P1_DIVKGRAD_STORED = 6
+HG_OP_N1_CURLCURL = 7
 HG_OP_P2_LAPLACE, HG_OP_P2_MASS, HG_OP_P2_DIVKGRAD = 3, 4, 5
 
 _P = ctypes.c_void_p

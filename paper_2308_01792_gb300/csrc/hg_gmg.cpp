@@ -484,6 +484,10 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
               op->lmax);
     return HG_ERR_LEVEL_RANGE;
   }
+  if (op->kind == HG_OP_N1_CURLCURL) {
+    set_error("multigrid for the Nedelec operator (Hiptmair smoothing, N1 transfers) is not built");
+    return HG_ERR_UNSUPPORTED;
+  }
   if (g->prm.smoother != HG_SMOOTH_JACOBI && g->prm.smoother != HG_SMOOTH_GS &&
       g->prm.smoother != HG_SMOOTH_CHEB) {
     set_error("unknown smoother %d", g->prm.smoother);

@@ -611,6 +611,7 @@ int Op::build(const Hier* h, int kind_, const double* coeff) {
   lmax = h->lmax;
   if (kind == HG_OP_P2_LAPLACE || kind == HG_OP_P2_MASS || kind == HG_OP_P2_DIVKGRAD)
     return build_p2(coeff);
+  if (kind == HG_OP_N1_CURLCURL) return build_n1(coeff);
   if (kind == HG_OP_P1_DIVKGRAD) return build_divkgrad(coeff);
   if (kind == HG_OP_P1_DIVKGRAD_STORED) {
     if (int r = build_divkgrad(coeff)) return r;

@@ -95,6 +95,7 @@ struct Op {
   const LevelHost& host(int l) const { return hier->lv[lattice_index(hier, space, l)]; }
   const LevelDev& dev(int l) const { return host(l).dev; }
   int build_p2(const double* coeff);
+  int build_n1(const double* coeff);
   std::vector<double*> sten64;  // per level [ncells][16][16] (constant-coefficient kinds)
   std::vector<float*> sten32;
   std::vector<int> pattern;     // per level: kPat7 when the interior stencils allow it

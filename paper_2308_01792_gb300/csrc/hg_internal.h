@@ -239,7 +239,18 @@ struct P2Cell {
   T vol;             // micro-cell volume (mass element matrix = vol * M_ref)
   T pad;
 };
-enum { P2_STIFF = 0, P2_MASS = 1, P2_DIAG = 2 };
+enum { P2_STIFF = 0, P2_MASS = 1, P2_DIAG = 2, P2_N1 = 3, P2_N1DIAG = 4 };
+// Lowest-order Nedelec (N1) operator alpha curl curl + beta I of one macro
+// cell and level: the DoFs are the micro-edges, stored at the edge-midpoint
+// points of the same level+1 lattice as the P2 edge DoFs (the vertex points
+// stay zero).  Per micro-cell type the 6x6 element matrix (local edges
+// (0,1),(0,2),(0,3),(1,2),(1,3),(2,3)) with the orientation signs of the
+// cell folded in; affine cells make it the same for every micro-cell of a
+// type.
+template <typename T>
+struct N1Cell {
+  T K[6][36];
+};
 // Apply of one P2 level: 8 colour phases accumulate the element products
 // into acc (zeroed first), a finish pass sums interface copies and forms the
 // operation (apply / residual / Jacobi with invdiag / 1 / diagonal).

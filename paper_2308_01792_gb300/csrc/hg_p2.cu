@@ -223,6 +223,81 @@ __global__ void __launch_bounds__(kP2Block, P2MinBlocks<T>::value) p2_phase_kern
   }
 }
 
+// N1 colour phase (lowest-order Nedelec, alpha curl curl + beta I): the same
+// anchors and cubes as the P2 phases; the DoFs are the cube points with an
+// odd doubled coordinate (edge midpoints), and every micro-cell applies its
+// type's 6x6 matrix from the cell's table (DIAG: adds the diagonal only).
+// Points of the cube that are no micro-edge of its cells receive 0.
+template <typename T, bool DIAG>
+__global__ void __launch_bounds__(kP2Block) n1_phase_kernel(const N1Cell<T>* __restrict__ cells,
+                                                            const uint32_t* __restrict__ anchors,
+                                                            int n_anchors, int n, int64_t stride,
+                                                            const T* __restrict__ x,
+                                                            T* __restrict__ acc) {
+  __shared__ N1Cell<T> C;
+  const int cell = blockIdx.y;
+  {
+    const int* src = reinterpret_cast<const int*>(cells + cell);
+    int* dst = reinterpret_cast<int*>(&C);
+    for (int q = threadIdx.x; q < (int)(sizeof(N1Cell<T>) / 4); q += blockDim.x) dst[q] = src[q];
+  }
+  __syncthreads();
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= n_anchors) return;
+  const uint32_t pk = __ldg(anchors + a);
+  const int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
+  const int s = i + j + k;
+  const int w2 = 2 * n + 1;
+  const int64_t base = (int64_t)cell * stride;
+  const T* __restrict__ xc = x + base;
+  T* __restrict__ yc = acc + base;
+  int rs[3][3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rs[b][c] = row_start(w2, 2 * j + b, 2 * k + c);
+  T X[27], Y[27];
+#pragma unroll
+  for (int c = 0; c < 27; ++c) {
+    const int dx = c % 3, dy = (c / 3) % 3, dz = c / 9;
+    const bool dof = ((dx | dy | dz) & 1) && 2 * s + dx + dy + dz <= 2 * n;
+    X[c] = (DIAG || !dof) ? T(0) : xc[rs[dy][dz] + 2 * i + dx];
+    Y[c] = T(0);
+  }
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    if (s > n - 1 - kDelta[t]) continue;
+    int eid[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int va = kEdge[e][0], vb = kEdge[e][1];
+      eid[e] = (kToff[t][va][0] + kToff[t][vb][0]) + 3 * (kToff[t][va][1] + kToff[t][vb][1]) +
+               9 * (kToff[t][va][2] + kToff[t][vb][2]);
+    }
+    const T* K = C.K[t];
+    if (DIAG) {
+#pragma unroll
+      for (int e = 0; e < 6; ++e) Y[eid[e]] += K[7 * e];
+    } else {
+      T xv[6];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) xv[e] = X[eid[e]];
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        T v = T(0);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) v += K[6 * e + f] * xv[f];
+        Y[eid[e]] += v;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 27; ++c) {
+    const int dx = c % 3, dy = (c / 3) % 3, dz = c / 9;
+    if (((dx | dy | dz) & 1) && 2 * s + dx + dy + dz <= 2 * n) yc[rs[dy][dz] + 2 * i + dx] += Y[c];
+  }
+}
+
 // Finish pass of one apply on the lattice L of the P2 level.
 template <typename T>
 struct P2Fin {
@@ -370,6 +445,22 @@ P2Fin<T> fin_args(const LevelDev& L, const StencilArgs& a, const P2Args& P, int 
   return F;
 }
 
+template <typename T, bool DIAG>
+int run_phases_n1(const P2Args& P, int64_t stride, const void* x, void* acc, int64_t n_stored,
+                  cudaStream_t s) {
+  HG_CUDA(cudaMemsetAsync(acc, 0, n_stored * sizeof(T), s));
+  const int* off = P.anchor_off;
+  for (int col = 0; col < 8; ++col) {
+    const int na = off[col + 1] - off[col];
+    if (na == 0) continue;
+    const dim3 grid((na + kP2Block - 1) / kP2Block, P.ncells);
+    n1_phase_kernel<T, DIAG><<<grid, kP2Block, 0, s>>>(
+        (const N1Cell<T>*)P.cells, P.anchors + off[col], na, P.n, stride, (const T*)x, (T*)acc);
+    HG_CUDA(cudaGetLastError());
+  }
+  return HG_OK;
+}
+
 template <typename T, int OP>
 int run_finish(const LevelDev& L, const StencilArgs& a, const P2Args& P, cudaStream_t s) {
   const int n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_citems_inner : L.n_citems;
@@ -383,8 +474,9 @@ int run_finish(const LevelDev& L, const StencilArgs& a, const P2Args& P, cudaStr
 template <typename T>
 int run_p2(const LevelDev& L, const StencilArgs& a, const P2Args& P, cudaStream_t s) {
   const void* x = a.x;
-  int r = P.mode == P2_MASS ? run_phases<T, P2_MASS>(P, L.cell_stride, x, P.acc, L.n_stored, s)
-                            : run_phases<T, P2_STIFF>(P, L.cell_stride, x, P.acc, L.n_stored, s);
+  int r = P.mode == P2_N1     ? run_phases_n1<T, false>(P, L.cell_stride, x, P.acc, L.n_stored, s)
+          : P.mode == P2_MASS ? run_phases<T, P2_MASS>(P, L.cell_stride, x, P.acc, L.n_stored, s)
+                              : run_phases<T, P2_STIFF>(P, L.cell_stride, x, P.acc, L.n_stored, s);
   if (r) return r;
   switch (a.op) {
     case OP_APPLY: return run_finish<T, OP_APPLY>(L, a, P, s);
@@ -425,12 +517,15 @@ int launch_p2_diag(const LevelDev& L, int dtype, const P2Args& P, void* invdiag,
   a.mode = HG_REPLACE;
   a.mask = HG_MASK_ALL;
   a.op = OP_INVDIAG;
+  const bool n1 = P.mode == P2_N1;
   if (dtype == HG_F64) {
-    if (int r = run_phases<double, P2_DIAG>(P, L.cell_stride, nullptr, P.acc, L.n_stored, s))
+    if (int r = n1 ? run_phases_n1<double, true>(P, L.cell_stride, nullptr, P.acc, L.n_stored, s)
+                   : run_phases<double, P2_DIAG>(P, L.cell_stride, nullptr, P.acc, L.n_stored, s))
       return r;
     return run_finish<double, OP_INVDIAG>(L, a, P, s);
   }
-  if (int r = run_phases<float, P2_DIAG>(P, L.cell_stride, nullptr, P.acc, L.n_stored, s))
+  if (int r = n1 ? run_phases_n1<float, true>(P, L.cell_stride, nullptr, P.acc, L.n_stored, s)
+                 : run_phases<float, P2_DIAG>(P, L.cell_stride, nullptr, P.acc, L.n_stored, s))
     return r;
   return run_finish<float, OP_INVDIAG>(L, a, P, s);
 }

@@ -163,4 +163,122 @@ int Op::build_p2(const double* coeff) {
   return HG_OK;
 }
 
+// Lowest-order Nedelec operator alpha curl curl + beta I on the P2 storage
+// (edge DoFs; Sec. 6, Nedelec elements for the curl-curl problem).  Per cell
+// and type the 6x6 element matrix of the Whitney basis
+//   w_e = l_a grad l_b - l_b grad l_a,  curl w_e = 2 grad l_a x grad l_b,
+//   K_ef = |T| curl w_e . curl w_f,  M_ef = int w_e . w_f (int l_i l_j = |T| (1 + d_ij) / 20),
+// scaled by the signs that map the local edge a -> b to the global
+// orientation (lower canonical key -> higher: the first nonzero of dz, dy, dx
+// of the edge vector is positive).
+int Op::build_n1(const double* coeff) {
+  space = HG_SPACE_P2;
+  lmin = std::max(0, hier->lmin - 1);
+  lmax = hier->lmax - 1;
+  if (lmax < lmin || lmax < 0) {
+    set_error("N1 needs a hierarchy with at least two levels above 0 (N1 level l uses lattice l+1)");
+    return HG_ERR_LEVEL_RANGE;
+  }
+  if (!coeff || !(coeff[0] >= 0.0) || !(coeff[1] > 0.0)) {
+    set_error("HG_OP_N1_CURLCURL needs coeff = {alpha >= 0, beta > 0}");
+    return HG_ERR_INVALID_ARG;
+  }
+  const double alpha = coeff[0], beta = coeff[1];
+  p2mode = P2_N1;
+  const Mesh& m = *hier->mesh;
+  const int nl = lmax - lmin + 1;
+  for (int dt = 0; dt < 2; ++dt) {
+    p2cells[dt].assign(nl, nullptr);
+    p2acc[dt].assign(nl, nullptr);
+    p2inv[dt].assign(nl, nullptr);
+  }
+  p2anchors.assign(nl, nullptr);
+  p2off.assign(nl, std::vector<int>(9, 0));
+  for (int l = lmin; l <= lmax; ++l) {
+    const int li = l - lmin, n = 1 << l;
+    if (n > 1023) {
+      set_error("N1 level %d too fine for packed anchors", l);
+      return HG_ERR_LEVEL_RANGE;
+    }
+    std::vector<uint32_t> anch;
+    for (int col = 0; col < 8; ++col) {
+      p2off[li][col] = (int)anch.size();
+      for (int k = col >> 2 & 1; k <= n - 1; k += 2)
+        for (int j = col >> 1 & 1; j + k <= n - 1; j += 2)
+          for (int i = col & 1; i + j + k <= n - 1; i += 2)
+            anch.push_back((uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20));
+    }
+    p2off[li][8] = (int)anch.size();
+    if (int r = upload_vec((void**)&p2anchors[li], anch)) return r;
+    std::vector<N1Cell<double>> c64(m.nc);
+    std::vector<N1Cell<float>> c32(m.nc);
+    for (int64_t c = 0; c < m.nc; ++c) {
+      const double* V[4];
+      for (int q = 0; q < 4; ++q) V[q] = &m.xyz[3 * m.cells[c][q]];
+      for (int t = 0; t < 6; ++t) {
+        double X[4][3], G[4][3], vol;
+        for (int a = 0; a < 4; ++a)
+          for (int r = 0; r < 3; ++r)
+            X[a][r] = V[0][r] + (kTypeOffP2[t][a][0] * (V[1][r] - V[0][r]) +
+                                 kTypeOffP2[t][a][1] * (V[2][r] - V[0][r]) +
+                                 kTypeOffP2[t][a][2] * (V[3][r] - V[0][r])) / (double)n;
+        bary_gradients(X, G, &vol);
+        double C[6][3], sg[6];
+        for (int e = 0; e < 6; ++e) {
+          const int a = kP2Edges[e][0], b = kP2Edges[e][1];
+          C[e][0] = 2.0 * (G[a][1] * G[b][2] - G[a][2] * G[b][1]);
+          C[e][1] = 2.0 * (G[a][2] * G[b][0] - G[a][0] * G[b][2]);
+          C[e][2] = 2.0 * (G[a][0] * G[b][1] - G[a][1] * G[b][0]);
+          double d[3], len = 0.0;
+          for (int r = 0; r < 3; ++r) {
+            d[r] = X[b][r] - X[a][r];
+            len += d[r] * d[r];
+          }
+          const double tol = 1e-9 * std::sqrt(len);
+          sg[e] = std::fabs(d[2]) > tol ? (d[2] > 0 ? 1.0 : -1.0)
+                  : std::fabs(d[1]) > tol ? (d[1] > 0 ? 1.0 : -1.0)
+                                          : (d[0] > 0 ? 1.0 : -1.0);
+        }
+        double GG[4][4];
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b)
+            GG[a][b] = G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2];
+        auto L = [](int i, int j) { return (i == j ? 2.0 : 1.0) / 20.0; };
+        for (int e = 0; e < 6; ++e)
+          for (int f = 0; f < 6; ++f) {
+            const int a = kP2Edges[e][0], b = kP2Edges[e][1];
+            const int cc = kP2Edges[f][0], dd = kP2Edges[f][1];
+            const double kc = C[e][0] * C[f][0] + C[e][1] * C[f][1] + C[e][2] * C[f][2];
+            const double ms = L(a, cc) * GG[b][dd] - L(a, dd) * GG[b][cc] - L(b, cc) * GG[a][dd] +
+                              L(b, dd) * GG[a][cc];
+            const double v = sg[e] * sg[f] * vol * (alpha * kc + beta * ms);
+            c64[c].K[t][6 * e + f] = v;
+            c32[c].K[t][6 * e + f] = (float)v;
+          }
+      }
+    }
+    if (int r = upload_vec(&p2cells[HG_F64][li], c64)) return r;
+    if (int r = upload_vec(&p2cells[HG_F32][li], c32)) return r;
+    const LevelDev& Ld = dev(l);
+    for (int dt = 0; dt < 2; ++dt) {
+      const size_t bytes = Ld.n_stored * (dt == HG_F64 ? 8 : 4);
+      HG_CUDA(cudaMalloc(&p2acc[dt][li], bytes));
+      HG_CUDA(cudaMalloc(&p2inv[dt][li], bytes));
+      HG_CUDA(cudaMemset(p2inv[dt][li], 0, bytes));
+      P2Args A;
+      A.n = n;
+      A.ncells = (int)m.nc;
+      A.cells = p2cells[dt][li];
+      A.anchors = p2anchors[li];
+      for (int q = 0; q < 9; ++q) A.anchor_off[q] = p2off[li][q];
+      A.mode = P2_N1;
+      A.acc = p2acc[dt][li];
+      A.invdiag = nullptr;
+      if (int r = launch_p2_diag(Ld, dt, A, p2inv[dt][li], 0)) return r;
+    }
+  }
+  HG_CUDA(cudaDeviceSynchronize());
+  return HG_OK;
+}
+
 }  // namespace hg
