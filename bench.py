@@ -404,6 +404,54 @@ def p2_comparison(stream, level=6, solve=True):
     return out
 
 
+N1_WORKLOAD = "cube48_L6_n1_curlcurl_apply"
+
+
+def n1_comparison(stream, level=6):
+    """Lowest-order Nedelec alpha curl curl + beta I (alpha = 1, beta = 0.3) on
+    the unit cube as 2x2x2 sub-cubes x 6 Kuhn tetrahedra (48 macro cells),
+    N1 level 6 (one DoF per micro-edge): FP32 and FP64 element-wise apply
+    (colour phases + finish pass), CUDA-event time per apply, 4 rotating
+    input vectors (> L2)."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    P2 = hg.HG_SPACE_P2
+    macro = sg.kuhn_cube(2)
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), level, level + 1)
+    op = hg.Operator(H, hg.HG_OP_N1_CURLCURL, coeff=(1.0, 0.3))
+    ns, nu, _, _ = H.size(level, space=P2)
+    n = 1 << level
+    cells = len(macro.cells)
+    # unique micro-edges = doubled-lattice points of the cube (2 * 2n + 1 per
+    # side for 2 sub-cubes per side) minus its vertex points (2n + 1 per side)
+    edges = (4 * n + 1) ** 3 - (2 * n + 1) ** 3
+    peak, kind = _peaks()
+    out = {"workload": N1_WORKLOAD, "edge_dofs": int(edges), "micro_cells": int(cells * 8 ** level)}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for dt, w in ((torch.float32, 4), (torch.float64, 8)):
+        xs = [torch.rand(ns, dtype=dt, device="cuda") for _ in range(4)]
+        ys = [torch.zeros_like(v) for v in xs]
+        for q in range(3):
+            op.apply(level, xs[q], ys[q], stream=stream)
+        torch.cuda.synchronize()
+        K = 20
+        e0.record(stream)
+        for q in range(K):
+            op.apply(level, xs[q % 4], ys[q % 4], stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / K * 1e-3
+        gbs = 2 * w * edges / t / 1e9
+        out["apply_f32" if w == 4 else "apply_f64"] = {
+            "us": t * 1e6, "gdof_per_s": edges / t / 1e9,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "peak_source": f"{kind} hbm_gbs",
+                         "algorithmic_bytes_per_launch": 2 * w * edges}}
+        del xs, ys
+    return out
+
+
 KERNELS_WORKLOAD = "cube384_L6_p1_laplace_kernels"
 
 
@@ -600,6 +648,7 @@ def main():
     ap.add_argument("--no-p2", action="store_true")
     ap.add_argument("--no-stencil", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
+    ap.add_argument("--no-n1", action="store_true")
     ap.add_argument("--stencil-case", type=int, nargs=2, default=[4, 6], metavar=("M", "LEVEL"),
                     help="stencil leg mesh (m^3 sub-cubes x 6 cells) and level (smaller for profiling)")
     ap.add_argument("--no-stencil-solve", action="store_true")
@@ -738,6 +787,8 @@ def main():
         out["batch"] = batch_comparison(stream)
     if rank == 0 and not args.no_p2:
         out["p2"] = p2_comparison(stream, args.p2_level, solve=not args.no_p2_solve)
+    if rank == 0 and not args.no_n1:
+        out["n1"] = n1_comparison(stream)
     if rank == 0 and not args.no_kernels:
         out["kernels"] = kernels_comparison(stream)
     if rank == 0 and not args.no_stencil:
