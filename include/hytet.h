@@ -187,6 +187,20 @@ int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
  * element matrices on the fly for variable coefficients). */
 int hg_op_create(const hg_hier* hier, int kind, const double* coeff, hg_op** out);
 
+/* Class table of the lowest-order Nedelec prolongation (host, needs no GPU).
+ * A fine N1 DoF sits at an odd point q of the fine F lattice (the level+1
+ * lattice of the fine N1 level); with q = 4p + r, r in {0..3}^3 and class
+ * c = r_x + 4 r_y + 16 r_z, its value is
+ *   s[fine_dir[c]] * sum_{t < n[c]} w[6c+t] * s[dir[6c+t]] * u_C(2p + off[6c+t])
+ * where u_C are the coarse N1 DoFs on the C lattice, off packs (x | y << 2 |
+ * z << 4), s[d] is the orientation sign of lattice direction d in the macro
+ * cell (+1 when its physical vector has a positive first nonzero of z, y, x)
+ * and the directions d = 0..6 are (1,0,0), (0,1,0), (-1,1,0), (0,0,1),
+ * (-1,0,1), (0,-1,1), (1,-1,1) (the midpoints of direction d have parity
+ * class d + 1).  Outputs (host, any may be NULL): n[64], off[384], dir[384],
+ * w[384], fine_dir[64] (-1 for classes of vertex points). */
+int hg_n1_prolong_table(int* n, int* off, int* dir, double* w, int* fine_dir);
+
 /* The quadrature rule of the P2 element matrices: the symmetric 14-point,
  * degree-5, positive-weight rule (orbits 4+4+6), derived by the library from
  * its moment equations.  Host outputs: bary 14x4 barycentric coordinates,

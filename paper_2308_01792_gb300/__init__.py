@@ -85,6 +85,7 @@ SIGNATURES = {
     "hg_gmg_set_lambda": (_I, [_P, _I, _D]),
     "hg_gmg_power_lambda": (_I, [_P, _I, _P, _I, _PD, _P]),
     "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
+    "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
 }
 
 HG_BATCH_GRAPH, HG_BATCH_AUTOTUNE = 1, 2
@@ -493,6 +494,19 @@ def learn_samples(op, level, r, xstar, x, omega, stride, offset, stream=None):
     _call("hg_learn_samples", op._h, level, _ptr(r), _ptr(xstar), _ptr(x), omega, stride, offset,
           _ptr(X), _ptr(t), ctypes.byref(cnt), _stream(stream))
     return X, t
+
+
+def n1_prolong_table():
+    """The library's Nedelec prolongation class table (host): dict of numpy
+    arrays n (64,), off, dir, w (64, 6), fine_dir (64,)."""
+    n = np.zeros(64, dtype=np.int32)
+    off = np.zeros((64, 6), dtype=np.int32)
+    dr = np.zeros((64, 6), dtype=np.int32)
+    w = np.zeros((64, 6), dtype=np.float64)
+    fd = np.zeros(64, dtype=np.int32)
+    _call("hg_n1_prolong_table", n.ctypes.data_as(_P), off.ctypes.data_as(_P),
+          dr.ctypes.data_as(_P), w.ctypes.data_as(_P), fd.ctypes.data_as(_P))
+    return {"n": n, "off": off, "dir": dr, "w": w, "fine_dir": fd}
 
 
 def quadrature_rule():

@@ -112,6 +112,23 @@ struct Op {
   ~Op();
 };
 
+// Lowest-order Nedelec prolongation by fine-point class r = q mod 4 (q in
+// the fine F lattice): up to 6 terms, coarse DoF at C-lattice offset `off`
+// (x | y << 2 | z << 4) from 2 floor(q / 4), its lattice direction `dir`
+// (index into kN1Dir) and the weight with the local orientation folded in;
+// fine_dir: the direction of the fine edge at q (-1 for vertex points).
+struct N1ProlongTable {
+  int n[64];
+  int off[64][6];
+  int dir[64][6];
+  double w[64][6];
+  int fine_dir[64];
+};
+// The 7 lattice edge directions, index = parity class (x | y << 1 | z << 2)
+// of the edge midpoints minus 1.
+extern const int kN1Dir[7][3];
+int n1_prolong_table(const N1ProlongTable** out);
+
 // Parameters and optimiser state of the learned smoother network (device).
 struct Mlp {
   float* params = nullptr;   // kMlpParams
