@@ -201,6 +201,15 @@ int hg_op_create(const hg_hier* hier, int kind, const double* coeff, hg_op** out
  * w[384], fine_dir[64] (-1 for classes of vertex points). */
 int hg_n1_prolong_table(int* n, int* off, int* dir, double* w, int* fine_dir);
 
+/* The transpose of that table, per coarse parity class pc = 1..7 (the coarse
+ * DoF c has direction pc - 1): entries start[pc] .. start[pc+1]-1 (start: 9
+ * ints, start[8] = total, at most 512) give the fine points 2c + delta
+ * (delta packed as dx+8 | (dy+8) << 5 | (dz+8) << 10, F-lattice units), so
+ *   r_C(c) = s[pc-1] * sum_e w[e] * s[fine_dir[e]] * r_F(2c + delta[e])
+ * over the fine points inside the cell.  Host, needs no GPU; any output may
+ * be NULL (d, w, fine_dir: at least start[8] entries). */
+int hg_n1_restrict_table(int* start, int* d, double* w, int* fine_dir);
+
 /* The quadrature rule of the P2 element matrices: the symmetric 14-point,
  * degree-5, positive-weight rule (orbits 4+4+6), derived by the library from
  * its moment equations.  Host outputs: bary 14x4 barycentric coordinates,

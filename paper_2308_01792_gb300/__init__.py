@@ -86,6 +86,7 @@ SIGNATURES = {
     "hg_gmg_power_lambda": (_I, [_P, _I, _P, _I, _PD, _P]),
     "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
+    "hg_n1_restrict_table": (_I, [_P, _P, _P, _P]),
 }
 
 HG_BATCH_GRAPH, HG_BATCH_AUTOTUNE = 1, 2
@@ -507,6 +508,20 @@ def n1_prolong_table():
     _call("hg_n1_prolong_table", n.ctypes.data_as(_P), off.ctypes.data_as(_P),
           dr.ctypes.data_as(_P), w.ctypes.data_as(_P), fd.ctypes.data_as(_P))
     return {"n": n, "off": off, "dir": dr, "w": w, "fine_dir": fd}
+
+
+def n1_restrict_table():
+    """The transposed (restriction) lists of the Nedelec prolongation table
+    (host): dict with start (9,), d, w, fine_dir (start[8],)."""
+    start = np.zeros(9, dtype=np.int32)
+    _call("hg_n1_restrict_table", start.ctypes.data_as(_P), None, None, None)
+    m = int(start[8])
+    d = np.zeros(max(m, 1), dtype=np.int32)
+    w = np.zeros(max(m, 1), dtype=np.float64)
+    fd = np.zeros(max(m, 1), dtype=np.int32)
+    _call("hg_n1_restrict_table", start.ctypes.data_as(_P), d.ctypes.data_as(_P),
+          w.ctypes.data_as(_P), fd.ctypes.data_as(_P))
+    return {"start": start, "d": d[:m], "w": w[:m], "fine_dir": fd[:m]}
 
 
 def quadrature_rule():

@@ -117,12 +117,21 @@ struct Op {
 // (x | y << 2 | z << 4) from 2 floor(q / 4), its lattice direction `dir`
 // (index into kN1Dir) and the weight with the local orientation folded in;
 // fine_dir: the direction of the fine edge at q (-1 for vertex points).
+// The restriction r_C = P^T r_F by coarse parity class pc (1..7; the coarse
+// DoF's direction is pc - 1): entries res_start[pc] .. res_start[pc+1]-1
+// with the fine point at F-lattice offset res_d (dx+8 | dy+8 << 5 | dz+8 <<
+// 10) from 2c, the weight and the fine point's direction.
+constexpr int kN1MaxRes = 512;
 struct N1ProlongTable {
   int n[64];
   int off[64][6];
   int dir[64][6];
   double w[64][6];
   int fine_dir[64];
+  int res_start[9];
+  int res_d[kN1MaxRes];
+  double res_w[kN1MaxRes];
+  int res_fdir[kN1MaxRes];
 };
 // The 7 lattice edge directions, index = parity class (x | y << 1 | z << 2)
 // of the edge midpoints minus 1.

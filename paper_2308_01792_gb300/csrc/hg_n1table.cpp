@@ -21,7 +21,8 @@
 // kernel multiplies by the orientation signs of the cell (one per lattice
 // direction: +1 when the direction's physical vector has a positive first
 // nonzero of z, y, x, the order of the canonical keys) for the fine and the
-// coarse DoF.
+// coarse DoF.  The restriction (the exact transpose) reads the same terms
+// regrouped per coarse DoF parity class.
 #include <cstring>
 #include <mutex>
 
@@ -119,6 +120,30 @@ int build() {
       T.w[cl][q] = sgn * w;
     }
   }
+  // transposed lists: the fine point q = 4p + r feeds the coarse DoF
+  // c = 2p + o, i.e. sits at F offset r - 2o from 2c (each pair once)
+  int cnt[8] = {};
+  for (int cl = 0; cl < 64; ++cl)
+    for (int q = 0; q < T.n[cl]; ++q) ++cnt[T.dir[cl][q] + 1];
+  T.res_start[0] = T.res_start[1] = 0;
+  for (int pc = 1; pc < 8; ++pc) T.res_start[pc + 1] = T.res_start[pc] + cnt[pc];
+  if (T.res_start[8] > kN1MaxRes) {
+    set_error("N1 transfer table: restriction lists too long");
+    return HG_ERR_INVALID_ARG;
+  }
+  int fill[8];
+  for (int pc = 0; pc < 8; ++pc) fill[pc] = T.res_start[pc];
+  for (int cl = 0; cl < 64; ++cl) {
+    const int r[3] = {cl & 3, (cl >> 2) & 3, cl >> 4};
+    for (int q = 0; q < T.n[cl]; ++q) {
+      const int o = T.off[cl][q];
+      const int dx = r[0] - 2 * (o & 3), dy = r[1] - 2 * ((o >> 2) & 3), dz = r[2] - 2 * (o >> 4);
+      const int e = fill[T.dir[cl][q] + 1]++;
+      T.res_d[e] = (dx + 8) | ((dy + 8) << 5) | ((dz + 8) << 10);
+      T.res_w[e] = T.w[cl][q];
+      T.res_fdir[e] = T.fine_dir[cl];
+    }
+  }
   return HG_OK;
 }
 
@@ -135,6 +160,19 @@ int n1_prolong_table(const N1ProlongTable** out) {
 }
 
 }  // namespace hg
+
+extern "C" int hg_n1_restrict_table(int* start, int* d, double* w, int* fine_dir) {
+  const hg::N1ProlongTable* T = nullptr;
+  if (int r = hg::n1_prolong_table(&T)) return r;
+  for (int c = 0; c < 9; ++c)
+    if (start) start[c] = T->res_start[c];
+  for (int e = 0; e < T->res_start[8]; ++e) {
+    if (d) d[e] = T->res_d[e];
+    if (w) w[e] = T->res_w[e];
+    if (fine_dir) fine_dir[e] = T->res_fdir[e];
+  }
+  return HG_OK;
+}
 
 extern "C" int hg_n1_prolong_table(int* n, int* off, int* dir, double* w, int* fine_dir) {
   const hg::N1ProlongTable* T = nullptr;

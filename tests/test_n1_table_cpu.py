@@ -78,3 +78,29 @@ def test_table_shape():
     # half-edges of coarse edges take half of the coarse DoF
     w = T["w"][T["w"] != 0]
     assert set(np.abs(w)) <= {0.25, 0.5}
+
+
+@pytest.mark.parametrize("macro", MESHES, ids=lambda m: m.name)
+def test_restriction_lists_are_the_transpose(macro):
+    R = hg.n1_restrict_table()
+    V = macro.vertices[macro.cells[0]]
+    E = np.stack([V[1] - V[0], V[2] - V[0], V[3] - V[0]])
+    s = _signs(E)
+    L = 2
+    fine, coarse = ne.NedelecLevel(macro, L), ne.NedelecLevel(macro, L - 1)
+    qf, fi = _edge_points(fine, V[0], E, L)
+    qc, ci = _edge_points(coarse, V[0], E, L - 1)
+    fidx = {tuple(p): i for p, i in zip(qf, fi)}
+    rf = sg.uniform_vector(32, fine.n)
+    ref = ne.nedelec_prolongation(fine, coarse).T @ rf
+    got = np.zeros(coarse.n)
+    for c, i in zip(qc, ci):
+        pc = (c[0] & 1) | ((c[1] & 1) << 1) | ((c[2] & 1) << 2)
+        acc = 0.0
+        for e in range(R["start"][pc], R["start"][pc + 1]):
+            dd = R["d"][e]
+            q = tuple(2 * c + np.array([(dd & 31) - 8, ((dd >> 5) & 31) - 8, (dd >> 10) - 8]))
+            if q in fidx:
+                acc += R["w"][e] * s[R["fine_dir"][e]] * rf[fidx[q]]
+        got[i] = s[pc - 1] * acc
+    assert np.allclose(got, ref, rtol=0, atol=1e-14)
