@@ -144,3 +144,70 @@ def test_p1_divkgrad_reduces_to_laplace_for_constant_k():
     A = fem.assemble(rm.cells, fem.p1_divkgrad(X, kv), rm.n_vertices)
     assert np.abs(A @ np.ones(rm.n_vertices)).max() < 1e-13
     assert abs(A - A.T).max() < 1e-14
+
+
+def _rand_tets(seed, count):
+    g = np.random.Generator(np.random.PCG64(seed))
+    X = g.uniform(-1, 1, size=(count, 4, 3))
+    return X
+
+
+def test_p1_divkgrad_is_the_exact_integral_for_linear_k():
+    """k linear: int_T k grad l_i . grad l_j = k(centroid) |T| grad l_i . grad l_j,
+    and k(centroid) is the mean of the vertex values.  Checked against a
+    degree-7 conical-product quadrature of k at the points (independent of the
+    vertex-mean formula)."""
+    X = _rand_tets(5, 6)
+    a, c = 0.7, np.array([0.3, -0.5, 0.9])
+
+    def k(x):
+        return a + x @ c
+
+    G, vol = fem.bary_gradients(X)
+    bary, w = quadrature.stroud_conical(4)
+    pts = np.einsum("qi,tid->tqd", bary, X)
+    kint = vol * np.einsum("q,tq->t", w, k(pts.reshape(-1, 3)).reshape(pts.shape[:2]))
+    ref = kint[:, None, None] * np.einsum("tid,tjd->tij", G, G)
+    kv = k(X.reshape(-1, 3)).reshape(6, 4)
+    assert np.allclose(fem.p1_divkgrad(X, kv), ref, rtol=1e-12, atol=1e-14)
+
+
+def test_p2_stiffness_with_linear_k_matches_an_independent_rule():
+    """k linear makes k grad phi_a . grad phi_b a cubic: the 14-point rule
+    (degree 5) and a conical-product rule (degree 7) integrate it exactly."""
+    X = _rand_tets(6, 4)
+    c = np.array([0.4, 1.1, -0.6])
+
+    def k(x):
+        return 1.5 + x @ c
+
+    K14 = fem.p2_stiffness(X, k)
+    K7 = fem.p2_stiffness(X, k, rule=quadrature.stroud_conical(4))
+    assert np.allclose(K14, K7, rtol=1e-12, atol=1e-13)
+    # exact integral by monomials: k = sum_m k_m lam_m, grad phi as lam-polynomial terms
+    G, vol = fem.bary_gradients(X)
+
+    def e(*idx):
+        a = [0, 0, 0, 0]
+        for i in idx:
+            a[i] += 1
+        return tuple(a)
+
+    for t in range(len(X)):
+        kv = k(X[t])
+        terms = [[(4.0, e(i), G[t, i]), (-1.0, e(), G[t, i])] for i in range(4)]
+        terms += [[(4.0, e(i), G[t, j]), (4.0, e(j), G[t, i])] for i, j in fem.P2_EDGES]
+        Kex = np.zeros((10, 10))
+        for a_ in range(10):
+            for b_ in range(10):
+                acc = 0.0
+                for ca, ea, ga in terms[a_]:
+                    for cb, eb, gb in terms[b_]:
+                        for m in range(4):
+                            al = tuple(x + y + (1 if i == m else 0) for i, (x, y) in enumerate(zip(ea, eb)))
+                            acc += kv[m] * ca * cb * (ga @ gb) * quadrature.exact_monomial(al)
+                Kex[a_, b_] = vol[t] * acc
+        assert np.allclose(K14[t], Kex, rtol=1e-12, atol=1e-13)
+    # and a coefficient-free check: k = 1 + 0 x gives the plain stiffness
+    assert np.allclose(fem.p2_stiffness(X, lambda x: np.ones(len(x))), fem.p2_stiffness(X),
+                       rtol=1e-14, atol=1e-14)

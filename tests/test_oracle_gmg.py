@@ -164,3 +164,41 @@ def test_fmg_reaches_discretization_accuracy():
     xh = spla.spsolve(lev.A.tocsc(), b)
     u = np.prod(np.sin(np.pi * lev.xyz), axis=1)[lev.interior]
     assert np.linalg.norm(x - xh) < 0.05 * np.linalg.norm(xh - u)
+
+
+def test_colour_gauss_seidel_is_the_sequential_sweep():
+    """With no coupling inside a colour, the colour-ordered sweep equals the
+    textbook point Gauss-Seidel sweep taken one DoF at a time in colour order;
+    on a diagonal matrix one sweep solves exactly."""
+    import scipy.sparse as sp
+    g = np.random.Generator(np.random.PCG64(12))
+    n = 40
+    colour = np.arange(n) % 4
+    # couple only DoFs of different colours (a symmetric, diagonally dominant matrix)
+    R = g.uniform(-1, 1, size=(n, n))
+    R = np.triu(R, 1) * (colour[:, None] != colour[None, :])
+    A = R + R.T
+    A += np.diag(np.abs(A).sum(axis=1) + 1.0)
+    As = sp.csr_matrix(A)
+    D = A.diagonal()
+    x0, b = g.uniform(-1, 1, n), g.uniform(-1, 1, n)
+    x = x0.copy()
+    for c in range(4):
+        for i in np.flatnonzero(colour == c):
+            x[i] += (b[i] - A[i] @ x) / A[i, i]
+    assert np.allclose(gmg.gauss_seidel_colours(As, D, x0, b, colour), x, rtol=1e-13, atol=1e-14)
+    Dm = sp.diags(np.linspace(1, 3, n)).tocsr()
+    xs = gmg.gauss_seidel_colours(Dm, Dm.diagonal(), x0, b, colour)
+    assert np.allclose(xs, b / Dm.diagonal(), rtol=1e-15)
+
+
+def test_fmg_coarse_start_is_the_galerkin_projection():
+    """With no V-cycles FMG returns P A_c^-1 P^T b on two levels.  For the P1
+    Laplacian A_c = P^T A P (Galerkin), so the residual is orthogonal to the
+    coarse space: P^T (b - A x) = 0."""
+    H = gmg.Hierarchy(sg.kuhn_cube(1), 2, 3)
+    lev = H.levels[3]
+    b = sg.uniform_vector(13, len(lev.interior))
+    x = gmg.fmg(H, b, cycles=0)
+    r = b - lev.A @ x
+    assert np.linalg.norm(H.P[3].T @ r) <= 1e-12 * np.linalg.norm(b)
