@@ -61,3 +61,17 @@ def test_single_hidden_unit_closed_form():
     assert np.isclose(L, (25 + 0.25) / 2)
     assert np.isclose(dw3[0], 15.0)
     assert np.isclose(dW1[0, 0], (2 / 2) * 5 * 2.0 * 1.0 * 3.0)
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """Bias-corrected Adam (Kingma & Ba 2015): after one step m_hat = g and
+    v_hat = g^2, so every parameter moves by lr * sign(g) (eps negligible);
+    with a constant gradient the step stays lr * sign(g)."""
+    g = np.array([0.3, -2.0, 5e-3, -1e-2])
+    p = np.zeros(4)
+    m, v = np.zeros(4), np.zeros(4)
+    lr = 1e-3
+    for step in (1, 2, 3):
+        before = p.copy()
+        mlp.adam_step([p], [g], [m], [v], step, lr=lr, eps=1e-12)
+        assert np.allclose(p - before, -lr * np.sign(g), rtol=1e-9, atol=0)
