@@ -104,3 +104,41 @@ def test_restriction_lists_are_the_transpose(macro):
                 acc += R["w"][e] * s[R["fine_dir"][e]] * rf[fidx[q]]
         got[i] = s[pc - 1] * acc
     assert np.allclose(got, ref, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("macro", [sg.kuhn_cube(1), sg.permuted_cells(sg.kuhn_cube(1), 3),
+                                   sg.permuted_cells(sg.kuhn_cube(2), 7)],
+                         ids=["cube1", "cube1perm", "cube2perm"])
+def test_table_on_multi_cell_meshes_gives_identical_copies(macro):
+    """Every cell applies the table with its own orientation signs to its own
+    lattice points; the copies of an interface edge (one per cell) must agree
+    exactly and equal the oracle's P u_c.  Weights and signs are exact, so a
+    transfer kernel needs no exchange between the copies."""
+    T = hg.n1_prolong_table()
+    L = 2
+    fine, coarse = ne.NedelecLevel(macro, L), ne.NedelecLevel(macro, L - 1)
+    uc = sg.uniform_vector(33, coarse.n)
+    ref = ne.nedelec_prolongation(fine, coarse) @ uc
+    seen = {}
+    for cell in macro.cells:
+        V = macro.vertices[cell]
+        E = np.stack([V[1] - V[0], V[2] - V[0], V[3] - V[0]])
+        s = _signs(E)
+        qf, fi = _edge_points(fine, V[0], E, L)
+        qc, ci = _edge_points(coarse, V[0], E, L - 1)
+        cidx = {tuple(p): i for p, i in zip(qc, ci)}
+        for q, i in zip(qf, fi):
+            r, p = q % 4, q // 4
+            cl = r[0] + 4 * r[1] + 16 * r[2]
+            acc = 0.0
+            for t in range(T["n"][cl]):
+                o = T["off"][cl, t]
+                c = tuple(2 * p + np.array([o & 3, (o >> 2) & 3, o >> 4]))
+                acc += T["w"][cl, t] * s[T["dir"][cl, t]] * uc[cidx[c]]
+            v = s[T["fine_dir"][cl]] * acc
+            if i in seen:
+                assert v == seen[i], (i, v, seen[i])
+            seen[i] = v
+    assert len(seen) == fine.n
+    got = np.array([seen[i] for i in range(fine.n)])
+    assert np.allclose(got, ref, rtol=0, atol=1e-14)
