@@ -210,6 +210,29 @@ int hg_n1_prolong_table(int* n, int* off, int* dir, double* w, int* fine_dir);
  * be NULL (d, w, fine_dir: at least start[8] entries). */
 int hg_n1_restrict_table(int* start, int* d, double* w, int* fine_dir);
 
+/* Nedelec transfers and discrete gradient (op: an HG_OP_N1_CURLCURL operator;
+ * N1 vectors are HG_SPACE_P2 vectors of the N1 level, P1 vectors of the P1
+ * level; dtype HG_F32 or HG_F64; device pointers; stream-ordered).
+ * - hg_n1_prolong_add: x_f += P e_c, fine N1 level `fine_level`, coarse
+ *   fine_level - 1 (P = tangential line integrals of the coarse function);
+ *   boundary (tangential Dirichlet) fine DoFs are left unchanged.
+ * - hg_n1_restrict: r_c = P^T r_f on the non-boundary coarse DoFs, 0 on the
+ *   boundary ones and at vertex points.
+ * - hg_n1_gradient: u = G phi on N1 level `level` from the P1 function phi of
+ *   the same level: (G phi)_e = phi(end) - phi(start) in the edge's
+ *   orientation, 0 at boundary edges and vertex points.
+ * - hg_n1_gradient_t: r_p = G^T r at the non-boundary vertices (0 on the
+ *   boundary); r's boundary entries are expected to be 0.
+ * Errors: HG_ERR_INVALID_ARG (not an N1 operator, bad pointers),
+ * HG_ERR_LEVEL_RANGE. */
+int hg_n1_prolong_add(const hg_op* op, int fine_level, int dtype, const void* ec, void* xf,
+                      void* stream);
+int hg_n1_restrict(const hg_op* op, int fine_level, int dtype, const void* rf, void* rc,
+                   void* stream);
+int hg_n1_gradient(const hg_op* op, int level, int dtype, const void* phi, void* u, void* stream);
+int hg_n1_gradient_t(const hg_op* op, int level, int dtype, const void* r, void* rp,
+                     void* stream);
+
 /* The quadrature rule of the P2 element matrices: the symmetric 14-point,
  * degree-5, positive-weight rule (orbits 4+4+6), derived by the library from
  * its moment equations.  Host outputs: bary 14x4 barycentric coordinates,

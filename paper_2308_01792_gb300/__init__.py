@@ -87,6 +87,10 @@ SIGNATURES = {
     "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
     "hg_n1_restrict_table": (_I, [_P, _P, _P, _P]),
+    "hg_n1_prolong_add": (_I, [_P, _I, _I, _P, _P, _P]),
+    "hg_n1_restrict": (_I, [_P, _I, _I, _P, _P, _P]),
+    "hg_n1_gradient": (_I, [_P, _I, _I, _P, _P, _P]),
+    "hg_n1_gradient_t": (_I, [_P, _I, _I, _P, _P, _P]),
 }
 
 HG_BATCH_GRAPH, HG_BATCH_AUTOTUNE = 1, 2
@@ -298,6 +302,22 @@ class Operator:
         """One colour sub-sweep (out of place) of 4-colour Gauss-Seidel."""
         _call("hg_gauss_seidel", self._h, level, _dtype_code(x), int(colour), _ptr(x), _ptr(b),
               _ptr(x_out), _stream(stream))
+
+    def n1_prolong_add(self, fine_level, ec, xf, stream=None):
+        _call("hg_n1_prolong_add", self._h, fine_level, _dtype_code(ec), _ptr(ec), _ptr(xf),
+              _stream(stream))
+
+    def n1_restrict(self, fine_level, rf, rc, stream=None):
+        _call("hg_n1_restrict", self._h, fine_level, _dtype_code(rf), _ptr(rf), _ptr(rc),
+              _stream(stream))
+
+    def n1_gradient(self, level, phi, u, stream=None):
+        _call("hg_n1_gradient", self._h, level, _dtype_code(phi), _ptr(phi), _ptr(u),
+              _stream(stream))
+
+    def n1_gradient_t(self, level, r, rp, stream=None):
+        _call("hg_n1_gradient_t", self._h, level, _dtype_code(r), _ptr(r), _ptr(rp),
+              _stream(stream))
 
     def jacobi(self, level, x, b, x_out, omega=2.0 / 3.0, stream=None):
         _call("hg_jacobi", self._h, level, _dtype_code(x), float(omega), _ptr(x), _ptr(b),

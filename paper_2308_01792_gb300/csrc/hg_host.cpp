@@ -833,6 +833,7 @@ Op::~Op() {
   for (int dt = 0; dt < 2; ++dt)
     for (auto* v : {&vk[dt], &vK[dt], &vinv[dt], &sst[dt]})
       for (void* p : *v) cudaFree(p);
+  cudaFree(n1sign);
 }
 
 }  // namespace hg
@@ -1103,6 +1104,53 @@ int hg_prolong_add(const hg_hier* h, int space, int fine_level, int dtype, const
   HG_CHECK(ec && xf && ec != xf, HG_ERR_INVALID_ARG, "hg_prolong_add: bad pointers");
   if (space == HG_SPACE_P2) return launch_prolong_p2(*F, *C, dtype, ec, xf, (cudaStream_t)stream);
   return launch_prolong_p1(*F, *C, dtype, ec, xf, (cudaStream_t)stream);
+}
+
+// Nedelec transfers and discrete gradient (the operator holds the cells'
+// orientation signs).  N1 level l is stored on lattice l+1 (P2 storage).
+static int n1_levels(const hg_op* op, int fine_level, bool gradient, const LevelDev** F,
+                     const LevelDev** C, const char* fn) {
+  HG_CHECK(op && op->kind == HG_OP_N1_CURLCURL, HG_ERR_INVALID_ARG, "%s: needs an N1 operator", fn);
+  const int lo = gradient ? std::max(op->lmin, op->hier->lmin) : op->lmin + 1;
+  if (fine_level < lo || fine_level > op->lmax) {
+    set_error("%s: level %d outside %d..%d", fn, fine_level, lo, op->lmax);
+    return HG_ERR_LEVEL_RANGE;
+  }
+  *F = &op->dev(fine_level);
+  *C = gradient ? level_of(op->hier, HG_SPACE_P1, fine_level) : &op->dev(fine_level - 1);
+  if (!*C) return HG_ERR_LEVEL_RANGE;
+  return HG_OK;
+}
+
+int hg_n1_prolong_add(const hg_op* op, int fine_level, int dtype, const void* ec, void* xf,
+                      void* stream) {
+  const LevelDev *F, *C;
+  if (int r = n1_levels(op, fine_level, false, &F, &C, "hg_n1_prolong_add")) return r;
+  HG_CHECK(ec && xf && ec != xf, HG_ERR_INVALID_ARG, "hg_n1_prolong_add: bad pointers");
+  return launch_n1_transfer(N1_PROLONG, *F, *C, dtype, op->n1sign, ec, xf, (cudaStream_t)stream);
+}
+
+int hg_n1_restrict(const hg_op* op, int fine_level, int dtype, const void* rf, void* rc,
+                   void* stream) {
+  const LevelDev *F, *C;
+  if (int r = n1_levels(op, fine_level, false, &F, &C, "hg_n1_restrict")) return r;
+  HG_CHECK(rf && rc && rf != rc, HG_ERR_INVALID_ARG, "hg_n1_restrict: bad pointers");
+  return launch_n1_transfer(N1_RESTRICT, *F, *C, dtype, op->n1sign, rf, rc, (cudaStream_t)stream);
+}
+
+int hg_n1_gradient(const hg_op* op, int level, int dtype, const void* phi, void* u, void* stream) {
+  const LevelDev *F, *C;
+  if (int r = n1_levels(op, level, true, &F, &C, "hg_n1_gradient")) return r;
+  HG_CHECK(phi && u && phi != u, HG_ERR_INVALID_ARG, "hg_n1_gradient: bad pointers");
+  return launch_n1_transfer(N1_GRAD, *F, *C, dtype, op->n1sign, phi, u, (cudaStream_t)stream);
+}
+
+int hg_n1_gradient_t(const hg_op* op, int level, int dtype, const void* r, void* rp,
+                     void* stream) {
+  const LevelDev *F, *C;
+  if (int e = n1_levels(op, level, true, &F, &C, "hg_n1_gradient_t")) return e;
+  HG_CHECK(r && rp && r != rp, HG_ERR_INVALID_ARG, "hg_n1_gradient_t: bad pointers");
+  return launch_n1_transfer(N1_GRADT, *F, *C, dtype, op->n1sign, r, rp, (cudaStream_t)stream);
 }
 
 int hg_dot(const hg_hier* h, int space, int level, int dtype, const void* x, const void* y,

@@ -186,6 +186,28 @@ int Op::build_n1(const double* coeff) {
   const double alpha = coeff[0], beta = coeff[1];
   p2mode = P2_N1;
   const Mesh& m = *hier->mesh;
+  // orientation sign of each lattice direction in each cell: +1 when the
+  // physical vector has a positive first nonzero of z, y, x
+  {
+    std::vector<int8_t> sg(8 * m.nc, 0);
+    for (int64_t c = 0; c < m.nc; ++c) {
+      const double* V[4];
+      for (int q = 0; q < 4; ++q) V[q] = &m.xyz[3 * m.cells[c][q]];
+      for (int d = 0; d < 7; ++d) {
+        double v[3], len = 0.0;
+        for (int r = 0; r < 3; ++r) {
+          v[r] = kN1Dir[d][0] * (V[1][r] - V[0][r]) + kN1Dir[d][1] * (V[2][r] - V[0][r]) +
+                 kN1Dir[d][2] * (V[3][r] - V[0][r]);
+          len += v[r] * v[r];
+        }
+        const double tol = 1e-9 * std::sqrt(len);
+        sg[8 * c + d] = std::fabs(v[2]) > tol ? (v[2] > 0 ? 1 : -1)
+                        : std::fabs(v[1]) > tol ? (v[1] > 0 ? 1 : -1)
+                                                : (v[0] > 0 ? 1 : -1);
+      }
+    }
+    if (int r = upload_vec((void**)&n1sign, sg)) return r;
+  }
   const int nl = lmax - lmin + 1;
   for (int dt = 0; dt < 2; ++dt) {
     p2cells[dt].assign(nl, nullptr);
