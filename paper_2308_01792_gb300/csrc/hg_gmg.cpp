@@ -35,6 +35,11 @@ struct Gmg {
   const Mlp* learned = nullptr;   // learned smoothing on the finest FP32 level
   bool learned_active = false;
   int learned_fallbacks = 0;
+  // Nedelec operators: Hiptmair smoothing with the P1 Laplacian of the same
+  // hierarchy as the potential-space operator (G^T A G = beta K_P1)
+  Op* pot = nullptr;
+  std::vector<void*> pwork[2][3];   // [dtype][residual, correction, zero][level - lmin]
+  bool is_n1() const { return op->kind == HG_OP_N1_CURLCURL; }
 
   const LevelDev& L(int l) const { return op->dev(l); }
   size_t bytes(int l, int dt) const { return L(l).n_stored * (dt == HG_F64 ? 8 : 4); }
@@ -50,9 +55,69 @@ struct Gmg {
         work[dt][kind][l - lmin] = p;
       }
     }
+    if (pot)
+      if (int r = alloc_pot(dt)) return r;
     return HG_OK;
   }
   void* W(int dt, int kind, int l) { return work[dt][kind][l - lmin]; }
+
+  int alloc_pot(int dt) {
+    if (!pwork[dt][0].empty()) return HG_OK;
+    for (int kind = 0; kind < 3; ++kind) {
+      pwork[dt][kind].assign(lmax - lmin + 1, nullptr);
+      for (int l = lmin + 1; l <= lmax; ++l) {
+        const size_t nb = pot->dev(l).n_stored * (dt == HG_F64 ? 8 : 4);
+        void* p = nullptr;
+        HG_CUDA(cudaMalloc(&p, nb));
+        HG_CUDA(cudaMemset(p, 0, nb));
+        pwork[dt][kind][l - lmin] = p;
+      }
+    }
+    return HG_OK;
+  }
+
+  int restrict_to(int l, int dt, const void* rf, void* rc, cudaStream_t s) {
+    if (is_n1()) return launch_n1_transfer(N1_RESTRICT, L(l), L(l - 1), dt, op->n1sign, rf, rc, s);
+    return op->space == HG_SPACE_P2 ? launch_restrict_p2(L(l), L(l - 1), dt, rf, rc, s)
+                                    : launch_restrict_p1(L(l), L(l - 1), dt, rf, rc, s);
+  }
+  int prolong_to(int l, int dt, const void* ec, void* xf, cudaStream_t s) {
+    if (is_n1()) return launch_n1_transfer(N1_PROLONG, L(l), L(l - 1), dt, op->n1sign, ec, xf, s);
+    return op->space == HG_SPACE_P2 ? launch_prolong_p2(L(l), L(l - 1), dt, ec, xf, s)
+                                    : launch_prolong_p1(L(l), L(l - 1), dt, ec, xf, s);
+  }
+
+  // Hiptmair hybrid smoothing (Sec. 6): per step a weighted-Jacobi step on A,
+  // the residual taken to the potential space by G^T, one weighted-Jacobi step
+  // from zero with G^T A G = beta K_P1 (weight omega / beta on the P1
+  // Laplacian), and the correction G e_p added; the steps ping-pong x and t.
+  int smooth_hiptmair(int l, int dt, void* x, const void* b, int nu, cudaStream_t s) {
+    void* t = W(dt, WT, l);
+    void* r = W(dt, WR, l);
+    void* rp = pwork[dt][0][l - lmin];
+    void* ep = pwork[dt][1][l - lmin];
+    void* z = pwork[dt][2][l - lmin];
+    const LevelDev& Lp = pot->dev(l);
+    for (int q = 0; q < nu; ++q) {
+      const void* src = (q % 2 == 0) ? x : t;
+      void* dst = (q % 2 == 0) ? t : x;
+      if (int e = cell_op(l, dt, OP_JACOBI, src, b, dst, s)) return e;
+      if (int e = cell_op(l, dt, OP_RESID, dst, b, r, s)) return e;
+      if (int e = launch_n1_transfer(N1_GRADT, L(l), Lp, dt, op->n1sign, r, rp, s)) return e;
+      StencilArgs a{};
+      a.x = z;
+      a.b = rp;
+      a.out = ep;
+      a.op = OP_JACOBI;
+      a.mode = HG_REPLACE;
+      a.mask = HG_MASK_INNER;
+      a.omega = prm.omega / op->n1beta;
+      if (int e = pot->launch(l, dt, a, s)) return e;
+      if (int e = launch_n1_transfer(N1_GRAD_ADD, L(l), Lp, dt, op->n1sign, ep, dst, s)) return e;
+    }
+    if (nu % 2) HG_CUDA(cudaMemcpyAsync(x, t, bytes(l, dt), cudaMemcpyDeviceToDevice, s));
+    return HG_OK;
+  }
 
   int dot(int l, int dt, const void* a, const void* b, double* out, cudaStream_t s) {
     if (int r = launch_dot(L(l), dt, a, b, HG_MASK_INNER, dot_scratch, dot_dev, s)) return r;
@@ -191,20 +256,13 @@ struct Gmg {
   int fmg(int level, int dt, void* x, const void* b, int cycles, cudaStream_t s) {
     auto X = [&](int l) { return l == level ? x : W(dt, WX, l); };
     auto B = [&](int l) { return l == level ? b : (const void*)W(dt, WF, l); };
-    for (int l = level; l > lmin; --l) {
-      const int r = op->space == HG_SPACE_P2
-                        ? launch_restrict_p2(L(l), L(l - 1), dt, B(l), W(dt, WF, l - 1), s)
-                        : launch_restrict_p1(L(l), L(l - 1), dt, B(l), W(dt, WF, l - 1), s);
-      if (r) return r;
-    }
+    for (int l = level; l > lmin; --l)
+      if (int r = restrict_to(l, dt, B(l), W(dt, WF, l - 1), s)) return r;
     HG_CUDA(cudaMemsetAsync(X(lmin), 0, bytes(lmin, dt), s));
     if (int r = launch_coarse_solve(L(lmin), coarse, dt, B(lmin), X(lmin), s)) return r;
     for (int l = lmin + 1; l <= level; ++l) {
       HG_CUDA(cudaMemsetAsync(X(l), 0, bytes(l, dt), s));
-      const int r = op->space == HG_SPACE_P2
-                        ? launch_prolong_p2(L(l), L(l - 1), dt, X(l - 1), X(l), s)
-                        : launch_prolong_p1(L(l), L(l - 1), dt, X(l - 1), X(l), s);
-      if (r) return r;
+      if (int r = prolong_to(l, dt, X(l - 1), X(l), s)) return r;
       for (int c = 0; c < cycles; ++c)
         if (int r2 = vcycle(l, dt, X(l), B(l), s)) return r2;
     }
@@ -214,6 +272,7 @@ struct Gmg {
   int smooth(int l, int dt, void* x, const void* b, int nu, cudaStream_t s) {
     void* t = W(dt, WT, l);
     const bool learn = learned_active && dt == HG_F32 && l == lmax;
+    if (is_n1()) return smooth_hiptmair(l, dt, x, b, nu, s);
     if (prm.smoother == HG_SMOOTH_CHEB && !learn) return smooth_cheb(l, dt, x, b, nu, s);
     if (prm.smoother == HG_SMOOTH_GS && !learn) {
       // nu 4-colour sweeps; 4 nu sub-sweeps ping-pong x and t and end in x
@@ -251,14 +310,10 @@ struct Gmg {
     if (int r = cell_op(l, dt, OP_RESID, x, b, res, s)) return r;
     void* bc = W(dt, WB, l - 1);
     void* xc = W(dt, WX, l - 1);
-    if (int r = op->space == HG_SPACE_P2 ? launch_restrict_p2(L(l), L(l - 1), dt, res, bc, s)
-                                         : launch_restrict_p1(L(l), L(l - 1), dt, res, bc, s))
-      return r;
+    if (int r = restrict_to(l, dt, res, bc, s)) return r;
     HG_CUDA(cudaMemsetAsync(xc, 0, bytes(l - 1, dt), s));
     if (int r = vcycle(l - 1, dt, xc, bc, s)) return r;
-    if (int r = op->space == HG_SPACE_P2 ? launch_prolong_p2(L(l), L(l - 1), dt, xc, x, s)
-                                         : launch_prolong_p1(L(l), L(l - 1), dt, xc, x, s))
-      return r;
+    if (int r = prolong_to(l, dt, xc, x, s)) return r;
     return smooth(l, dt, x, b, prm.nu2, s);
   }
 
@@ -280,8 +335,16 @@ int Gmg::build_coarse() {
   }
   std::vector<int32_t> int_of_canon(Lc.n_unique, -1);
   std::vector<int64_t> rep;
+  // N1: only the edge points (an odd lattice coordinate) are unknowns
+  std::vector<uint8_t> edge_pt;
+  if (is_n1()) {
+    edge_pt.assign(Lc.cell_stride, 0);
+    for (int k = 0; k <= Lc.n; ++k)
+      for (int j = 0; j + k <= Lc.n; ++j)
+        for (int i = 0; i + j + k <= Lc.n; ++i) edge_pt[tw(Lc.w, i, j, k)] = ((i | j | k) & 1) ? 1 : 0;
+  }
   for (int64_t u = 0; u < Lc.n_unique; ++u)
-    if (!H.dirichlet[u]) {
+    if (!H.dirichlet[u] && (edge_pt.empty() || edge_pt[H.canon_rep[u] % Lc.cell_stride])) {
       int_of_canon[u] = (int32_t)rep.size();
       rep.push_back(H.canon_rep[u]);
     }
@@ -437,6 +500,10 @@ Gmg::~Gmg() {
   cudaFree(coarse.stored_rep);
   cudaFree(coarse.int_of_canon);
   cudaFree(coarse.xint);
+  for (auto& per_dt : pwork)
+    for (auto& per_kind : per_dt)
+      for (void* p : per_kind) cudaFree(p);
+  delete pot;
 }
 
 }  // namespace hg
@@ -484,8 +551,8 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
               op->lmax);
     return HG_ERR_LEVEL_RANGE;
   }
-  if (op->kind == HG_OP_N1_CURLCURL) {
-    set_error("multigrid for the Nedelec operator (Hiptmair smoothing, N1 transfers) is not built");
+  if (op->kind == HG_OP_N1_CURLCURL && g->prm.smoother != HG_SMOOTH_JACOBI) {
+    set_error("Nedelec multigrid: Hiptmair smoothing with weighted Jacobi in both spaces only");
     return HG_ERR_UNSUPPORTED;
   }
   if (g->prm.smoother != HG_SMOOTH_JACOBI && g->prm.smoother != HG_SMOOTH_GS &&
@@ -516,6 +583,10 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
     set_error("bad Chebyshev parameters order=%d iters=%d interval [%g, %g]", g->prm.cheb_order,
               g->prm.cheb_iters, g->prm.cheb_lo, g->prm.cheb_hi);
     return HG_ERR_INVALID_ARG;
+  }
+  if (op->kind == HG_OP_N1_CURLCURL) {
+    g->pot = new Op();
+    if (int r = g->pot->build(g->hier, HG_OP_P1_LAPLACE, nullptr)) return r;
   }
   if (int r = g->alloc_work(HG_F64)) return r;
   const size_t nl = g->L(g->lmax).n_stored;
@@ -1098,6 +1169,10 @@ int hg_gmg_clone(const hg_gmg* src, hg_gmg** out) {
   g->lmax = src->lmax;
   g->learned = src->learned;
   g->lam = src->lam;
+  if (src->pot) {
+    g->pot = new Op();
+    if (int r = g->pot->build(g->hier, HG_OP_P1_LAPLACE, nullptr)) return r;
+  }
   if (int r = g->alloc_work(HG_F64)) return r;
   const size_t nl = g->L(g->lmax).n_stored;
   HG_CUDA(cudaMalloc(&g->r64, nl * sizeof(double)));

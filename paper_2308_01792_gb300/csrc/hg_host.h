@@ -97,6 +97,7 @@ struct Op {
   int build_p2(const double* coeff);
   int build_n1(const double* coeff);
   int8_t* n1sign = nullptr;      // N1: orientation sign per (cell, lattice direction), [nc][8]
+  double n1alpha = 0.0, n1beta = 0.0;  // N1: alpha curl curl + beta I
   std::vector<double*> sten64;  // per level [ncells][16][16] (constant-coefficient kinds)
   std::vector<float*> sten32;
   std::vector<int> pattern;     // per level: kPat7 when the interior stencils allow it
@@ -142,7 +143,7 @@ int n1_prolong_table(const N1ProlongTable** out);
 // per-cell orientation signs (int8 [ncells][8]): N1_PROLONG xf += P ec,
 // N1_RESTRICT rc = P^T rf (fine N1 level l, coarse l-1); N1_GRAD u = G phi
 // (P1 level l on C to N1 level l on F), N1_GRADT rp = G^T r.
-enum { N1_PROLONG = 0, N1_RESTRICT = 1, N1_GRAD = 2, N1_GRADT = 3 };
+enum { N1_PROLONG = 0, N1_RESTRICT = 1, N1_GRAD = 2, N1_GRADT = 3, N1_GRAD_ADD = 4 };
 int launch_n1_transfer(int which, const LevelDev& F, const LevelDev& C, int dtype,
                        const int8_t* sign, const void* src, void* dst, cudaStream_t s);
 

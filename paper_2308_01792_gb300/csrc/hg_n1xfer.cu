@@ -224,8 +224,9 @@ __global__ void __launch_bounds__(kNBlock) n1_restrict_kernel(NDesc<T> D) {
     rc[i] = n1_restrict_partial<T>(rf, fl, s, nf, i, j, k);
 }
 
-// (G phi) at every point of every cell of F (one warp per row, lanes over i).
-template <typename T>
+// (G phi) at every point of every cell of F (one warp per row, lanes over i);
+// ADD: u += G phi (vertex points and boundary edges unchanged).
+template <typename T, bool ADD>
 __global__ void __launch_bounds__(kNBlock) n1_grad_kernel(NDesc<T> D) {
   const int lane = threadIdx.x & 31;
   const int r = blockIdx.x * kNWarps + (threadIdx.x >> 5);
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(kNBlock) n1_grad_kernel(NDesc<T> D) {
       const T b = phi[tw32(wc, (i + d[0]) >> 1, (j + d[1]) >> 1, (k + d[2]) >> 1)];
       v = T(s[par - 1]) * (b - a);
     }
-    u[i] = v;
+    u[i] = ADD ? u[i] + v : v;
   }
 }
 
@@ -349,10 +350,14 @@ int run(int which, const LevelDev& F, const LevelDev& C, const int8_t* sign, con
       n1_restrict_kernel<T><<<D.nb_items + blocks_of(D.n_rows), kNBlock, 0, s>>>(D);
       break;
     }
-    case 2: {  // gradient: every row of F, no items
+    case 2:
+    case 4: {  // gradient (4: added): every row of F, no items
       NDesc<T> D = ndesc<T>(F, C, F, sign, src, dst);
       D.nb_items = 0;
-      n1_grad_kernel<T><<<blocks_of(D.n_rows), kNBlock, 0, s>>>(D);
+      if (which == 2)
+        n1_grad_kernel<T, false><<<blocks_of(D.n_rows), kNBlock, 0, s>>>(D);
+      else
+        n1_grad_kernel<T, true><<<blocks_of(D.n_rows), kNBlock, 0, s>>>(D);
       break;
     }
     default: {  // gradient transpose: sweep C

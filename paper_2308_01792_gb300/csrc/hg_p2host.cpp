@@ -184,6 +184,8 @@ int Op::build_n1(const double* coeff) {
     return HG_ERR_INVALID_ARG;
   }
   const double alpha = coeff[0], beta = coeff[1];
+  n1alpha = alpha;
+  n1beta = beta;
   p2mode = P2_N1;
   const Mesh& m = *hier->mesh;
   // orientation sign of each lattice direction in each cell: +1 when the

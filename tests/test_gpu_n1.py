@@ -5,8 +5,7 @@ N1 DoFs are stored as P2-space vectors at the edge-midpoint points; in the
 P2 canonical order the edge points must be exactly the oracle's N1 DoFs (same
 keys, same order) with the same boundary set.  Bars: apply (ALL and INNER
 masks), residual and Jacobi within 1e-12 (FP64) / 1e-5 (FP32) relative,
-vertex points untouched, interface copies bit-identical; multigrid for N1 is
-rejected (not built)."""
+vertex points untouched, interface copies bit-identical."""
 import numpy as np
 import pytest
 
@@ -119,12 +118,8 @@ def test_n1_residual_and_jacobi_match_oracle(case, dtype):
     assert np.all(got[lev.boundary] == 0)
 
 
-def test_n1_multigrid_rejected():
+def test_n1_rejects_bad_coefficients():
     macro = sg.kuhn_cube(1)
     H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 0, 3)
-    op = hg.Operator(H, hg.HG_OP_N1_CURLCURL, coeff=AB)
-    with pytest.raises(hg.HGError) as e:
-        hg.GMG(op)
-    assert e.value.code == -7
     with pytest.raises(hg.HGError):
         hg.Operator(H, hg.HG_OP_N1_CURLCURL, coeff=(1.0, 0.0))
