@@ -83,7 +83,7 @@ enum {
                             stored as HG_SPACE_P2 vectors at the edge-midpoint
                             points (vertex points stay 0); element-wise 6x6
                             matrices; apply, residual, Jacobi and Chebyshev
-                            steps (no multigrid yet)                           */
+                            steps; multigrid with Hiptmair smoothing           */
 };
 
 typedef struct hg_mesh hg_mesh;
@@ -312,7 +312,12 @@ int hg_dot_noalloc(const hg_hier* hier, int space, int level, int dtype, const v
  * restriction P^T and prolongation P (nodal interpolation), and an exact
  * FP64 solve on the coarsest level (dense Cholesky inverse, <= 2048
  * unknowns; built at creation by applying the operator to unit vectors).
- * Every P1 and P2 operator kind is accepted. */
+ * Every P1 and P2 operator kind is accepted.  For HG_OP_N1_CURLCURL the
+ * smoothing is Hiptmair's hybrid scheme (Sec. 6): a weighted-Jacobi step on
+ * the edge operator, the residual taken to the P1 potential space by G^T, a
+ * weighted-Jacobi step with G^T A G = beta * (P1 Laplacian) and the
+ * correction G e_p added; N1 transfers; weighted Jacobi only (use omega <=
+ * 1/2: lambda_max(D^-1 A) exceeds 3 for the edge matrices). */
 enum { HG_PREC_F64 = 0,   /* plain FP64 V-cycles                                  */
        HG_PREC_MIXED = 1  /* FP32 V-cycles inside FP64 iterative refinement: the
                              outer residual, norms and coarse solve stay FP64   */
