@@ -316,8 +316,9 @@ int hg_dot_noalloc(const hg_hier* hier, int space, int level, int dtype, const v
  * smoothing is Hiptmair's hybrid scheme (Sec. 6): a weighted-Jacobi step on
  * the edge operator, the residual taken to the P1 potential space by G^T, a
  * weighted-Jacobi step with G^T A G = beta * (P1 Laplacian) and the
- * correction G e_p added; N1 transfers; weighted Jacobi only (use omega <=
- * 1/2: lambda_max(D^-1 A) exceeds 3 for the edge matrices). */
+ * correction G e_p added; N1 transfers; weighted Jacobi only, omega in
+ * (0, 0.6] (lambda_max(D^-1 A) exceeds 3 for the edge matrices; 1/2 is the
+ * tested choice), else HG_ERR_INVALID_ARG. */
 enum { HG_PREC_F64 = 0,   /* plain FP64 V-cycles                                  */
        HG_PREC_MIXED = 1  /* FP32 V-cycles inside FP64 iterative refinement: the
                              outer residual, norms and coarse solve stay FP64   */

@@ -555,6 +555,11 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
     set_error("Nedelec multigrid: Hiptmair smoothing with weighted Jacobi in both spaces only");
     return HG_ERR_UNSUPPORTED;
   }
+  if (op->kind == HG_OP_N1_CURLCURL && !(g->prm.omega > 0.0 && g->prm.omega <= 0.6)) {
+    // lambda_max(D^-1 A) of the edge matrices exceeds 3: larger weights diverge
+    set_error("Nedelec multigrid: Jacobi weight %g outside (0, 0.6]", g->prm.omega);
+    return HG_ERR_INVALID_ARG;
+  }
   if (g->prm.smoother != HG_SMOOTH_JACOBI && g->prm.smoother != HG_SMOOTH_GS &&
       g->prm.smoother != HG_SMOOTH_CHEB) {
     set_error("unknown smoother %d", g->prm.smoother);
