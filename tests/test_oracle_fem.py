@@ -28,7 +28,7 @@ def test_p1_element_matrices_closed_forms():
 
 
 @pytest.mark.parametrize("macro,level", [(sg.reference_tet(), 3), (sg.kuhn_cube(1), 2),
-                                         (sg.kuhn_cube(2), 1)])
+                                         (sg.kuhn_cube(2), 1), (sg.permuted_cells(sg.kuhn_cube(1), 3), 2)])
 def test_p1_laplace_symmetric_zero_rowsum_patch(macro, level):
     rm, A = _assembled(macro, level)
     assert abs(A - A.T).max() < 1e-14
@@ -38,7 +38,8 @@ def test_p1_laplace_symmetric_zero_rowsum_patch(macro, level):
     assert np.abs(r[rm.interior]).max() < 1e-12            # linear patch test
 
 
-@pytest.mark.parametrize("macro,vol", [(sg.reference_tet(), 1 / 6), (sg.kuhn_cube(2), 1.0)])
+@pytest.mark.parametrize("macro,vol", [(sg.reference_tet(), 1 / 6), (sg.kuhn_cube(2), 1.0),
+                                       (sg.permuted_cells(sg.kuhn_cube(2), 7), 1.0)])
 def test_p1_mass_total(macro, vol):
     rm, M = _assembled(macro, 2, "mass")
     one = np.ones(rm.n_vertices)
@@ -109,8 +110,10 @@ def test_quadrature_exactness():
                 assert abs(q - quadrature.exact_monomial(al)) < 1e-14
 
 
-def test_p2_stiffness_and_mass_invariants():
-    macro, level = sg.kuhn_cube(1), 2
+@pytest.mark.parametrize("macro", [sg.kuhn_cube(1), sg.permuted_cells(sg.kuhn_cube(1), 3)],
+                         ids=["cube1", "cube1perm"])
+def test_p2_stiffness_and_mass_invariants(macro):
+    level = 2
     rm = RefinedMesh(macro, level)
     num = fem.P2Numbering(rm)
     assert num.n == (2 * 2 ** level + 1) ** 3

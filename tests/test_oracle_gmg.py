@@ -13,7 +13,8 @@ def _manufactured_rhs(lev):
     return (lev.M_full @ f)[lev.interior]
 
 
-@pytest.mark.parametrize("macro,lmin,lmax", [(sg.reference_tet(), 2, 4), (sg.kuhn_cube(1), 1, 3)])
+@pytest.mark.parametrize("macro,lmin,lmax", [(sg.reference_tet(), 2, 4), (sg.kuhn_cube(1), 1, 3),
+                                            (sg.permuted_cells(sg.kuhn_cube(1), 3), 1, 3)])
 def test_galerkin_identity_p1(macro, lmin, lmax):
     H = gmg.Hierarchy(macro, lmin, lmax)
     for l in range(lmin + 1, lmax + 1):
@@ -22,15 +23,17 @@ def test_galerkin_identity_p1(macro, lmin, lmax):
         assert np.allclose(Ac, H.levels[l - 1].A.toarray(), atol=1e-13)
 
 
-def test_prolongation_reproduces_linear_and_quadratic_functions():
-    H = gmg.Hierarchy(sg.kuhn_cube(1), 1, 3)
+@pytest.mark.parametrize("macro", [sg.kuhn_cube(1), sg.permuted_cells(sg.kuhn_cube(1), 3)],
+                         ids=["cube1", "cube1perm"])
+def test_prolongation_reproduces_linear_and_quadratic_functions(macro):
+    H = gmg.Hierarchy(macro, 1, 3)
     f = lambda X: 0.3 + X @ np.array([1.0, -2.0, 0.5])
     for l in (2, 3):
         fi, co = H.levels[l], H.levels[l - 1]
         from oracle.gmg import p1_prolongation
         P = p1_prolongation(fi, co)
         assert np.allclose(P @ f(co.xyz), f(fi.xyz), atol=1e-14)
-    H2 = gmg.Hierarchy(sg.kuhn_cube(1), 1, 2, space="P2")
+    H2 = gmg.Hierarchy(macro, 1, 2, space="P2")
     fi, co = H2.levels[2], H2.levels[1]
     q = lambda X: X[:, 0] ** 2 - 0.5 * X[:, 1] * X[:, 2] + X[:, 2]
     P = gmg.p2_prolongation(fi, co)
