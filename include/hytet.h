@@ -151,6 +151,14 @@ int hg_from_canonical(const hg_hier* hier, int space, int level, int dtype,
  * the same word at their synchronisation points. */
 int hg_device_status(const hg_hier* hier, void* stream);
 
+/* The plane-window tiles the constant-stencil and stored-stencil apply
+ * kernels use on one cell lattice of `level` (host, needs no GPU; the same
+ * for every cell), 4 ints per tile: (k | windows << 16, lattice offset of
+ * lane 0's first point, j0 << 16 | i0 of that point, 0).  *n_tiles gets the
+ * count; out may be NULL to query it.  Exported so that tests can check the
+ * kernels' lane walk against the lattice on the CPU. */
+int hg_plane_tiles(int level, int* out, int* n_tiles);
+
 /* ----------------------------------------------------- index functions --
  * t_w(i,j,k) = N_tet(w) - N_tet(w-k) + N_tri(w-k) - N_tri(w-k-j) + i
  * (Sec. 4).  Host evaluation; HG_ERR_INVALID_ARG if (i,j,k) not in I_tet(w). */

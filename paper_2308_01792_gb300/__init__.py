@@ -86,6 +86,7 @@ SIGNATURES = {
     "hg_gmg_power_lambda": (_I, [_P, _I, _P, _I, _PD, _P]),
     "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
+    "hg_plane_tiles": (_I, [_I, _P, ctypes.POINTER(ctypes.c_int)]),
     "hg_n1_restrict_table": (_I, [_P, _P, _P, _P]),
     "hg_n1_prolong_add": (_I, [_P, _I, _I, _P, _P, _P]),
     "hg_n1_restrict": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -528,6 +529,15 @@ def n1_prolong_table():
     _call("hg_n1_prolong_table", n.ctypes.data_as(_P), off.ctypes.data_as(_P),
           dr.ctypes.data_as(_P), w.ctypes.data_as(_P), fd.ctypes.data_as(_P))
     return {"n": n, "off": off, "dir": dr, "w": w, "fine_dir": fd}
+
+
+def plane_tiles(level):
+    """The apply kernels' plane-window tiles of one cell lattice (host): (n, 4) int32."""
+    n = ctypes.c_int()
+    _call("hg_plane_tiles", level, None, ctypes.byref(n))
+    out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
+    _call("hg_plane_tiles", level, out.ctypes.data_as(_P), ctypes.byref(n))
+    return out[:n.value]
 
 
 def n1_restrict_table():

@@ -288,21 +288,7 @@ int Hier::build_level(int l) {
   }
   L.n_citems = (int)citems.size();
   if (int r = upload(&L.citems, citems)) return r;
-  // plane-window tiles: in plane k (1..n-3) the interior points lie in the
-  // cell-local offset range [rs(1,k)+1, rs(n-k-2,k)+1]; a window covers 30
-  // consecutive offsets (lanes 1..30, halo lanes 0 and 31), a tile up to
-  // kPlaneSteps windows; (j0, i0) is the lattice row/column of lane 0's offset
-  std::vector<int4> ptiles;
-  for (int k = 1; k <= n - 3; ++k) {
-    const int ga = (int)row_start(w, 1, k) + 1, gb = (int)row_start(w, n - k - 2, k) + 1;
-    const int nwin = (gb - ga + 1 + 29) / 30;
-    for (int t0 = 0; t0 < nwin; t0 += kPlaneSteps) {
-      const int z = ga - 1 + 30 * t0;
-      int j = 0, r = z - (int)row_start(w, 0, k), len = w - k;
-      while (r >= len) { r -= len; --len; ++j; }
-      ptiles.push_back({k | (std::min(kPlaneSteps, nwin - t0) << 16), z, (j << 16) | r, 0});
-    }
-  }
+  const std::vector<int4> ptiles = plane_tiles(n);
   L.n_ptiles_cell = (int)ptiles.size();
   if (int r = upload(&L.ptiles, ptiles)) return r;
   // canonical numbering by exact lattice coordinates
@@ -595,6 +581,28 @@ void p1_cell_stencils(const Mesh& m, int64_t c, int n, int kind, double S[16][16
         }
       }
   }
+}
+
+// Plane-window tiles of one cell lattice with n intervals: in plane k
+// (1..n-3) the interior points lie in the cell-local offset range
+// [rs(1,k)+1, rs(n-k-2,k)+1]; a window covers 30 consecutive offsets (lanes
+// 1..30, halo lanes 0 and 31), a tile up to kPlaneSteps windows; a tile is
+// (k | windows << 16, lane-0 offset, j0 << 16 | i0, 0) with (j0, i0) the
+// lattice row and column of lane 0's offset.
+std::vector<int4> plane_tiles(int n) {
+  const int w = n + 1;
+  std::vector<int4> ptiles;
+  for (int k = 1; k <= n - 3; ++k) {
+    const int ga = (int)row_start(w, 1, k) + 1, gb = (int)row_start(w, n - k - 2, k) + 1;
+    const int nwin = (gb - ga + 1 + 29) / 30;
+    for (int t0 = 0; t0 < nwin; t0 += kPlaneSteps) {
+      const int z = ga - 1 + 30 * t0;
+      int j = 0, r = z - (int)row_start(w, 0, k), len = w - k;
+      while (r >= len) { r -= len; --len; ++j; }
+      ptiles.push_back({k | (std::min(kPlaneSteps, nwin - t0) << 16), z, (j << 16) | r, 0});
+    }
+  }
+  return ptiles;
 }
 
 int lattice_index(const Hier* h, int space, int level) {
@@ -970,6 +978,20 @@ int hg_device_status(const hg_hier* h, void* stream) {
   if (int r = h->fetch_error(s)) return r;
   HG_CUDA(cudaStreamSynchronize(s));
   return h->check_error();
+}
+
+int hg_plane_tiles(int level, int* out, int* n_tiles) {
+  HG_CHECK(level >= 0 && level <= 12 && n_tiles, HG_ERR_INVALID_ARG, "hg_plane_tiles: bad argument");
+  const std::vector<int4> t = plane_tiles(1 << level);
+  *n_tiles = (int)t.size();
+  if (out)
+    for (size_t q = 0; q < t.size(); ++q) {
+      out[4 * q] = t[q].x;
+      out[4 * q + 1] = t[q].y;
+      out[4 * q + 2] = t[q].z;
+      out[4 * q + 3] = t[q].w;
+    }
+  return HG_OK;
 }
 
 int hg_index_tw(int64_t w, int64_t i, int64_t j, int64_t k, int64_t* out) {

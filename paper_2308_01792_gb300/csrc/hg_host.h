@@ -80,6 +80,8 @@ struct Hier {
 // Index into Hier::lv of the lattice that stores `space` on `level` (P2 on
 // level l uses the lattice of level l+1), or -1 if the hierarchy lacks it.
 int lattice_index(const Hier* h, int space, int level);
+// Plane-window tiles of one cell lattice with n intervals (the same for every cell).
+std::vector<int4> plane_tiles(int n);
 
 struct Op {
   const Hier* hier = nullptr;
