@@ -159,6 +159,15 @@ int hg_device_status(const hg_hier* hier, void* stream);
  * kernels' lane walk against the lattice on the CPU. */
 int hg_plane_tiles(int level, int* out, int* n_tiles);
 
+/* The anchors of the element-wise colour phases of a P2 or N1 level (host,
+ * needs no GPU): packed i | j << 10 | k << 20 (anchor p of the unit cube
+ * [p, p+1]^3 that holds the six micro-cells of p), grouped by parity colour
+ * c = (i & 1) | (j & 1) << 1 | (k & 1) << 2 in [off[c], off[c+1]) (off: 9
+ * ints).  *n_anchors gets the count; out and off may be NULL.  Exported so
+ * that tests can check on the CPU that the threads of one phase touch
+ * disjoint DoFs. */
+int hg_p2_anchors(int level, uint32_t* out, int* off, int* n_anchors);
+
 /* ----------------------------------------------------- index functions --
  * t_w(i,j,k) = N_tet(w) - N_tet(w-k) + N_tri(w-k) - N_tri(w-k-j) + i
  * (Sec. 4).  Host evaluation; HG_ERR_INVALID_ARG if (i,j,k) not in I_tet(w). */

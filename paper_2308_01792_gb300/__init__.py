@@ -87,6 +87,7 @@ SIGNATURES = {
     "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
     "hg_plane_tiles": (_I, [_I, _P, ctypes.POINTER(ctypes.c_int)]),
+    "hg_p2_anchors": (_I, [_I, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "hg_n1_restrict_table": (_I, [_P, _P, _P, _P]),
     "hg_n1_prolong_add": (_I, [_P, _I, _I, _P, _P, _P]),
     "hg_n1_restrict": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -538,6 +539,17 @@ def plane_tiles(level):
     out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
     _call("hg_plane_tiles", level, out.ctypes.data_as(_P), ctypes.byref(n))
     return out[:n.value]
+
+
+def p2_anchors(level):
+    """Anchors of the P2/N1 colour phases (host): (anchors (n, 3) int, colour offsets (9,))."""
+    n = ctypes.c_int()
+    off = np.zeros(9, dtype=np.int32)
+    _call("hg_p2_anchors", level, None, off.ctypes.data_as(_P), ctypes.byref(n))
+    a = np.zeros(max(n.value, 1), dtype=np.uint32)
+    _call("hg_p2_anchors", level, a.ctypes.data_as(_P), off.ctypes.data_as(_P), ctypes.byref(n))
+    a = a[:n.value].astype(np.int64)
+    return np.stack([a & 1023, (a >> 10) & 1023, a >> 20], axis=1), off
 
 
 def n1_restrict_table():

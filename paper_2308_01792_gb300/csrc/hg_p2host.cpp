@@ -39,6 +39,23 @@ void p2_basis(const double l[4], double phi[10]) {
 
 }  // namespace
 
+// Anchors of the element-wise phases on a P2/N1 level with n intervals, by
+// parity colour (i, j, k mod 2): packed i | j << 10 | k << 20, colour c in
+// [off[c], off[c+1]).  Anchors of one colour have disjoint closed cubes
+// [p, p+1]^3, so the threads of a phase never touch the same DoF.
+std::vector<uint32_t> p2_anchors(int n, int off[9]) {
+  std::vector<uint32_t> anch;
+  for (int col = 0; col < 8; ++col) {
+    off[col] = (int)anch.size();
+    for (int k = col >> 2 & 1; k <= n - 1; k += 2)
+      for (int j = col >> 1 & 1; j + k <= n - 1; j += 2)
+        for (int i = col & 1; i + j + k <= n - 1; i += 2)
+          anch.push_back((uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20));
+  }
+  off[8] = (int)anch.size();
+  return anch;
+}
+
 int Op::build_p2(const double* coeff) {
   space = HG_SPACE_P2;
   lmin = std::max(0, hier->lmin - 1);
@@ -85,15 +102,7 @@ int Op::build_p2(const double* coeff) {
       return HG_ERR_LEVEL_RANGE;
     }
     // anchors (all types admit i+j+k <= n-1 at most) by parity colour
-    std::vector<uint32_t> anch;
-    for (int col = 0; col < 8; ++col) {
-      p2off[li][col] = (int)anch.size();
-      for (int k = col >> 2 & 1; k <= n - 1; k += 2)
-        for (int j = col >> 1 & 1; j + k <= n - 1; j += 2)
-          for (int i = col & 1; i + j + k <= n - 1; i += 2)
-            anch.push_back((uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20));
-    }
-    p2off[li][8] = (int)anch.size();
+    const std::vector<uint32_t> anch = p2_anchors(n, p2off[li].data());
     if (int r = upload_vec((void**)&p2anchors[li], anch)) return r;
     // element data per cell
     std::vector<P2Cell<double>> c64(m.nc);
@@ -224,15 +233,7 @@ int Op::build_n1(const double* coeff) {
       set_error("N1 level %d too fine for packed anchors", l);
       return HG_ERR_LEVEL_RANGE;
     }
-    std::vector<uint32_t> anch;
-    for (int col = 0; col < 8; ++col) {
-      p2off[li][col] = (int)anch.size();
-      for (int k = col >> 2 & 1; k <= n - 1; k += 2)
-        for (int j = col >> 1 & 1; j + k <= n - 1; j += 2)
-          for (int i = col & 1; i + j + k <= n - 1; i += 2)
-            anch.push_back((uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20));
-    }
-    p2off[li][8] = (int)anch.size();
+    const std::vector<uint32_t> anch = p2_anchors(n, p2off[li].data());
     if (int r = upload_vec((void**)&p2anchors[li], anch)) return r;
     std::vector<N1Cell<double>> c64(m.nc);
     std::vector<N1Cell<float>> c32(m.nc);
@@ -306,3 +307,18 @@ int Op::build_n1(const double* coeff) {
 }
 
 }  // namespace hg
+
+extern "C" int hg_p2_anchors(int level, uint32_t* out, int* off, int* n_anchors) {
+  if (level < 0 || level > 9 || !n_anchors) {
+    hg::set_error("hg_p2_anchors: bad argument");
+    return HG_ERR_INVALID_ARG;
+  }
+  int o[9];
+  const std::vector<uint32_t> a = hg::p2_anchors(1 << level, o);
+  *n_anchors = (int)a.size();
+  if (off)
+    for (int c = 0; c < 9; ++c) off[c] = o[c];
+  if (out)
+    for (size_t q = 0; q < a.size(); ++q) out[q] = a[q];
+  return HG_OK;
+}
