@@ -87,11 +87,15 @@ def test_mass_matrix_by_quadrature():
     assert np.allclose(K, np.swapaxes(K, 1, 2)) and np.linalg.eigvalsh(M).min() > 0
 
 
-# the permuted mesh has local orientations that disagree with the global ones
+# the permuted mesh has local orientations that disagree with the global ones;
+# the skewed tetrahedron has no edge along a coordinate axis
 PERM = sg.permuted_cells(sg.kuhn_cube(1), 3)
+SKEW = sg.MacroMesh(np.array([[0, 0, 0], [2, 1, 0], [1, 3, 1], [0, 1, 2]], dtype=np.int64),
+                    np.array([[0, 1, 2, 3]], dtype=np.int64), 1, "skew_tet")
 
 
-@pytest.mark.parametrize("macro,level", [(sg.kuhn_cube(1), 2), (sg.reference_tet(), 3), (PERM, 2)])
+@pytest.mark.parametrize("macro,level", [(sg.kuhn_cube(1), 2), (sg.reference_tet(), 3), (PERM, 2),
+                                         (SKEW, 2)])
 def test_curl_grad_zero_and_gradient_mass_is_p1_stiffness(macro, level):
     lev = ne.NedelecLevel(macro, level)
     KG = lev.K_full @ lev.G_full
@@ -114,7 +118,8 @@ def test_interpolant_energies_on_the_unit_cube(macro):
     assert abs(uc @ lev.M_full @ uc - exact) <= 1e-12
 
 
-@pytest.mark.parametrize("macro,level", [(sg.kuhn_cube(1), 2), (sg.reference_tet(), 2), (PERM, 2)])
+@pytest.mark.parametrize("macro,level", [(sg.kuhn_cube(1), 2), (sg.reference_tet(), 2), (PERM, 2),
+                                         (SKEW, 2)])
 def test_prolongation_commutes_with_gradient_and_reproduces_rotations(macro, level):
     f, c = ne.NedelecLevel(macro, level), ne.NedelecLevel(macro, level - 1)
     P = ne.nedelec_prolongation(f, c)
@@ -165,7 +170,7 @@ def _rate(H, L, cycles=6, **kw):
     return (r[-1] / r[2]) ** (1 / (cycles - 2))
 
 
-@pytest.mark.parametrize("macro", [sg.kuhn_cube(1), sg.reference_tet(), PERM])
+@pytest.mark.parametrize("macro", [sg.kuhn_cube(1), sg.reference_tet(), PERM, SKEW])
 def test_galerkin_identity(macro):
     """Coarse N1 functions are fine N1 functions (nested spaces), so
     P^T A_f P equals the rediscretised coarse matrix."""
