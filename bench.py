@@ -23,6 +23,7 @@ import json
 import os
 import re
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -78,7 +79,7 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"hytet_clocks_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -88,7 +89,6 @@ class ClockSampler:
                 ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
-            time.sleep(0.3)
         except Exception:
             self.proc = None
 
@@ -693,6 +693,15 @@ def main():
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
+    # the timed region lasts milliseconds, far below the 100 ms sampling
+    # interval: keep the GPU under the same apply load (untimed) for 0.5 s so
+    # that the samples show the clocks of this workload
+    t_load, s_extra = time.perf_counter(), 0
+    while time.perf_counter() - t_load < 0.5:
+        for _ in range(64):
+            step(s_extra)
+            s_extra += 1
+        torch.cuda.synchronize()
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
@@ -707,6 +716,9 @@ def main():
         pg.barrier()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    if clk is not None:
+        clk["window"] = (f"0.5 s of the same apply (untimed) before the timed region "
+                         f"({ms:.1f} ms) and the region itself")
     ms_step, value = aggregate_replicas(ms, nu, args.steps, pg, "cuda")
 
     # end to end through the public API: every step copies its canonical input
