@@ -64,7 +64,7 @@ struct FusedArgs {
   int gs_colour;          // OP_GS: the colour updated
   T* dvec;                // OP_CHEB: direction, updated in place
   T cheb_a;               // OP_CHEB: weight of the previous direction
-  int* err;            // device error word (reserved for bounded waits; these kernels do not wait)
+  int* err;            // device error word (bounded waits record HG_ERR_TIMEOUT)
 };
 
 // Face point p (rows b = 1..n-2 of n-1-b points) -> barycentric weights.
