@@ -16,7 +16,13 @@ tetrahedral grids"):
                   global matrix (Sec. 5.2, element-wise sum).
 * ``quadrature``- the fixed quadrature rules used by the variable-coefficient
                   P2 operator and an error-bound rule.
-* ``gmg``       - textbook geometric multigrid on the assembled matrices.
+* ``gmg``       - textbook geometric multigrid on the assembled matrices
+                  (Jacobi, colour-ordered Gauss-Seidel, Chebyshev, FMG).
+* ``nedelec``   - lowest-order Nedelec elements for the curl-curl problem of
+                  Sec. 6: Whitney basis, transfers, discrete gradient and
+                  Hiptmair multigrid.
+* ``surrogate`` - polynomial surrogate stencils of the variable-coefficient P1
+                  operator (Sec. 5.2, surrogates).
 * ``mlp``       - FP64 forward/backward of the local learned smoother network.
 
 Parity status of each function is stated in its module docstring.
