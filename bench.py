@@ -452,6 +452,71 @@ def n1_comparison(stream, level=6):
     return out
 
 
+N1_SOLVE_WORKLOAD = "cube48_L6_n1_curlcurl_hiptmair_gmg_to_1e-8"
+
+
+def n1_solve_comparison(stream, level=6, m=2):
+    """The Nedelec problem alpha curl curl u + beta u = f (alpha = 1,
+    beta = 0.3) on the same 48-cell cube at N1 level 6 (14.8 M edge DoFs),
+    seeded U[-1,1] right-hand side on the interior edges: multigrid with
+    Hiptmair's hybrid smoother (weighted Jacobi, omega = 1/2, in the edge and
+    the potential space), coarsest level 1.  Solves to 1e-8 relative residual
+    with FP32 V(2,2) cycles in FP64 refinement and with FP64 V(2,2) cycles,
+    and one FP32 FMG pass with 5 V(1,1) per level."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    P2 = hg.HG_SPACE_P2
+    macro = sg.kuhn_cube(m)
+    t0 = time.perf_counter()
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 0, level + 1)
+    op = hg.Operator(H, hg.HG_OP_N1_CURLCURL, coeff=(1.0, 0.3))
+    _, xyz, dirich = H.canonical_info(level, space=P2)
+    # edge DoFs: points of the level+1 lattice with an odd coordinate
+    q = np.rint(xyz * (m << (level + 1))).astype(np.int64)
+    edge = np.any(q % 2 == 1, axis=1)
+    bc = sg.uniform_vector(11, len(xyz))
+    bc[dirich | ~edge] = 0.0
+    b = H.from_canonical(level, torch.tensor(bc, device="cuda"), space=P2)
+    setup_s = time.perf_counter() - t0
+    out = {"workload": N1_SOLVE_WORKLOAD, "edge_dofs": int(edge.sum()),
+           "interior_edge_dofs": int((edge & ~dirich).sum()), "tol": 1e-8, "setup_s": setup_s,
+           "smoother": "Hiptmair, weighted Jacobi omega = 0.5 in both spaces",
+           "fp32_cycles_per_refinement_step": INNER_CYCLES}
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    G = hg.GMG(op, nu1=2, nu2=2, omega=0.5, lmin=1, inner_cycles=INNER_CYCLES)
+    for name, prec, warm in (("mixed_f32_ir", hg.HG_PREC_MIXED, True),
+                             ("plain_f64", hg.HG_PREC_F64, False)):
+        x = H.zeros(level, torch.float64, space=P2)
+        if warm:
+            G.solve(x, b, tol=1e-8, max_iter=100, precision=prec, stream=stream, check=False)
+            torch.cuda.synchronize()
+        e0.record(stream)
+        it, rel = G.solve(x, b, tol=1e-8, max_iter=100, precision=prec, stream=stream, check=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel,
+                     "timed_after_warmup": warm}
+    out["mixed_vs_f64_speedup"] = out["plain_f64"]["s"] / out["mixed_f32_ir"]["s"]
+    del G
+    G = hg.GMG(op, nu1=1, nu2=1, omega=0.5, lmin=1)
+    xf = H.zeros(level, torch.float32, space=P2)
+    bf = b.float()
+    G.fmg(level, xf, bf, cycles=5, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    G.fmg(level, xf, bf, cycles=5, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r = H.zeros(level, torch.float64, space=P2)
+    op.residual(level, xf.double(), b, r)
+    out["fmg_f32"] = {"s": e0.elapsed_time(e1) / 1e3, "cycles_per_level": 5,
+                      "rel_res": float(np.sqrt(H.dot(level, r, r, space=P2) /
+                                               H.dot(level, b, b, space=P2)))}
+    del G
+    return out
+
+
 KERNELS_WORKLOAD = "cube384_L6_p1_laplace_kernels"
 
 
@@ -649,6 +714,7 @@ def main():
     ap.add_argument("--no-stencil", action="store_true")
     ap.add_argument("--no-kernels", action="store_true")
     ap.add_argument("--no-n1", action="store_true")
+    ap.add_argument("--no-n1-solve", action="store_true")
     ap.add_argument("--stencil-case", type=int, nargs=2, default=[4, 6], metavar=("M", "LEVEL"),
                     help="stencil leg mesh (m^3 sub-cubes x 6 cells) and level (smaller for profiling)")
     ap.add_argument("--no-stencil-solve", action="store_true")
@@ -808,6 +874,12 @@ def main():
                                             solve=not args.no_stencil_solve)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_spmv()
+    if rank == 0 and not args.no_n1_solve:
+        # last leg; an error here is recorded in the line instead of ending the run
+        try:
+            out["n1_solve"] = n1_solve_comparison(stream)
+        except Exception as e:                                    # noqa: BLE001
+            out["n1_solve"] = {"workload": N1_SOLVE_WORKLOAD, "error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(out))
         sys.stdout.flush()
