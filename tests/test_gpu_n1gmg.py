@@ -1,7 +1,8 @@
 """Nedelec multigrid with Hiptmair's hybrid smoother through the C ABI
 against the oracle (oracle.nedelec): V(1,1) iterates with weighted Jacobi
 (omega = 1/2) in the edge and the potential space, FMG, and solves to 1e-8
-in FP64 and mixed precision, on a Kuhn cube and a permuted-cell cube."""
+in FP64 and mixed precision, on a Kuhn cube, a permuted-cell cube and the
+48-cell cube (2 x 2 x 2 sub-cubes)."""
 import numpy as np
 import pytest
 
@@ -19,8 +20,8 @@ import paper_2308_01792_gb300 as hg
 P2 = hg.HG_SPACE_P2
 AB = (1.0, 0.3)
 L = 3
-CASES = [sg.kuhn_cube(1), sg.permuted_cells(sg.kuhn_cube(1), 3)]
-IDS = ["cube1", "cube1perm"]
+CASES = [sg.kuhn_cube(1), sg.permuted_cells(sg.kuhn_cube(1), 3), sg.kuhn_cube(2)]
+IDS = ["cube1", "cube1perm", "cube2"]
 
 
 @pytest.fixture(scope="module", params=range(len(CASES)), ids=IDS)

@@ -1,7 +1,8 @@
 """Nedelec transfers and discrete gradient through the C ABI against the
 oracle (oracle.nedelec): prolongation P (tangential line integrals of the
 coarse function), restriction P^T, the discrete gradient G and G^T, on meshes
-with Kuhn-ordered and permuted cells (other local orientations).  Bars: FP64
+with Kuhn-ordered and permuted cells (other local orientations) and on the
+48-cell cube (interior macro vertices and edges).  Bars: FP64
 1e-13, FP32 1e-6 relative; boundary entries as documented."""
 import numpy as np
 import pytest
@@ -19,8 +20,8 @@ import paper_2308_01792_gb300 as hg
 
 P2 = hg.HG_SPACE_P2
 TOL = {torch.float64: 1e-13, torch.float32: 1e-6}
-CASES = [sg.kuhn_cube(1), sg.permuted_cells(sg.kuhn_cube(1), 3), sg.reference_tet()]
-IDS = ["cube1", "cube1perm", "tet"]
+CASES = [sg.kuhn_cube(1), sg.permuted_cells(sg.kuhn_cube(1), 3), sg.reference_tet(), sg.kuhn_cube(2)]
+IDS = ["cube1", "cube1perm", "tet", "cube2"]
 L = 2
 
 
