@@ -107,7 +107,8 @@ struct Op {
   std::vector<int> pattern;     // per level: kPat7 when the interior stencils allow it
   // variable-coefficient P1 (per level): k at stored vertices, element rows, 1/diag
   std::vector<void*> vk[2], vK[2], vinv[2];
-  // stored-stencil P1 (per level): partial stencils of every stored point, [15][n_stored]
+  // stored-stencil P1 (per level): per stored point 16 values, point-major [n_stored][16]:
+  // the 15 partial-stencil weights and the inverse centre weight
   std::vector<void*> sst[2];
 
   int build(const Hier* h, int kind, const double* coeff);
