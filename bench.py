@@ -166,6 +166,37 @@ def cpu_baseline_spmv(seconds=10.0):
                       f"{SAMPLE_LEVEL} ({rm.n_vertices} DoFs), {reps} reps in {dt:.1f} s"}
 
 
+ORACLE_GMG_LEVEL = 4          # oracle GMG sample: the GMG workload's mesh two levels coarser
+
+
+def cpu_baseline_gmg(level=ORACLE_GMG_LEVEL):
+    """The oracle's FP64 GMG (SciPy CSR, V(3,3) weighted Jacobi omega = 2/3,
+    exact coarse solve on level 0) on the GMG workload's problem: 4x4x4 Kuhn
+    cube, P1 -div(k grad) with the same log-normal k (seed 1000) and the same
+    seeded right-hand side, to 1e-8 relative residual, at `level` instead of
+    6.  Assembly is timed apart from the solve.  The level-6 figure is
+    extrapolated linearly in the DoFs at the sample's V-cycle count, and
+    labelled so."""
+    from oracle import gmg as og
+    macro = sg.kuhn_cube(4)
+    p = sg.rff_params(1000)
+    t0 = time.perf_counter()
+    H = og.Hierarchy(macro, 0, level, kind="divkgrad", coeff=lambda xyz: sg.rff_eval(p, xyz))
+    setup_s = time.perf_counter() - t0
+    lev = H.levels[level]
+    b = sg.uniform_vector(9, lev.n)[lev.interior]
+    t0 = time.perf_counter()
+    _, it, hist = og.solve(H, b, tol=1e-8, max_iter=200)
+    solve_s = time.perf_counter() - t0
+    n6 = (4 * 64 + 1) ** 3
+    return {"kind": "oracle", "cores": 1, "level": level, "unique_dofs": int(lev.n),
+            "assembly_s": setup_s, "solve_s": solve_s, "v_cycles": it, "rel_res": hist[-1],
+            "level6_solve_s_extrapolated": solve_s * n6 / lev.n,
+            "sample": f"oracle GMG (SciPy CSR, single thread) of the GMG workload's problem at level "
+                      f"{level} ({lev.n} DoFs); the level-6 time is extrapolated linearly in the "
+                      f"DoFs at {it} V-cycles"}
+
+
 GMG_WORKLOAD = "cube384_L6_p1_lognormal_gmg_to_1e-8"
 # FP32 V-cycles per FP64 refinement step of the mixed solves (one FP64
 # residual per step; measured on GB300: 3 beats 1 and 2 for both the P1
@@ -874,6 +905,7 @@ def main():
                                             solve=not args.no_stencil_solve)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_spmv()
+        out["cpu_baseline"]["gmg"] = cpu_baseline_gmg()
     if rank == 0 and not args.no_n1_solve:
         # last leg; an error here is recorded in the line instead of ending the run
         try:

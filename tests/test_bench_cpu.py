@@ -1,0 +1,45 @@
+"""Host-side pieces of bench.py that need no GPU: the oracle's GMG sample of
+the CPU baseline converges on a small level and reports what it ran, and the
+clock sampler's parser reads nvidia-smi's CSV (median SM clock, the throttle
+reasons that were active)."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_oracle_gmg_sample_converges_and_labels_the_extrapolation():
+    g = bench.cpu_baseline_gmg(level=2)
+    assert g["kind"] == "oracle" and g["level"] == 2
+    assert g["unique_dofs"] == (4 * 4 + 1) ** 3
+    assert g["rel_res"] <= 1e-8 and 5 <= g["v_cycles"] <= 60
+    assert g["level6_solve_s_extrapolated"] == pytest.approx(
+        g["solve_s"] * (4 * 64 + 1) ** 3 / g["unique_dofs"])
+    assert "extrapolated" in g["sample"]
+
+
+def test_clock_sampler_parses_nvidia_smi_csv(tmp_path):
+    c = bench.ClockSampler(0)
+    c.path = str(tmp_path / "clk.csv")
+    with open(c.path, "w") as f:
+        f.write("0, 1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n")
+        f.write("0, 1980, 2070, 950.0, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("0, 1995, 2070, 990.2, 0x4, Not Active, Not Active, Not Active, Active\n")
+        f.write("garbage line\n")
+
+    class Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    c.proc = Done()
+    c.f = open(os.devnull, "w")
+    r = c.stop()
+    assert r == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
