@@ -34,8 +34,12 @@
  * - `stream` is a cudaStream_t passed as void* (NULL = legacy default
  *   stream).  Calls are asynchronous with respect to the host unless stated.
  * - Dirichlet DoFs are those on macro faces with one incident macro cell and
- *   on the edges/vertices of such faces.  HG_MASK_INNER leaves them
- *   untouched in the destination; HG_MASK_ALL computes the full Neumann rows.
+ *   on the edges/vertices of such faces.  HG_MASK_INNER computes the rows of
+ *   the other DoFs (taking x as given at the Dirichlet DoFs) and sets the
+ *   Dirichlet entries of the destination to 0 for an apply (HG_REPLACE and
+ *   HG_ADD alike) and a residual, and to x's values for the smoothing steps
+ *   (Jacobi, Gauss-Seidel, Chebyshev); HG_MASK_ALL computes the full Neumann
+ *   rows.
  */
 #ifndef HYTET_H
 #define HYTET_H

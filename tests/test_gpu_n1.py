@@ -5,7 +5,7 @@ N1 DoFs are stored as P2-space vectors at the edge-midpoint points; in the
 P2 canonical order the edge points must be exactly the oracle's N1 DoFs (same
 keys, same order) with the same boundary set.  Bars: apply (ALL and INNER
 masks), residual and Jacobi within 1e-12 (FP64) / 1e-5 (FP32) relative,
-vertex points untouched, interface copies bit-identical."""
+vertex points 0, interface copies bit-identical."""
 import numpy as np
 import pytest
 

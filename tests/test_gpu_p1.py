@@ -135,6 +135,27 @@ def test_apply_matches_assembled_oracle(case, dtype, kind):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_inner_mask_add_zeroes_dirichlet_entries(case, dtype):
+    """HG_ADD with HG_MASK_INNER: y + A x on the other DoFs, 0 at the
+    Dirichlet DoFs (the documented mask semantics)."""
+    macro, H = case
+    op = hg.Operator(H)
+    L = H.lmax
+    rm, A = _oracle_level(macro, L)
+    xi = sg.uniform_vector(200 + L, rm.n_vertices)
+    xi[rm.boundary] = 0
+    y0 = sg.uniform_vector(300 + L, rm.n_vertices)
+    x = H.from_canonical(L, torch.tensor(xi, dtype=dtype, device="cuda"))
+    y = H.from_canonical(L, torch.tensor(y0, dtype=dtype, device="cuda"))
+    op.apply(L, x, y, mode=hg.HG_ADD)
+    yc = H.to_canonical(L, y).cpu().double().numpy()
+    ii = rm.interior
+    if len(ii):
+        assert rel_err(yc[ii], (y0 + A @ xi)[ii]) <= TOL[dtype] * 2
+    assert np.all(yc[rm.boundary] == 0)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_residual_and_jacobi_match_oracle(case, dtype):
     macro, H = case
     op = hg.Operator(H)
