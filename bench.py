@@ -79,14 +79,38 @@ class ClockSampler:
     def __init__(self, device_index):
         self.dev = device_index
         self.proc = None
+        self.gpu_id = None
         self.path = os.path.join(tempfile.gettempdir(), f"hytet_clocks_{os.getpid()}.csv")
+
+    @staticmethod
+    def smi_gpu_id(device_index, run=subprocess.run):
+        """The nvidia-smi --id of torch device `device_index`.  torch numbers
+        only the devices CUDA_VISIBLE_DEVICES exposes, while nvidia-smi numbers
+        every GPU of the machine, so the index can name another GPU; the
+        device's UUID names the same one in both.  The UUID is used when torch
+        reports it and nvidia-smi accepts it, else the index."""
+        try:
+            import torch
+            u = str(torch.cuda.get_device_properties(device_index).uuid)
+        except Exception:
+            return str(device_index)
+        gid = u if u.startswith("GPU-") else f"GPU-{u}"
+        try:
+            p = run(["nvidia-smi", f"--id={gid}", "--query-gpu=index", "--format=csv,noheader"],
+                    capture_output=True, text=True, timeout=30)
+            if p.returncode == 0 and p.stdout.strip():
+                return gid
+        except Exception:
+            pass
+        return str(device_index)
 
     def start(self):
         try:
+            self.gpu_id = self.smi_gpu_id(self.dev)
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
-                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                ["nvidia-smi", f"--id={self.gpu_id}", f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
@@ -117,8 +141,11 @@ class ClockSampler:
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        r = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons),
+             "samples": len(sm)}
+        if self.gpu_id is not None:
+            r["gpu"] = self.gpu_id
+        return r
 
 
 def _dist():

@@ -43,3 +43,42 @@ def test_clock_sampler_parses_nvidia_smi_csv(tmp_path):
     c.f = open(os.devnull, "w")
     r = c.stop()
     assert r == {"sm_mhz": 1980.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+
+
+def test_clock_sampler_names_the_gpu_by_uuid_when_nvidia_smi_accepts_it(monkeypatch):
+    torch = pytest.importorskip("torch")
+
+    class Props:
+        uuid = "3f1c2a9e-0000-1111-2222-333344445555"
+
+    class Result:
+        def __init__(self, rc, out):
+            self.returncode, self.stdout = rc, out
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", lambda i: Props())
+    calls = []
+
+    def accepts(cmd, **kw):
+        calls.append(cmd)
+        return Result(0, "5\n")
+
+    gid = bench.ClockSampler.smi_gpu_id(0, run=accepts)
+    assert gid == "GPU-3f1c2a9e-0000-1111-2222-333344445555"
+    assert calls[0][1] == f"--id={gid}"
+    # nvidia-smi refuses the id (or is missing): the torch index is kept
+    assert bench.ClockSampler.smi_gpu_id(2, run=lambda cmd, **kw: Result(6, "")) == "2"
+
+    def missing(cmd, **kw):
+        raise FileNotFoundError("nvidia-smi")
+
+    assert bench.ClockSampler.smi_gpu_id(1, run=missing) == "1"
+
+
+def test_clock_sampler_falls_back_to_the_index_without_device_properties(monkeypatch):
+    torch = pytest.importorskip("torch")
+
+    def no_gpu(i):
+        raise RuntimeError("no CUDA device")
+
+    monkeypatch.setattr(torch.cuda, "get_device_properties", no_gpu)
+    assert bench.ClockSampler.smi_gpu_id(3) == "3"
