@@ -1,7 +1,8 @@
 """Host-side pieces of bench.py that need no GPU: the oracle's GMG sample of
 the CPU baseline converges on a small level and reports what it ran, and the
 clock sampler's parser reads nvidia-smi's CSV (median SM clock, the throttle
-reasons that were active)."""
+reasons that were active), and the sampler names the GPU by its UUID when
+nvidia-smi accepts it, else by torch's index."""
 import os
 import sys
 
