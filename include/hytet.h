@@ -106,7 +106,9 @@ const char* hg_last_error(void);
  *           vertex order v0..v3 of the macro cell and fixes its refinement
  *           (inner edge v02-v13, Sec. 3.1).
  * Checks: ids in range, no repeated vertex in a cell, nonzero volume, every
- * face shared by at most two cells.  Errors: HG_ERR_INVALID_ARG,
+ * face shared by at most two cells, which lie on opposite sides of it (a
+ * cell listed twice, or two cells folded over a common face, overlap and are
+ * rejected).  Errors: HG_ERR_INVALID_ARG,
  * HG_ERR_BAD_MESH.  Copies the input; caller keeps ownership. */
 int hg_mesh_create(const double* xyz, int64_t nv, const int64_t* cells, int64_t nc,
                    hg_mesh** out);

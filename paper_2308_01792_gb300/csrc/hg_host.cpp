@@ -124,6 +124,34 @@ int Mesh::build(const double* xyz_, int64_t nv_, const int64_t* cells_, int64_t 
     f.dirichlet = f.cells.size() == 1;
     n_boundary_faces += f.dirichlet;
   }
+  // Sec. 2: cells meet only in common faces, edges or vertices, so the two
+  // cells of an interior face lie on opposite sides of it (a repeated or
+  // folded-over cell puts both opposite vertices on the same side)
+  for (const auto& f : faces) {
+    if (f.cells.size() != 2) continue;
+    const int fid = (int)(&f - faces.data());
+    const double* a = &xyz[3 * f.vid[0]];
+    const double* b = &xyz[3 * f.vid[1]];
+    const double* d = &xyz[3 * f.vid[2]];
+    const double u[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const double w[3] = {d[0] - a[0], d[1] - a[1], d[2] - a[2]};
+    const double nrm[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2],
+                           u[0] * w[1] - u[1] * w[0]};
+    double side[2];
+    for (int q = 0; q < 2; ++q) {
+      const int64_t c = f.cells[q];
+      int opp = 0;
+      while (cell_face[c][opp] != fid) ++opp;
+      const double* p = &xyz[3 * cells[c][opp]];
+      side[q] = nrm[0] * (p[0] - a[0]) + nrm[1] * (p[1] - a[1]) + nrm[2] * (p[2] - a[2]);
+    }
+    if (!(side[0] * side[1] < 0)) {
+      set_error("cells %d and %d lie on the same side of their common face (%lld,%lld,%lld): "
+                "they overlap", f.cells[0], f.cells[1], (long long)f.vid[0],
+                (long long)f.vid[1], (long long)f.vid[2]);
+      return HG_ERR_BAD_MESH;
+    }
+  }
   std::vector<char> vb(nv, 0);
   std::set<std::array<int64_t, 2>> be;
   for (auto& f : faces)

@@ -75,6 +75,27 @@ def test_bad_meshes_are_rejected(built):
         hg.Mesh(xyz, np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]]))
 
 
+def test_overlapping_cells_are_rejected(built):
+    """Cells meet only in common faces, edges or vertices (Sec. 2): the two
+    cells of an interior face lie on opposite sides of it.  A cell listed
+    twice (in any vertex order) or folded over a shared face overlaps its
+    neighbour; two cells on opposite sides pass."""
+    r = sg.reference_tet()
+    for cells in ([[0, 1, 2, 3], [0, 1, 2, 3]], [[0, 1, 2, 3], [1, 0, 2, 3]]):
+        with pytest.raises(hg.HGError) as e:
+            hg.Mesh(r.xyz, np.array(cells))
+        assert e.value.code == -2 and "overlap" in str(e.value)
+    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0.2, 0.2, 0.5], [0, 0, -1]], float)
+    with pytest.raises(hg.HGError) as e:
+        hg.Mesh(xyz, np.array([[0, 1, 2, 3], [0, 1, 2, 4]]))
+    assert "same side" in str(e.value)
+    hg.Mesh(xyz, np.array([[0, 1, 2, 3], [0, 1, 2, 5]]))
+    for m in (1, 2, 3):
+        for seed in range(4):
+            c = sg.permuted_cells(sg.kuhn_cube(m), seed)
+            hg.Mesh(c.xyz, c.cells)
+
+
 def test_quadrature_rule_exact_to_degree_five():
     """The library derives its P2 rule from the moment equations: positive
     weights summing to 1, points inside the tetrahedron, every barycentric
