@@ -759,7 +759,7 @@ def run_reference(args):
     sys.stdout.flush()
 
 
-def main():
+def make_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -780,7 +780,11 @@ def main():
                     help="P2 leg: apply only (for profiling)")
     ap.add_argument("--p2-level", type=int, default=6,
                     help="P2 level of the P2 leg (6 = the 17 M DoF workload; smaller for profiling)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = make_parser().parse_args()
     if args.impl == "reference":
         return run_reference(args)
 

@@ -2,7 +2,8 @@
 the CPU baseline converges on a small level and reports what it ran, and the
 clock sampler's parser reads nvidia-smi's CSV (median SM clock, the throttle
 reasons that were active), and the sampler names the GPU by its UUID when
-nvidia-smi accepts it, else by torch's index."""
+nvidia-smi accepts it, else by torch's index; the bench command lines quoted
+in the committed profile summaries parse with the current bench.py."""
 import os
 import sys
 
@@ -83,3 +84,29 @@ def test_clock_sampler_falls_back_to_the_index_without_device_properties(monkeyp
 
     monkeypatch.setattr(torch.cuda, "get_device_properties", no_gpu)
     assert bench.ClockSampler.smi_gpu_id(3) == "3"
+
+
+def _profile_commands():
+    """Every `python bench.py ...` command quoted in profiles/*.md, with
+    backslash continuations joined and redirections dropped."""
+    import glob
+    import shlex
+    out = []
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
+        text = open(path).read().replace("\\\n", " ")
+        for line in text.splitlines():
+            at = line.find("python bench.py")
+            if at < 0:
+                continue
+            words = shlex.split(line[at:].split(">")[0].split("&&")[0])
+            out.append((os.path.basename(path), words[2:]))
+    return out
+
+
+def test_profile_command_lines_parse_with_the_current_bench():
+    cmds = _profile_commands()
+    assert len(cmds) >= 6
+    ap = bench.make_parser()
+    for name, argv in cmds:
+        args = ap.parse_args(argv)
+        assert args.impl == "gb300", name
