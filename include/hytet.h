@@ -121,7 +121,11 @@ int hg_mesh_counts(const hg_mesh* mesh, int64_t counts[6]);
  * Refinement of every macro cell to levels lmin..lmax (Sec. 3.1, Bey's
  * rule applied recursively; Sec. 5.1, functions allocated on a level range).
  * 0 <= lmin <= lmax <= 9.  Uploads per-level maps to the current device.
- * Errors: HG_ERR_LEVEL_RANGE, HG_ERR_CUDA. */
+ * Limits, checked before anything is allocated (HG_ERR_UNSUPPORTED): at most
+ * 2^31 - 1 stored points on level lmax; on meshes with coordinates on a
+ * lattice of spacing 1/D, |coordinate| x D x 2^lmax below 2^20; no macro
+ * face, edge or vertex in more than 255 cells.
+ * Errors: HG_ERR_LEVEL_RANGE, HG_ERR_UNSUPPORTED, HG_ERR_CUDA. */
 int hg_hier_create(const hg_mesh* mesh, int lmin, int lmax, hg_hier** out);
 void hg_hier_destroy(hg_hier* hier);
 

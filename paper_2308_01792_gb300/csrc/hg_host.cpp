@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <array>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -445,11 +446,45 @@ void Mesh::find_colouring() {
       }
 }
 
+// Limits of the per-level tables, checked on the finest lattice before
+// anything is allocated: the stored->canonical map and the row items are
+// int32; the canonical keys pack each exact lattice coordinate (vertex
+// coordinate x D x 2^level) into 21 bits around an offset of 2^20; interface
+// items keep a primitive's copy count in 8 bits.
+int Hier::check_limits() const {
+  const int64_t n = int64_t(1) << lmax;
+  const int64_t n_stored = (ntet(n + 1) + 32 + 31) / 32 * 32 * mesh->nc;
+  if (n_stored > INT32_MAX) {
+    set_error("level %d of %lld cells has %lld stored points; at most 2^31 - 1 are supported",
+              lmax, (long long)mesh->nc, (long long)n_stored);
+    return HG_ERR_UNSUPPORTED;
+  }
+  if (mesh->grid_denom) {
+    int64_t amax = 0;
+    for (int64_t x : mesh->ixyz) amax = std::max(amax, x < 0 ? -x : x);
+    if (amax * n >= (int64_t(1) << 20)) {
+      set_error("lattice coordinates reach %lld at level %d (vertex coordinates x %d x 2^%d); the "
+                "canonical numbering holds magnitudes below 2^20: scale the mesh down",
+                (long long)(amax * n), lmax, mesh->grid_denom, lmax);
+      return HG_ERR_UNSUPPORTED;
+    }
+  }
+  for (const auto* prims : {&mesh->faces, &mesh->edges, &mesh->verts})
+    for (const auto& p : *prims)
+      if (p.cells.size() > 255) {
+        set_error("a macro primitive is shared by %zu cells; at most 255 are supported",
+                  p.cells.size());
+        return HG_ERR_UNSUPPORTED;
+      }
+  return HG_OK;
+}
+
 int Hier::build(const Mesh* m, int lmin_, int lmax_) {
   mesh = m;
   const_cast<Mesh*>(m)->find_colouring();
   lmin = lmin_;
   lmax = lmax_;
+  if (int r = check_limits()) return r;
   lv.resize(lmax - lmin + 1);
   HG_CUDA(cudaMalloc(&err_dev, sizeof(int)));
   HG_CUDA(cudaMemset(err_dev, 0, sizeof(int)));

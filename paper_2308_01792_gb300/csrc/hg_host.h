@@ -70,6 +70,7 @@ struct Hier {
   int* err_host = nullptr;  // pinned mirror
 
   int build(const Mesh* m, int lmin, int lmax);
+  int check_limits() const;
   int build_level(int l);
   // Enqueue a read of the error word on s (no sync); check_error() after a sync.
   int fetch_error(cudaStream_t s) const;

@@ -116,3 +116,54 @@ def test_quadrature_rule_exact_to_degree_five():
         worst[d] = max(worst.get(d, 0.0), abs(got - ex))
     assert max(worst[d] for d in range(6)) < 1e-15
     assert worst[6] > 1e-6
+
+
+def _fan_mesh(g=7):
+    """A cube's surface cut into 2 g^2 triangles per side, each joined to the
+    centre: a conforming mesh of 12 g^2 cells that all share the centre
+    vertex (integer corners, centre at half-integers)."""
+    verts = {}
+    xyz = []
+
+    def vid(p):
+        if p not in verts:
+            verts[p] = len(xyz)
+            xyz.append(p)
+        return verts[p]
+
+    centre = vid((g / 2, g / 2, g / 2))
+    cells = []
+    for ax in range(3):
+        for side in (0, g):
+            for a in range(g):
+                for b in range(g):
+                    def pt(u, v):
+                        p = [0, 0, 0]
+                        p[ax], p[(ax + 1) % 3], p[(ax + 2) % 3] = side, u, v
+                        return vid(tuple(float(c) for c in p))
+                    q = [pt(a, b), pt(a + 1, b), pt(a + 1, b + 1), pt(a, b + 1)]
+                    cells += [[centre, q[0], q[1], q[2]], [centre, q[0], q[2], q[3]]]
+    return np.array(xyz, dtype=float), np.array(cells, dtype=np.int64)
+
+
+def test_hierarchy_limits_are_checked_before_any_allocation(built):
+    """Sizes the per-level tables cannot represent are refused with
+    HG_ERR_UNSUPPORTED before the GPU is touched (so this runs without one):
+    more than 2^31 - 1 stored points, lattice coordinates of magnitude 2^20 or
+    more (the canonical keys' 21 bits), and a primitive shared by more than
+    255 cells (the interface items' 8-bit copy count)."""
+    c = sg.kuhn_cube(4)                      # 384 cells x N_tet(513) > 2^31 at level 9
+    with pytest.raises(hg.HGError) as e:
+        hg.Hierarchy(hg.Mesh(c.xyz, c.cells), 0, 9)
+    assert e.value.code == -7 and "stored points" in str(e.value)
+    r = sg.reference_tet()
+    big = np.asarray(r.xyz, dtype=float) * 4096   # 4096 x 2^9 = 2^21
+    with pytest.raises(hg.HGError) as e:
+        hg.Hierarchy(hg.Mesh(big, r.cells), 0, 9)
+    assert e.value.code == -7 and "2^20" in str(e.value)
+    xyz, cells = _fan_mesh()
+    m = hg.Mesh(xyz, cells)
+    assert m.counts()["cells"] == len(cells) == 588 and m.counts()["boundary_faces"] == 588
+    with pytest.raises(hg.HGError) as e:
+        hg.Hierarchy(m, 0, 1)
+    assert e.value.code == -7 and "shared by 588 cells" in str(e.value)
