@@ -201,8 +201,9 @@ int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
 /* ---------------------------------------------------------- operators --
  * kind: HG_OP_*.  coeff: for HG_OP_P1_DIVKGRAD(_STORED), host array of k at the
  * unique vertices of level lmax in canonical order (injected to coarser
- * levels); for HG_OP_P2_DIVKGRAD, host {a, b}; for HG_OP_N1_CURLCURL, host
- * {alpha, beta}; otherwise NULL.
+ * levels), every value positive and finite; for HG_OP_P2_DIVKGRAD, host
+ * {a, b} with finite a > |b| (k stays positive); for HG_OP_N1_CURLCURL, host
+ * {alpha >= 0, beta > 0}; otherwise NULL.  Other values: HG_ERR_INVALID_ARG.
  * P2 operators (levels max(0, lmin-1) .. lmax-1 of the hierarchy) are
  * element-wise: per micro-cell the 10x10 element matrix acts on the fly by
  * the 14-point rule of hg_quadrature_rule, with k evaluated exactly at every

@@ -285,7 +285,16 @@ class Operator:
         h = _P()
         carr = None
         if coeff is not None:
-            carr = np.ascontiguousarray(coeff, dtype=np.float64)
+            carr = np.ascontiguousarray(coeff, dtype=np.float64).ravel()
+            if kind in (HG_OP_P1_DIVKGRAD, HG_OP_P1_DIVKGRAD_STORED):
+                need = hier.size(hier.lmax)[1]     # k at the unique vertices of level lmax
+            elif kind in (HG_OP_P2_DIVKGRAD, HG_OP_N1_CURLCURL):
+                need = 2                           # {a, b} / {alpha, beta}
+            else:
+                need = carr.size
+            if carr.size != need:
+                raise ValueError(f"operator kind {kind} takes {need} coefficient values, "
+                                 f"got {carr.size}")
         _call("hg_op_create", hier._h, kind, carr.ctypes.data_as(_P) if carr is not None else None,
               ctypes.byref(h))
         self._h = h

@@ -762,6 +762,15 @@ int Op::build_divkgrad(const double* coeff) {
     set_error("HG_OP_P1_DIVKGRAD needs vertex coordinates on an exact lattice");
     return HG_ERR_UNSUPPORTED;
   }
+  // -div(k grad) is elliptic only for k > 0 (a nonpositive or non-finite
+  // value would make the operator indefinite or undefined)
+  const int64_t nk = h->lv[h->lmax - h->lmin].dev.n_unique;
+  for (int64_t u = 0; u < nk; ++u)
+    if (!(coeff[u] > 0.0) || !std::isfinite(coeff[u])) {
+      set_error("HG_OP_P1_DIVKGRAD: k must be positive and finite; canonical vertex %lld of level "
+                "%d has %g", (long long)u, h->lmax, coeff[u]);
+      return HG_ERR_INVALID_ARG;
+    }
   const int nl = h->lmax - h->lmin + 1;
   for (int dt = 0; dt < 2; ++dt) {
     vk[dt].assign(nl, nullptr);

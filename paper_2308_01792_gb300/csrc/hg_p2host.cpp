@@ -72,6 +72,12 @@ int Op::build_p2(const double* coeff) {
     }
     ka = coeff[0];
     kb = coeff[1];
+    // k = a + b sin sin sin lies in [a - |b|, a + |b|]: positive iff a > |b|
+    if (!std::isfinite(ka) || !std::isfinite(kb) || !(ka > std::fabs(kb))) {
+      set_error("HG_OP_P2_DIVKGRAD: k = a + b sin(2 pi x) sin(2 pi y) sin(2 pi z) must stay "
+                "positive, which needs finite a > |b|; got a = %g, b = %g", ka, kb);
+      return HG_ERR_INVALID_ARG;
+    }
   }
   p2mode = kind == HG_OP_P2_MASS ? P2_MASS : P2_STIFF;
   double qb[14][4], qw[14];

@@ -118,3 +118,22 @@ def test_divkgrad_gmg_matches_oracle(case, precision):
     assert rel <= 1e-8 and ro <= 1.01e-8
     _, ito, _ = og.solve(Ho, bc[lev.interior], tol=1e-8)
     assert abs(it - ito) <= (1 if precision == hg.HG_PREC_F64 else 3)
+
+
+def test_divkgrad_rejects_coefficients_that_are_not_positive_and_finite():
+    """-div(k grad) is elliptic only for k > 0: a zero, negative, NaN or
+    infinite vertex value is refused at creation (both forms), and so is a
+    coefficient array of the wrong length; a positive constant is accepted."""
+    macro = sg.kuhn_cube(1)
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 1, 3)
+    n = H.size(3)[1]
+    for kind in (hg.HG_OP_P1_DIVKGRAD, hg.HG_OP_P1_DIVKGRAD_STORED):
+        for bad in (0.0, -1.0, np.nan, np.inf):
+            k = np.ones(n)
+            k[n // 2] = bad
+            with pytest.raises(hg.HGError) as e:
+                hg.Operator(H, kind, coeff=k)
+            assert e.value.code == -1 and "positive and finite" in str(e.value)
+        with pytest.raises(ValueError):
+            hg.Operator(H, kind, coeff=np.ones(n - 1))
+        hg.Operator(H, kind, coeff=np.full(n, 2.0))

@@ -170,3 +170,17 @@ def test_p2_solve_manufactured(setup, precision):
     assert rel <= tol and ro <= tol * 1.01
     xd = spla.spsolve(lev.A.tocsc(), bo)
     assert np.linalg.norm(xg - xd) <= 1e3 * tol * np.linalg.norm(xd)
+
+
+def test_p2_divkgrad_rejects_a_coefficient_that_is_not_positive():
+    """k = a + b sin(2 pi x) sin(2 pi y) sin(2 pi z) ranges over [a - |b|,
+    a + |b|], so creation needs finite a > |b|; {a, b} must be two values."""
+    macro = sg.kuhn_cube(1)
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 0, 3)
+    for bad in ((0.5, 0.5), (1.0, -1.5), (-1.0, 0.0), (np.nan, 0.0), (1.0, np.inf)):
+        with pytest.raises(hg.HGError) as e:
+            hg.Operator(H, hg.HG_OP_P2_DIVKGRAD, coeff=bad)
+        assert e.value.code == -1 and "a > |b|" in str(e.value)
+    with pytest.raises(ValueError):
+        hg.Operator(H, hg.HG_OP_P2_DIVKGRAD, coeff=(1.0,))
+    hg.Operator(H, hg.HG_OP_P2_DIVKGRAD, coeff=(1.0, 0.99))
