@@ -195,6 +195,20 @@ class Hierarchy:
         self._h = h
         self.mesh = mesh
         self.lmin, self.lmax = lmin, lmax
+        self._n_stored = {}
+
+    def _vec(self, level, space, dtype, *ts):
+        """Check that each tensor is a contiguous CUDA tensor of `dtype` with
+        at least the stored length of `level` in `space`: the kernels index
+        that many elements of every vector they are given."""
+        key = (level, space)
+        n = self._n_stored.get(key)
+        if n is None:
+            n = self._n_stored[key] = self.size(level, space)[0]
+        for t in ts:
+            if t.dtype != dtype:
+                raise TypeError(f"vector of dtype {t.dtype} where {dtype} is expected")
+            _ptr(t, n)
 
     def size(self, level, space=HG_SPACE_P1):
         v = [ctypes.c_int64() for _ in range(4)]
@@ -244,21 +258,31 @@ class Hierarchy:
         return out[:nr.value]
 
     def restrict(self, fine_level, r_fine, r_coarse, space=HG_SPACE_P1, stream=None):
+        self._vec(fine_level, space, r_fine.dtype, r_fine)
+        self._vec(fine_level - 1, space, r_fine.dtype, r_coarse)
         _call("hg_restrict", self._h, space, fine_level, _dtype_code(r_fine), _ptr(r_fine),
               _ptr(r_coarse), _stream(stream))
 
     def prolong_add(self, fine_level, e_coarse, x_fine, space=HG_SPACE_P1, stream=None):
+        self._vec(fine_level - 1, space, e_coarse.dtype, e_coarse)
+        self._vec(fine_level, space, e_coarse.dtype, x_fine)
         _call("hg_prolong_add", self._h, space, fine_level, _dtype_code(e_coarse),
               _ptr(e_coarse), _ptr(x_fine), _stream(stream))
 
     def dot(self, level, x, y, mask=HG_MASK_INNER, space=HG_SPACE_P1, stream=None):
         r = ctypes.c_double()
+        self._vec(level, space, x.dtype, x, y)
         _call("hg_dot", self._h, space, level, _dtype_code(x), _ptr(x), _ptr(y), mask,
               ctypes.byref(r), _stream(stream))
         return r.value
 
     def dot_noalloc(self, level, x, y, out, mask=HG_MASK_INNER, space=HG_SPACE_P1, stream=None):
         """hg_dot_noalloc: writes the dot into out[0] (CUDA float64 tensor), no sync."""
+        import torch
+        self._vec(level, space, x.dtype, x, y)
+        if out.dtype != torch.float64:
+            raise TypeError("out must be a float64 tensor")
+        _ptr(out, 1)
         _call("hg_dot_noalloc", self._h, space, level, _dtype_code(x), _ptr(x), _ptr(y), mask,
               _ptr(out), _stream(stream))
 
@@ -300,37 +324,53 @@ class Operator:
         self._h = h
         self.hier = hier
         self.kind = kind
+        # P2 and N1 vectors live in the P2 space; their finest level is lmax - 1
+        self.space = HG_SPACE_P2 if kind in (HG_OP_P2_LAPLACE, HG_OP_P2_MASS, HG_OP_P2_DIVKGRAD,
+                                             HG_OP_N1_CURLCURL) else HG_SPACE_P1
+        self.lmax = hier.lmax - (1 if self.space == HG_SPACE_P2 else 0)
 
     def apply(self, level, x, y, mode=HG_REPLACE, mask=HG_MASK_INNER, stream=None):
+        self.hier._vec(level, self.space, x.dtype, x, y)
         _call("hg_apply", self._h, level, _dtype_code(x), _ptr(x), _ptr(y), mode, mask,
               _stream(stream))
 
     def residual(self, level, x, b, r, stream=None):
+        self.hier._vec(level, self.space, x.dtype, x, b, r)
         _call("hg_residual", self._h, level, _dtype_code(x), _ptr(x), _ptr(b), _ptr(r),
               _stream(stream))
 
     def gauss_seidel(self, level, x, b, x_out, colour, stream=None):
         """One colour sub-sweep (out of place) of 4-colour Gauss-Seidel."""
+        self.hier._vec(level, self.space, x.dtype, x, b, x_out)
         _call("hg_gauss_seidel", self._h, level, _dtype_code(x), int(colour), _ptr(x), _ptr(b),
               _ptr(x_out), _stream(stream))
 
     def n1_prolong_add(self, fine_level, ec, xf, stream=None):
+        self.hier._vec(fine_level - 1, HG_SPACE_P2, ec.dtype, ec)
+        self.hier._vec(fine_level, HG_SPACE_P2, ec.dtype, xf)
         _call("hg_n1_prolong_add", self._h, fine_level, _dtype_code(ec), _ptr(ec), _ptr(xf),
               _stream(stream))
 
     def n1_restrict(self, fine_level, rf, rc, stream=None):
+        self.hier._vec(fine_level, HG_SPACE_P2, rf.dtype, rf)
+        self.hier._vec(fine_level - 1, HG_SPACE_P2, rf.dtype, rc)
         _call("hg_n1_restrict", self._h, fine_level, _dtype_code(rf), _ptr(rf), _ptr(rc),
               _stream(stream))
 
     def n1_gradient(self, level, phi, u, stream=None):
+        self.hier._vec(level, HG_SPACE_P1, phi.dtype, phi)
+        self.hier._vec(level, HG_SPACE_P2, phi.dtype, u)
         _call("hg_n1_gradient", self._h, level, _dtype_code(phi), _ptr(phi), _ptr(u),
               _stream(stream))
 
     def n1_gradient_t(self, level, r, rp, stream=None):
+        self.hier._vec(level, HG_SPACE_P2, r.dtype, r)
+        self.hier._vec(level, HG_SPACE_P1, r.dtype, rp)
         _call("hg_n1_gradient_t", self._h, level, _dtype_code(r), _ptr(r), _ptr(rp),
               _stream(stream))
 
     def jacobi(self, level, x, b, x_out, omega=2.0 / 3.0, stream=None):
+        self.hier._vec(level, self.space, x.dtype, x, b, x_out)
         _call("hg_jacobi", self._h, level, _dtype_code(x), float(omega), _ptr(x), _ptr(b),
               _ptr(x_out), _stream(stream))
 
@@ -357,10 +397,12 @@ class GMG:
         self.op = op
 
     def vcycle(self, level, x, b, stream=None):
+        self.op.hier._vec(level, self.op.space, x.dtype, x, b)
         _call("hg_vcycle", self._h, level, _dtype_code(x), _ptr(x), _ptr(b), _stream(stream))
 
     def fmg(self, level, x, b, cycles=5, stream=None):
         """Full multigrid to `level`: x <- FMG(b) with `cycles` V-cycles per level."""
+        self.op.hier._vec(level, self.op.space, x.dtype, x, b)
         _call("hg_fmg", self._h, level, _dtype_code(x), _ptr(x), _ptr(b), cycles, _stream(stream))
 
     def lam(self, level):
@@ -374,15 +416,19 @@ class GMG:
 
     def power_lambda(self, level, v0, iters=20, stream=None):
         """Power-iteration estimate of lambda_max(D^-1 A) from the FP64 stored vector v0."""
+        import torch
         v = ctypes.c_double()
+        self.op.hier._vec(level, self.op.space, torch.float64, v0)
         _call("hg_gmg_power_lambda", self._h, level, _ptr(v0), iters, ctypes.byref(v),
               _stream(stream))
         return v.value
 
     def solve(self, x, b, tol=1e-8, max_iter=100, precision=HG_PREC_F64, stream=None,
               check=True):
+        import torch
         it = ctypes.c_int()
         rel = ctypes.c_double()
+        self.op.hier._vec(self.op.lmax, self.op.space, torch.float64, x, b)
         r = lib().hg_solve(self._h, precision, _ptr(x), _ptr(b), tol, max_iter, ctypes.byref(it),
                            ctypes.byref(rel), _stream(stream))
         if r != 0 and (check or r != -5):
