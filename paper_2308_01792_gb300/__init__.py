@@ -514,6 +514,19 @@ class Batch:
 N_MLP_PARAMS = 512 + 1024 + 32
 
 
+def _samples(X, dtype, t=None):
+    """n rows of 16 features of `dtype` (contiguous CUDA) and, if given, n FP32
+    targets: the network kernels read 16 n features and n targets."""
+    import torch
+    if X.dtype != dtype or X.dim() != 2 or X.shape[1] != 16:
+        raise ValueError(f"samples must be [n, 16] of {dtype}, got {tuple(X.shape)} {X.dtype}")
+    _ptr(X)
+    if t is not None:
+        if t.dtype != torch.float32:
+            raise TypeError("targets must be float32")
+        _ptr(t, X.shape[0])
+
+
 class MLP:
     """The learned local smoother network (BF16 tensor-core kernels)."""
 
@@ -537,12 +550,18 @@ class MLP:
 
     def forward(self, X, out=None, stream=None):
         import torch
+        _samples(X, torch.float32)
         if out is None:
             out = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+        if out.dtype != torch.float32:
+            raise TypeError("out must be float32")
+        _ptr(out, X.shape[0])
         _call("hg_mlp_forward", self._h, _ptr(X), X.shape[0], _ptr(out), _stream(stream))
         return out
 
     def grad(self, X, t, stream=None):
+        import torch
+        _samples(X, torch.bfloat16, t)
         g = np.empty(N_MLP_PARAMS, dtype=np.float32)
         loss = ctypes.c_double()
         _call("hg_mlp_grad", self._h, _ptr(X), _ptr(t), X.shape[0], g.ctypes.data_as(_P),
@@ -550,6 +569,8 @@ class MLP:
         return loss.value, g
 
     def train(self, X, t, steps, batch, lr, stream=None):
+        import torch
+        _samples(X, torch.bfloat16, t)
         loss = ctypes.c_double()
         _call("hg_mlp_train", self._h, _ptr(X), _ptr(t), X.shape[0], steps, batch, lr,
               ctypes.byref(loss), _stream(stream))
@@ -564,6 +585,7 @@ class MLP:
 def learn_samples(op, level, r, xstar, x, omega, stride, offset, stream=None):
     """Training pairs (X bf16 [count,16], t float32 [count]) from one state."""
     import torch
+    op.hier._vec(level, op.space, torch.float32, r, xstar, x)
     cnt = ctypes.c_int64()
     _call("hg_learn_samples", op._h, level, None, None, None, omega, stride, offset, None, None,
           ctypes.byref(cnt), _stream(stream))

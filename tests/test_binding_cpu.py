@@ -2,7 +2,8 @@
 index the full stored length of every vector they are given and read every
 vector in the dtype of the first, so the binding refuses a vector that is
 shorter than the level's stored length or has another dtype before the call
-reaches the library.  Stand-in tensors (dtype, device flag, length) and a
+reaches the library; the network calls check their [n, 16] samples and n
+targets the same way.  Stand-in tensors (dtype, device flag, length) and a
 hierarchy whose sizes are set by hand stand in for CUDA objects here."""
 import pytest
 
@@ -77,3 +78,29 @@ def test_operator_and_multigrid_calls_check_their_vectors_first():
         G.solve(FakeTensor(200), FakeTensor(200))
     with pytest.raises(ValueError):
         G.vcycle(3, FakeTensor(1000), FakeTensor(999))
+
+
+class FakeRows(FakeTensor):
+    def __init__(self, shape, dtype, **kw):
+        super().__init__(shape[0] * (shape[1] if len(shape) > 1 else 1), dtype, **kw)
+        self.shape = shape
+
+    def dim(self):
+        return len(self.shape)
+
+
+def test_network_calls_check_samples_and_targets():
+    net = hg.MLP.__new__(hg.MLP)
+    net._h = None
+    with pytest.raises(ValueError, match=r"\[n, 16\]"):
+        net.forward(FakeRows((100, 15), torch.float32))
+    with pytest.raises(ValueError, match=r"\[n, 16\]"):
+        net.forward(FakeRows((100, 16), torch.bfloat16))
+    with pytest.raises(ValueError, match="need 100"):
+        net.forward(FakeRows((100, 16), torch.float32), out=FakeTensor(99, torch.float32))
+    with pytest.raises(ValueError, match=r"\[n, 16\]"):
+        net.grad(FakeRows((100, 16), torch.float32), FakeTensor(100, torch.float32))
+    with pytest.raises(TypeError):
+        net.grad(FakeRows((100, 16), torch.bfloat16), FakeTensor(100, torch.float64))
+    with pytest.raises(ValueError, match="need 100"):
+        net.train(FakeRows((100, 16), torch.bfloat16), FakeTensor(50, torch.float32), 1, 10, 1e-3)
