@@ -105,7 +105,8 @@ const char* hg_last_error(void);
  *   cells : host, nc*4 int64 vertex ids; the order in each row is the local
  *           vertex order v0..v3 of the macro cell and fixes its refinement
  *           (inner edge v02-v13, Sec. 3.1).
- * Checks: ids in range, no repeated vertex in a cell, nonzero volume, every
+ * Checks: ids in range, no repeated vertex in a cell, every vertex in some
+ * cell, nonzero volume, every
  * face shared by at most two cells, which lie on opposite sides of it (a
  * cell listed twice, or two cells folded over a common face, overlap and are
  * rejected).  Errors: HG_ERR_INVALID_ARG,

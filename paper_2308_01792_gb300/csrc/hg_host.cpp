@@ -115,6 +115,13 @@ int Mesh::build(const double* xyz_, int64_t nv_, const int64_t* cells_, int64_t 
   for (int64_t v = 0; v < nv; ++v) verts[v].vid = {v, -1, -1};
   for (int64_t c = 0; c < nc; ++c)
     for (int m = 0; m < 4; ++m) verts[cells[c][m]].cells.push_back((int)c);
+  // every macro vertex is a primitive with one copy per containing cell; a
+  // vertex of no cell would have none
+  for (int64_t v = 0; v < nv; ++v)
+    if (verts[v].cells.empty()) {
+      set_error("vertex %lld belongs to no cell", (long long)v);
+      return HG_ERR_BAD_MESH;
+    }
   n_boundary_faces = 0;
   for (auto& f : faces) {
     if (f.cells.size() > 2) {

@@ -75,6 +75,16 @@ def test_bad_meshes_are_rejected(built):
         hg.Mesh(xyz, np.array([[0, 1, 2, 3], [0, 1, 2, 4], [0, 1, 2, 5]]))
 
 
+def test_vertices_of_no_cell_are_rejected(built):
+    """Every macro vertex is a primitive with a copy in each containing cell;
+    a vertex that no cell lists is refused at creation."""
+    r = sg.reference_tet()
+    xyz = np.vstack([np.asarray(r.xyz, dtype=float), [[5.0, 5.0, 5.0]]])
+    with pytest.raises(hg.HGError) as e:
+        hg.Mesh(xyz, np.asarray(r.cells))
+    assert e.value.code == -2 and "vertex 4 belongs to no cell" in str(e.value)
+
+
 def test_overlapping_cells_are_rejected(built):
     """Cells meet only in common faces, edges or vertices (Sec. 2): the two
     cells of an interior face lie on opposite sides of it.  A cell listed
@@ -85,11 +95,12 @@ def test_overlapping_cells_are_rejected(built):
         with pytest.raises(hg.HGError) as e:
             hg.Mesh(r.xyz, np.array(cells))
         assert e.value.code == -2 and "overlap" in str(e.value)
-    xyz = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1], [0.2, 0.2, 0.5], [0, 0, -1]], float)
+    base = [[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]]
+    two = np.array([[0, 1, 2, 3], [0, 1, 2, 4]])
     with pytest.raises(hg.HGError) as e:
-        hg.Mesh(xyz, np.array([[0, 1, 2, 3], [0, 1, 2, 4]]))
+        hg.Mesh(np.array(base + [[0.2, 0.2, 0.5]], float), two)
     assert "same side" in str(e.value)
-    hg.Mesh(xyz, np.array([[0, 1, 2, 3], [0, 1, 2, 5]]))
+    hg.Mesh(np.array(base + [[0, 0, -1]], float), two)
     for m in (1, 2, 3):
         for seed in range(4):
             c = sg.permuted_cells(sg.kuhn_cube(m), seed)
