@@ -181,7 +181,9 @@ int hg_p2_anchors(int level, uint32_t* out, int* off, int* n_anchors);
 
 /* ----------------------------------------------------- index functions --
  * t_w(i,j,k) = N_tet(w) - N_tet(w-k) + N_tri(w-k) - N_tri(w-k-j) + i
- * (Sec. 4).  Host evaluation; HG_ERR_INVALID_ARG if (i,j,k) not in I_tet(w). */
+ * (Sec. 4).  Host evaluation, 1 <= w <= 2^20 (N_tet(w) fits in int64);
+ * HG_ERR_INVALID_ARG if w is out of that range, (i,j,k) is not in I_tet(w)
+ * or out is NULL. */
 int hg_index_tw(int64_t w, int64_t i, int64_t j, int64_t k, int64_t* out);
 
 /* Device enumeration of I_tet(w) with the same traversal the operator

@@ -1074,7 +1074,11 @@ int hg_plane_tiles(int level, int* out, int* n_tiles) {
 }
 
 int hg_index_tw(int64_t w, int64_t i, int64_t j, int64_t k, int64_t* out) {
-  HG_CHECK(out && w >= 1 && i >= 0 && j >= 0 && k >= 0 && i + j + k < w, HG_ERR_INVALID_ARG,
+  HG_CHECK(out, HG_ERR_INVALID_ARG, "hg_index_tw: null output");
+  // N_tet(w) = w (w+1) (w+2) / 6 must fit in int64: w <= 2^20
+  HG_CHECK(w <= (int64_t(1) << 20), HG_ERR_INVALID_ARG,
+           "hg_index_tw: w = %lld above 2^20 (N_tet(w) would overflow int64)", (long long)w);
+  HG_CHECK(w >= 1 && i >= 0 && j >= 0 && k >= 0 && i + j + k < w, HG_ERR_INVALID_ARG,
            "hg_index_tw: (%lld,%lld,%lld) not in I_tet(%lld)", (long long)i, (long long)j,
            (long long)k, (long long)w);
   *out = tw(w, i, j, k);

@@ -47,6 +47,17 @@ def test_host_tw_matches_oracle(built):
         hg.index_tw(3, 2, 1, 0)
 
 
+def test_host_tw_rejects_what_it_cannot_index(built):
+    """t_w is defined on I_tet(w); w above 2^20 would overflow N_tet in int64."""
+    big = 1 << 20
+    assert hg.index_tw(big, big - 1, 0, 0) == big - 1
+    assert hg.index_tw(big, 5, 7, big - 13) == ix.tw(big, 5, 7, big - 13)
+    for args in ((big + 1, 0, 0, 0), (3, -1, 0, 0), (3, 1, 1, 1), (0, 0, 0, 0)):
+        with pytest.raises(hg.HGError) as e:
+            hg.index_tw(*args)
+        assert e.value.code == -1
+
+
 def test_mesh_primitive_graph_counts(built):
     for m in (1, 2, 3):
         mm = sg.kuhn_cube(m)
