@@ -189,3 +189,28 @@ def test_hierarchy_limits_are_checked_before_any_allocation(built):
     with pytest.raises(hg.HGError) as e:
         hg.Hierarchy(m, 0, 1)
     assert e.value.code == -7 and "shared by 588 cells" in str(e.value)
+
+
+def _prototypes():
+    """name -> (return type is void, parameter count) from include/hytet.h,
+    comments removed."""
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    out = {}
+    for m in re.finditer(r"\b(void|int|const\s+char\s*\*)\s+(hg_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", src):
+        params = m.group(3).strip()
+        n = 0 if params in ("", "void") else params.count(",") + 1
+        out[m.group(2)] = (m.group(1) == "void", n)
+    return out
+
+
+def test_binding_signatures_match_the_header_prototypes(built):
+    """Each ctypes signature has as many arguments as its C prototype, and
+    void functions have no result type: a mismatch would pass arguments in
+    the wrong registers."""
+    protos = _prototypes()
+    assert set(protos) == set(hg.SIGNATURES)
+    for name, (res, args) in hg.SIGNATURES.items():
+        is_void, n = protos[name]
+        assert len(args) == n, (name, len(args), n)
+        assert (res is None) == is_void, name
