@@ -320,7 +320,6 @@ int Hier::build_level(int l) {
     const int per = P.ncopies <= 32 ? 32 / P.ncopies : 32;
     const int np = prim_points(P.dim, n);
     for (int p0 = 0; p0 < np; p0 += per) citems.push_back({P.first_copy, p0, meta, std::min(per, np - p0)});
-    if (q + 1 == L.n_prims_inner) L.n_citems_inner = (int)citems.size();
   }
   L.n_citems = (int)citems.size();
   if (int r = upload(&L.citems, citems)) return r;

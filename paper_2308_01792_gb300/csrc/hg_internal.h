@@ -146,7 +146,7 @@ struct LevelDev {
   int n_items, n_items_inner;
   // operator-application work items
   int4* citems;              // interface items of the apply: (first_copy, p0, meta as above,
-  int n_citems, n_citems_inner;  //   points); points = floor(32 / ncopies), one lane per copy
+  int n_citems;              //   points); points = floor(32 / ncopies), one lane per copy
   int4* ptiles;              // plane-window tiles of ONE cell (the same for every cell):
   int n_ptiles_cell;         //   (k | windows << 16, lane-0 offset z, j0 << 16 | i0, 0)
   uint8_t* colour;           // Gauss-Seidel colour (0..3) per stored point, or null

@@ -35,18 +35,6 @@ static __device__ __align__(256) double g_noalloc_partials[hg::kNoAllocMaxBlocks
 namespace hg {
 namespace {
 
-// Row item r of a level: cell = r / ntri(w), then plane k and row j
-// (plane k has w-k rows, R(k) = k(2w-k+1)/2 rows precede it).
-__device__ __forceinline__ void noalloc_row(int w, int r, int& cell, int& j, int& k) {
-  const int per = ntri32(w);
-  cell = r / per;
-  const int rr = r - cell * per;
-  int kk = 0;
-  while ((kk + 1) * (2 * w - kk) / 2 <= rr) ++kk;
-  k = kk;
-  j = rr - kk * (2 * w - kk + 1) / 2;
-}
-
 template <typename T>
 __global__ void __launch_bounds__(kNoAllocThreads) noalloc_dot_partial(
     int n, int64_t stride, const uint8_t* __restrict__ flags, int n_rows, const T* __restrict__ X,
@@ -58,7 +46,7 @@ __global__ void __launch_bounds__(kNoAllocThreads) noalloc_dot_partial(
   const int r_end = min(n_rows, (int)(blockIdx.x + 1) * kNoAllocRowsPerBlock);
   for (int r = blockIdx.x * kNoAllocRowsPerBlock + warp; r < r_end; r += kW) {
     int cell, j, k;
-    noalloc_row(w, r, cell, j, k);
+    row_item(w, r, cell, j, k);
     const int64_t r0 = (int64_t)cell * stride + row_start(w, j, k);
     const uint8_t* fl = flags + cell * 16;
     for (int i = lane; i + j + k <= n; i += 32) {
@@ -93,7 +81,10 @@ __global__ void __launch_bounds__(kNoAllocMaxBlocks) noalloc_dot_final(
 }
 
 // Device address of g_noalloc_partials, looked up once per device (with that
-// device current) on the first call made on it.
+// device current) on the first call made on it, and kept for the life of the
+// process.  The cached address does not survive a reset of the device's
+// context (cudaDeviceReset): after one, this library must not be used again in
+// the same process.
 constexpr int kMaxDevices = 64;
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[kMaxDevices] = {};

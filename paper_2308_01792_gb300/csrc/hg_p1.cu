@@ -559,7 +559,7 @@ FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
 
 template <typename T, int OP>
 int run_p1(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
-  const int n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_citems_inner : L.n_citems;
+  const int n_items = L.n_citems;
   FusedArgs<T> A = fused_args<T>(L, a, n_items);
   const int grid = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   if (grid == 0) return HG_OK;
@@ -1005,7 +1005,7 @@ size_t p1_desc_bytes(int dtype) {
 }
 
 int p1_make_desc(const LevelDev& L, int dtype, const StencilArgs& a, void* dst, int* units) {
-  const int n_items = (a.op == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_citems_inner : L.n_citems;
+  const int n_items = L.n_citems;
   if (dtype == HG_F64) {
     const FusedArgs<double> A = fused_args<double>(L, a, n_items);
     memcpy(dst, &A, sizeof A);

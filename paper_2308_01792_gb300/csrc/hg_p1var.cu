@@ -421,7 +421,7 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.n_tiles_cell = L.n_ptiles_cell;
   A.n_tiles = L.n_ptiles_cell * L.ncells;
   A.items = L.citems;
-  A.n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_citems_inner : L.n_citems;
+  A.n_items = L.n_citems;
   A.nb_items = (A.n_items + kWarps - 1) / kWarps;
   A.copies = L.copies;
   A.x = (const T*)a.x;

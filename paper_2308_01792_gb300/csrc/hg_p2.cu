@@ -463,7 +463,7 @@ int run_phases_n1(const P2Args& P, int64_t stride, const void* x, void* acc, int
 
 template <typename T, int OP>
 int run_finish(const LevelDev& L, const StencilArgs& a, const P2Args& P, cudaStream_t s) {
-  const int n_items = (OP == OP_APPLY && a.mask == HG_MASK_INNER) ? L.n_citems_inner : L.n_citems;
+  const int n_items = L.n_citems;
   const P2Fin<T> F = fin_args<T>(L, a, P, n_items);
   const int grid = F.nb_items + (F.n_rows + kFinWarps - 1) / kFinWarps;
   p2_finish_kernel<T, OP><<<grid, kFinBlock, 0, s>>>(F);

@@ -71,6 +71,16 @@ def test_divkgrad_apply_matches_assembled(case, dtype):
         if len(ii):
             assert rel_err(got[ii], (A @ xi)[ii]) <= TOL[dtype] * 4
         assert np.all(got[rm.boundary] == 0)
+        # INNER on a nonzero destination, both modes: Dirichlet entries 0
+        y0 = sg.uniform_vector(60 + L, rm.n_vertices)
+        y0r = torch.tensor(y0, dtype=dtype).double().numpy()
+        for mode, base in ((hg.HG_REPLACE, 0.0), (hg.HG_ADD, y0r)):
+            y = H.from_canonical(L, torch.tensor(y0, dtype=dtype, device="cuda"))
+            op.apply(L, x, y, mode=mode)
+            got = H.to_canonical(L, y).cpu().double().numpy()
+            if len(ii):
+                assert rel_err(got[ii], (base + A @ xi)[ii]) <= TOL[dtype] * 4
+            assert np.all(got[rm.boundary] == 0)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])

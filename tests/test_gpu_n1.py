@@ -80,6 +80,17 @@ def test_n1_apply_matches_oracle(case, dtype):
     ii = lev.interior
     assert rel_err(got[edge][ii], (lev.A_full @ xi)[ii]) <= TOL[dtype]
     assert np.all(got[edge][lev.boundary] == 0)
+    # INNER on a nonzero destination (edge points), both modes: Dirichlet
+    # edges 0, vertex points keep 0
+    y0 = sg.uniform_vector(54, lev.n)
+    y0r = torch.tensor(y0, dtype=dtype).double().numpy()
+    for mode, base in ((hg.HG_REPLACE, 0.0), (hg.HG_ADD, y0r)):
+        y = _stored(H, L, num.n, edge, y0, dtype)
+        op.apply(L, x, y, mode=mode)
+        got = _canon(H, L, y)
+        assert rel_err(got[edge][ii], (base + lev.A_full @ xi)[ii]) <= 2 * TOL[dtype]
+        assert np.all(got[edge][lev.boundary] == 0)
+        assert np.all(got[vert] == 0)
 
 
 def test_n1_copies_bit_identical(case):

@@ -135,24 +135,34 @@ def test_apply_matches_assembled_oracle(case, dtype, kind):
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_inner_mask_add_zeroes_dirichlet_entries(case, dtype):
-    """HG_ADD with HG_MASK_INNER: y + A x on the other DoFs, 0 at the
-    Dirichlet DoFs (the documented mask semantics)."""
+@pytest.mark.parametrize("mode", ["replace", "add"])
+@pytest.mark.parametrize("kind", ["laplace", "mass"])
+def test_inner_mask_zeroes_dirichlet_entries(case, dtype, mode, kind):
+    """HG_MASK_INNER on a destination that starts NONZERO everywhere: A x
+    (REPLACE) or y + A x (ADD) on the other DoFs, exactly 0 at the Dirichlet
+    DoFs (homogeneous Dirichlet values), for both modes."""
     macro, H = case
-    op = hg.Operator(H)
+    op = hg.Operator(H, hg.HG_OP_P1_LAPLACE if kind == "laplace" else hg.HG_OP_P1_MASS)
     L = H.lmax
-    rm, A = _oracle_level(macro, L)
+    rm, A = _oracle_level(macro, L, kind)
     xi = sg.uniform_vector(200 + L, rm.n_vertices)
     xi[rm.boundary] = 0
     y0 = sg.uniform_vector(300 + L, rm.n_vertices)
     x = H.from_canonical(L, torch.tensor(xi, dtype=dtype, device="cuda"))
     y = H.from_canonical(L, torch.tensor(y0, dtype=dtype, device="cuda"))
-    op.apply(L, x, y, mode=hg.HG_ADD)
+    add = mode == "add"
+    op.apply(L, x, y, mode=hg.HG_ADD if add else hg.HG_REPLACE)
     yc = H.to_canonical(L, y).cpu().double().numpy()
+    y0r = torch.tensor(y0, dtype=dtype).double().numpy()
+    ref = (y0r if add else 0.0) + A @ xi
     ii = rm.interior
     if len(ii):
-        assert rel_err(yc[ii], (y0 + A @ xi)[ii]) <= TOL[dtype] * 2
+        assert rel_err(yc[ii], ref[ii]) <= TOL[dtype] * 2
     assert np.all(yc[rm.boundary] == 0)
+    s2c, _, _ = H.canonical_info(L)
+    ys = y.cpu().double().numpy()
+    valid = s2c >= 0
+    assert np.array_equal(ys[valid], yc[s2c[valid]])
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])

@@ -71,13 +71,20 @@ def test_p2_apply_matches_oracle(setup, which, dtype, tol):
     ops[which].apply(L, x, y, mask=hg.HG_MASK_ALL)
     got = _canon(H, L, y)
     assert rel_err(got, ref) <= tol
-    # INNER: interior rows only, Dirichlet rows of the destination untouched
-    marker = 7.0
-    y2 = _stored(H, L, np.full(lev.n, marker), dtype)
+    # INNER on a nonzero destination: interior rows, Dirichlet rows set to 0
+    # (REPLACE), and y + A x on the interior rows (ADD)
+    y0 = sg.uniform_vector(23, lev.n)
+    y0r = torch.tensor(y0, dtype=dtype).double().numpy()
+    y2 = _stored(H, L, y0, dtype)
     ops[which].apply(L, x, y2)
     got2 = _canon(H, L, y2)
     assert rel_err(got2[lev.interior], ref[lev.interior]) <= tol
-    assert np.all(got2[lev.boundary] == marker)
+    assert np.all(got2[lev.boundary] == 0)
+    y3 = _stored(H, L, y0, dtype)
+    ops[which].apply(L, x, y3, mode=hg.HG_ADD)
+    got3 = _canon(H, L, y3)
+    assert rel_err(got3[lev.interior], (y0r + ref)[lev.interior]) <= 2 * tol
+    assert np.all(got3[lev.boundary] == 0)
 
 
 def test_p2_copies_bit_identical(setup):

@@ -29,15 +29,23 @@ def test_noalloc_dot_matches_hg_dot_twice(macro, level, dtype):
                                              device="cuda"))
     y = H.from_canonical(level, torch.tensor(sg.uniform_vector(22, nu), dtype=dtype,
                                              device="cuda"))
+    # the canonical vectors as the GPU holds them (rounded to dtype), in FP64
+    a = torch.tensor(sg.uniform_vector(21, nu), dtype=dtype).double().numpy()
+    c = torch.tensor(sg.uniform_vector(22, nu), dtype=dtype).double().numpy()
+    _, _, dirich = H.canonical_info(level)
+    inner = ~np.asarray(dirich, dtype=bool)
     out = torch.full((1,), float("nan"), dtype=torch.float64, device="cuda")
     for mask in (hg.HG_MASK_INNER, hg.HG_MASK_ALL):
         ref = H.dot(level, x, y, mask=mask)
-        scale = max(abs(ref), 1.0)
+        keep = inner if mask == hg.HG_MASK_INNER else np.ones(nu, dtype=bool)
+        exact = a[keep] @ c[keep]               # each unique DoF once (NumPy)
+        bound = TOL * np.abs(a * c).sum()
         for _ in range(2):                      # two calls in a row share the array
             out.fill_(float("nan"))
             H.dot_noalloc(level, x, y, out, mask=mask)
             got = out.item()
-            assert abs(got - ref) <= TOL * scale, (mask, got, ref)
+            assert abs(got - ref) <= TOL * max(abs(ref), 1.0), (mask, got, ref)
+            assert abs(got - exact) <= bound, (mask, got, exact)
 
 
 def test_noalloc_dot_rejects_levels_beyond_its_scratch():
