@@ -87,6 +87,9 @@ SIGNATURES = {
     "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
     "hg_plane_tiles": (_I, [_I, _P, ctypes.POINTER(ctypes.c_int)]),
+    "hg_stream_schedule": (_I, [_I, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "hg_stream_layout": (_I, [_I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_int)]),
     "hg_p2_anchors": (_I, [_I, _P, _P, ctypes.POINTER(ctypes.c_int)]),
     "hg_n1_restrict_table": (_I, [_P, _P, _P, _P]),
     "hg_n1_prolong_add": (_I, [_P, _I, _I, _P, _P, _P]),
@@ -616,6 +619,24 @@ def plane_tiles(level):
     out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
     _call("hg_plane_tiles", level, out.ctypes.data_as(_P), ctypes.byref(n))
     return out[:n.value]
+
+
+def stream_schedule(level, ncells, nctas):
+    """Runs of the streaming apply kernel (host): ((n, 4) int32 runs, (nctas+1,) int32 offsets)."""
+    n = ctypes.c_int()
+    _call("hg_stream_schedule", level, ncells, nctas, None, None, ctypes.byref(n))
+    units = np.zeros((max(n.value, 1), 4), dtype=np.int32)
+    begin = np.zeros(nctas + 1, dtype=np.int32)
+    _call("hg_stream_schedule", level, ncells, nctas, units.ctypes.data_as(_P),
+          begin.ctypes.data_as(_P), ctypes.byref(n))
+    return units[:n.value], begin
+
+
+def stream_layout(level, dtype_code):
+    """Shared-memory layout of the streaming kernel (host): (ring slots, slot elements, guard)."""
+    r, s, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _call("hg_stream_layout", level, dtype_code, ctypes.byref(r), ctypes.byref(s), ctypes.byref(g))
+    return r.value, s.value, g.value
 
 
 def p2_anchors(level):

@@ -225,7 +225,67 @@ uint8_t Mesh::class_flags(int64_t c, int cls) const {
   uint8_t f = 0;
   if (p->dirichlet) f |= CF_DIRICHLET;
   if (p->cells.front() == (int)c) f |= CF_OWNER;
+  if (p->cells.size() >= 2) f |= CF_MULTI;
   return f;
+}
+
+// ------------------------------------------------------------ streaming schedule
+// Lattice rows of band j0 present in plane k: j0 .. min(j0 + kStreamBand, w - k) - 1.
+static int64_t band_outputs(int w, int j0, int k) {
+  int64_t o = 0;
+  for (int j = j0; j < std::min(j0 + kStreamBand, w - k); ++j) o += w - k - j;
+  return o;
+}
+// Elements staged for plane k of band j0: rows max(j0-1,0) .. min(j0+kStreamBand, w-1-k).
+static int64_t band_loaded(int w, int j0, int k) {
+  int64_t o = 0;
+  for (int j = std::max(j0 - 1, 0); j <= std::min(j0 + kStreamBand, w - 1 - k); ++j) o += w - k - j;
+  return o;
+}
+
+int stream_ctas(int n, int ncells, int n_items, int sms) {
+  const int64_t pts = (int64_t)ncells * ntet(n + 1);
+  const int64_t want = std::max<int64_t>((pts + 2047) / 2048, ((int64_t)n_items + 15) / 16);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(std::max(sms, 1), want));
+}
+
+void stream_schedule(int n, int ncells, int nctas, std::vector<int4>& units,
+                     std::vector<int32_t>& cta_begin) {
+  const int w = n + 1;
+  // the sequence (cell, band, plane) with a cost per plane: outputs, staged
+  // elements and a fixed part for the plane's waits and row set-up
+  struct Step { int cell, j0, k; double cost; };
+  std::vector<Step> seq;
+  double total = 0;
+  for (int c = 0; c < ncells; ++c)
+    for (int j0 = 0; j0 < w; j0 += kStreamBand)
+      for (int k = 0; k <= w - 1 - j0; ++k) {
+        const double cost = (double)band_outputs(w, j0, k) + 0.25 * band_loaded(w, j0, k) + 48.0;
+        seq.push_back({c, j0, k, cost});
+        total += cost;
+      }
+  units.clear();
+  cta_begin.assign(nctas + 1, 0);
+  size_t q = 0;
+  double acc = 0;
+  for (int g = 0; g < nctas; ++g) {
+    cta_begin[g] = (int32_t)units.size();
+    const double target = total * (g + 1) / nctas;
+    while (q < seq.size() && (g == nctas - 1 || acc + 0.5 * seq[q].cost <= target)) {
+      // one run: consecutive planes of the same (cell, band)
+      const Step& s0 = seq[q];
+      int k1 = s0.k;
+      while (q < seq.size() && seq[q].cell == s0.cell && seq[q].j0 == s0.j0 &&
+             (g == nctas - 1 || acc + 0.5 * seq[q].cost <= target)) {
+        acc += seq[q].cost;
+        k1 = seq[q].k + 1;
+        ++q;
+      }
+      const int rows = std::min(kStreamBand, w - s0.j0);
+      units.push_back({s0.cell, s0.j0 | (rows << 16), s0.k | (k1 << 16), 0});
+    }
+  }
+  cta_begin[nctas] = (int32_t)units.size();
 }
 
 // ------------------------------------------------------------ hierarchy
@@ -323,6 +383,31 @@ int Hier::build_level(int l) {
   }
   L.n_citems = (int)citems.size();
   if (int r = upload(&L.citems, citems)) return r;
+  // the same items restricted to primitives with two or more copies (the
+  // streaming kernel forms every single-copy point inside its runs)
+  std::vector<int4> mitems;
+  for (int q = 0; q < (int)prims.size(); ++q) {
+    const IfacePrim& P = prims[q];
+    if (P.ncopies < 2) continue;
+    const int meta = P.dim | (P.ncopies << 4) | (P.dirichlet << 12);
+    const int per = P.ncopies <= 32 ? 32 / P.ncopies : 32;
+    const int np = prim_points(P.dim, n);
+    for (int p0 = 0; p0 < np; p0 += per) mitems.push_back({P.first_copy, p0, meta, std::min(per, np - p0)});
+    if (!P.dirichlet) L.n_mitems_inner = (int)mitems.size();
+  }
+  L.n_mitems = (int)mitems.size();
+  if (int r = upload(&L.mitems, mitems)) return r;
+  {
+    int dev = 0, sms = 0;
+    HG_CUDA(cudaGetDevice(&dev));
+    HG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    std::vector<int4> su;
+    std::vector<int32_t> sc;
+    L.n_scta = stream_ctas(n, (int)mesh->nc, L.n_mitems, sms);
+    stream_schedule(n, (int)mesh->nc, L.n_scta, su, sc);
+    if (int r = upload(&L.sunits, su)) return r;
+    if (int r = upload(&L.scta, sc)) return r;
+  }
   const std::vector<int4> ptiles = plane_tiles(n);
   L.n_ptiles_cell = (int)ptiles.size();
   if (int r = upload(&L.ptiles, ptiles)) return r;
@@ -415,6 +500,7 @@ int Hier::build_level(int l) {
   if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
       (L.n_items && (!L.items || !L.item_prim)) ||
       (L.n_citems && !L.citems) || (L.n_ptiles_cell && !L.ptiles) ||
+      (L.n_mitems && !L.mitems) || !L.scta ||
       (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
     set_error("internal: level %d device tables incomplete", l);
     return HG_ERR_CUDA;
@@ -532,6 +618,9 @@ Hier::~Hier() {
     cudaFree(L.copies);
     cudaFree(L.prim_point_base);
     cudaFree(L.citems);
+    cudaFree(L.mitems);
+    cudaFree(L.sunits);
+    cudaFree(L.scta);
     cudaFree(L.colour);
     cudaFree(L.ptiles);
     cudaFree(L.items);
@@ -1069,6 +1158,26 @@ int hg_plane_tiles(int level, int* out, int* n_tiles) {
       out[4 * q + 2] = t[q].z;
       out[4 * q + 3] = t[q].w;
     }
+  return HG_OK;
+}
+
+int hg_stream_schedule(int level, int ncells, int nctas, int* units, int* cta_begin,
+                       int* n_units) {
+  HG_CHECK(level >= 0 && level <= 12 && ncells >= 1 && nctas >= 1 && n_units, HG_ERR_INVALID_ARG,
+           "hg_stream_schedule: bad argument");
+  std::vector<int4> u;
+  std::vector<int32_t> cb;
+  stream_schedule(1 << level, ncells, nctas, u, cb);
+  *n_units = (int)u.size();
+  if (units)
+    for (size_t q = 0; q < u.size(); ++q) {
+      units[4 * q] = u[q].x;
+      units[4 * q + 1] = u[q].y;
+      units[4 * q + 2] = u[q].z;
+      units[4 * q + 3] = u[q].w;
+    }
+  if (cta_begin)
+    for (int g = 0; g <= nctas; ++g) cta_begin[g] = cb[g];
   return HG_OK;
 }
 

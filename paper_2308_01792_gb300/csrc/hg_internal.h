@@ -77,7 +77,9 @@ HG_HD int point_class(int n, int i, int j, int k) {
 }
 
 // Per-(cell, class) flags.
-enum : uint8_t { CF_DIRICHLET = 1, CF_OWNER = 2 };
+// CF_MULTI: the point lies on a macro primitive contained in two or more
+// cells, so its value is a sum over copies (the interface items form it).
+enum : uint8_t { CF_DIRICHLET = 1, CF_OWNER = 2, CF_MULTI = 4 };
 
 // Point of a macro primitive, seen from one of the cells that contain it.
 struct IfaceCopy {
@@ -147,6 +149,11 @@ struct LevelDev {
   // operator-application work items
   int4* citems;              // interface items of the apply: (first_copy, p0, meta as above,
   int n_citems;              //   points); points = floor(32 / ncopies), one lane per copy
+  int4* mitems;              // apply items of the primitives with >= 2 copies only
+  int n_mitems, n_mitems_inner;  //   (non-Dirichlet first): the streaming kernel's exchange
+  int4* sunits;              // streaming schedule: runs (cell, j0 | rows << 16, k0 | k1 << 16, 0)
+  int32_t* scta;             //   [n_scta + 1]: runs of CTA g are sunits[scta[g] .. scta[g+1])
+  int n_scta;
   int4* ptiles;              // plane-window tiles of ONE cell (the same for every cell):
   int n_ptiles_cell;         //   (k | windows << 16, lane-0 offset z, j0 << 16 | i0, 0)
   uint8_t* colour;           // Gauss-Seidel colour (0..3) per stored point, or null
@@ -158,6 +165,19 @@ struct LevelDev {
 #define HG_PLANE_STEPS 16
 #endif
 constexpr int kPlaneSteps = HG_PLANE_STEPS;
+
+// Streaming constant-stencil kernel (hg_p1stream.cu): a cell's lattice is cut
+// into bands of kStreamBand consecutive rows j; a band is marched plane by
+// plane (k) with the rows j0-1 .. j0+kStreamBand of every plane staged in
+// shared memory.  The schedule gives every CTA (one per SM) a contiguous
+// stretch of the sequence (cell, band, plane) of about equal cost; each
+// stretch is a list of runs (cell, band, planes [k0, k1)).
+constexpr int kStreamBand = 8;
+// CTAs of the streaming kernel for a level (at most one per SM).
+int stream_ctas(int n, int ncells, int n_items, int sms);
+// Runs of every CTA: units[cta_begin[g] .. cta_begin[g+1]) belong to CTA g.
+void stream_schedule(int n, int ncells, int nctas, std::vector<int4>& units,
+                     std::vector<int32_t>& cta_begin);
 
 // Dense FP64 coarse-grid solver data.
 struct CoarseDev {
@@ -213,6 +233,8 @@ struct StencilArgs {
 };
 
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);
+// The streaming form of the constant-stencil operator (a.sten, a.pattern).
+int launch_p1_stream(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------- P2
 // A P2 function on level l (vertex and edge DoFs of the level-l micro-cells)
