@@ -14,16 +14,18 @@
 //    mbarrier; it runs up to R slots ahead of the consumers, so tens of KB
 //    per SM are in flight from HBM at any time;
 //  * the consumers compute a plane of the band once the slots of planes k-1,
-//    k, k+1 have landed, each warp taking 32-point chunks of the band's rows
-//    (all addressing warp-uniform per row), write the results to HBM
-//    directly, and release the slot of plane k-1; a slot is thus read for
-//    three consecutive planes and every x value crosses HBM once;
+//    k, k+1 have landed, the 32-point chunks of the band's rows going
+//    round-robin over the warps (all addressing warp-uniform per row; the
+//    round-robin continues across planes, so short planes near the top of a
+//    band spread over the warps too), write the results to HBM directly, and
+//    release the slot of plane k-1; a slot is thus read for three
+//    consecutive planes and every x value crosses HBM once;
 //  * points of the cell's boundary that lie on a primitive of this cell only
 //    (boundary faces, edges and vertices) are formed in the same pass from
 //    the cell's partial stencil; points shared by several cells (the
-//    ghost-layer exchange of Sec. 2) are formed by the interface items, which
-//    the consumer warps run first while the producer's first copies are in
-//    flight.
+//    ghost-layer exchange of Sec. 2) are formed by the interface items, a
+//    contiguous share per CTA that its consumer warps take after their runs
+//    (the producer prefetches the share's item records into L2 at the start).
 //
 // Every wait on an mbarrier is bounded (about one second): on expiry the
 // kernel records HG_ERR_TIMEOUT in the hierarchy's error word, the other
@@ -47,6 +49,11 @@ constexpr unsigned long long kWaitNs = 1000000000ull;
 
 template <typename T>
 __host__ __device__ constexpr int vec_elems() { return 16 / (int)sizeof(T); }
+
+// HG_ADD applies get their own instantiation (y += A x) so that a replacing
+// apply never reads the destination.
+constexpr int kOpApplyAdd = 100;
+__host__ __device__ constexpr bool is_apply(int op) { return op == OP_APPLY || op == kOpApplyAdd; }
 
 // Elements of one slot: kStreamBand + 2 rows of at most w points plus the
 // 16-byte rounding of both ends, in whole 128-byte lines.
@@ -112,6 +119,10 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       "l"(src), "r"(bytes), "r"(smem_addr(b))
       : "memory");
 }
+// Bulk prefetch of [p, p + bytes) into L2 (16-byte aligned, size a multiple of 16).
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
 __device__ __forceinline__ unsigned long long global_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -148,7 +159,9 @@ __device__ __forceinline__ void staged_range(int w, int j0, int rows, int kk, in
 template <typename T, int OP>
 __device__ __forceinline__ void stream_out(const FusedArgs<T>& A, int64_t g, T c, T acc, T wd) {
   if (OP == OP_APPLY) {
-    A.y[g] = A.mode == HG_ADD ? A.y[g] + acc : acc;
+    A.y[g] = acc;
+  } else if (OP == kOpApplyAdd) {
+    A.y[g] += acc;
   } else if (OP == OP_RESID) {
     A.y[g] = A.b[g] - acc;
   } else if (OP == OP_GS) {
@@ -173,7 +186,7 @@ __device__ __noinline__ void stream_boundary_point(const FusedArgs<T>& A, int ce
   const int cls = (i == len - 1 ? 1 : 0) | (i == 0 ? 2 : 0) | (j == 0 ? 4 : 0) | (k == 0 ? 8 : 0);
   const uint8_t f = __ldg(A.flags + cell * 16 + cls);
   const T c = P0[i];
-  if ((f & CF_DIRICHLET) && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
+  if ((f & CF_DIRICHLET) && (!is_apply(OP) || A.mask == HG_MASK_INNER)) {
     A.y[g] = op_scaled(OP) ? c : T(0);
     return;
   }
@@ -224,6 +237,12 @@ __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArg
   if (warp == kSWarps) {
     // ------------------------------------------------------------ producer
     if (lane != 0) return;
+    {
+      // the interface items of this CTA (read after its runs) into L2
+      const int ib = (int)((int64_t)A.n_items * blockIdx.x / gridDim.x);
+      const int ie = (int)((int64_t)A.n_items * (blockIdx.x + 1) / gridDim.x);
+      if (ie > ib) l2_prefetch(A.items + ib, (uint32_t)(ie - ib) * (uint32_t)sizeof(int4));
+    }
     int q = 0;
     bool ok = true;
     for (int u = ub; u < ue && ok; ++u) {
@@ -256,13 +275,8 @@ __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArg
   }
 
   // -------------------------------------------------------------- consumers
-  // 1. points shared by several cells (interface items), while the first
-  //    copies are in flight
-  for (int it = blockIdx.x + gridDim.x * warp; it < A.n_items; it += gridDim.x * kSWarps)
-    interface_item<T, OP, false>(A, it, lane);
-
-  // 2. the runs of this CTA
-  int q = 0;
+  // 1. the runs of this CTA; their chunks go round-robin over the warps
+  int q = 0, cbase = 0;
   for (int u = ub; u < ue; ++u) {
     const int4 U = S.units[u];
     const int cell = U.x, j0 = U.y & 0xffff, rows = U.y >> 16;
@@ -306,9 +320,10 @@ __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArg
         staged_range<T>(w, j0, rows, k + 1, gap, ge);
         sp = ring + ((qk + 1) % R) * S.slot;
       }
-      // 32-point chunks of the band's rows in this plane, in turn over the warps
+      // 32-point chunks of the band's rows in this plane, continuing the
+      // round-robin over the warps from the previous plane
       const int jn = min(rows, w - k - j0);
-      int it = warp, cb = 0;
+      int it = (warp - cbase % kSWarps + kSWarps) % kSWarps, cb = 0;
       for (int r = 0; r < jn; ++r) {
         const int j = j0 + r, len = w - k - j;
         const int nch = (len + 31) >> 5;
@@ -350,6 +365,7 @@ __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArg
         }
         cb += nch;
       }
+      cbase += cb;
       // release the slots no later plane of this run reads
       __syncwarp();
       if (lane == 0) {
@@ -362,6 +378,13 @@ __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArg
     }
     q += kl - kf + 1;
   }
+
+  // 2. points shared by several cells (interface items): a contiguous share
+  //    per CTA, after the runs, when most of x has passed through L2
+  const int ib = (int)((int64_t)A.n_items * blockIdx.x / gridDim.x);
+  const int ie = (int)((int64_t)A.n_items * (blockIdx.x + 1) / gridDim.x);
+  for (int it = ib + warp; it < ie; it += kSWarps)
+    interface_item<T, is_apply(OP) ? OP_APPLY : OP, false>(A, it, lane);
 }
 
 template <typename T, int OP, int PAT>
@@ -374,7 +397,7 @@ int run_stream(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
   A.stride = L.cell_stride;
   A.flags = L.cls_flags;
   A.items = L.mitems;
-  A.n_items = (OP == OP_APPLY && a.mask == HG_MASK_ALL) ? L.n_mitems : L.n_mitems_inner;
+  A.n_items = (is_apply(OP) && a.mask == HG_MASK_ALL) ? L.n_mitems : L.n_mitems_inner;
   A.prims = L.prims;
   A.copies = L.copies;
   A.x = (const T*)a.x;
@@ -414,7 +437,9 @@ int run_stream(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
 template <typename T, int PAT>
 int run_stream_op(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
   switch (a.op) {
-    case OP_APPLY: return run_stream<T, OP_APPLY, PAT>(L, a, s);
+    case OP_APPLY:
+      return a.mode == HG_ADD ? run_stream<T, kOpApplyAdd, PAT>(L, a, s)
+                              : run_stream<T, OP_APPLY, PAT>(L, a, s);
     case OP_RESID: return run_stream<T, OP_RESID, PAT>(L, a, s);
     case OP_JACOBI: return run_stream<T, OP_JACOBI, PAT>(L, a, s);
     case OP_GS: return run_stream<T, OP_GS, PAT>(L, a, s);
