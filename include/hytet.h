@@ -170,20 +170,22 @@ int hg_device_status(const hg_hier* hier, void* stream);
  * kernels' lane walk against the lattice on the CPU. */
 int hg_plane_tiles(int level, int* out, int* n_tiles);
 
-/* The work schedule of the streaming constant-stencil apply kernel on one
- * level of a mesh with `ncells` macro cells, split over `nctas` CTAs (host,
- * needs no GPU).  A run is 4 ints (cell, j0 | rows << 16, k0 | k1 << 16, 0):
- * the lattice rows j0 .. j0+rows-1 of that cell in the planes k0 .. k1-1.
- * Runs of CTA g are units[4 cta_begin[g] ..] up to units[4 cta_begin[g+1]];
- * cta_begin holds nctas + 1 ints.  *n_units gets the number of runs; units
- * and cta_begin may be NULL to query it.  Exported so that tests can check on
- * the CPU that the runs cover every lattice point once. */
-int hg_stream_schedule(int level, int ncells, int nctas, int* units, int* cta_begin,
-                       int* n_units);
+/* The plan of the streaming constant-stencil apply kernel for one level of a
+ * mesh with `ncells` macro cells, split over `nctas` CTAs, for dtype
+ * HG_F32/HG_F64 (host, needs no GPU).  copies: 4 ints per copy (cell, first
+ * element, elements, 0); items: 12 ints per item (cell, plane k, ja | jb << 16,
+ * arrival counts; the CTA-local copies holding planes k, k-1, k+1 or -1; the
+ * first elements of those copies); cta_copies / cta_items: nctas + 1 offsets.
+ * counts receives (copies, items, rows per band).  Any output pointer may be
+ * NULL (counts only).  Exported so that tests can check on the CPU that the
+ * items cover every lattice point once and read inside the staged copies. */
+int hg_stream_plan(int level, int ncells, int nctas, int dtype, int* copies, int* items,
+                   int* cta_copies, int* cta_items, int* counts);
 
 /* Shared-memory layout of the streaming kernel on `level` for dtype
- * HG_F32/HG_F64 (host, needs no GPU): the number of ring slots, the elements
- * per slot and the guard elements before the first and after the last slot.
+ * HG_F32/HG_F64 (host, needs no GPU): the number of ring slots (copy c of a
+ * CTA goes to slot c mod ring_slots), the elements per slot and the guard
+ * elements before the first and after the last slot.
  * Exported so that tests can check the kernel's index arithmetic on the CPU. */
 int hg_stream_layout(int level, int dtype, int* ring_slots, int* slot_elems, int* guard_elems);
 

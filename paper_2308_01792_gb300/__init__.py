@@ -87,7 +87,7 @@ SIGNATURES = {
     "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
     "hg_plane_tiles": (_I, [_I, _P, ctypes.POINTER(ctypes.c_int)]),
-    "hg_stream_schedule": (_I, [_I, _I, _I, _P, _P, ctypes.POINTER(ctypes.c_int)]),
+    "hg_stream_plan": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P]),
     "hg_stream_layout": (_I, [_I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int)]),
     "hg_p2_anchors": (_I, [_I, _P, _P, ctypes.POINTER(ctypes.c_int)]),
@@ -621,15 +621,21 @@ def plane_tiles(level):
     return out[:n.value]
 
 
-def stream_schedule(level, ncells, nctas):
-    """Runs of the streaming apply kernel (host): ((n, 4) int32 runs, (nctas+1,) int32 offsets)."""
-    n = ctypes.c_int()
-    _call("hg_stream_schedule", level, ncells, nctas, None, None, ctypes.byref(n))
-    units = np.zeros((max(n.value, 1), 4), dtype=np.int32)
-    begin = np.zeros(nctas + 1, dtype=np.int32)
-    _call("hg_stream_schedule", level, ncells, nctas, units.ctypes.data_as(_P),
-          begin.ctypes.data_as(_P), ctypes.byref(n))
-    return units[:n.value], begin
+def stream_plan(level, ncells, nctas, dtype_code):
+    """Plan of the streaming apply kernel (host): dict of copies (n, 4), items
+    (m, 12), cta_copies and cta_items (nctas + 1,), band_rows."""
+    cnt = np.zeros(3, dtype=np.int32)
+    _call("hg_stream_plan", level, ncells, nctas, dtype_code, None, None, None, None,
+          cnt.ctypes.data_as(_P))
+    copies = np.zeros((max(cnt[0], 1), 4), dtype=np.int32)
+    items = np.zeros((max(cnt[1], 1), 12), dtype=np.int32)
+    cc = np.zeros(nctas + 1, dtype=np.int32)
+    ci = np.zeros(nctas + 1, dtype=np.int32)
+    _call("hg_stream_plan", level, ncells, nctas, dtype_code, copies.ctypes.data_as(_P),
+          items.ctypes.data_as(_P), cc.ctypes.data_as(_P), ci.ctypes.data_as(_P),
+          cnt.ctypes.data_as(_P))
+    return {"copies": copies[:cnt[0]], "items": items[:cnt[1]], "cta_copies": cc,
+            "cta_items": ci, "band_rows": int(cnt[2])}
 
 
 def stream_layout(level, dtype_code):

@@ -229,63 +229,176 @@ uint8_t Mesh::class_flags(int64_t c, int cls) const {
   return f;
 }
 
-// ------------------------------------------------------------ streaming schedule
-// Lattice rows of band j0 present in plane k: j0 .. min(j0 + kStreamBand, w - k) - 1.
-static int64_t band_outputs(int w, int j0, int k) {
-  int64_t o = 0;
-  for (int j = j0; j < std::min(j0 + kStreamBand, w - k); ++j) o += w - k - j;
-  return o;
-}
-// Elements staged for plane k of band j0: rows max(j0-1,0) .. min(j0+kStreamBand, w-1-k).
-static int64_t band_loaded(int w, int j0, int k) {
-  int64_t o = 0;
-  for (int j = std::max(j0 - 1, 0); j <= std::min(j0 + kStreamBand, w - 1 - k); ++j) o += w - k - j;
-  return o;
-}
-
+// ------------------------------------------------------------ streaming plan
 int stream_ctas(int n, int ncells, int n_items, int sms) {
   const int64_t pts = (int64_t)ncells * ntet(n + 1);
   const int64_t want = std::max<int64_t>((pts + 2047) / 2048, ((int64_t)n_items + 15) / 16);
   return (int)std::max<int64_t>(1, std::min<int64_t>(std::max(sms, 1), want));
 }
 
-void stream_schedule(int n, int ncells, int nctas, std::vector<int4>& units,
-                     std::vector<int32_t>& cta_begin) {
+int stream_band_rows(int n, int esize) {
   const int w = n + 1;
-  // the sequence (cell, band, plane) with a cost per plane: outputs, staged
-  // elements and a fixed part for the plane's waits and row set-up
-  struct Step { int cell, j0, k; double cost; };
-  std::vector<Step> seq;
+  // whole planes when plane 0 (the largest) fits a slot with its 16-byte rounding
+  if (ntri(w) * esize + 32 <= kStreamSlotBytes) return w;
+  // else bands of rows whose staged range (rows j0-1 .. j0+rows) fits a slot
+  return std::max(1, kStreamSlotBytes / (w * esize) - 2);
+}
+
+int stream_plan(int n, int ncells, int nctas, int esize, StreamPlanHost& P) {
+  const int w = n + 1;
+  const int V = 16 / esize;
+  const int JB = stream_band_rows(n, esize);
+  if (JB < w && (int64_t)(JB + 2) * w * esize + 32 > kStreamSlotBytes) {
+    set_error("streaming plan: no band of rows fits a slot at w = %d", w);
+    return HG_ERR_UNSUPPORTED;
+  }
+  auto rs = [&](int j, int k) { return (int64_t)tw(w, 0, j, k); };
+  // the sequence of pieces (cell, plane k, rows [ja, jb)): per cell, band and
+  // plane, consecutive rows of at most kStreamPiece points (one row at least)
+  struct Piece { int cell, k, ja, jb; double cost; };
+  std::vector<Piece> seq;
   double total = 0;
   for (int c = 0; c < ncells; ++c)
-    for (int j0 = 0; j0 < w; j0 += kStreamBand)
+    for (int j0 = 0; j0 < w; j0 += JB)
       for (int k = 0; k <= w - 1 - j0; ++k) {
-        const double cost = (double)band_outputs(w, j0, k) + 0.25 * band_loaded(w, j0, k) + 48.0;
-        seq.push_back({c, j0, k, cost});
-        total += cost;
+        const int jend = std::min(j0 + JB, w - k);
+        for (int ja = j0; ja < jend;) {
+          int jb = ja;
+          int64_t pts = 0;
+          while (jb < jend && (jb == ja || pts + (w - k - jb) <= kStreamPiece)) pts += w - k - jb++;
+          // cost: points, staged elements (three planes' rows) and a fixed part
+          const double cost = (double)pts + 0.75 * (double)pts + 96.0;
+          seq.push_back({c, k, ja, jb, cost});
+          total += cost;
+          ja = jb;
+        }
       }
-  units.clear();
-  cta_begin.assign(nctas + 1, 0);
+  P = StreamPlanHost{};
+  P.nctas = nctas;
+  P.band_rows = JB;
+  P.cta_copies.assign(nctas + 1, 0);
+  P.cta_items.assign(nctas + 1, 0);
   size_t q = 0;
   double acc = 0;
   for (int g = 0; g < nctas; ++g) {
-    cta_begin[g] = (int32_t)units.size();
+    P.cta_copies[g] = (int32_t)P.copies.size();
+    P.cta_items[g] = (int32_t)(P.items.size() / 3);
+    const int copy0 = (int)P.copies.size();
+    const size_t item0 = P.items.size();
     const double target = total * (g + 1) / nctas;
-    while (q < seq.size() && (g == nctas - 1 || acc + 0.5 * seq[q].cost <= target)) {
-      // one run: consecutive planes of the same (cell, band)
-      const Step& s0 = seq[q];
-      int k1 = s0.k;
-      while (q < seq.size() && seq[q].cell == s0.cell && seq[q].j0 == s0.j0 &&
-             (g == nctas - 1 || acc + 0.5 * seq[q].cost <= target)) {
-        acc += seq[q].cost;
-        k1 = seq[q].k + 1;
-        ++q;
+    const size_t q0 = q;
+    while (q < seq.size() && (g == nctas - 1 || acc + 0.5 * seq[q].cost <= target)) acc += seq[q++].cost;
+    // the rows each (cell, band, plane) must have staged: the union over the
+    // CTA's pieces of rows max(ja-1,0) .. min(jb, w-1-kk) of planes kk = k-1..k+1
+    struct Need { int cell, j0, kk, jlo, jhi; };
+    std::vector<Need> need;   // in (cell, band, plane) order
+    auto band_of = [&](int ja) { return ja / JB * JB; };
+    for (size_t t = q0; t < q; ++t) {
+      const Piece& p = seq[t];
+      for (int kk = std::max(p.k - 1, 0); kk <= std::min(p.k + 1, w - 1); ++kk) {
+        const int jlo = std::max(p.ja - 1, 0), jhi = std::min(p.jb, w - 1 - kk);
+        if (jlo > jhi) continue;
+        const int j0 = band_of(p.ja);
+        bool found = false;
+        for (auto& nd : need)
+          if (nd.cell == p.cell && nd.j0 == j0 && nd.kk == kk) {
+            nd.jlo = std::min(nd.jlo, jlo);
+            nd.jhi = std::max(nd.jhi, jhi);
+            found = true;
+            break;
+          }
+        if (!found) need.push_back({p.cell, j0, kk, jlo, jhi});
       }
-      const int rows = std::min(kStreamBand, w - s0.j0);
-      units.push_back({s0.cell, s0.j0 | (rows << 16), s0.k | (k1 << 16), 0});
+    }
+    std::sort(need.begin(), need.end(), [](const Need& x, const Need& y) {
+      return x.cell != y.cell ? x.cell < y.cell : x.j0 != y.j0 ? x.j0 < y.j0 : x.kk < y.kk;
+    });
+    // copies: consecutive staged ranges that are contiguous in the cell's
+    // array (whole-plane tails and heads) share a copy while it fits a slot
+    std::vector<int> cop(need.size());
+    std::vector<int64_t> cga(need.size());
+    for (size_t a0 = 0; a0 < need.size();) {
+      const int64_t g0 = rs(need[a0].jlo, need[a0].kk);
+      int64_t gend = rs(need[a0].jhi, need[a0].kk) + (w - need[a0].kk - need[a0].jhi);
+      size_t a1 = a0 + 1;
+      while (a1 < need.size() && a1 - a0 < 64 && need[a1].cell == need[a0].cell &&
+             need[a1].j0 == need[a0].j0 && need[a1].kk == need[a1 - 1].kk + 1) {
+        const int64_t h0 = rs(need[a1].jlo, need[a1].kk);
+        const int64_t h1 = rs(need[a1].jhi, need[a1].kk) + (w - need[a1].kk - need[a1].jhi);
+        if (h0 != gend) break;  // not contiguous with the previous range
+        if (((h1 + V - 1) / V * V - g0 / V * V) * esize > kStreamSlotBytes) break;
+        gend = h1;
+        ++a1;
+      }
+      const int64_t ga = g0 / V * V, ge = (gend + V - 1) / V * V;
+      if ((ge - ga) * esize > kStreamSlotBytes) {
+        set_error("streaming plan: a staged range of %lld elements exceeds a slot", (long long)(ge - ga));
+        return HG_ERR_UNSUPPORTED;
+      }
+      const int c = (int)P.copies.size() - copy0;
+      P.copies.push_back({need[a0].cell, (int)ga, (int)(ge - ga), 0});
+      for (size_t t = a0; t < a1; ++t) {
+        cop[t] = c;
+        cga[t] = ga;
+      }
+      a0 = a1;
+    }
+    auto copy_of = [&](int cell, int j0, int kk, int& c, int64_t& ga) {
+      for (size_t t = 0; t < need.size(); ++t)
+        if (need[t].cell == cell && need[t].j0 == j0 && need[t].kk == kk) {
+          c = cop[t];
+          ga = cga[t];
+          return;
+        }
+      c = -1;
+      ga = 0;
+    };
+    // items: the pieces, with the copies holding planes k, k-1, k+1
+    for (size_t t = q0; t < q; ++t) {
+      const Piece& p = seq[t];
+      const int j0 = band_of(p.ja);
+      int c0, cm = -1, cp = -1;
+      int64_t g0 = 0, gm = 0, gp = 0;
+      copy_of(p.cell, j0, p.k, c0, g0);
+      if (p.k >= 1) copy_of(p.cell, j0, p.k - 1, cm, gm);
+      if (p.k + 1 <= w - 1 && std::max(p.ja - 1, 0) <= std::min(p.jb, w - 1 - (p.k + 1)))
+        copy_of(p.cell, j0, p.k + 1, cp, gp);
+      P.items.push_back({p.cell, p.k, p.ja | (p.jb << 16), 0});
+      P.items.push_back({c0, cm, cp, 0});
+      P.items.push_back({(int)g0, (int)gm, (int)gp, 0});
+    }
+    // arrivals: every slot phase expects kStreamArrive; each item arrives once on
+    // each distinct copy it reads, the first reader of a copy adds the rest
+    const int ncop = (int)P.copies.size() - copy0;
+    std::vector<int> readers(ncop, 0);
+    for (size_t t = item0; t < P.items.size(); t += 3) {
+      const int4 c = P.items[t + 1];
+      readers[c.x]++;
+      if (c.y >= 0 && c.y != c.x) readers[c.y]++;
+      if (c.z >= 0 && c.z != c.x && c.z != c.y) readers[c.z]++;
+    }
+    for (int c = 0; c < ncop; ++c)
+      if (readers[c] < 1 || readers[c] > kStreamArrive) {
+        set_error("streaming plan: copy %d of CTA %d has %d readers", c, g, readers[c]);
+        return HG_ERR_UNSUPPORTED;
+      }
+    std::vector<char> seen(ncop, 0);
+    for (size_t t = item0; t < P.items.size(); t += 3) {
+      const int4 c = P.items[t + 1];
+      auto cnt = [&](int cc) {
+        const int r = seen[cc] ? 1 : 1 + kStreamArrive - readers[cc];
+        seen[cc] = 1;
+        return r;
+      };
+      const int n0 = cnt(c.x);
+      const int nm = (c.y >= 0 && c.y != c.x) ? cnt(c.y) : 0;
+      const int np = (c.z >= 0 && c.z != c.x && c.z != c.y) ? cnt(c.z) : 0;
+      P.items[t].w = n0 | (nm << 10) | (np << 20);
     }
   }
-  cta_begin[nctas] = (int32_t)units.size();
+  P.cta_copies[nctas] = (int32_t)P.copies.size();
+  P.cta_items[nctas] = (int32_t)(P.items.size() / 3);
+  return HG_OK;
 }
 
 // ------------------------------------------------------------ hierarchy
@@ -398,15 +511,22 @@ int Hier::build_level(int l) {
   L.n_mitems = (int)mitems.size();
   if (int r = upload(&L.mitems, mitems)) return r;
   {
+    // the streaming kernel's plans, one per element size
     int dev = 0, sms = 0;
     HG_CUDA(cudaGetDevice(&dev));
     HG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    std::vector<int4> su;
-    std::vector<int32_t> sc;
-    L.n_scta = stream_ctas(n, (int)mesh->nc, L.n_mitems, sms);
-    stream_schedule(n, (int)mesh->nc, L.n_scta, su, sc);
-    if (int r = upload(&L.sunits, su)) return r;
-    if (int r = upload(&L.scta, sc)) return r;
+    const int nctas = stream_ctas(n, (int)mesh->nc, L.n_mitems, sms);
+    for (int dt = 0; dt < 2; ++dt) {
+      StreamPlanHost P;
+      if (int r = stream_plan(n, (int)mesh->nc, nctas, dt == HG_F64 ? 8 : 4, P)) return r;
+      StreamPlanDev& D = L.splan[dt];
+      D.nctas = nctas;
+      D.band_rows = P.band_rows;
+      if (int r = upload(&D.copies, P.copies)) return r;
+      if (int r = upload(&D.items, P.items)) return r;
+      if (int r = upload(&D.cta_copies, P.cta_copies)) return r;
+      if (int r = upload(&D.cta_items, P.cta_items)) return r;
+    }
   }
   const std::vector<int4> ptiles = plane_tiles(n);
   L.n_ptiles_cell = (int)ptiles.size();
@@ -500,7 +620,7 @@ int Hier::build_level(int l) {
   if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
       (L.n_items && (!L.items || !L.item_prim)) ||
       (L.n_citems && !L.citems) || (L.n_ptiles_cell && !L.ptiles) ||
-      (L.n_mitems && !L.mitems) || !L.scta ||
+      (L.n_mitems && !L.mitems) || !L.splan[0].cta_items || !L.splan[1].cta_items ||
       (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
     set_error("internal: level %d device tables incomplete", l);
     return HG_ERR_CUDA;
@@ -619,8 +739,12 @@ Hier::~Hier() {
     cudaFree(L.prim_point_base);
     cudaFree(L.citems);
     cudaFree(L.mitems);
-    cudaFree(L.sunits);
-    cudaFree(L.scta);
+    for (auto& D : L.splan) {
+      cudaFree(D.copies);
+      cudaFree(D.items);
+      cudaFree(D.cta_copies);
+      cudaFree(D.cta_items);
+    }
     cudaFree(L.colour);
     cudaFree(L.ptiles);
     cudaFree(L.items);
@@ -1161,23 +1285,29 @@ int hg_plane_tiles(int level, int* out, int* n_tiles) {
   return HG_OK;
 }
 
-int hg_stream_schedule(int level, int ncells, int nctas, int* units, int* cta_begin,
-                       int* n_units) {
-  HG_CHECK(level >= 0 && level <= 12 && ncells >= 1 && nctas >= 1 && n_units, HG_ERR_INVALID_ARG,
-           "hg_stream_schedule: bad argument");
-  std::vector<int4> u;
-  std::vector<int32_t> cb;
-  stream_schedule(1 << level, ncells, nctas, u, cb);
-  *n_units = (int)u.size();
-  if (units)
-    for (size_t q = 0; q < u.size(); ++q) {
-      units[4 * q] = u[q].x;
-      units[4 * q + 1] = u[q].y;
-      units[4 * q + 2] = u[q].z;
-      units[4 * q + 3] = u[q].w;
-    }
-  if (cta_begin)
-    for (int g = 0; g <= nctas; ++g) cta_begin[g] = cb[g];
+int hg_stream_plan(int level, int ncells, int nctas, int dtype, int* copies, int* items,
+                   int* cta_copies, int* cta_items, int* counts) {
+  HG_CHECK(level >= 0 && level <= 12 && ncells >= 1 && nctas >= 1 && counts &&
+               (dtype == HG_F32 || dtype == HG_F64),
+           HG_ERR_INVALID_ARG, "hg_stream_plan: bad argument");
+  StreamPlanHost P;
+  if (int r = stream_plan(1 << level, ncells, nctas, dtype == HG_F64 ? 8 : 4, P)) return r;
+  counts[0] = (int)P.copies.size();
+  counts[1] = (int)(P.items.size() / 3);
+  counts[2] = P.band_rows;
+  auto put = [](int* out, const std::vector<int4>& v) {
+    if (out)
+      for (size_t q = 0; q < v.size(); ++q) {
+        out[4 * q] = v[q].x;
+        out[4 * q + 1] = v[q].y;
+        out[4 * q + 2] = v[q].z;
+        out[4 * q + 3] = v[q].w;
+      }
+  };
+  put(copies, P.copies);
+  put(items, P.items);
+  if (cta_copies) std::copy(P.cta_copies.begin(), P.cta_copies.end(), cta_copies);
+  if (cta_items) std::copy(P.cta_items.begin(), P.cta_items.end(), cta_items);
   return HG_OK;
 }
 

@@ -127,6 +127,46 @@ HG_HD void copy_local_ijk(const IfaceCopy& c, int dim, const int wts[3], int& i,
   }
 }
 
+// Streaming constant-stencil kernel (hg_p1stream.cu).  One CTA per SM copies
+// a contiguous stretch of the (cell, band, plane) sequence into a ring of
+// kStreamSlots shared-memory slots, kStreamSlotBytes each, by 1-D bulk
+// copies, and forms the band's points of every plane from the staged rows of
+// planes k-1, k, k+1.  A band is the rows j0 .. j0+rows-1 of a plane; when a
+// whole plane fits a slot the band is the whole plane and consecutive planes
+// (contiguous in t_w order) share one copy.  The plan, built
+// on the host per level and element size, lists per CTA:
+//  * copies {cell, ga, nelem, 0}: [ga, ga+nelem) of the cell's stored array
+//    (16-byte aligned), copy c of the CTA into slot c mod kStreamSlots;
+//  * items, 3 int4 each: {cell, k, ja | jb << 16, arrivals},
+//    {c0, cm, cp, 0}, {ga0, gam, gap, 0}: the rows [ja, jb) of plane k, the
+//    CTA-local copies holding planes k, k-1, k+1 (-1: none) and their ga;
+//    arrivals packs the counts (10 bits each) with which the item arrives on
+//    the distinct copies c0, cm, cp after reading them: every slot phase
+//    expects kStreamArrive arrivals, the first reader of a copy adds the
+//    readers that do not exist.
+constexpr int kStreamSlotBytes = 40 * 1024;
+constexpr int kStreamSlots = 4;
+constexpr int kStreamArrive = 256;
+constexpr int kStreamPiece = 1024;
+struct StreamPlanDev {
+  int4* copies;
+  int4* items;
+  int32_t* cta_copies;  // [nctas + 1]
+  int32_t* cta_items;   // [nctas + 1]
+  int nctas;
+  int band_rows;
+};
+struct StreamPlanHost {
+  std::vector<int4> copies, items;
+  std::vector<int32_t> cta_copies, cta_items;
+  int nctas = 0, band_rows = 0;
+};
+// CTAs of the streaming kernel for a level (at most one per SM).
+int stream_ctas(int n, int ncells, int n_items, int sms);
+// Rows per band at n intervals per edge and element size esize (w = n+1: whole planes).
+int stream_band_rows(int n, int esize);
+int stream_plan(int n, int ncells, int nctas, int esize, StreamPlanHost& P);
+
 // Device-resident description of one level of one hierarchy (P1 vertex lattice).
 struct LevelDev {
   int level, n, w;           // w = n + 1 vertices per macro edge
@@ -151,9 +191,7 @@ struct LevelDev {
   int n_citems;              //   points); points = floor(32 / ncopies), one lane per copy
   int4* mitems;              // apply items of the primitives with >= 2 copies only
   int n_mitems, n_mitems_inner;  //   (non-Dirichlet first): the streaming kernel's exchange
-  int4* sunits;              // streaming schedule: runs (cell, j0 | rows << 16, k0 | k1 << 16, 0)
-  int32_t* scta;             //   [n_scta + 1]: runs of CTA g are sunits[scta[g] .. scta[g+1])
-  int n_scta;
+  StreamPlanDev splan[2];    // the streaming kernel's plans for HG_F32 and HG_F64
   int4* ptiles;              // plane-window tiles of ONE cell (the same for every cell):
   int n_ptiles_cell;         //   (k | windows << 16, lane-0 offset z, j0 << 16 | i0, 0)
   uint8_t* colour;           // Gauss-Seidel colour (0..3) per stored point, or null
@@ -165,19 +203,6 @@ struct LevelDev {
 #define HG_PLANE_STEPS 16
 #endif
 constexpr int kPlaneSteps = HG_PLANE_STEPS;
-
-// Streaming constant-stencil kernel (hg_p1stream.cu): a cell's lattice is cut
-// into bands of kStreamBand consecutive rows j; a band is marched plane by
-// plane (k) with the rows j0-1 .. j0+kStreamBand of every plane staged in
-// shared memory.  The schedule gives every CTA (one per SM) a contiguous
-// stretch of the sequence (cell, band, plane) of about equal cost; each
-// stretch is a list of runs (cell, band, planes [k0, k1)).
-constexpr int kStreamBand = 8;
-// CTAs of the streaming kernel for a level (at most one per SM).
-int stream_ctas(int n, int ncells, int n_items, int sms);
-// Runs of every CTA: units[cta_begin[g] .. cta_begin[g+1]) belong to CTA g.
-void stream_schedule(int n, int ncells, int nctas, std::vector<int4>& units,
-                     std::vector<int32_t>& cta_begin);
 
 // Dense FP64 coarse-grid solver data.
 struct CoarseDev {
@@ -233,7 +258,9 @@ struct StencilArgs {
 };
 
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);
-// The streaming form of the constant-stencil operator (a.sten, a.pattern).
+// The streaming form of the constant-stencil operator (a.sten, a.pattern), for
+// levels whose slot ring fits in shared memory (p1_stream_fits).
+bool p1_stream_fits(int w, int dtype);
 int launch_p1_stream(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------- P2

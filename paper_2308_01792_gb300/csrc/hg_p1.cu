@@ -651,8 +651,9 @@ int64_t xfer_warps(int64_t n_rows) { return (n_rows + kXferRows - 1) / kXferRows
 }  // namespace
 
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s) {
-  // constant stencils: the streaming kernel; stored stencils: the plane windows
-  if (!a.sst) return launch_p1_stream(L, dtype, a, s);
+  // constant stencils: the streaming kernel; stored stencils, and levels too
+  // large for the streaming kernel's shared-memory ring: the plane windows
+  if (!a.sst && p1_stream_fits(L.w, dtype)) return launch_p1_stream(L, dtype, a, s);
   return dtype == HG_F64 ? run_p1_op<double>(L, a, s) : run_p1_op<float>(L, a, s);
 }
 

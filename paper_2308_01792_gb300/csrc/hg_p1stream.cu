@@ -2,35 +2,35 @@
 // (Sec. 5.2 apply(), stencil-based pattern, one stencil per macro cell).
 //
 // A macro cell's lattice is stored plane by plane (k), row by row (j), with
-// unit-stride x-lines (i) (the t_w order of Sec. 4).  The rows j0 .. j0+7 of
-// one plane ("a band") are one contiguous offset range, and so are the rows
-// j0-1 .. j0+8 that the 15-point stencil of the band reads in planes k-1, k
-// and k+1.  The kernel marches bands plane by plane:
+// unit-stride x-lines (i) (the t_w order of Sec. 4), so any run of rows of one
+// plane is one contiguous range, and consecutive whole planes are too.  The
+// 15-point stencil of plane k reads planes k-1, k and k+1.
 //
-//  * one CTA per SM, a producer warp and kSWarps consumer warps;
-//  * the producer copies the staged rows of every plane of its runs into a
-//    ring of shared-memory slots with 1-D bulk copies (cp.async.bulk, the
-//    TMA engine), one copy per plane, completion counted on the slot's
-//    mbarrier; it runs up to R slots ahead of the consumers, so tens of KB
-//    per SM are in flight from HBM at any time;
-//  * the consumers compute a plane of the band once the slots of planes k-1,
-//    k, k+1 have landed, the 32-point chunks of the band's rows going
-//    round-robin over the warps (all addressing warp-uniform per row; the
-//    round-robin continues across planes, so short planes near the top of a
-//    band spread over the warps too), write the results to HBM directly, and
-//    release the slot of plane k-1; a slot is thus read for three
-//    consecutive planes and every x value crosses HBM once;
-//  * points of the cell's boundary that lie on a primitive of this cell only
-//    (boundary faces, edges and vertices) are formed in the same pass from
-//    the cell's partial stencil; points shared by several cells (the
-//    ghost-layer exchange of Sec. 2) are formed by the interface items, a
-//    contiguous share per CTA that its consumer warps take after their runs
-//    (the producer prefetches the share's item records into L2 at the start).
+//  * One CTA per SM: a producer warp and kSWarps consumer warps.  A plan built
+//    on the host (stream_plan) gives the CTA a contiguous stretch of the
+//    sequence (cell, band of rows, plane), as a list of copies and a list of
+//    items (see hg_internal.h).
+//  * The producer moves the copies into a ring of kStreamSlots slots of
+//    kStreamSlotBytes with 1-D bulk copies (cp.async.bulk, the TMA engine),
+//    completion counted in bytes on the slot's mbarrier.  A bulk copy costs
+//    the TMA engine a fixed time of the order of 0.2 us, so copies are made
+//    large: whole planes where a plane fits a slot, several consecutive planes
+//    per copy when they are small.
+//  * Consumer warp w takes items w, w + kSWarps, ...: it waits for the copies
+//    holding planes k-1, k, k+1, forms the item's interior points from shared
+//    memory (32-point chunks of a row, all addresses 32-bit shared addresses),
+//    then its boundary points, writes y to HBM directly, and arrives on the
+//    copies' release barriers.  Every x value crosses HBM once.
+//  * Points on the cell's boundary that lie on a primitive of this cell only
+//    (boundary faces, edges and vertices) are formed in the pass from the
+//    cell's partial stencil; points shared by several cells (the ghost-layer
+//    exchange of Sec. 2) by the interface items, which the consumer warps run
+//    first, while the first copies are in flight.
 //
-// Every wait on an mbarrier is bounded (about one second): on expiry the
-// kernel records HG_ERR_TIMEOUT in the hierarchy's error word, the other
-// warps stop at their next wait, and the producer waits (again bounded) for
-// the copies it issued before the CTA exits.
+// Every wait is bounded (about one second): on expiry the kernel records
+// HG_ERR_TIMEOUT in the hierarchy's error word, the other warps stop at their
+// next wait, and the producer waits (again bounded) for the copies it issued
+// before the CTA exits.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -44,38 +44,31 @@ namespace {
 
 constexpr int kSWarps = 16;                    // consumer warps
 constexpr int kSThreads = (kSWarps + 1) * 32;  // and one producer warp
-constexpr int kRingBytes = 160 * 1024;         // shared memory for the slot ring
 constexpr unsigned long long kWaitNs = 1000000000ull;
+// Longest suspension of one try_wait (the thread resumes as soon as the
+// phase completes): waiting warps then take no issue slots.
+constexpr int kSuspendNs = 100000;
 
 template <typename T>
-__host__ __device__ constexpr int vec_elems() { return 16 / (int)sizeof(T); }
+__host__ __device__ constexpr int slot_elems() { return kStreamSlotBytes / (int)sizeof(T); }
+// Elements before the first and after the last slot: the shared-memory loads
+// of lanes past a row's end or next to a copy's edge reach at most w + 2
+// elements before a copy's data and 2 w + 33 after it.
+inline int guard_elems(int w) { return (4 * w + 64 + 31) / 32 * 32; }
+// Barriers (full, empty), the stop flag and one copy tag per slot.
+__host__ __device__ constexpr int barrier_bytes() {
+  return (2 * kStreamSlots * 8 + 16 + 4 * kStreamSlots + 127) / 128 * 128;
+}
 
 // HG_ADD applies get their own instantiation (y += A x) so that a replacing
 // apply never reads the destination.
 constexpr int kOpApplyAdd = 100;
 __host__ __device__ constexpr bool is_apply(int op) { return op == OP_APPLY || op == kOpApplyAdd; }
 
-// Elements of one slot: kStreamBand + 2 rows of at most w points plus the
-// 16-byte rounding of both ends, in whole 128-byte lines.
-inline int slot_elems(int w) { return ((kStreamBand + 2) * w + 8 + 31) / 32 * 32; }
-// Elements before the first and after the last slot: the unconditional
-// shared-memory loads of lanes past a row's end or next to a band's edge reach
-// at most w + 2 elements before a slot's data and 2 w + 33 after it.
-inline int guard_elems(int w) { return (4 * w + 64 + 31) / 32 * 32; }
-template <typename T>
-int ring_slots(int w) {
-  const int r = kRingBytes / (slot_elems(w) * (int)sizeof(T));
-  return r < 4 ? 4 : r > 32 ? 32 : r;
-}
-__host__ __device__ inline int barrier_bytes(int R) { return (2 * R * 8 + 16 + 127) / 128 * 128; }
-
 template <typename T>
 struct StreamArgs {
   FusedArgs<T> f;             // operands, stencils, flags and the interface items
-  const int4* units;          // runs (cell, j0 | rows << 16, k0 | k1 << 16, 0)
-  const int32_t* cta_begin;
-  int R;                      // ring slots
-  int slot;                   // elements per slot
+  StreamPlanDev plan;
   int guard;                  // elements before / after the ring
 };
 
@@ -96,17 +89,18 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
                "r"(bytes)
                : "memory");
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+__device__ __forceinline__ void mbar_arrive_cnt(uint64_t* b, int count) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(count)
+               : "memory");
 }
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(smem_addr(b)), "r"(parity)
+      : "r"(smem_addr(b)), "r"(parity), "n"(kSuspendNs)
       : "memory");
   return ok != 0;
 }
@@ -143,16 +137,38 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
   return false;
 }
 
-// Offsets [ga, ge) (16-byte aligned) of the rows staged for plane kk of the
-// band j0 .. j0+rows-1: rows max(j0-1, 0) .. min(j0+rows, w-1-kk).
-template <typename T>
-__device__ __forceinline__ void staged_range(int w, int j0, int rows, int kk, int& ga, int& ge) {
-  constexpr int V = vec_elems<T>();
-  const int jlo = max(j0 - 1, 0), jhi = min(j0 + rows, w - 1 - kk);
-  const int g0 = row_start(w, jlo, kk);
-  const int g1 = row_start(w, jhi, kk) + (w - kk - jhi);
-  ga = g0 & ~(V - 1);
-  ge = (g1 + V - 1) & ~(V - 1);
+// Shared-memory load from a 32-bit shared address plus a constant byte offset
+// (kept in order after the barrier waits, which are volatile as well).
+template <int OFF>
+__device__ __forceinline__ float lds(float*, uint32_t a) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
+  return v;
+}
+template <int OFF>
+__device__ __forceinline__ double lds(double*, uint32_t a) {
+  double v;
+  asm volatile("ld.shared.f64 %0, [%1+%2];" : "=d"(v) : "r"(a), "n"(OFF));
+  return v;
+}
+#define HG_LDS(T, OFF, a) lds<(OFF) * (int)sizeof(T)>((T*)nullptr, (a))
+
+// Wait until stream position q has landed in its slot: first until the
+// producer has started q's copy there (tag), then for the copy's barrier
+// phase.  False after kWaitNs or once *stop is set.
+__device__ __forceinline__ bool slot_wait(uint64_t* full, volatile int* tag, int q, int rmask,
+                                          int rlog, volatile int* stop) {
+  const int s = q & rmask;
+  if (tag[s] != q) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; tag[s] != q; ++it) {
+      if (it >= 8) __nanosleep(32);  // leave the issue slots to the computing warps
+      if ((it & 63) == 63 && (*stop || global_ns() - t0 > kWaitNs)) return false;
+      if (it > (1ll << 40)) return false;
+    }
+  }
+  __threadfence_block();
+  return mbar_wait(&full[s], (q >> rlog) & 1, stop);
 }
 
 // The operation's output at stored index g from the stencil sum acc.
@@ -176,22 +192,17 @@ __device__ __forceinline__ void stream_out(const FusedArgs<T>& A, int64_t g, T c
   }
 }
 
-// A point of the cell's boundary (class cls != 0) of the band row whose
-// plane-k, plane-(k+1) and plane-(k-1) rows j start at P0, Pp and Pm.
+// A point of the cell's boundary (class cls != 0) that lies on a primitive of
+// this cell only and is not a fixed Dirichlet value: the cell's partial
+// stencil is the whole row of the operator.  The band row's plane-k,
+// plane-(k+1) and plane-(k-1) rows j start at P0, Pp and Pm.
 template <typename T, int OP>
 __device__ __noinline__ void stream_boundary_point(const FusedArgs<T>& A, int cell, int i, int j,
                                                    int k, int len, const T* P0, const T* Pp,
                                                    const T* Pm, int64_t g) {
   const int n = A.n;
   const int cls = (i == len - 1 ? 1 : 0) | (i == 0 ? 2 : 0) | (j == 0 ? 4 : 0) | (k == 0 ? 8 : 0);
-  const uint8_t f = __ldg(A.flags + cell * 16 + cls);
   const T c = P0[i];
-  if ((f & CF_DIRICHLET) && (!is_apply(OP) || A.mask == HG_MASK_INNER)) {
-    A.y[g] = op_scaled(OP) ? c : T(0);
-    return;
-  }
-  if (f & CF_MULTI) return;  // a sum over cells: the interface items form it
-  // single copy: this cell's partial stencil is the whole row of the operator
   const T* S = A.sten + (int64_t)cell * 256 + cls * 16;
   T sv[kNDir], xv[kNDir];
 #pragma unroll
@@ -212,179 +223,248 @@ __device__ __noinline__ void stream_boundary_point(const FusedArgs<T>& A, int ce
   stream_out<T, OP>(A, g, c, acc, wd);
 }
 
+// Wait until copy c of the CTA has landed in its slot: first until the
+// producer has started copy c there (tag), then for the slot's barrier phase.
+// The tag makes the phase parity unambiguous: warps work on different items,
+// so one may want a slot a use or two ahead of the others.
+__device__ __forceinline__ bool copy_wait(uint64_t* full, volatile int* tag, int c,
+                                          volatile int* stop) {
+  const int s = c % kStreamSlots;
+  if (tag[s] != c) {
+    const unsigned long long t0 = global_ns();
+    for (long long it = 0; tag[s] != c; ++it) {
+      if (it >= 8) __nanosleep(32);  // leave the issue slots to the computing warps
+      if ((it & 63) == 63 && (*stop || global_ns() - t0 > kWaitNs)) return false;
+      if (it > (1ll << 40)) return false;
+    }
+  }
+  __threadfence_block();
+  return mbar_wait(&full[s], (c / kStreamSlots) & 1, stop);
+}
+
+// One item in shared memory: the rows [ja, jb) of plane k; element g (cell
+// offset) of plane k / k+1 / k-1 is at byte address vb0 / vbp / vbm + g * E.
+// A plane that is not in the stream aliases plane k (only boundary points lie
+// next to it, and they do not read it).
+struct ItemView {
+  int cell, k, ja, jb;
+  uint32_t vb0, vbp, vbm;
+};
+
+// Interior points (j >= 1, k >= 1, 1 <= i <= len-2) of the item's rows: per
+// row, 32-point chunks; the boundary points are left to item_boundary.
+template <typename T, int OP, int PAT>
+__device__ __forceinline__ void item_interior(const FusedArgs<T>& A, const ItemView& V,
+                                              const T s[kNDir], T wdc, int64_t base, int lane) {
+  constexpr int E = (int)sizeof(T);
+  const int w = A.w, k = V.k;
+  if (k == 0) return;  // the plane k = 0 is a face of the cell
+  const int Tk = ntri32(w - k), Tk1 = ntri32(w - k + 1);
+  int rs = row_start(w, V.ja, k);
+  for (int j = V.ja; j < V.jb; ++j) {
+    const int len = w - k - j;
+    if (j >= 1 && len >= 3) {
+      const uint32_t L = (uint32_t)(len * E);
+      // element i = 1 + lane of row j in planes k, k+1 (row j at rs + T(w-k) - j)
+      // and k-1 (row j at rs - T(w-k+1) + j)
+      uint32_t a0 = V.vb0 + (uint32_t)((rs + 1 + lane) * E);
+      uint32_t ap = V.vbp + (uint32_t)((rs + Tk - j + 1 + lane) * E);
+      uint32_t am = V.vbm + (uint32_t)((rs - Tk1 + j + 1 + lane) * E);
+      int64_t g = base + rs + 1 + lane;
+#pragma unroll 2
+      for (int i0 = 1; i0 <= len - 2; i0 += 32) {
+        // the 15 neighbours; rows j-1 / j+1 of plane k start at -(len+1) / +len,
+        // row j-1 of plane k+1 at -len, row j+1 of plane k-1 at +len+1
+        const T c = HG_LDS(T, 0, a0);
+        const T x1 = HG_LDS(T, 1, a0), x2 = HG_LDS(T, -1, a0);
+        const T x7 = HG_LDS(T, -1, a0 + L), x8 = HG_LDS(T, 0, a0 - L);
+        const T x11 = HG_LDS(T, 0, ap - L), x12 = HG_LDS(T, 1, am + L);
+        T acc;
+        if (PAT == kPat7) {
+          const T a0s = s[0] * c + s[1] * x1 + s[2] * x2 + s[7] * x7 + s[8] * x8;
+          acc = a0s + (s[11] * x11 + s[12] * x12);
+        } else {
+          const T x3 = HG_LDS(T, 0, a0 + L), x4 = HG_LDS(T, -1, a0 - L);
+          const T x5 = HG_LDS(T, 0, ap), x6 = HG_LDS(T, 0, am);
+          const T x9 = HG_LDS(T, -1, ap), x10 = HG_LDS(T, 1, am);
+          const T x13 = HG_LDS(T, 1, ap - L), x14 = HG_LDS(T, 0, am + L);
+          const T a0s = s[0] * c + s[1] * x1 + s[2] * x2 + s[3] * x3 + s[4] * x4 + s[7] * x7 +
+                        s[8] * x8;
+          const T a1 = s[5] * x5 + s[9] * x9 + s[11] * x11 + s[13] * x13;
+          const T a2 = s[6] * x6 + s[10] * x10 + s[12] * x12 + s[14] * x14;
+          acc = a0s + (a1 + a2);
+        }
+        if (i0 + lane <= len - 2) stream_out<T, OP>(A, g, c, acc, wdc);
+        a0 += 32 * E;
+        ap += 32 * E;
+        am += 32 * E;
+        g += 32;
+      }
+    }
+    rs += len;
+  }
+}
+
+// A boundary point (i, j) of the item's plane: a fixed Dirichlet value, a
+// point the interface items form (left alone), or (rare) a single-copy
+// partial row.
+template <typename T, int OP>
+__device__ __forceinline__ void item_boundary_point(const FusedArgs<T>& A, const ItemView& V,
+                                                    ulonglong2 fw, int64_t base, int j, int rs,
+                                                    int i) {
+  constexpr int E = (int)sizeof(T);
+  const int w = A.w, k = V.k, len = w - k - j;
+  const int cls = (i == len - 1 ? 1 : 0) | (i == 0 ? 2 : 0) | (j == 0 ? 4 : 0) | (k == 0 ? 8 : 0);
+  const unsigned f = (unsigned)((cls < 8 ? fw.x >> (8 * cls) : fw.y >> (8 * (cls - 8))) & 0xffu);
+  const int64_t g = base + rs + i;
+  if ((f & CF_DIRICHLET) && (!is_apply(OP) || A.mask == HG_MASK_INNER)) {
+    A.y[g] = op_scaled(OP) ? HG_LDS(T, 0, V.vb0 + (uint32_t)((rs + i) * E)) : T(0);
+  } else if (!(f & CF_MULTI)) {
+    const T* P0 = reinterpret_cast<const T*>(__cvta_shared_to_generic(V.vb0 + (uint32_t)(rs * E)));
+    const T* Pp = reinterpret_cast<const T*>(
+        __cvta_shared_to_generic(V.vbp + (uint32_t)((rs + ntri32(w - k) - j) * E)));
+    const T* Pm = reinterpret_cast<const T*>(
+        __cvta_shared_to_generic(V.vbm + (uint32_t)((rs - ntri32(w - k + 1) + j) * E)));
+    stream_boundary_point<T, OP>(A, V.cell, i, j, k, len, P0, Pp, Pm, g);
+  }
+}
+
+// The boundary points of the item: both ends of every row, and all of row
+// j = 0 and of plane k = 0.
+template <typename T, int OP>
+__device__ __forceinline__ void item_boundary(const FusedArgs<T>& A, const ItemView& V,
+                                              ulonglong2 fw, int64_t base, int lane) {
+  const int w = A.w, k = V.k;
+  int rs = row_start(w, V.ja, k);
+  for (int j0 = V.ja; j0 < V.jb; j0 += 16) {
+    // lane 2 m + e: end e of row j0 + m; rows in plane 0 and row 0 whole
+    const int m = lane >> 1, e = lane & 1;
+    const int j = j0 + m;
+    int rsj = rs;
+    for (int t = j0; t < min(j, V.jb); ++t) rsj += w - k - t;
+    if (j < V.jb) {
+      const int len = w - k - j;
+      if (k == 0 || j == 0) {
+        for (int i = e; i < len; i += 2) item_boundary_point<T, OP>(A, V, fw, base, j, rsj, i);
+      } else if (!(e && len == 1)) {
+        item_boundary_point<T, OP>(A, V, fw, base, j, rsj, e ? len - 1 : 0);
+      }
+    }
+    for (int t = j0; t < min(j0 + 16, V.jb); ++t) rs += w - k - t;
+  }
+}
+
 template <typename T, int OP, int PAT>
 __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArgs<T> S) {
   extern __shared__ __align__(128) unsigned char smem[];
   const FusedArgs<T>& A = S.f;
-  const int R = S.R;
+  constexpr int R = kStreamSlots;
+  constexpr int SE = slot_elems<T>();
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
   uint64_t* empty = full + R;
   volatile int* stop = reinterpret_cast<volatile int*>(empty + R);
-  T* ring = reinterpret_cast<T*>(smem + barrier_bytes(R)) + S.guard;
+  volatile int* tag = stop + 4;  // tag[s]: the copy the producer last started in slot s
+  T* ring = reinterpret_cast<T*>(smem + barrier_bytes()) + S.guard;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < R; ++s) {
       mbar_init(&full[s], 1);
-      mbar_init(&empty[s], kSWarps);
+      mbar_init(&empty[s], kStreamArrive);
+      tag[s] = -1;
     }
     *stop = 0;
     mbar_init_fence();
   }
   __syncthreads();
-  const int w = A.w;
-  const int ub = S.cta_begin[blockIdx.x], ue = S.cta_begin[blockIdx.x + 1];
+  const int cb = S.plan.cta_copies[blockIdx.x], ce = S.plan.cta_copies[blockIdx.x + 1];
+  const int ib = S.plan.cta_items[blockIdx.x], ie = S.plan.cta_items[blockIdx.x + 1];
 
   if (warp == kSWarps) {
     // ------------------------------------------------------------ producer
     if (lane != 0) return;
-    {
-      // the interface items of this CTA (read after its runs) into L2
-      const int ib = (int)((int64_t)A.n_items * blockIdx.x / gridDim.x);
-      const int ie = (int)((int64_t)A.n_items * (blockIdx.x + 1) / gridDim.x);
-      if (ie > ib) l2_prefetch(A.items + ib, (uint32_t)(ie - ib) * (uint32_t)sizeof(int4));
-    }
-    int q = 0;
+    int c = 0;
     bool ok = true;
-    for (int u = ub; u < ue && ok; ++u) {
-      const int4 U = S.units[u];
-      const int cell = U.x, j0 = U.y & 0xffff, rows = U.y >> 16;
-      const int k0 = U.z & 0xffff, k1 = U.z >> 16;
-      const int kf = max(k0 - 1, 0), kl = min(k1, w - 1);
-      const T* xc = A.x + (int64_t)cell * A.stride;
-      for (int kk = kf; kk <= kl; ++kk) {
-        const int s = q % R, m = q / R;
-        if (m > 0 && !mbar_wait(&empty[s], (m - 1) & 1, stop)) {
-          ok = false;
-          break;
-        }
-        int ga, ge;
-        staged_range<T>(w, j0, rows, kk, ga, ge);
-        const uint32_t bytes = (uint32_t)(ge - ga) * (uint32_t)sizeof(T);
-        mbar_expect_tx(&full[s], bytes);
-        bulk_g2s(ring + s * S.slot, xc + ga, bytes, &full[s]);
-        ++q;
+    for (; c < ce - cb; ++c) {
+      const int4 C = S.plan.copies[cb + c];
+      const int s = c % R;
+      if (c >= R && !mbar_wait(&empty[s], (c / R - 1) & 1, stop)) {
+        ok = false;
+        break;
       }
+      const uint32_t bytes = (uint32_t)C.z * (uint32_t)sizeof(T);
+      mbar_expect_tx(&full[s], bytes);
+      bulk_g2s(ring + s * SE, A.x + (int64_t)C.x * A.stride + C.y, bytes, &full[s]);
+      __threadfence_block();
+      tag[s] = c;
     }
     if (!ok) {
       atomicCAS(A.err, 0, HG_ERR_TIMEOUT);
       *stop = 1;
     }
     // every copy issued must have landed before the CTA's memory is released
-    for (int t = q > R ? q - R : 0; t < q; ++t) mbar_wait(&full[t % R], (t / R) & 1, nullptr);
+    for (int t = c > R ? c - R : 0; t < c; ++t) mbar_wait(&full[t % R], (t / R) & 1, nullptr);
     return;
   }
 
   // -------------------------------------------------------------- consumers
-  // 1. the runs of this CTA; their chunks go round-robin over the warps
-  int q = 0, cbase = 0;
-  for (int u = ub; u < ue; ++u) {
-    const int4 U = S.units[u];
-    const int cell = U.x, j0 = U.y & 0xffff, rows = U.y >> 16;
-    const int k0 = U.z & 0xffff, k1 = U.z >> 16;
-    const int kf = max(k0 - 1, 0), kl = min(k1, w - 1);
-    const int64_t base = (int64_t)cell * A.stride;
-    T s[kNDir];
-    {
-      const T* Sc = A.sten + (int64_t)cell * 256;
+  // 1. points shared by several cells (interface items), a contiguous share
+  //    per CTA, while the first copies are in flight
+  {
+    const int jb0 = (int)((int64_t)A.n_items * blockIdx.x / gridDim.x);
+    const int je0 = (int)((int64_t)A.n_items * (blockIdx.x + 1) / gridDim.x);
+    for (int it = jb0 + warp; it < je0; it += kSWarps)
+      interface_item<T, is_apply(OP) ? OP_APPLY : OP, false>(A, it, lane);
+  }
+  // 2. the items of this CTA
+  const uint32_t ring_addr = smem_addr(ring);
+  int cur_cell = -1;
+  T s[kNDir];
+  T wdc = T(0);
+  ulonglong2 fw = make_ulonglong2(0, 0);
+  for (int t = ib + warp; t < ie; t += kSWarps) {
+    const int4 I0 = S.plan.items[3 * t], I1 = S.plan.items[3 * t + 1], I2 = S.plan.items[3 * t + 2];
+    ItemView V;
+    V.cell = I0.x;
+    V.k = I0.y;
+    V.ja = I0.z & 0xffff;
+    V.jb = I0.z >> 16;
+    const int c0 = I1.x, cm = I1.y, cp = I1.z;
+    bool ok = copy_wait(full, tag, c0, stop);
+    if (cm >= 0 && cm != c0) ok = ok && copy_wait(full, tag, cm, stop);
+    if (cp >= 0 && cp != c0 && cp != cm) ok = ok && copy_wait(full, tag, cp, stop);
+    if (!ok) {
+      if (lane == 0) {
+        atomicCAS(A.err, 0, HG_ERR_TIMEOUT);
+        *stop = 1;
+      }
+      return;
+    }
+    constexpr int E = (int)sizeof(T);
+    // virtual bases (modulo 2^32: only base + g * E, inside the slot, is used)
+    V.vb0 = ring_addr + (uint32_t)((c0 % R) * SE * E) - (uint32_t)I2.x * (uint32_t)E;
+    V.vbp = cp >= 0 ? ring_addr + (uint32_t)((cp % R) * SE * E) - (uint32_t)I2.z * (uint32_t)E
+                    : V.vb0;
+    V.vbm = cm >= 0 ? ring_addr + (uint32_t)((cm % R) * SE * E) - (uint32_t)I2.y * (uint32_t)E
+                    : V.vb0;
+    if (V.cell != cur_cell) {
+      cur_cell = V.cell;
+      const T* Sc = A.sten + (int64_t)cur_cell * 256;
 #pragma unroll
       for (int d = 0; d < kNDir; ++d) s[d] = __ldg(Sc + d);
+      wdc = (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / s[0] : OP == OP_GS ? T(1) / s[0] : T(0);
+      fw = __ldg(reinterpret_cast<const ulonglong2*>(A.flags + cur_cell * 16));
     }
-    const T wdc = (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / s[0]
-                  : OP == OP_GS                      ? T(1) / s[0]
-                                                     : T(0);
-    for (int k = k0; k < k1; ++k) {
-      const int qk = q + (k - kf);
-      bool ok = true;
-      if (k == k0) {
-        if (k > kf) ok = mbar_wait(&full[(qk - 1) % R], ((qk - 1) / R) & 1, stop);
-        ok = ok && mbar_wait(&full[qk % R], (qk / R) & 1, stop);
-      }
-      if (k < kl) ok = ok && mbar_wait(&full[(qk + 1) % R], ((qk + 1) / R) & 1, stop);
-      if (!ok) {
-        if (lane == 0) {
-          atomicCAS(A.err, 0, HG_ERR_TIMEOUT);
-          *stop = 1;
-        }
-        return;
-      }
-      int ga0, gam, gap, ge;
-      staged_range<T>(w, j0, rows, k, ga0, ge);
-      const T* s0 = ring + (qk % R) * S.slot;
-      const T* sm = s0;
-      const T* sp = s0;
-      if (k > kf) {
-        staged_range<T>(w, j0, rows, k - 1, gam, ge);
-        sm = ring + ((qk - 1) % R) * S.slot;
-      }
-      if (k < kl) {
-        staged_range<T>(w, j0, rows, k + 1, gap, ge);
-        sp = ring + ((qk + 1) % R) * S.slot;
-      }
-      // 32-point chunks of the band's rows in this plane, continuing the
-      // round-robin over the warps from the previous plane
-      const int jn = min(rows, w - k - j0);
-      int it = (warp - cbase % kSWarps + kSWarps) % kSWarps, cb = 0;
-      for (int r = 0; r < jn; ++r) {
-        const int j = j0 + r, len = w - k - j;
-        const int nch = (len + 31) >> 5;
-        if (it < cb + nch) {
-          const int rs0 = row_start(w, j, k);
-          const T* P0 = s0 + (rs0 - ga0);
-          const T* Pp = k < kl ? sp + (rs0 + ntri32(w - k) - j - gap) : P0;
-          const T* Pm = k > kf ? sm + (rs0 - ntri32(w - k + 1) + j - gam) : P0;
-          const bool jk_in = j >= 1 && k >= 1;
-          do {
-            const int i = (it - cb) * 32 + lane;
-            // the 15 neighbours; rows j-1 / j+1 of plane k start at -(len+1) / +len,
-            // row j-1 of plane k+1 at -len, row j+1 of plane k-1 at +len+1
-            const T c = P0[i];
-            const T x1 = P0[i + 1], x2 = P0[i - 1];
-            const T x7 = P0[len + i - 1], x8 = P0[i - len];
-            const T x11 = Pp[i - len], x12 = Pm[len + 1 + i];
-            T acc;
-            if (PAT == kPat7) {
-              const T a0 = s[0] * c + s[1] * x1 + s[2] * x2 + s[7] * x7 + s[8] * x8;
-              acc = a0 + (s[11] * x11 + s[12] * x12);
-            } else {
-              const T x3 = P0[len + i], x4 = P0[i - len - 1];
-              const T x5 = Pp[i], x6 = Pm[i];
-              const T x9 = Pp[i - 1], x10 = Pm[i + 1];
-              const T x13 = Pp[i - len + 1], x14 = Pm[len + i];
-              const T a0 = s[0] * c + s[1] * x1 + s[2] * x2 + s[3] * x3 + s[4] * x4 + s[7] * x7 +
-                           s[8] * x8;
-              const T a1 = s[5] * x5 + s[9] * x9 + s[11] * x11 + s[13] * x13;
-              const T a2 = s[6] * x6 + s[10] * x10 + s[12] * x12 + s[14] * x14;
-              acc = a0 + (a1 + a2);
-            }
-            if (jk_in && i >= 1 && i <= len - 2)
-              stream_out<T, OP>(A, base + rs0 + i, c, acc, wdc);
-            else if (i < len)
-              stream_boundary_point<T, OP>(A, cell, i, j, k, len, P0, Pp, Pm, base + rs0 + i);
-            it += kSWarps;
-          } while (it < cb + nch);
-        }
-        cb += nch;
-      }
-      cbase += cb;
-      // release the slots no later plane of this run reads
-      __syncwarp();
-      if (lane == 0) {
-        if (k > kf) mbar_arrive(&empty[(qk - 1) % R]);
-        if (k == k1 - 1) {
-          mbar_arrive(&empty[qk % R]);
-          if (k < kl) mbar_arrive(&empty[(qk + 1) % R]);
-        }
-      }
+    const int64_t base = (int64_t)V.cell * A.stride;
+    item_interior<T, OP, PAT>(A, V, s, wdc, base, lane);
+    item_boundary<T, OP>(A, V, fw, base, lane);
+    // release the copies this item read
+    __syncwarp();
+    if (lane == 0) {
+      mbar_arrive_cnt(&empty[c0 % R], I0.w & 1023);
+      if (cm >= 0 && cm != c0) mbar_arrive_cnt(&empty[cm % R], (I0.w >> 10) & 1023);
+      if (cp >= 0 && cp != c0 && cp != cm) mbar_arrive_cnt(&empty[cp % R], (I0.w >> 20) & 1023);
     }
-    q += kl - kf + 1;
   }
-
-  // 2. points shared by several cells (interface items): a contiguous share
-  //    per CTA, after the runs, when most of x has passed through L2
-  const int ib = (int)((int64_t)A.n_items * blockIdx.x / gridDim.x);
-  const int ie = (int)((int64_t)A.n_items * (blockIdx.x + 1) / gridDim.x);
-  for (int it = ib + warp; it < ie; it += kSWarps)
-    interface_item<T, is_apply(OP) ? OP_APPLY : OP, false>(A, it, lane);
 }
 
 template <typename T, int OP, int PAT>
@@ -412,12 +492,10 @@ int run_stream(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
   A.dvec = (T*)a.dvec;
   A.cheb_a = (T)a.cheb_a;
   A.err = L.err;
-  S.units = L.sunits;
-  S.cta_begin = L.scta;
-  S.R = ring_slots<T>(L.w);
-  S.slot = slot_elems(L.w);
+  S.plan = L.splan[sizeof(T) == 8 ? HG_F64 : HG_F32];
   S.guard = guard_elems(L.w);
-  const size_t smem = barrier_bytes(S.R) + (size_t)(2 * S.guard + S.R * S.slot) * sizeof(T);
+  const size_t smem =
+      barrier_bytes() + (size_t)(2 * S.guard + kStreamSlots * slot_elems<T>()) * sizeof(T);
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(once, [] {
@@ -429,7 +507,7 @@ int run_stream(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
     set_error("streaming kernel: %zu bytes of shared memory at w = %d", smem, L.w);
     return HG_ERR_UNSUPPORTED;
   }
-  p1_stream_kernel<T, OP, PAT><<<L.n_scta, kSThreads, smem, s>>>(S);
+  p1_stream_kernel<T, OP, PAT><<<S.plan.nctas, kSThreads, smem, s>>>(S);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
@@ -451,6 +529,12 @@ int run_stream_op(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
 
 }  // namespace
 
+bool p1_stream_fits(int w, int dtype) {
+  const size_t e = dtype == HG_F64 ? 8 : 4;
+  return barrier_bytes() + (2 * guard_elems(w)) * e + (size_t)kStreamSlots * kStreamSlotBytes <=
+         227 * 1024;
+}
+
 int launch_p1_stream(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s) {
   if (a.pattern == kPat7)
     return dtype == HG_F64 ? run_stream_op<double, kPat7>(L, a, s)
@@ -468,8 +552,8 @@ extern "C" int hg_stream_layout(int level, int dtype, int* ring_slots, int* slot
     return HG_ERR_INVALID_ARG;
   }
   const int w = (1 << level) + 1;
-  *ring_slots = dtype == HG_F64 ? hg::ring_slots<double>(w) : hg::ring_slots<float>(w);
-  *slot_elems = hg::slot_elems(w);
+  *ring_slots = hg::kStreamSlots;
+  *slot_elems = dtype == HG_F64 ? hg::slot_elems<double>() : hg::slot_elems<float>();
   *guard_elems = hg::guard_elems(w);
   return HG_OK;
 }
