@@ -147,7 +147,7 @@ HG_HD void copy_local_ijk(const IfaceCopy& c, int dim, const int wts[3], int& i,
 constexpr int kStreamSlotBytes = 40 * 1024;
 constexpr int kStreamSlots = 4;
 constexpr int kStreamArrive = 256;
-constexpr int kStreamPiece = 1024;
+constexpr int kStreamPiece = 512;
 struct StreamPlanDev {
   int4* copies;
   int4* items;

@@ -6,7 +6,8 @@
 // plane is one contiguous range, and consecutive whole planes are too.  The
 // 15-point stencil of plane k reads planes k-1, k and k+1.
 //
-//  * One CTA per SM: a producer warp and kSWarps consumer warps.  A plan built
+//  * One CTA per SM: a producer warp and 20 (FP32) or 12 (FP64) consumer
+//    warps.  A plan built
 //    on the host (stream_plan) gives the CTA a contiguous stretch of the
 //    sequence (cell, band of rows, plane), as a list of copies and a list of
 //    items (see hg_internal.h).
@@ -16,16 +17,17 @@
 //    the TMA engine a fixed time of the order of 0.2 us, so copies are made
 //    large: whole planes where a plane fits a slot, several consecutive planes
 //    per copy when they are small.
-//  * Consumer warp w takes items w, w + kSWarps, ...: it waits for the copies
-//    holding planes k-1, k, k+1, forms the item's interior points from shared
-//    memory (32-point chunks of a row, all addresses 32-bit shared addresses),
-//    then its boundary points, writes y to HBM directly, and arrives on the
-//    copies' release barriers.  Every x value crosses HBM once.
+//  * Consumer warp w takes items w, w + W, ... (W warps): it waits for the
+//    copies holding planes k-1, k, k+1, forms the item's interior points from
+//    shared memory (32 columns at a time, marching the item's rows with the
+//    previous row's values kept in registers; 32-bit shared addresses), then
+//    its boundary points, writes y to HBM directly, and arrives on the copies'
+//    release barriers.  Every x value crosses HBM once.
 //  * Points on the cell's boundary that lie on a primitive of this cell only
 //    (boundary faces, edges and vertices) are formed in the pass from the
 //    cell's partial stencil; points shared by several cells (the ghost-layer
-//    exchange of Sec. 2) by the interface items, which the consumer warps run
-//    first, while the first copies are in flight.
+//    exchange of Sec. 2) by the interface items, a contiguous share per CTA
+//    that its consumer warps take after their items.
 //
 // Every wait is bounded (about one second): on expiry the kernel records
 // HG_ERR_TIMEOUT in the hierarchy's error word, the other warps stop at their
@@ -42,8 +44,12 @@
 namespace hg {
 namespace {
 
-constexpr int kSWarps = 16;                    // consumer warps
-constexpr int kSThreads = (kSWarps + 1) * 32;  // and one producer warp
+// Consumer warps (plus one producer warp): as many as the register budget of
+// the stencil allows, the consumers being latency-bound.
+template <typename T>
+__host__ __device__ constexpr int swarps() { return sizeof(T) == 4 ? 20 : 12; }
+template <typename T>
+__host__ __device__ constexpr int sthreads() { return (swarps<T>() + 1) * 32; }
 constexpr unsigned long long kWaitNs = 1000000000ull;
 // Longest suspension of one try_wait (the thread resumes as soon as the
 // phase completes): waiting warps then take no issue slots.
@@ -137,39 +143,30 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile
   return false;
 }
 
-// Shared-memory load from a 32-bit shared address plus a constant byte offset
-// (kept in order after the barrier waits, which are volatile as well).
+// Shared-memory load from a 32-bit shared address plus a constant byte offset.
+// Not volatile, so that loads can be scheduled together; the addresses derive
+// from a token produced after the barrier waits (wait_token), which keeps the
+// loads after them.
 template <int OFF>
 __device__ __forceinline__ float lds(float*, uint32_t a) {
   float v;
-  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
+  asm("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(a), "n"(OFF));
   return v;
 }
 template <int OFF>
 __device__ __forceinline__ double lds(double*, uint32_t a) {
   double v;
-  asm volatile("ld.shared.f64 %0, [%1+%2];" : "=d"(v) : "r"(a), "n"(OFF));
+  asm("ld.shared.f64 %0, [%1+%2];" : "=d"(v) : "r"(a), "n"(OFF));
   return v;
 }
-#define HG_LDS(T, OFF, a) lds<(OFF) * (int)sizeof(T)>((T*)nullptr, (a))
-
-// Wait until stream position q has landed in its slot: first until the
-// producer has started q's copy there (tag), then for the copy's barrier
-// phase.  False after kWaitNs or once *stop is set.
-__device__ __forceinline__ bool slot_wait(uint64_t* full, volatile int* tag, int q, int rmask,
-                                          int rlog, volatile int* stop) {
-  const int s = q & rmask;
-  if (tag[s] != q) {
-    const unsigned long long t0 = global_ns();
-    for (long long it = 0; tag[s] != q; ++it) {
-      if (it >= 8) __nanosleep(32);  // leave the issue slots to the computing warps
-      if ((it & 63) == 63 && (*stop || global_ns() - t0 > kWaitNs)) return false;
-      if (it > (1ll << 40)) return false;
-    }
-  }
-  __threadfence_block();
-  return mbar_wait(&full[s], (q >> rlog) & 1, stop);
+// A zero the compiler cannot see through, produced in program order after
+// the preceding waits.
+__device__ __forceinline__ uint32_t wait_token() {
+  uint32_t z;
+  asm volatile("mov.u32 %0, 0;" : "=r"(z)::"memory");
+  return z;
 }
+#define HG_LDS(T, OFF, a) lds<(OFF) * (int)sizeof(T)>((T*)nullptr, (a))
 
 // The operation's output at stored index g from the stencil sum acc.
 template <typename T, int OP>
@@ -251,8 +248,13 @@ struct ItemView {
   uint32_t vb0, vbp, vbm;
 };
 
-// Interior points (j >= 1, k >= 1, 1 <= i <= len-2) of the item's rows: per
-// row, 32-point chunks; the boundary points are left to item_boundary.
+// Interior points (j >= 1, k >= 1, 1 <= i <= len-2) of the item.  A warp
+// takes 32 columns i at a time and marches the item's rows j: the values of
+// row j (i-1, i, i+1) and of row j-1 (i, i+1) come from the previous step, so
+// a step loads three values of row j+1 and two (seven-point) or six (15-point)
+// of planes k+1 and k-1; row starts and shared addresses advance by warp-
+// uniform amounts (row j+1 starts len elements after row j, len shrinks by 1).
+// The boundary points are left to item_boundary.
 template <typename T, int OP, int PAT>
 __device__ __forceinline__ void item_interior(const FusedArgs<T>& A, const ItemView& V,
                                               const T s[kNDir], T wdc, int64_t base, int lane) {
@@ -260,48 +262,70 @@ __device__ __forceinline__ void item_interior(const FusedArgs<T>& A, const ItemV
   const int w = A.w, k = V.k;
   if (k == 0) return;  // the plane k = 0 is a face of the cell
   const int Tk = ntri32(w - k), Tk1 = ntri32(w - k + 1);
-  int rs = row_start(w, V.ja, k);
-  for (int j = V.ja; j < V.jb; ++j) {
-    const int len = w - k - j;
-    if (j >= 1 && len >= 3) {
-      const uint32_t L = (uint32_t)(len * E);
-      // element i = 1 + lane of row j in planes k, k+1 (row j at rs + T(w-k) - j)
-      // and k-1 (row j at rs - T(w-k+1) + j)
-      uint32_t a0 = V.vb0 + (uint32_t)((rs + 1 + lane) * E);
-      uint32_t ap = V.vbp + (uint32_t)((rs + Tk - j + 1 + lane) * E);
-      uint32_t am = V.vbm + (uint32_t)((rs - Tk1 + j + 1 + lane) * E);
-      int64_t g = base + rs + 1 + lane;
-#pragma unroll 2
-      for (int i0 = 1; i0 <= len - 2; i0 += 32) {
-        // the 15 neighbours; rows j-1 / j+1 of plane k start at -(len+1) / +len,
-        // row j-1 of plane k+1 at -len, row j+1 of plane k-1 at +len+1
-        const T c = HG_LDS(T, 0, a0);
-        const T x1 = HG_LDS(T, 1, a0), x2 = HG_LDS(T, -1, a0);
-        const T x7 = HG_LDS(T, -1, a0 + L), x8 = HG_LDS(T, 0, a0 - L);
-        const T x11 = HG_LDS(T, 0, ap - L), x12 = HG_LDS(T, 1, am + L);
-        T acc;
-        if (PAT == kPat7) {
-          const T a0s = s[0] * c + s[1] * x1 + s[2] * x2 + s[7] * x7 + s[8] * x8;
-          acc = a0s + (s[11] * x11 + s[12] * x12);
-        } else {
-          const T x3 = HG_LDS(T, 0, a0 + L), x4 = HG_LDS(T, -1, a0 - L);
-          const T x5 = HG_LDS(T, 0, ap), x6 = HG_LDS(T, 0, am);
-          const T x9 = HG_LDS(T, -1, ap), x10 = HG_LDS(T, 1, am);
-          const T x13 = HG_LDS(T, 1, ap - L), x14 = HG_LDS(T, 0, am + L);
-          const T a0s = s[0] * c + s[1] * x1 + s[2] * x2 + s[3] * x3 + s[4] * x4 + s[7] * x7 +
-                        s[8] * x8;
-          const T a1 = s[5] * x5 + s[9] * x9 + s[11] * x11 + s[13] * x13;
-          const T a2 = s[6] * x6 + s[10] * x10 + s[12] * x12 + s[14] * x14;
-          acc = a0s + (a1 + a2);
-        }
-        if (i0 + lane <= len - 2) stream_out<T, OP>(A, g, c, acc, wdc);
-        a0 += 32 * E;
-        ap += 32 * E;
-        am += 32 * E;
-        g += 32;
-      }
+  const int j1 = max(V.ja, 1);
+  if (j1 >= V.jb) return;
+  const int len1 = w - k - j1;
+  const int rs1 = row_start(w, j1, k);
+  for (int c0 = 1; c0 <= len1 - 2; c0 += 32) {
+    const int i = c0 + lane;
+    int len = len1, j = j1;
+    uint32_t L = (uint32_t)(len * E);
+    // element i of row j in planes k, k+1 (row j at offset T(w-k) - j from
+    // plane k's row j) and k-1 (at -T(w-k+1) + j)
+    uint32_t a0 = V.vb0 + (uint32_t)((rs1 + i) * E);
+    uint32_t ap = V.vbp + (uint32_t)((rs1 + Tk - j1 + i) * E);
+    uint32_t am = V.vbm + (uint32_t)((rs1 - Tk1 + j1 + i) * E);
+    int64_t g = base + rs1 + i;
+    // row j of plane k at i-1, i, i+1; row j-1 (starts len+1 earlier) at i, i+1
+    T cm1 = HG_LDS(T, -1, a0), c0v = HG_LDS(T, 0, a0), cp1 = HG_LDS(T, 1, a0);
+    T pm_i = HG_LDS(T, 0, a0 - L - E), pm_ip1 = HG_LDS(T, 1, a0 - L - E);
+    // 15-point: plane k+1 row j-1 at i, i+1 (starts len before row j of k+1),
+    // plane k-1 row j at i, i+1
+    T up_i = T(0), up_ip1 = T(0), dn_i = T(0), dn_ip1 = T(0);
+    if (PAT != kPat7) {
+      up_i = HG_LDS(T, 0, ap - L);
+      up_ip1 = HG_LDS(T, 1, ap - L);
+      dn_i = HG_LDS(T, 0, am);
+      dn_ip1 = HG_LDS(T, 1, am);
     }
-    rs += len;
+    for (; j < V.jb && c0 <= len - 2; ++j) {
+      // row j+1 of plane k (starts len after row j) at i-1, i, i+1
+      const T nm1 = HG_LDS(T, -1, a0 + L), n0 = HG_LDS(T, 0, a0 + L), np1 = HG_LDS(T, 1, a0 + L);
+      T acc;
+      if (PAT == kPat7) {
+        // (0,-1,+1): plane k+1 row j-1 at i; (0,+1,-1): plane k-1 row j+1 at i
+        const T x11 = HG_LDS(T, 0, ap - L), x12 = HG_LDS(T, 1, am + L);
+        acc = ((s[0] * c0v + s[1] * cp1) + (s[2] * cm1 + s[7] * nm1)) +
+              ((s[8] * pm_ip1 + s[11] * x11) + s[12] * x12);
+      } else {
+        // plane k+1 row j at i-1, i, i+1; plane k-1 row j+1 at i-1, i, i+1
+        const T q9 = HG_LDS(T, -1, ap), q5 = HG_LDS(T, 0, ap), qp = HG_LDS(T, 1, ap);
+        const T r14 = HG_LDS(T, 0, am + L), r12 = HG_LDS(T, 1, am + L), rp = HG_LDS(T, 2, am + L);
+        const T a0s = s[0] * c0v + s[1] * cp1 + s[2] * cm1 + s[3] * n0 + s[4] * pm_i +
+                      s[7] * nm1 + s[8] * pm_ip1;
+        const T a1 = s[5] * q5 + s[9] * q9 + s[11] * up_i + s[13] * up_ip1;
+        const T a2 = s[6] * dn_i + s[10] * dn_ip1 + s[12] * r12 + s[14] * r14;
+        acc = a0s + (a1 + a2);
+        // next step: plane k+1 row j at i, i+1; plane k-1 row j+1 at i, i+1
+        up_i = q5;
+        up_ip1 = qp;
+        dn_i = r12;
+        dn_ip1 = rp;
+      }
+      if (i <= len - 2) stream_out<T, OP>(A, g, c0v, acc, wdc);
+      // shift the rows: row j-1 <- row j, row j <- row j+1
+      pm_i = c0v;
+      pm_ip1 = cp1;
+      cm1 = nm1;
+      c0v = n0;
+      cp1 = np1;
+      g += len;
+      a0 += L;
+      ap += L - E;
+      am += L + E;
+      --len;
+      L -= E;
+    }
   }
 }
 
@@ -329,33 +353,38 @@ __device__ __forceinline__ void item_boundary_point(const FusedArgs<T>& A, const
   }
 }
 
-// The boundary points of the item: both ends of every row, and all of row
-// j = 0 and of plane k = 0.
+// The boundary points of the item: all of plane k = 0 and of row j = 0 (32
+// points per step), and both ends of every other row (16 rows per step).
 template <typename T, int OP>
 __device__ __forceinline__ void item_boundary(const FusedArgs<T>& A, const ItemView& V,
                                               ulonglong2 fw, int64_t base, int lane) {
   const int w = A.w, k = V.k;
-  int rs = row_start(w, V.ja, k);
-  for (int j0 = V.ja; j0 < V.jb; j0 += 16) {
-    // lane 2 m + e: end e of row j0 + m; rows in plane 0 and row 0 whole
-    const int m = lane >> 1, e = lane & 1;
-    const int j = j0 + m;
-    int rsj = rs;
-    for (int t = j0; t < min(j, V.jb); ++t) rsj += w - k - t;
+  int jfirst = V.ja;
+  if (k == 0 || V.ja == 0) {
+    const int jlast = k == 0 ? V.jb : V.ja + 1;  // whole rows: all of plane 0, else row 0
+    int rs = row_start(w, V.ja, k);
+    for (int j = V.ja; j < jlast; ++j) {
+      const int len = w - k - j;
+      for (int i = lane; i < len; i += 32) item_boundary_point<T, OP>(A, V, fw, base, j, rs, i);
+      rs += len;
+    }
+    jfirst = jlast;
+  }
+  for (int j0 = jfirst; j0 < V.jb; j0 += 16) {
+    // lane 2 m + e: end e of row j0 + m (a row of length 1 has one end)
+    const int j = j0 + (lane >> 1), e = lane & 1;
     if (j < V.jb) {
       const int len = w - k - j;
-      if (k == 0 || j == 0) {
-        for (int i = e; i < len; i += 2) item_boundary_point<T, OP>(A, V, fw, base, j, rsj, i);
-      } else if (!(e && len == 1)) {
-        item_boundary_point<T, OP>(A, V, fw, base, j, rsj, e ? len - 1 : 0);
-      }
+      if (!(e && len == 1))
+        item_boundary_point<T, OP>(A, V, fw, base, j, row_start(w, j, k), e ? len - 1 : 0);
     }
-    for (int t = j0; t < min(j0 + 16, V.jb); ++t) rs += w - k - t;
   }
 }
 
 template <typename T, int OP, int PAT>
-__global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArgs<T> S) {
+__global__ void __launch_bounds__(sthreads<T>(), 1) p1_stream_kernel(
+    const __grid_constant__ StreamArgs<T> S) {
+  constexpr int kSWarps = swarps<T>();
   extern __shared__ __align__(128) unsigned char smem[];
   const FusedArgs<T>& A = S.f;
   constexpr int R = kStreamSlots;
@@ -407,15 +436,7 @@ __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArg
   }
 
   // -------------------------------------------------------------- consumers
-  // 1. points shared by several cells (interface items), a contiguous share
-  //    per CTA, while the first copies are in flight
-  {
-    const int jb0 = (int)((int64_t)A.n_items * blockIdx.x / gridDim.x);
-    const int je0 = (int)((int64_t)A.n_items * (blockIdx.x + 1) / gridDim.x);
-    for (int it = jb0 + warp; it < je0; it += kSWarps)
-      interface_item<T, is_apply(OP) ? OP_APPLY : OP, false>(A, it, lane);
-  }
-  // 2. the items of this CTA
+  // 1. the items of this CTA
   const uint32_t ring_addr = smem_addr(ring);
   int cur_cell = -1;
   T s[kNDir];
@@ -440,11 +461,12 @@ __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArg
       return;
     }
     constexpr int E = (int)sizeof(T);
+    const uint32_t tok = wait_token();
     // virtual bases (modulo 2^32: only base + g * E, inside the slot, is used)
-    V.vb0 = ring_addr + (uint32_t)((c0 % R) * SE * E) - (uint32_t)I2.x * (uint32_t)E;
-    V.vbp = cp >= 0 ? ring_addr + (uint32_t)((cp % R) * SE * E) - (uint32_t)I2.z * (uint32_t)E
+    V.vb0 = ring_addr + tok + (uint32_t)((c0 % R) * SE * E) - (uint32_t)I2.x * (uint32_t)E;
+    V.vbp = cp >= 0 ? ring_addr + tok + (uint32_t)((cp % R) * SE * E) - (uint32_t)I2.z * (uint32_t)E
                     : V.vb0;
-    V.vbm = cm >= 0 ? ring_addr + (uint32_t)((cm % R) * SE * E) - (uint32_t)I2.y * (uint32_t)E
+    V.vbm = cm >= 0 ? ring_addr + tok + (uint32_t)((cm % R) * SE * E) - (uint32_t)I2.y * (uint32_t)E
                     : V.vb0;
     if (V.cell != cur_cell) {
       cur_cell = V.cell;
@@ -464,6 +486,14 @@ __global__ void __launch_bounds__(kSThreads, 1) p1_stream_kernel(const StreamArg
       if (cm >= 0 && cm != c0) mbar_arrive_cnt(&empty[cm % R], (I0.w >> 10) & 1023);
       if (cp >= 0 && cp != c0 && cp != cm) mbar_arrive_cnt(&empty[cp % R], (I0.w >> 20) & 1023);
     }
+  }
+  // 2. points shared by several cells (interface items), a contiguous share
+  //    per CTA, after its items, when most of x has passed through L2
+  {
+    const int jb0 = (int)((int64_t)A.n_items * blockIdx.x / gridDim.x);
+    const int je0 = (int)((int64_t)A.n_items * (blockIdx.x + 1) / gridDim.x);
+    for (int it = jb0 + warp; it < je0; it += kSWarps)
+      interface_item<T, is_apply(OP) ? OP_APPLY : OP, false>(A, it, lane);
   }
 }
 
@@ -507,7 +537,7 @@ int run_stream(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
     set_error("streaming kernel: %zu bytes of shared memory at w = %d", smem, L.w);
     return HG_ERR_UNSUPPORTED;
   }
-  p1_stream_kernel<T, OP, PAT><<<S.plan.nctas, kSThreads, smem, s>>>(S);
+  p1_stream_kernel<T, OP, PAT><<<S.plan.nctas, sthreads<T>(), smem, s>>>(S);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }

@@ -3,9 +3,9 @@ on the CPU (no GPU).
 
 For every CTA of the library's own plan (hg_stream_plan) and shared-memory
 layout (hg_stream_layout) the emulation replays the producer (copy c of the
-CTA into slot c mod R) and the consumers' walk over the items (interior rows
-in 32-point chunks at i = 1 + lane, then the boundary points), with the
-kernel's virtual slot bases.  It checks that:
+CTA into slot c mod R) and the consumers' walk over the items (32 columns at
+a time marching the rows, the loads of each step, then the boundary points),
+with the kernel's virtual slot bases.  It checks that:
   * every bulk copy starts on a 16-byte boundary, stays inside the padded
     cell and fits its slot;
   * an item's copies sit in distinct slots, and every slot phase receives
@@ -118,15 +118,70 @@ def _emulate(level, ncells, nctas, dtype_code):
                     lo, hi = span[dk]
                     assert got.min() >= lo and got.max() < hi, (level, k, j, (di, dj, dk))
 
+            # interior: 32 columns at a time, marching the rows; every load the
+            # kernel issues (also for lanes past a row's end) is in bounds and,
+            # for the points it serves, is the lattice point it stands for
+            def lds(pl, addr, di, dj, i, j, use):
+                """A load of plane k+pl at ring address addr meant for (i+di, j+dj, k+pl)."""
+                assert addr.min() >= lo_bound and addr.max() < hi_bound, (level, g, t)
+                a, bb, c2 = i + di, j + dj, k + pl
+                inc = (a >= 0) & (bb >= 0) & (c2 >= 0) & (a + bb + c2 <= n)
+                chk = use & inc
+                if chk.any():
+                    assert pl in refs
+                    got = addr[chk] - vb[pl]
+                    assert np.array_equal(got, TW[a[chk], bb, c2]), (level, k, j, (di, dj, pl))
+                    lo, hi = span[pl]
+                    assert got.min() >= lo and got.max() < hi
+
+            j1 = max(ja, 1)
+            if k >= 1 and j1 < jb:
+                len1 = w - k - j1
+                rs1 = ix.tw(w, 0, j1, k)
+                Tk, Tk1 = _ntri(w - k), _ntri(w - k + 1)
+                for c0 in range(1, len1 - 1, 32):
+                    i = c0 + lanes
+                    ln, j = len1, j1
+                    a0 = vb[0] + rs1 + i
+                    ap = vb[1] + rs1 + Tk - j1 + i
+                    am = vb[-1] + rs1 - Tk1 + j1 + i
+                    gg = rs1 + i
+                    use = i <= ln - 2
+                    # the first values: row j at i-1, i, i+1, row j-1 at i, i+1; the
+                    # 15-point form's plane k+1 row j-1 and plane k-1 row j at i, i+1
+                    lds(0, a0 - 1, -1, 0, i, j, use)
+                    lds(0, a0, 0, 0, i, j, use)
+                    lds(0, a0 + 1, 1, 0, i, j, use)
+                    lds(0, a0 - ln - 1, 0, -1, i, j, use)
+                    lds(0, a0 - ln, 1, -1, i, j, use)
+                    lds(1, ap - ln, 0, -1, i, j, use)
+                    lds(1, ap - ln + 1, 1, -1, i, j, use)
+                    lds(-1, am, 0, 0, i, j, use)
+                    lds(-1, am + 1, 1, 0, i, j, use)
+                    while j < jb and c0 <= ln - 2:
+                        use = i <= ln - 2
+                        lds(0, a0 + ln - 1, -1, 1, i, j, use)
+                        lds(0, a0 + ln, 0, 1, i, j, use)
+                        lds(0, a0 + ln + 1, 1, 1, i, j, use)
+                        lds(1, ap - ln, 0, -1, i, j, use)
+                        lds(-1, am + ln + 1, 0, 1, i, j, use)
+                        lds(1, ap - 1, -1, 0, i, j, use)
+                        lds(1, ap, 0, 0, i, j, use)
+                        lds(1, ap + 1, 1, 0, i, j, use)
+                        lds(-1, am + ln, -1, 1, i, j, use)
+                        lds(-1, am + ln + 2, 1, 1, i, j, use)
+                        visits[cell, gg[use]] += 1
+                        assert np.array_equal(gg[use], TW[i[use], j, k])
+                        gg = gg + ln
+                        a0 = a0 + ln
+                        ap = ap + ln - 1
+                        am = am + ln + 1
+                        ln -= 1
+                        j += 1
+            # boundary points: whole rows in plane 0 and row 0, row ends elsewhere
             rs = ix.tw(w, 0, ja, k)
             for j in range(ja, jb):
                 ln = w - k - j
-                if k >= 1 and j >= 1 and ln >= 3:
-                    for i0 in range(1, ln - 1, 32):
-                        i = i0 + lanes
-                        valid = i <= ln - 2
-                        visits[cell, rs + i[valid]] += 1
-                        check(i, valid, j, rs, True)
                 ib = np.arange(ln) if (k == 0 or j == 0) else np.array(sorted({0, ln - 1}))
                 visits[cell, rs + ib] += 1
                 check(ib, np.ones(len(ib), bool), j, rs, False)
