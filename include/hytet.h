@@ -237,6 +237,21 @@ int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
  * element matrices on the fly for variable coefficients). */
 int hg_op_create(const hg_hier* hier, int kind, const double* coeff, hg_op** out);
 
+/* Kernel of the P1 constant-stencil operators (apply, residual, Jacobi,
+ * Gauss-Seidel and Chebyshev steps), process-wide, for calls made after it:
+ *   HG_P1_KERNEL_AUTO (default): the streaming kernel (whole planes staged in
+ *     shared memory by bulk copies, one CTA per SM, plus a light exchange
+ *     launch) for FP32 levels of at least 8 Mi stored points; the
+ *     plane-window kernel (one launch) otherwise, where launch latency or
+ *     FP64 arithmetic dominates;
+ *   HG_P1_KERNEL_WINDOWS / HG_P1_KERNEL_STREAM: always that kernel (the
+ *     streaming one falls back to plane windows on levels whose staged
+ *     planes do not fit in shared memory).
+ * Both give the same results up to rounding order.  Other values:
+ * HG_ERR_INVALID_ARG.  Not synchronised with calls in flight. */
+enum { HG_P1_KERNEL_AUTO = 0, HG_P1_KERNEL_WINDOWS = 1, HG_P1_KERNEL_STREAM = 2 };
+int hg_set_p1_kernel(int mode);
+
 /* Class table of the lowest-order Nedelec prolongation (host, needs no GPU).
  * A fine N1 DoF sits at an odd point q of the fine F lattice (the level+1
  * lattice of the fine N1 level); with q = 4p + r, r in {0..3}^3 and class

@@ -88,6 +88,7 @@ SIGNATURES = {
     "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
     "hg_plane_tiles": (_I, [_I, _P, ctypes.POINTER(ctypes.c_int)]),
     "hg_stream_plan": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P]),
+    "hg_set_p1_kernel": (_I, [_I]),
     "hg_stream_layout": (_I, [_I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int)]),
     "hg_p2_anchors": (_I, [_I, _P, _P, ctypes.POINTER(ctypes.c_int)]),
@@ -619,6 +620,14 @@ def plane_tiles(level):
     out = np.zeros((max(n.value, 1), 4), dtype=np.int32)
     _call("hg_plane_tiles", level, out.ctypes.data_as(_P), ctypes.byref(n))
     return out[:n.value]
+
+
+HG_P1_KERNEL_AUTO, HG_P1_KERNEL_WINDOWS, HG_P1_KERNEL_STREAM = 0, 1, 2
+
+
+def set_p1_kernel(mode):
+    """Kernel of the P1 constant-stencil operators for later calls (HG_P1_KERNEL_*)."""
+    _call("hg_set_p1_kernel", mode)
 
 
 def stream_plan(level, ncells, nctas, dtype_code):

@@ -510,6 +510,28 @@ int Hier::build_level(int l) {
   }
   L.n_mitems = (int)mitems.size();
   if (int r = upload(&L.mitems, mitems)) return r;
+  // per item and lane (point pt, copy c = lane - pt C): the copy's stored
+  // index and its class-stencil row cell * 16 + class ({-1, 0}: no copy; items
+  // of primitives with more than 32 copies derive theirs in the kernel)
+  {
+    std::vector<int2> ml((size_t)L.n_mitems * 32, int2{-1, 0});
+    for (int q = 0; q < L.n_mitems; ++q) {
+      const int4 it = mitems[q];
+      const int dim = it.z & 15, C = (it.z >> 4) & 255;
+      if (C > 32) continue;
+      for (int lane = 0; lane < it.w * C && lane < 32; ++lane) {
+        const int pt = lane / C, c = lane - pt * C;
+        int wts[3];
+        prim_point_weights(dim, n, it.y + pt, wts);
+        const IfaceCopy& cp = copies[it.x + c];
+        int i, j, k;
+        copy_local_ijk(cp, dim, wts, i, j, k);
+        const int64_t g = (int64_t)cp.cell * L.cell_stride + tw(w, i, j, k);
+        ml[(size_t)q * 32 + lane] = int2{(int)g, cp.cell * 16 + point_class(n, i, j, k)};
+      }
+    }
+    if (int r = upload(&L.mlanes, ml)) return r;
+  }
   {
     // the streaming kernel's plans, one per element size
     int dev = 0, sms = 0;
@@ -620,7 +642,7 @@ int Hier::build_level(int l) {
   if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
       (L.n_items && (!L.items || !L.item_prim)) ||
       (L.n_citems && !L.citems) || (L.n_ptiles_cell && !L.ptiles) ||
-      (L.n_mitems && !L.mitems) || !L.splan[0].cta_items || !L.splan[1].cta_items ||
+      (L.n_mitems && (!L.mitems || !L.mlanes)) || !L.splan[0].cta_items || !L.splan[1].cta_items ||
       (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
     set_error("internal: level %d device tables incomplete", l);
     return HG_ERR_CUDA;
@@ -739,6 +761,7 @@ Hier::~Hier() {
     cudaFree(L.prim_point_base);
     cudaFree(L.citems);
     cudaFree(L.mitems);
+    cudaFree(L.mlanes);
     for (auto& D : L.splan) {
       cudaFree(D.copies);
       cudaFree(D.items);
@@ -1284,6 +1307,8 @@ int hg_plane_tiles(int level, int* out, int* n_tiles) {
     }
   return HG_OK;
 }
+
+int hg_set_p1_kernel(int mode) { return set_p1_kernel(mode); }
 
 int hg_stream_plan(int level, int ncells, int nctas, int dtype, int* copies, int* items,
                    int* cta_copies, int* cta_items, int* counts) {

@@ -191,6 +191,8 @@ struct LevelDev {
   int n_citems;              //   points); points = floor(32 / ncopies), one lane per copy
   int4* mitems;              // apply items of the primitives with >= 2 copies only
   int n_mitems, n_mitems_inner;  //   (non-Dirichlet first): the streaming kernel's exchange
+  int2* mlanes;              // [n_mitems * 32]: per lane the copy's stored index and
+                             //   cell * 16 + class ({-1, 0}: none; not for > 32 copies)
   StreamPlanDev splan[2];    // the streaming kernel's plans for HG_F32 and HG_F64
   int4* ptiles;              // plane-window tiles of ONE cell (the same for every cell):
   int n_ptiles_cell;         //   (k | windows << 16, lane-0 offset z, j0 << 16 | i0, 0)
@@ -261,6 +263,8 @@ int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStre
 // The streaming form of the constant-stencil operator (a.sten, a.pattern), for
 // levels whose slot ring fits in shared memory (p1_stream_fits).
 bool p1_stream_fits(int w, int dtype);
+// The kernel choice of hg_set_p1_kernel (HG_P1_KERNEL_*).
+int set_p1_kernel(int mode);
 int launch_p1_stream(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s);
 
 // ------------------------------------------------------------------- P2

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -650,10 +651,31 @@ int64_t xfer_warps(int64_t n_rows) { return (n_rows + kXferRows - 1) / kXferRows
 
 }  // namespace
 
+namespace {
+std::atomic<int> g_p1_kernel{HG_P1_KERNEL_AUTO};
+// Stored points from which the streaming kernel pays off in AUTO mode
+// (measured on GB300: 113 vs 134 us per apply at 18 M stored points, 20.6 vs
+// 15.1 us at 2.2 M, FP64 slower at both).
+constexpr int64_t kStreamAutoPoints = int64_t(8) << 20;
+}  // namespace
+
+int set_p1_kernel(int mode) {
+  if (mode != HG_P1_KERNEL_AUTO && mode != HG_P1_KERNEL_WINDOWS && mode != HG_P1_KERNEL_STREAM) {
+    set_error("hg_set_p1_kernel: unknown mode %d", mode);
+    return HG_ERR_INVALID_ARG;
+  }
+  g_p1_kernel.store(mode);
+  return HG_OK;
+}
+
 int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStream_t s) {
-  // constant stencils: the streaming kernel; stored stencils, and levels too
-  // large for the streaming kernel's shared-memory ring: the plane windows
-  if (!a.sst && p1_stream_fits(L.w, dtype)) return launch_p1_stream(L, dtype, a, s);
+  // constant stencils: the streaming kernel or the plane windows (see
+  // hg_set_p1_kernel); stored stencils: the plane windows
+  const int mode = g_p1_kernel.load();
+  const bool stream = !a.sst && p1_stream_fits(L.w, dtype) &&
+                      (mode == HG_P1_KERNEL_STREAM ||
+                       (mode == HG_P1_KERNEL_AUTO && dtype == HG_F32 && L.n_stored >= kStreamAutoPoints));
+  if (stream) return launch_p1_stream(L, dtype, a, s);
   return dtype == HG_F64 ? run_p1_op<double>(L, a, s) : run_p1_op<float>(L, a, s);
 }
 

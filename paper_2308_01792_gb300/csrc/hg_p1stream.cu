@@ -23,11 +23,12 @@
 //    previous row's values kept in registers; 32-bit shared addresses), then
 //    its boundary points, writes y to HBM directly, and arrives on the copies'
 //    release barriers.  Every x value crosses HBM once.
-//  * Points on the cell's boundary that lie on a primitive of this cell only
-//    (boundary faces, edges and vertices) are formed in the pass from the
-//    cell's partial stencil; points shared by several cells (the ghost-layer
-//    exchange of Sec. 2) by the interface items, a contiguous share per CTA
-//    that its consumer warps take after their items.
+//  * Points on the cell's boundary are formed in the pass from the
+//    cell's partial stencil: the whole row where the point lies on a
+//    primitive of this cell only, the cell's partial where several cells share
+//    it.  A second, light launch (the ghost-layer exchange of Sec. 2) adds the
+//    copies' partials of every shared point and writes the operation's output
+//    to all of them.
 //
 // Every wait is bounded (about one second): on expiry the kernel records
 // HG_ERR_TIMEOUT in the hierarchy's error word, the other warps stop at their
@@ -194,9 +195,10 @@ __device__ __forceinline__ void stream_out(const FusedArgs<T>& A, int64_t g, T c
 // stencil is the whole row of the operator.  The band row's plane-k,
 // plane-(k+1) and plane-(k-1) rows j start at P0, Pp and Pm.
 template <typename T, int OP>
-__device__ __noinline__ void stream_boundary_point(const FusedArgs<T>& A, int cell, int i, int j,
-                                                   int k, int len, const T* P0, const T* Pp,
-                                                   const T* Pm, int64_t g) {
+__device__ __forceinline__ void stream_boundary_point(const FusedArgs<T>& A, int cell, int i,
+                                                      int j, int k, int len, const T* P0,
+                                                      const T* Pp, const T* Pm, int64_t g,
+                                                      bool partial, bool owner) {
   const int n = A.n;
   const int cls = (i == len - 1 ? 1 : 0) | (i == 0 ? 2 : 0) | (j == 0 ? 4 : 0) | (k == 0 ? 8 : 0);
   const T c = P0[i];
@@ -215,6 +217,13 @@ __device__ __noinline__ void stream_boundary_point(const FusedArgs<T>& A, int ce
     xv[d] = in ? P[ro + a] : T(0);
   }
   const T acc = dot15<T>(sv, xv);
+  if (partial) {
+    // a point several cells share: this cell's partial sum, which the
+    // interface pass (interface_sum_kernel) adds over the copies; an HG_ADD
+    // apply keeps y in the owner's (first) copy
+    A.y[g] = (OP == kOpApplyAdd && owner) ? A.y[g] + acc : acc;
+    return;
+  }
   const T wd = (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / sv[0] : OP == OP_GS ? T(1) / sv[0]
                                                                                   : T(0);
   stream_out<T, OP>(A, g, c, acc, wd);
@@ -288,6 +297,7 @@ __device__ __forceinline__ void item_interior(const FusedArgs<T>& A, const ItemV
       dn_i = HG_LDS(T, 0, am);
       dn_ip1 = HG_LDS(T, 1, am);
     }
+#pragma unroll 4
     for (; j < V.jb && c0 <= len - 2; ++j) {
       // row j+1 of plane k (starts len after row j) at i-1, i, i+1
       const T nm1 = HG_LDS(T, -1, a0 + L), n0 = HG_LDS(T, 0, a0 + L), np1 = HG_LDS(T, 1, a0 + L);
@@ -329,9 +339,9 @@ __device__ __forceinline__ void item_interior(const FusedArgs<T>& A, const ItemV
   }
 }
 
-// A boundary point (i, j) of the item's plane: a fixed Dirichlet value, a
-// point the interface items form (left alone), or (rare) a single-copy
-// partial row.
+// A boundary point (i, j) of the item's plane: a fixed Dirichlet value, or
+// the cell's partial stencil sum: the whole row where the point has one copy,
+// else a partial that the interface pass adds over the copies.
 template <typename T, int OP>
 __device__ __forceinline__ void item_boundary_point(const FusedArgs<T>& A, const ItemView& V,
                                                     ulonglong2 fw, int64_t base, int j, int rs,
@@ -343,13 +353,14 @@ __device__ __forceinline__ void item_boundary_point(const FusedArgs<T>& A, const
   const int64_t g = base + rs + i;
   if ((f & CF_DIRICHLET) && (!is_apply(OP) || A.mask == HG_MASK_INNER)) {
     A.y[g] = op_scaled(OP) ? HG_LDS(T, 0, V.vb0 + (uint32_t)((rs + i) * E)) : T(0);
-  } else if (!(f & CF_MULTI)) {
+  } else {
     const T* P0 = reinterpret_cast<const T*>(__cvta_shared_to_generic(V.vb0 + (uint32_t)(rs * E)));
     const T* Pp = reinterpret_cast<const T*>(
         __cvta_shared_to_generic(V.vbp + (uint32_t)((rs + ntri32(w - k) - j) * E)));
     const T* Pm = reinterpret_cast<const T*>(
         __cvta_shared_to_generic(V.vbm + (uint32_t)((rs - ntri32(w - k + 1) + j) * E)));
-    stream_boundary_point<T, OP>(A, V.cell, i, j, k, len, P0, Pp, Pm, g);
+    stream_boundary_point<T, OP>(A, V.cell, i, j, k, len, P0, Pp, Pm, g, (f & CF_MULTI) != 0,
+                                 (f & CF_OWNER) != 0);
   }
 }
 
@@ -487,14 +498,92 @@ __global__ void __launch_bounds__(sthreads<T>(), 1) p1_stream_kernel(
       if (cp >= 0 && cp != c0 && cp != cm) mbar_arrive_cnt(&empty[cp % R], (I0.w >> 20) & 1023);
     }
   }
-  // 2. points shared by several cells (interface items), a contiguous share
-  //    per CTA, after its items, when most of x has passed through L2
-  {
-    const int jb0 = (int)((int64_t)A.n_items * blockIdx.x / gridDim.x);
-    const int je0 = (int)((int64_t)A.n_items * (blockIdx.x + 1) / gridDim.x);
-    for (int it = jb0 + warp; it < je0; it += kSWarps)
-      interface_item<T, is_apply(OP) ? OP_APPLY : OP, false>(A, it, lane);
+}
+
+// The operation's output at an interface point from the sum of the copies'
+// partials (sum) and centre weights (diag), read at stored index g (every copy
+// holds the same x, b and d).  OP_CHEB writes the new direction: to this copy,
+// or (all == true) to every copy of the item's point with weights wts.
+template <typename T, int OP>
+__device__ __forceinline__ T interface_output(const FusedArgs<T>& A, int64_t g, T sum, T diag,
+                                              bool all, int first_copy, int C, int dim,
+                                              const int* wts) {
+  if (OP == OP_APPLY || OP == kOpApplyAdd) return sum;
+  if (OP == OP_RESID) return A.b[g] - sum;
+  if (OP == OP_GS) return A.colour[g] == A.gs_colour ? A.x[g] + (A.b[g] - sum) / diag : A.x[g];
+  if (OP == OP_CHEB) {
+    T dn = A.omega * (A.b[g] - sum) / diag;
+    if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[g];
+    if (all) {
+      for (int q = 0; q < C; ++q) {
+        const IfaceCopy cpy = A.copies[first_copy + q];
+        int i, j, k;
+        copy_local_ijk(cpy, dim, wts, i, j, k);
+        A.dvec[(int64_t)cpy.cell * A.stride + tw32(A.w, i, j, k)] = dn;
+      }
+    } else {
+      A.dvec[g] = dn;
+    }
+    return A.x[g] + dn;
   }
+  return A.x[g] + A.omega * (A.b[g] - sum) / diag;
+}
+
+// The ghost-layer exchange (Sec. 2) after the streaming pass: every point of
+// a macro face, edge or vertex shared by several cells holds, in each copy,
+// that cell's partial sum; lane pt * C + c of an interface item reads copy c
+// of point pt (its stored index precomputed per lane), the partials are added
+// in ascending cell order (lane order), and every lane writes the operation's
+// output to its copy, so copies stay bit-identical.  Primitives with more
+// than 32 copies take one lane per point and derive the copies' indices.
+template <typename T, int OP>
+__global__ void __launch_bounds__(256) interface_sum_kernel(const __grid_constant__ FusedArgs<T> A,
+                                                            const int2* __restrict__ lanes) {
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (item >= A.n_items) return;
+  const int4 it = A.items[item];
+  const int dim = it.z & 15, C = (it.z >> 4) & 255;
+  if (C > 32) {
+    // one lane per point, the copies in turn
+    if (lane >= it.w) return;
+    const int n = A.n, w = A.w;
+    int wts[3];
+    prim_weights(dim, n, it.y + lane, wts);
+    T sum = T(0), diag = T(0);
+    int64_t g0 = 0;
+    for (int q = 0; q < C; ++q) {
+      const IfaceCopy cpy = A.copies[it.x + q];
+      int i, j, k;
+      copy_local_ijk(cpy, dim, wts, i, j, k);
+      const int64_t g = (int64_t)cpy.cell * A.stride + tw32(w, i, j, k);
+      if (q == 0) g0 = g;
+      sum += A.y[g];
+      if (op_scaled(OP)) diag += __ldg(A.sten + (int64_t)cpy.cell * 256 + point_class(n, i, j, k) * 16);
+    }
+    const T v = interface_output<T, OP>(A, g0, sum, diag, true, it.x, C, dim, wts);
+    for (int q = 0; q < C; ++q) {
+      const IfaceCopy cpy = A.copies[it.x + q];
+      int i, j, k;
+      copy_local_ijk(cpy, dim, wts, i, j, k);
+      A.y[(int64_t)cpy.cell * A.stride + tw32(w, i, j, k)] = v;
+    }
+    return;
+  }
+  const int2 ln = __ldg(lanes + (int64_t)item * 32 + lane);
+  const bool act = ln.x >= 0;
+  const int64_t g = act ? ln.x : 0;
+  const T mine = act ? A.y[g] : T(0);
+  const T mdiag = op_scaled(OP) && act ? __ldg(A.sten + (int64_t)ln.y * 16) : T(0);
+  // the point's C lanes, ascending copy (= cell) order
+  const int b0 = lane / C * C;
+  T sum = T(0), diag = T(0);
+  for (int q = 0; q < C; ++q) {
+    sum += __shfl_sync(0xffffffffu, mine, (b0 + q) & 31);
+    if (op_scaled(OP)) diag += __shfl_sync(0xffffffffu, mdiag, (b0 + q) & 31);
+  }
+  if (!act) return;
+  A.y[g] = interface_output<T, OP>(A, g, sum, diag, false, 0, 0, 0, nullptr);
 }
 
 template <typename T, int OP, int PAT>
@@ -539,6 +628,10 @@ int run_stream(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
   }
   p1_stream_kernel<T, OP, PAT><<<S.plan.nctas, sthreads<T>(), smem, s>>>(S);
   HG_CUDA(cudaGetLastError());
+  if (A.n_items > 0) {
+    interface_sum_kernel<T, OP><<<(A.n_items + 7) / 8, 256, 0, s>>>(A, L.mlanes);
+    HG_CUDA(cudaGetLastError());
+  }
   return HG_OK;
 }
 
