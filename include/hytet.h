@@ -539,6 +539,22 @@ int hg_mlp_train(hg_mlp* mlp, const void* X, const float* t, int64_t n, int step
 int hg_learn_samples(const hg_op* op, int level, const float* r, const float* xstar,
                      const float* x, double omega, int stride, int offset, void* X, float* t,
                      int64_t* count, void* stream);
+/* One learned smoothing step on `level` of a P1 operator with a stored
+ * diagonal (HG_OP_P1_DIVKGRAD, or its stored-stencil form): with s = D^-1 r
+ * (r = b - A x given, FP32 stored vectors; D the operator's diagonal),
+ *   x_out = x + omega s + N(F)  at macro-cell-interior DoFs, where F holds s
+ *           at the DoF and its 14 lattice neighbours in the cell's own
+ *           directions, in the order (0,0,0), (+-1,0,0), (0,+-1,0),
+ *           (0,0,+-1), +-(-1,1,0), +-(-1,0,1), +-(0,-1,1), +-(1,-1,1), then 0;
+ *   x_out = x + omega s  at the other non-Dirichlet DoFs;  x_out = x  at
+ *           Dirichlet DoFs.
+ * The step V-cycles use with hg_gmg_set_learned, exposed for tests.  x, r,
+ * x_out: device FP32, stored layout; x_out must not alias x or r.  Errors:
+ * HG_ERR_INVALID_ARG, HG_ERR_LEVEL_RANGE, HG_ERR_UNSUPPORTED (no stored
+ * diagonal). */
+int hg_learned_step(const hg_op* op, const hg_mlp* mlp, int level, const float* x,
+                    const float* r, double omega, float* x_out, void* stream);
+
 /* Use `mlp` (NULL: none) for the smoothing steps on the finest level of
  * FP32 V-cycles (hg_vcycle with HG_F32, hg_solve with HG_PREC_MIXED).  In a
  * solve, a refinement step that increases the FP64 residual switches the

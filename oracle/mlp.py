@@ -50,6 +50,17 @@ def forward(W1, W2, w3, X):
     return out, (X, z1, h1, z2, h2)
 
 
+def forward_bf16(W1, W2, w3, X):
+    """The network with the rounding points of the BF16 tensor-core kernels:
+    inputs, W1, W2 and the first hidden layer rounded to bfloat16, w3 to
+    FP32, every sum exact (their FP32 accumulation, emulated in FP64)."""
+    Xb = bf16(X)
+    z1 = Xb @ bf16(np.asarray(W1, dtype=np.float32)).T
+    h1 = bf16(np.maximum(z1, 0.0))
+    z2 = h1 @ bf16(np.asarray(W2, dtype=np.float32)).T
+    return np.maximum(z2, 0.0) @ np.asarray(w3, dtype=np.float32).astype(np.float64)
+
+
 def loss_and_grad(W1, W2, w3, X, t):
     """Mean squared error and its gradient by back-propagation."""
     out, (X, z1, h1, z2, h2) = forward(W1, W2, w3, X)

@@ -72,6 +72,7 @@ SIGNATURES = {
     "hg_mlp_train": (_I, [_P, _P, _P, _L, _I, _L, _D, _PD, _P]),
     "hg_learn_samples": (_I, [_P, _I, _P, _P, _P, _D, _I, _I, _P, _P, _PL, _P]),
     "hg_gmg_set_learned": (_I, [_P, _P]),
+    "hg_learned_step": (_I, [_P, _P, _I, _P, _P, _D, _P, _P]),
     "hg_gmg_learned_fallbacks": (_I, [_P, ctypes.POINTER(ctypes.c_int)]),
     "hg_gmg_clone": (_I, [_P, ctypes.POINTER(_P)]),
     "hg_quadrature_rule": (_I, [_P, _P, ctypes.POINTER(ctypes.c_int)]),
@@ -584,6 +585,14 @@ class MLP:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hg_mlp_destroy(self._h)
             self._h = None
+
+
+def learned_step(op, mlp, level, x, r, x_out, omega, stream=None):
+    """One learned smoothing step x_out = x + omega s + N(s) (hg_learned_step)."""
+    import torch
+    op.hier._vec(level, op.space, torch.float32, x, r, x_out)
+    _call("hg_learned_step", op._h, mlp._h, level, _ptr(x), _ptr(r), omega, _ptr(x_out),
+          _stream(stream))
 
 
 def learn_samples(op, level, r, xstar, x, omega, stride, offset, stream=None):

@@ -131,6 +131,20 @@ int hg_mlp_train(hg_mlp* m, const void* Xbf16, const float* t, int64_t n, int st
   return HG_OK;
 }
 
+int hg_learned_step(const hg_op* op, const hg_mlp* mlp, int level, const float* x,
+                    const float* r, double omega, float* x_out, void* stream) {
+  HG_CHECK(op && mlp && x && r && x_out, HG_ERR_INVALID_ARG, "hg_learned_step: null argument");
+  HG_CHECK(x_out != x && x_out != r, HG_ERR_INVALID_ARG, "hg_learned_step: x_out aliases an input");
+  const Hier* h = op->hier;
+  HG_CHECK(op->space == HG_SPACE_P1, HG_ERR_UNSUPPORTED, "hg_learned_step: P1 operators only");
+  HG_CHECK(level >= h->lmin && level <= h->lmax, HG_ERR_LEVEL_RANGE, "level out of range");
+  HG_CHECK(!op->vinv[HG_F32].empty(), HG_ERR_UNSUPPORTED,
+           "hg_learned_step: operator has no stored diagonal");
+  const LevelDev& L = h->lv[level - h->lmin].dev;
+  return launch_learned_step(L, x, r, (const float*)op->vinv[HG_F32][level - h->lmin],
+                             (float)omega, mlp->params, x_out, (cudaStream_t)stream);
+}
+
 int hg_learn_samples(const hg_op* op, int level, const float* r, const float* xstar,
                      const float* x, double omega, int stride, int offset, void* X, float* t,
                      int64_t* count, void* stream) {

@@ -132,3 +132,104 @@ def test_learned_smoother_gain_over_plain():
     assert res["learned"][1] <= 1e-8 and res["plain"][1] <= 1e-8
     # what the network gains: fewer refinement steps than the plain smoother
     assert res["learned"][0] <= res["plain"][0]
+
+
+# ---------------------------------------------------------------------------
+# the smoothing step and the training samples against the oracle's restatement
+# (oracle/learned.py), on a mesh whose cells list their vertices in permuted
+# order, so that every cell gathers its features in a different lattice frame
+
+def _perm_problem(L=4):
+    from oracle import fem
+    from oracle.mesh import RefinedMesh
+    macro = sg.permuted_cells(sg.kuhn_cube(1), 3)
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), L - 1, L)
+    _, xyz, dirich = H.canonical_info(L)
+    kfun = lambda p: learned.lognormal_coefficient(p, 1000)
+    op = hg.Operator(H, hg.HG_OP_P1_DIVKGRAD, coeff=kfun(xyz))
+    rm = RefinedMesh(macro, L)
+    kv = kfun(rm.xyz)[rm.cells]
+    A = fem.assemble(rm.cells, fem.p1_divkgrad(rm.cell_xyz, kv), rm.n_vertices)
+    return macro, H, op, rm, A.diagonal().copy(), dirich
+
+
+def _gpu_residual(H, op, L, xc, bc):
+    x = H.from_canonical(L, torch.tensor(xc, dtype=torch.float32, device="cuda"))
+    b = H.from_canonical(L, torch.tensor(bc, dtype=torch.float32, device="cuda"))
+    r = H.zeros(L, torch.float32)
+    op.residual(L, x, b, r)
+    return x, r, H.to_canonical(L, r).cpu().double().numpy()
+
+
+def test_learned_step_matches_oracle():
+    from oracle import learned as ol
+    L = 4
+    macro, H, op, rm, D, dirich = _perm_problem(L)
+    xc = sg.uniform_vector(11, rm.n_vertices)
+    bc = sg.uniform_vector(12, rm.n_vertices)
+    xc[dirich] = 0
+    bc[dirich] = 0
+    x, r, rc = _gpu_residual(H, op, L, xc, bc)
+    W1, W2, w3 = om.init_weights(9, scale=2.0)
+    net = hg.MLP(_flat(W1, W2, w3))
+    out = H.zeros(L, torch.float32)
+    hg.learned_step(op, net, L, x, r, out, 0.6)
+    got = H.to_canonical(L, out).cpu().double().numpy()
+    x32 = xc.astype(np.float32).astype(np.float64)
+    ref = ol.learned_step(macro, rm, x32, rc, D, W1, W2, w3, 0.6, forward=om.forward_bf16)
+    corr = ref - ol.learned_step(macro, rm, x32, rc, D, np.zeros_like(W1), np.zeros_like(W2),
+                                 np.zeros_like(w3), 0.6)
+    assert np.abs(corr).max() > 0.05 * np.abs(ref).max()        # the network matters here
+    # FP32 step, bf16 features (a feature may round to the other neighbour of
+    # its bf16 interval when s differs in the last FP32 bits)
+    assert np.abs(got - ref).max() <= 1e-5 * np.abs(ref).max() + 2e-2 * np.abs(corr).max()
+    assert np.array_equal(got[dirich], x32[dirich])
+
+
+@pytest.mark.parametrize("d", [0, 1, 4, 7, 10, 11, 13, 14])
+def test_learned_step_gathers_in_each_cells_frame(d):
+    """A network returning max(F_d, 0), with x = 0 and omega = 0: the step is
+    bf16(max(s, 0)) at the neighbour in local direction d of every
+    cell-interior vertex, 0 elsewhere."""
+    from oracle import learned as ol
+    L = 4
+    macro, H, op, rm, D, dirich = _perm_problem(L)
+    bc = sg.uniform_vector(13, rm.n_vertices)
+    bc[dirich] = 0
+    x, r, rc = _gpu_residual(H, op, L, np.zeros(rm.n_vertices), bc)
+    W1 = np.zeros((32, 16))
+    W1[0, d] = 1.0
+    W2 = np.zeros((32, 32))
+    W2[0, 0] = 1.0
+    w3 = np.zeros(32)
+    w3[0] = 1.0
+    net = hg.MLP(_flat(W1, W2, w3))
+    out = H.zeros(L, torch.float32)
+    hg.learned_step(op, net, L, x, r, out, 0.0)
+    got = H.to_canonical(L, out).cpu().double().numpy()
+    ref = ol.learned_step(macro, rm, np.zeros(rm.n_vertices), rc, D, W1, W2, w3, 0.0,
+                          forward=om.forward_bf16)
+    assert np.count_nonzero(ref) > 0.2 * rm.n_vertices / 8
+    assert np.allclose(got, ref, rtol=2 ** -7, atol=0)
+
+
+def test_learned_samples_match_oracle():
+    from oracle import learned as ol
+    L = 4
+    macro, H, op, rm, D, dirich = _perm_problem(L)
+    xc = sg.uniform_vector(14, rm.n_vertices)
+    bc = sg.uniform_vector(15, rm.n_vertices)
+    xs = sg.uniform_vector(16, rm.n_vertices)
+    for v in (xc, bc, xs):
+        v[dirich] = 0
+    x, r, rc = _gpu_residual(H, op, L, xc, bc)
+    xstar = H.from_canonical(L, torch.tensor(xs, dtype=torch.float32, device="cuda"))
+    for stride, offset in ((1, 0), (3, 1)):
+        X, t = hg.learn_samples(op, L, r, xstar, x, 0.5, stride, offset)
+        Xr, tr = ol.learned_samples(macro, rm, rc, D, xs.astype(np.float32).astype(np.float64),
+                                    xc.astype(np.float32).astype(np.float64), 0.5, stride, offset)
+        Xg = X.float().cpu().double().numpy()
+        tg = t.cpu().double().numpy()
+        assert Xg.shape == Xr.shape
+        assert np.abs(Xg - Xr).max() <= 2 ** -8 * 1.01         # bf16 features of unit vectors
+        assert np.abs(tg - tr).max() <= 1e-4 * np.abs(tr).max()

@@ -1,0 +1,112 @@
+"""Pins of the oracle's learned smoothing step and samples (oracle/learned.py)
+against what fixes them independently of its implementation: a zero network
+is the weighted Jacobi step; a network returning max(F_d, 0) returns s at the
+neighbour found from physical coordinates, for every direction d, on a mesh
+whose cells list their vertices in permuted order (local frames differ from
+cell to cell); positive homogeneity; unit-norm features."""
+import numpy as np
+import pytest
+
+import synthgen as sg
+from oracle import fem
+from oracle import learned as ol
+from oracle import gmg as og
+from oracle import mlp as om
+from oracle.mesh import RefinedMesh, coord_key
+
+MESHES = [(sg.reference_tet(), 4), (sg.permuted_cells(sg.kuhn_cube(1), 3), 3)]
+IDS = ["tet_L4", "cube1perm_L3"]
+
+
+def _level(macro, L):
+    rm = RefinedMesh(macro, L)
+    A = fem.assemble(rm.cells, fem.p1_stiffness(rm.cell_xyz), rm.n_vertices)
+    return rm, A, A.diagonal().copy()
+
+
+def _one_hot(d):
+    """W1 row 0 = e_d, W2[0,0] = 1, w3[0] = 1: N(F) = max(F_d, 0)."""
+    W1 = np.zeros((32, 16))
+    W1[0, d] = 1.0
+    W2 = np.zeros((32, 32))
+    W2[0, 0] = 1.0
+    w3 = np.zeros(32)
+    w3[0] = 1.0
+    return W1, W2, w3
+
+
+@pytest.mark.parametrize("case", range(len(MESHES)), ids=IDS)
+def test_zero_network_is_weighted_jacobi(case):
+    macro, L = MESHES[case]
+    rm, A, D = _level(macro, L)
+    x = sg.uniform_vector(1, rm.n_vertices)
+    b = sg.uniform_vector(2, rm.n_vertices)
+    x[rm.boundary] = 0
+    b[rm.boundary] = 0
+    r = b - A @ x
+    z = np.zeros((32, 16)), np.zeros((32, 32)), np.zeros(32)
+    got = ol.learned_step(macro, rm, x, r, D, *z, 2.0 / 3.0)
+    ii = rm.interior
+    AII = A[ii][:, ii]
+    assert np.allclose(got[ii], og.jacobi(AII, D[ii], x[ii], b[ii], 2.0 / 3.0), rtol=0, atol=1e-13)
+    assert np.array_equal(got[rm.boundary], x[rm.boundary])
+
+
+@pytest.mark.parametrize("case", range(len(MESHES)), ids=IDS)
+def test_one_hot_network_reads_the_neighbour_in_the_cells_frame(case):
+    """With omega = 0 and x = 0 the step is max(s(neighbour), 0) at every
+    cell-interior vertex; the neighbour in local direction (di, dj, dk) is the
+    vertex at physical offset (di (v1-v0) + dj (v2-v0) + dk (v3-v0)) / n."""
+    macro, L = MESHES[case]
+    rm, A, D = _level(macro, L)
+    r = sg.uniform_vector(3, rm.n_vertices)
+    r[rm.boundary] = 0
+    s = np.where(rm.boundary, 0.0, r / D)
+    keys = coord_key(rm.coords, rm.side)
+    V = np.asarray(macro.vertices, dtype=np.int64)
+    pts = ol.cell_interior_points(rm.n)
+    for d, off in enumerate(ol.DIRS):
+        got = ol.learned_step(macro, rm, np.zeros(rm.n_vertices), r, D, *_one_hot(d), 0.0)
+        for c, cell in enumerate(macro.cells):
+            X0, X1, X2, X3 = (V[q] for q in cell)
+            here = X0 * rm.n + pts[:, :1] * (X1 - X0) + pts[:, 1:2] * (X2 - X0) + pts[:, 2:3] * (X3 - X0)
+            step = off[0] * (X1 - X0) + off[1] * (X2 - X0) + off[2] * (X3 - X0)
+            ih = np.searchsorted(keys, coord_key(here, rm.side))
+            inb = np.searchsorted(keys, coord_key(here + step[None], rm.side))
+            assert np.array_equal(got[ih], np.maximum(s[inb], 0.0)), (case, d, c)
+
+
+def test_step_is_positively_homogeneous_in_the_residual():
+    macro, L = MESHES[1]
+    rm, A, D = _level(macro, L)
+    W = om.init_weights(7)
+    x = sg.uniform_vector(4, rm.n_vertices)
+    x[rm.boundary] = 0
+    r = sg.uniform_vector(5, rm.n_vertices)
+    r[rm.boundary] = 0
+    a = ol.learned_step(macro, rm, x, r, D, *W, 0.5) - x
+    b = ol.learned_step(macro, rm, x, 2.5 * r, D, *W, 0.5) - x
+    assert np.allclose(b, 2.5 * a, rtol=1e-12, atol=1e-14)
+
+
+def test_samples_are_normalised_and_count_every_stride():
+    macro, L = MESHES[1]
+    rm, A, D = _level(macro, L)
+    r = sg.uniform_vector(6, rm.n_vertices)
+    r[rm.boundary] = 0
+    x = sg.uniform_vector(7, rm.n_vertices)
+    xs = sg.uniform_vector(8, rm.n_vertices)
+    n_int = len(macro.cells) * len(ol.cell_interior_points(rm.n))
+    for stride, offset in ((1, 0), (3, 2)):
+        X, t = ol.learned_samples(macro, rm, r, D, xs, x, 0.5, stride, offset)
+        assert len(t) == len(range(offset, n_int, stride))
+        assert np.allclose(np.sqrt((X[:, :15] ** 2).sum(axis=1)), 1.0)
+        assert np.all(X[:, 15] == 0)
+    # stride 1: t |F| + omega s(centre) = x* - x at the sampled vertices
+    X, t = ol.learned_samples(macro, rm, r, D, xs, x, 0.5, 1, 0)
+    s = np.where(rm.boundary, 0.0, r / D)
+    feats = ol.features(macro, rm, s)
+    ids = np.concatenate([f[0] for f in feats])
+    F = np.concatenate([f[1] for f in feats])
+    nrm = np.sqrt((F[:, :15] ** 2).sum(axis=1))
+    assert np.allclose(t * nrm + 0.5 * s[ids], xs[ids] - x[ids], atol=1e-12)
