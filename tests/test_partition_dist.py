@@ -1,0 +1,184 @@
+"""Distribution of the macro cells over ranks (Sec. 2: primitives distributed
+over processes, one ghost-layer exchange per application) on the CPU, with
+gloo ranks (world size 2) and no GPU.
+
+The library's partition (hg_partition_cells) and exchange plan
+(hg_exchange_plan) are host code.  Each rank stores only its own cells;
+the per-copy partial sums are taken from the oracle (the assembled matrix of
+each macro cell's own micro-cells), exchanged by gloo point-to-point
+messages along the plan, and summed by the plan's recipe.  Checked: every
+cross-rank point gets the global row of the assembled operator, and the
+plan's order reproduces the single-device order (all copies in ascending
+cell id) bit for bit."""
+import os
+
+import numpy as np
+import pytest
+
+import synthgen as sg
+from oracle import fem
+from oracle.mesh import RefinedMesh
+
+from helpers import oracle_stored_to_canonical
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import paper_2308_01792_gb300 as hg
+
+MESHES = {"cube2": sg.kuhn_cube(2), "cube2perm": sg.permuted_cells(sg.kuhn_cube(2), 7)}
+
+
+def _cell_partials(macro, rm, x):
+    """partial[c] = A_c x: the P1 Laplacian of macro cell c's micro-cells only."""
+    per = 8 ** rm.level
+    Ke = fem.p1_stiffness(rm.cell_xyz)
+    out = []
+    for c in range(len(macro.cells)):
+        sl = slice(c * per, (c + 1) * per)
+        out.append(fem.assemble(rm.cells[sl], Ke[sl], rm.n_vertices) @ x)
+    return out
+
+
+def _local_partials(macro, rm, part, rank, stride, x):
+    """The rank's local stored vector of partials: slot (local cell, t) holds
+    the partial of its own cell at that lattice point."""
+    s2c = oracle_stored_to_canonical(macro, rm, stride)
+    parts = _cell_partials(macro, rm, x)
+    mine = np.flatnonzero(part == rank)
+    y = np.zeros(len(mine) * stride)
+    gids = np.full(len(mine) * stride, -1, dtype=np.int64)
+    for lc, c in enumerate(mine):
+        g = s2c[c * stride:(c + 1) * stride]
+        ok = g >= 0
+        y[lc * stride:(lc + 1) * stride][ok] = parts[c][g[ok]]
+        gids[lc * stride:(lc + 1) * stride] = g
+    return y, gids, parts
+
+
+@pytest.mark.parametrize("nparts", [1, 2, 3, 5, 8, 48])
+def test_partition_is_balanced_and_deterministic(nparts):
+    m = MESHES["cube2"]
+    M = hg.Mesh(m.xyz, m.cells)
+    p = hg.partition_cells(M, nparts)
+    assert np.array_equal(p, hg.partition_cells(M, nparts))
+    cnt = np.bincount(p, minlength=nparts)
+    assert cnt.min() >= 1 and cnt.max() - cnt.min() <= 1, cnt
+    with pytest.raises(hg.HGError):
+        hg.partition_cells(M, 49)
+
+
+def test_bisection_cuts_across_the_longest_extent():
+    """Two parts of the 2x2x2 cube: the cut is a coordinate plane through the
+    middle, so each part is the cells of one half (centroids on one side)."""
+    m = MESHES["cube2"]
+    p = hg.partition_cells(hg.Mesh(m.xyz, m.cells), 2)
+    cen = m.xyz[m.cells].mean(axis=1)
+    assert np.all(cen[p == 0, 0] < 0.5) and np.all(cen[p == 1, 0] > 0.5)
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+@pytest.mark.parametrize("level,nparts", [(1, 2), (2, 2), (2, 3), (3, 4)])
+def test_plan_pairs_and_covers_every_cross_rank_point(name, level, nparts):
+    """Send counts of r to s equal receive counts of s from r; the planned
+    points are exactly the lattice points whose copies lie on two or more
+    ranks (found from the oracle's canonical numbering); every term of a
+    point is one copy, in ascending cell id."""
+    macro = MESHES[name]
+    M = hg.Mesh(macro.xyz, macro.cells)
+    part = hg.partition_cells(M, nparts)
+    rm = RefinedMesh(macro, level)
+    plans = [hg.exchange_plan(M, level, part, r) for r in range(nparts)]
+    stride = plans[0]["stride"]
+    s2c = oracle_stored_to_canonical(macro, rm, stride)
+    for r in range(nparts):
+        for s in range(nparts):
+            assert plans[r]["send_count"][s] == plans[s]["recv_count"][r]
+    # cells holding every canonical point
+    holders = [set() for _ in range(rm.n_vertices)]
+    for c in range(len(macro.cells)):
+        for g in s2c[c * stride:(c + 1) * stride]:
+            if g >= 0:
+                holders[g].add(c)
+    for r in range(nparts):
+        P = plans[r]
+        mine = np.flatnonzero(part == r)
+        gl = lambda li: s2c[mine[li // stride] * stride + li % stride]  # noqa: E731
+        want = sorted(g for g in range(rm.n_vertices)
+                      if len({part[c] for c in holders[g]}) > 1 and
+                      any(part[c] == r for c in holders[g]))
+        got = []
+        for p in range(len(P["point_start"]) - 1):
+            tg = P["target_idx"][P["target_start"][p]:P["target_start"][p + 1]]
+            g = {int(gl(t)) for t in tg}
+            assert len(g) == 1                              # one lattice point
+            g = g.pop()
+            got.append(g)
+            assert len(tg) == sum(part[c] == r for c in holders[g])
+            assert P["point_start"][p + 1] - P["point_start"][p] == len(holders[g])
+        assert sorted(got) == want
+
+
+def _rank_main(rank, port, name, level, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    try:
+        macro = MESHES[name]
+        M = hg.Mesh(macro.xyz, macro.cells)
+        part = hg.partition_cells(M, 2)
+        P = hg.exchange_plan(M, level, part, rank)
+        rm = RefinedMesh(macro, level)
+        x = sg.uniform_vector(77, rm.n_vertices)
+        y, gids, parts = _local_partials(macro, rm, part, rank, P["stride"], x)
+        # the exchange: partials of this rank's copies to the other rank
+        other = 1 - rank
+        sendbuf = torch.tensor(y[P["send_idx"]], dtype=torch.float64)
+        recvbuf = torch.zeros(int(P["recv_count"][other]), dtype=torch.float64)
+        reqs = [dist.isend(sendbuf, other), dist.irecv(recvbuf, other)]
+        for q in reqs:
+            q.wait()
+        recv = recvbuf.numpy()
+        yo = y.copy()
+        for p in range(len(P["point_start"]) - 1):
+            acc = 0.0
+            for src in P["term_src"][P["point_start"][p]:P["point_start"][p + 1]]:
+                acc += y[src] if src >= 0 else recv[-1 - src]
+            yo[P["target_idx"][P["target_start"][p]:P["target_start"][p + 1]]] = acc
+        # single-device order: all copies' partials in ascending cell id
+        ref_order = {}
+        stride = P["stride"]
+        s2c = oracle_stored_to_canonical(macro, rm, stride)
+        for c in range(len(macro.cells)):
+            for g in s2c[c * stride:(c + 1) * stride]:
+                if g >= 0:
+                    ref_order.setdefault(int(g), []).append(c)
+        A = fem.assemble(rm.cells, fem.p1_stiffness(rm.cell_xyz), rm.n_vertices)
+        full = A @ x
+        tg = P["target_idx"]
+        res = {"n_points": len(P["point_start"]) - 1, "exact_order": True, "max_rel": 0.0}
+        for t in tg:
+            g = int(gids[t])
+            acc = 0.0
+            for c in ref_order[g]:
+                acc += parts[c][g]
+            res["exact_order"] &= bool(yo[t] == acc)
+            res["max_rel"] = max(res["max_rel"], abs(yo[t] - full[g]) / np.abs(full).max())
+        out[rank] = res
+    finally:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("name,level", [("cube2", 2), ("cube2perm", 3)])
+def test_two_rank_exchange_reproduces_the_global_apply(name, level):
+    port = 29500 + (os.getpid() + level) % 1000
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.spawn(_rank_main, args=(port, name, level, out), nprocs=2, join=True)
+        res = dict(out)
+    for rank in (0, 1):
+        r = res[rank]
+        assert r["n_points"] > 0
+        assert r["exact_order"], r
+        assert r["max_rel"] <= 1e-13, r
