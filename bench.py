@@ -188,7 +188,7 @@ def cpu_baseline_spmv(seconds=10.0):
         reps += 1
     dt = time.perf_counter() - t0
     return {"value": rm.n_vertices * reps / dt / 1e9, "unit": "GDoF/s", "cores": 1,
-            "kind": "oracle",
+            "kind": "oracle", "host_cores": _host_cores(),
             "sample": f"SciPy CSR SpMV of the same P1 operator on the same mesh at level "
                       f"{SAMPLE_LEVEL} ({rm.n_vertices} DoFs), {reps} reps in {dt:.1f} s"}
 
@@ -216,7 +216,8 @@ def cpu_baseline_gmg(level=ORACLE_GMG_LEVEL):
     _, it, hist = og.solve(H, b, tol=1e-8, max_iter=200)
     solve_s = time.perf_counter() - t0
     n6 = (4 * 64 + 1) ** 3
-    return {"kind": "oracle", "cores": 1, "level": level, "unique_dofs": int(lev.n),
+    return {"kind": "oracle", "cores": 1, "host_cores": _host_cores(), "level": level,
+            "unique_dofs": int(lev.n),
             "assembly_s": setup_s, "solve_s": solve_s, "v_cycles": it, "rel_res": hist[-1],
             "level6_solve_s_extrapolated": solve_s * n6 / lev.n,
             "sample": f"oracle GMG (SciPy CSR, single thread) of the GMG workload's problem at level "
@@ -390,6 +391,10 @@ P2_WORKLOAD = "cube48_L6_p2_sinprod"
 P2_FLOPS_PER_CELL = 14 * 2 * (3 + 1 + 4 + 16 + 20 + 16)
 # FP32 CUDA-core peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x max SM clock
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP32 operations per micro-cell of the element-wise P1 -div(k grad) apply
+# (scatter form, the minimum): k_T = mean of 4 vertex values (4), y_T = K x_T
+# (16 FMA = 32), scaled by k_T (4)
+DIVKGRAD_FLOPS_PER_CELL = 4 + 32 + 4
 
 
 def p2_comparison(stream, level=6, solve=True):
@@ -543,18 +548,17 @@ def n1_solve_comparison(stream, level=6, m=2):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     G = hg.GMG(op, nu1=2, nu2=2, omega=0.5, lmin=1, inner_cycles=INNER_CYCLES)
-    for name, prec, warm in (("mixed_f32_ir", hg.HG_PREC_MIXED, True),
-                             ("plain_f64", hg.HG_PREC_F64, False)):
+    for name, prec in (("mixed_f32_ir", hg.HG_PREC_MIXED), ("plain_f64", hg.HG_PREC_F64)):
         x = H.zeros(level, torch.float64, space=P2)
-        if warm:
-            G.solve(x, b, tol=1e-8, max_iter=100, precision=prec, stream=stream, check=False)
-            torch.cuda.synchronize()
+        G.solve(x, b, tol=1e-8, max_iter=100, precision=prec, stream=stream, check=False)
+        torch.cuda.synchronize()                                  # warm-up, then from x = 0
+        x.zero_()
         e0.record(stream)
         it, rel = G.solve(x, b, tol=1e-8, max_iter=100, precision=prec, stream=stream, check=False)
         e1.record(stream)
         torch.cuda.synchronize()
         out[name] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel,
-                     "timed_after_warmup": warm}
+                     "timed_after_warmup": True}
     out["mixed_vs_f64_speedup"] = out["plain_f64"]["s"] / out["mixed_f32_ir"]["s"]
     del G
     G = hg.GMG(op, nu1=1, nu2=1, omega=0.5, lmin=1)
@@ -637,6 +641,22 @@ def kernels_comparison(stream):
             rec("dot_f32", tm(lambda: H.dot(L, x, b, stream=stream), 10), 2 * w * nu,
                 "includes the host read of the result")
         del x, b, y
+    # the copy ceiling: a device-to-device copy moving the apply's algorithmic
+    # bytes (4 B read + 4 B written per unique DoF) at both sizes, HBM-cold
+    # (rotating buffers), CUDA events over 20 copies after 3 warm-up
+    n1u = (1 * (1 << LEVEL) + 1) ** 3
+    for name, cnt in (("copy_ceiling_cube6_L7", n1u), ("copy_ceiling_cube384_L6", nu)):
+        nb = max(2, int(np.ceil(4 * 129e6 / (8 * cnt))))         # > 4x L2 in all
+        src = [torch.empty(cnt, dtype=torch.float32, device="cuda").fill_(1.0) for _ in range(nb)]
+        dst = [torch.empty_like(v) for v in src]
+        it = iter(range(1 << 30))
+
+        def cp():
+            q = next(it) % nb
+            dst[q].copy_(src[q])
+        rec(name, tm(cp), 8 * cnt, "torch copy_ (library kernel) of the apply's bytes: the "
+                                   "device-side ceiling at this size")
+        del src, dst
     # the headline apply with x and y resident in L2
     m1 = sg.kuhn_cube(1)
     H1 = hg.Hierarchy(hg.Mesh(m1.xyz, m1.cells), LEVEL, LEVEL)
@@ -702,6 +722,18 @@ def stencil_comparison(stream, m=4, L=6, solve=True):
     out["stored"]["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                                  "frac": ach / peak, "peak_source": f"{kind} hbm_gbs",
                                  "algorithmic_bytes_per_launch": bytes_st}
+    # on the fly: x, y and k (FP32) once per unique DoF; per micro-cell the
+    # element-wise form's k_T (3 adds + 1 multiply), the 4x4 element row
+    # products (16 FMA) and the scaling of the 4 results by k_T
+    t_fly = out["onthefly"]["apply_us"] * 1e-6
+    micro = len(macro.cells) * 8 ** L
+    gbs_fly = 12 * nu / t_fly / 1e9
+    tf_fly = DIVKGRAD_FLOPS_PER_CELL * micro / t_fly / 1e12
+    out["onthefly"]["roofline"] = {
+        "bound": "alu", "achieved": tf_fly, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+        "frac": tf_fly / FP32_PEAK_TFLOPS, "flops_per_micro_cell": DIVKGRAD_FLOPS_PER_CELL,
+        "hbm": {"achieved": gbs_fly, "peak": peak, "unit": "GB/s", "frac": gbs_fly / peak,
+                "algorithmic_bytes_per_launch": 12 * nu, "peak_source": f"{kind} hbm_gbs"}}
     out["stored_vs_onthefly_apply_speedup"] = out["onthefly"]["apply_us"] / out["stored"]["apply_us"]
     if not solve:
         return out
@@ -721,6 +753,299 @@ def stencil_comparison(stream, m=4, L=6, solve=True):
         out[name]["mixed_solve_cheb2_v11" if cheb else "mixed_solve"] = {
             "s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel}
         del G
+    return out
+
+
+LEARNED_WORKLOAD = "learned_smoother_kernels"
+# Tensor-core work of the network per sample: layer 1 (16 x 32) and layer 2
+# (32 x 32) multiply-adds, 2 flops each; the gradient adds dW2, dH1 and dW1
+# (32 x 32, 32 x 32, 16 x 32 multiply-adds).
+MLP_FWD_TC_FLOPS = 2 * (16 * 32 + 32 * 32)
+MLP_GRAD_TC_FLOPS = MLP_FWD_TC_FLOPS + 2 * (32 * 32 + 32 * 32 + 16 * 32)
+
+
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def learned_kernels_comparison(stream, m=4, L=6, samples=1 << 22):
+    """The learned smoother's BF16 tensor-core kernels on their own: the
+    forward pass over `samples` FP32 feature rows (16 per sample), the
+    gradient over as many BF16 rows (with its partial sums and the host read
+    of the 1568 gradient values), and one learned smoothing step on the
+    m^3 x 6 Kuhn cube at level L (FP32 x, r and the inverse diagonal of the
+    log-normal -div(k grad) operator).  Per kernel: CUDA-event time per call
+    (mean of 10 after 3 warm-up), bytes that must cross HBM and tensor-core
+    flops against the measured bf16 peak."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    peak_hbm, kind = _peaks()
+    peak_tc, kind_tc = _bf16_peak()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    net = hg.MLP(np.load(WEIGHTS)) if os.path.exists(WEIGHTS) else hg.MLP(
+        sg.uniform_vector(3, hg.N_MLP_PARAMS) * 0.2)
+    X = torch.rand(samples, 16, device="cuda", generator=g) * 2 - 1
+    Xb = X.to(torch.bfloat16)
+    t = torch.rand(samples, device="cuda", generator=g)
+    out_f = torch.empty(samples, device="cuda")
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+
+    def tm(f, K=10):
+        for _ in range(3):
+            f()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(K):
+            f()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / K * 1e-3
+
+    def rec(tsec, nbytes, tc_flops):
+        gbs, tf = nbytes / tsec / 1e9, tc_flops / tsec / 1e12
+        return {"us": tsec * 1e6, "hbm": {"achieved": gbs, "peak": peak_hbm, "unit": "GB/s",
+                                          "frac": gbs / peak_hbm, "bytes": int(nbytes)},
+                "tensor": {"achieved": tf, "peak": peak_tc, "unit": "TFLOP/s",
+                           "frac": tf / peak_tc, "flops": int(tc_flops),
+                           "peak_source": f"{kind_tc} bf16_tflops"}}
+
+    out = {"workload": LEARNED_WORKLOAD, "samples": samples,
+           "mma": "mma.sync m16n8k16 bf16 -> f32"}
+    out["mlp_forward"] = rec(tm(lambda: net.forward(X, out=out_f, stream=stream)),
+                             samples * (64 + 4), samples * MLP_FWD_TC_FLOPS)
+    out["mlp_grad"] = rec(tm(lambda: net.grad(Xb, t, stream=stream)), samples * (32 + 4),
+                          samples * MLP_GRAD_TC_FLOPS)
+    out["mlp_grad"]["note"] = "includes the partial-sum pass and the host read of the gradient"
+    del X, Xb, t, out_f
+    macro = sg.kuhn_cube(m)
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), L, L)
+    _, xyz, _ = H.canonical_info(L)
+    k = sg.rff_eval_torch(sg.rff_params(1000), xyz, dtype=torch.float32)
+    op = hg.Operator(H, hg.HG_OP_P1_DIVKGRAD, coeff=k)
+    ns, nu, _, _ = H.size(L)
+    x = H.from_canonical(L, torch.tensor(sg.uniform_vector(41, nu), dtype=torch.float32,
+                                         device="cuda"))
+    r = H.from_canonical(L, torch.tensor(sg.uniform_vector(42, nu), dtype=torch.float32,
+                                         device="cuda"))
+    xo = torch.empty_like(x)
+    n = 1 << L
+    interior = len(macro.cells) * (n - 1) * (n - 2) * (n - 3) // 6     # cell-interior DoFs
+    ts = tm(lambda: hg.learned_step(op, net, L, x, r, xo, 2.0 / 3.0, stream=stream))
+    out["learned_step"] = rec(ts, 16 * ns, interior * MLP_FWD_TC_FLOPS)
+    out["learned_step"].update({"mesh": f"cube{len(macro.cells)}_L{L}", "stored_points": int(ns),
+                                "cell_interior_dofs": int(interior)})
+    return out
+
+
+def _host_cores():
+    """Cores of this host as the process sees them (affinity), and in all."""
+    try:
+        usable = len(os.sched_getaffinity(0))
+    except AttributeError:
+        usable = os.cpu_count()
+    return {"usable": usable, "total": os.cpu_count()}
+
+
+def _oracle_threads():
+    """Threads the oracle's SciPy/NumPy calls use: CSR products are single
+    threaded; dense BLAS (the coarse solve) may use the BLAS pool."""
+    return 1
+
+
+def _manufactured_rhs(H, mass, level, stream, dtype=None):
+    """b = M I_h f (interior rows, Dirichlet rows 0) of f = 3 pi^2 sin(pi x)
+    sin(pi y) sin(pi z), with the library's P1 mass operator; returns
+    (b stored FP64, u = I_h u canonical, xyz, dirichlet mask)."""
+    import torch
+    _, xyz, dirich = H.canonical_info(level)
+    u = np.prod(np.sin(np.pi * xyz), axis=1)
+    f = 3 * np.pi ** 2 * u
+    b = H.zeros(level, torch.float64)
+    mass.apply(level, H.from_canonical(level, torch.tensor(f, device="cuda")), b, stream=stream)
+    return b, u, xyz, dirich
+
+
+REFTET_WORKLOAD = "reftet_L4_p1_poisson_f64"
+
+
+def reftet_comparison(stream, level=4, reps=100):
+    """The reference tetrahedron (0,0,0),(1,0,0),(0,1,0),(0,0,1) refined to
+    level 4 (n = 16, 969 vertex DoFs), P1 Poisson with zero Dirichlet values,
+    FP64: (a) 100 operator applications to a seeded U[-1,1] vector (CUDA
+    events around the 100 launches; the apply is launch-bound at this size),
+    (b) GMG V(3,3), weighted Jacobi 2/3, coarsest level 2, from x = 0 to 1e-10
+    relative residual with b = M I_h f, f = 3 pi^2 sin(pi x) sin(pi y) sin(pi z)
+    (not zero on the slanted face; the solve is defined all the same).  The
+    oracle (SciPy CSR, one thread) does the same work on the host, timed
+    beside it, and gives the parity of both results."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    from oracle import gmg as og
+    macro = sg.reference_tet()
+    H = hg.Hierarchy(hg.Mesh(macro.xyz, macro.cells), 2, level)
+    op = hg.Operator(H)
+    mass = hg.Operator(H, hg.HG_OP_P1_MASS)
+    ns, nu, ni, _ = H.size(level)
+    _, xyz, dirich = H.canonical_info(level)
+    xc = sg.uniform_vector(31, nu)
+    xc[dirich] = 0.0
+    x = H.from_canonical(level, torch.tensor(xc, device="cuda"))
+    y = H.zeros(level, torch.float64)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(10):
+        op.apply(level, x, y, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        op.apply(level, x, y, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_mv = e0.elapsed_time(e1) * 1e-3
+    yg = H.to_canonical(level, y).cpu().numpy()
+    Ho = og.Hierarchy(macro, 2, level)
+    lev = Ho.levels[level]
+    ii = lev.interior
+    xi = xc[ii]
+    yo = lev.A @ xi
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        yo = lev.A @ xi
+    t_mv_cpu = time.perf_counter() - t0
+    out = {"workload": REFTET_WORKLOAD, "unique_dofs": int(nu), "interior_dofs": int(ni),
+           "matvecs": {"count": reps, "gpu_s": t_mv, "us_per_matvec": t_mv / reps * 1e6,
+                       "gdof_per_s": nu * reps / t_mv / 1e9,
+                       "max_rel_err_vs_oracle": float(np.abs(yg[ii] - yo).max() / np.abs(yo).max()),
+                       "oracle_s": t_mv_cpu, "oracle_threads": _oracle_threads(),
+                       "note": "launch-bound: 969 DoFs per launch"}}
+    b, u, _, _ = _manufactured_rhs(H, mass, level, stream)
+    G = hg.GMG(op)
+    xs = H.zeros(level, torch.float64)
+    G.solve(xs, b, tol=1e-10, max_iter=100, stream=stream)          # warm-up
+    torch.cuda.synchronize()
+    xs.zero_()
+    e0.record(stream)
+    it, rel = G.solve(xs, b, tol=1e-10, max_iter=100, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    xg = H.to_canonical(level, xs).cpu().numpy()[ii]
+    bo = H.to_canonical(level, b).cpu().numpy()[ii]
+    t0 = time.perf_counter()
+    xo, ito, _ = og.solve(Ho, bo, tol=1e-10)
+    t_cpu = time.perf_counter() - t0
+    out["vcycle_solve"] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel,
+                           "smoother": "weighted Jacobi 2/3, V(3,3), coarsest level 2",
+                           "rel_diff_vs_oracle_solution": float(np.linalg.norm(xg - xo) /
+                                                                np.linalg.norm(xo)),
+                           "oracle_s": t_cpu, "oracle_iters": ito,
+                           "oracle_threads": _oracle_threads()}
+    out["host_cores"] = _host_cores()
+    return out
+
+
+CUBE6_WORKLOAD = "cube6_L7_p1_poisson_sweeps_and_solve"
+
+
+def cube6_comparison(stream, level=LEVEL, series=(3, 4, 5, 6, 7), oracle_levels=(3, 4, 5)):
+    """The headline mesh (unit cube as 6 Kuhn macro-tetrahedra, level 7,
+    129^3 DoFs, P1 Poisson, zero Dirichlet values): the FP64 apply sweep
+    HBM-cold (32 rotating x/y pairs, 1.1 GB), the GMG V(3,3) solve of the
+    manufactured problem u = sin(pi x) sin(pi y) sin(pi z) to 1e-10 (FP64
+    cycles, and FP32 cycles in FP64 refinement), and the discretisation
+    error ||I_h u - u_h||_M for levels 3..7 (ratios near 4 for O(h^2)), the
+    oracle's errors beside it on the levels it finishes in seconds."""
+    import torch
+    import paper_2308_01792_gb300 as hg
+    from oracle import gmg as og
+    macro = sg.kuhn_cube(1)
+    mesh = hg.Mesh(macro.xyz, macro.cells)
+    peak, kind = _peaks()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    H = hg.Hierarchy(mesh, 1, level)
+    op = hg.Operator(H)
+    mass = hg.Operator(H, hg.HG_OP_P1_MASS)
+    ns, nu, ni, _ = H.size(level)
+    _, _, dirich = H.canonical_info(level)
+    out = {"workload": CUBE6_WORKLOAD, "unique_dofs": int(nu), "stored_dofs": int(ns)}
+    xs, ys = [], []
+    for p in range(N_PAIRS):
+        c = sg.uniform_vector(2000 + p, nu)
+        c[dirich] = 0.0
+        xs.append(H.from_canonical(level, torch.tensor(c, device="cuda")))
+        ys.append(H.zeros(level, torch.float64))
+    for q in range(3):
+        op.apply(level, xs[q], ys[q], stream=stream)
+    torch.cuda.synchronize()
+    K = 64
+    e0.record(stream)
+    for q in range(K):
+        op.apply(level, xs[q % N_PAIRS], ys[q % N_PAIRS], stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / K * 1e-3
+    gbs = 16 * nu / t / 1e9
+    out["apply_f64"] = {"us": t * 1e6, "gdof_per_s": nu / t / 1e9,
+                        "l2": f"{N_PAIRS} rotating x/y pairs, {N_PAIRS * 2 * ns * 8 / 1e9:.1f} GB",
+                        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                     "frac": gbs / peak, "peak_source": f"{kind} hbm_gbs",
+                                     "algorithmic_bytes_per_launch": 16 * nu}}
+    del xs, ys
+    b, u, _, _ = _manufactured_rhs(H, mass, level, stream)
+    for name, prec in (("plain_f64", hg.HG_PREC_F64), ("mixed_f32_ir", hg.HG_PREC_MIXED)):
+        G = hg.GMG(op, inner_cycles=INNER_CYCLES)
+        x = H.zeros(level, torch.float64)
+        G.solve(x, b, tol=1e-10, max_iter=100, precision=prec, stream=stream)   # warm-up
+        torch.cuda.synchronize()
+        x.zero_()
+        e0.record(stream)
+        it, rel = G.solve(x, b, tol=1e-10, max_iter=100, precision=prec, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[name + "_solve"] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel,
+                                "smoother": "weighted Jacobi 2/3, V(3,3), coarsest level 1",
+                                "timed_after_warmup": True}
+        del G
+    del H, op, mass
+    # discretisation error series
+    errs = {}
+    for L in series:
+        HL = hg.Hierarchy(mesh, 1, L)
+        opL = hg.Operator(HL)
+        mL = hg.Operator(HL, hg.HG_OP_P1_MASS)
+        bL, uL, _, _ = _manufactured_rhs(HL, mL, L, stream)
+        G = hg.GMG(opL)
+        x = HL.zeros(L, torch.float64)
+        G.solve(x, bL, tol=1e-10, max_iter=100, stream=stream)
+        e = x - HL.from_canonical(L, torch.tensor(uL, device="cuda"))
+        Me = HL.zeros(L, torch.float64)
+        mL.apply(L, e, Me, mask=hg.HG_MASK_ALL, stream=stream)
+        errs[L] = float(np.sqrt(max(HL.dot(L, e, Me, mask=hg.HG_MASK_ALL), 0.0)))
+        del G, HL, opL, mL
+    ser = {"levels": list(series), "l2_mass_norm_err": [errs[L] for L in series],
+           "ratios": [errs[a] / errs[b] for a, b in zip(series[:-1], series[1:])]}
+    oerr, t0 = [], time.perf_counter()
+    for L in oracle_levels:
+        Ho = og.Hierarchy(macro, 1, L)
+        lev = Ho.levels[L]
+        uo = np.prod(np.sin(np.pi * lev.xyz), axis=1)
+        bo = (lev.M_full @ (3 * np.pi ** 2 * uo))[lev.interior]
+        xo, _, _ = og.solve(Ho, bo, tol=1e-10)
+        eo = -uo
+        eo[lev.interior] += xo
+        oerr.append(float(np.sqrt(eo @ (lev.M_full @ eo))))
+    ser["oracle"] = {"levels": list(oracle_levels), "l2_mass_norm_err": oerr,
+                     "s": time.perf_counter() - t0, "threads": _oracle_threads()}
+    ser["max_rel_diff_vs_oracle"] = float(max(abs(errs[L] - e) / e for L, e in
+                                              zip(oracle_levels, oerr)))
+    out["l2_error_series"] = ser
+    out["host_cores"] = _host_cores()
     return out
 
 
@@ -767,6 +1092,14 @@ def make_parser():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-gmg", action="store_true")
+    ap.add_argument("--no-reftet", action="store_true")
+    ap.add_argument("--no-learned-kernels", action="store_true")
+    ap.add_argument("--learned-samples", type=int, default=1 << 22,
+                    help="samples of the learned-kernel leg (smaller for profiling)")
+    ap.add_argument("--only", default=None,
+                    help="comma-separated legs to run besides the headline apply (e.g. "
+                         "learned_kernels,cube6); the others are skipped")
+    ap.add_argument("--no-cube6", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-p2", action="store_true")
     ap.add_argument("--no-stencil", action="store_true")
@@ -785,6 +1118,12 @@ def make_parser():
 
 def main():
     args = make_parser().parse_args()
+    if args.only is not None:
+        keep = set(args.only.split(","))
+        for leg in ("gmg", "batch", "p2", "stencil", "kernels", "n1", "n1_solve", "reftet",
+                    "cube6", "learned_kernels", "cpu_baseline"):
+            if leg not in keep:
+                setattr(args, "no_" + leg, True)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -849,54 +1188,48 @@ def main():
                          f"({ms:.1f} ms) and the region itself")
     ms_step, value = aggregate_replicas(ms, nu, args.steps, pg, "cuda")
 
-    # end to end through the public API: every step copies its canonical input
-    # from pinned host memory, scatters it to the stored layout, applies the
-    # operator, gathers the result and copies it to pinned host memory.  Steps
-    # are pipelined over three buffer sets and three streams (H2D, compute,
-    # D2H), so one step's copies overlap the neighbouring steps' kernels.
+    # end to end through the public API with host buffers: every step copies
+    # its canonical input from pinned host memory into a function of the
+    # library (hg_function_copy_canonical: host -> device, then every stored
+    # copy set), applies the operator to the functions (hg_apply_function)
+    # and copies the result back (one value per DoF gathered, device -> host).
+    # Steps rotate over three streams, each with its own pair of functions
+    # and host buffers, so that one step's copies overlap the neighbouring
+    # steps' kernels.
     NB = 3
-    s_in, s_c, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
-    x0h = torch.tensor(sg.uniform_vector(7, nu), dtype=dt)
-    x0h[torch.from_numpy(dirich.astype(bool))] = 0
+    e2e_streams = [torch.cuda.Stream() for _ in range(NB)]
+    x0 = sg.uniform_vector(7, nu).astype(np.float32)
+    x0[dirich] = 0.0
     bufs = []
     for _ in range(NB):
-        bufs.append({"xh": x0h.clone().pin_memory(), "yh": torch.empty(nu, dtype=dt).pin_memory(),
-                     "xd": torch.empty(nu, dtype=dt, device="cuda"),
-                     "yd": torch.empty(nu, dtype=dt, device="cuda"),
-                     "xs": H.zeros(LEVEL, dt), "ys": H.zeros(LEVEL, dt),
-                     "ein": torch.cuda.Event(), "eout": torch.cuda.Event(),
-                     "efree": torch.cuda.Event()})
-    for b in bufs:
-        b["efree"].record(s_out)
+        bufs.append({"xh": torch.from_numpy(x0.copy()).pin_memory(),
+                     "yh": torch.empty(nu, dtype=dt).pin_memory(),
+                     "x": hg.Function(H, dt, levels=[LEVEL]), "y": hg.Function(H, dt, levels=[LEVEL])})
     e2e_steps = max(12, args.steps // 4)
 
     def e2e_step(q):
-        b = bufs[q % NB]
-        s_in.wait_event(b["efree"])
-        with torch.cuda.stream(s_in):
-            b["xd"].copy_(b["xh"], non_blocking=True)
-        b["ein"].record(s_in)
-        s_c.wait_event(b["ein"])
-        H.from_canonical(LEVEL, b["xd"], out=b["xs"], stream=s_c)
-        op.apply(LEVEL, b["xs"], b["ys"], stream=s_c)
-        H.to_canonical(LEVEL, b["ys"], stream=s_c, out=b["yd"])
-        b["eout"].record(s_c)
-        s_out.wait_event(b["eout"])
-        with torch.cuda.stream(s_out):
-            b["yh"].copy_(b["yd"], non_blocking=True)
-        b["efree"].record(s_out)
+        b, s = bufs[q % NB], e2e_streams[q % NB]
+        b["x"].copy_from_host(LEVEL, b["xh"], stream=s)
+        op.apply_function(LEVEL, b["x"], b["y"], stream=s)
+        b["y"].copy_to_host(LEVEL, b["yh"], stream=s)
 
     for q in range(2 * NB):
         e2e_step(q)
     torch.cuda.synchronize()
-    e0.record(s_in)
+    e0.record(stream)
+    for s in e2e_streams:
+        s.wait_event(e0)
     for q in range(e2e_steps):
         e2e_step(q)
-    e1.record(s_out)
+    for s in e2e_streams:
+        ev = torch.cuda.Event()
+        ev.record(s)
+        stream.wait_event(ev)
+    e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / e2e_steps
     ref_y = torch.zeros(nu, dtype=dt, device="cuda")
-    H.to_canonical(LEVEL, bufs[0]["ys"], out=ref_y)
+    H.to_canonical(LEVEL, bufs[0]["y"][LEVEL], out=ref_y)
     if not torch.equal(bufs[0]["yh"], ref_y.cpu()):
         raise RuntimeError("e2e: host result differs from the device result")
 
@@ -917,12 +1250,20 @@ def main():
                      "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch":
                          BYTES_PER_DOF * nu},
         "e2e": {"value": nu / (e2e_ms * 1e-3) / 1e9, "unit": "GDoF/s",
-                "h2d_bytes_per_step": 4 * nu, "d2h_bytes_per_step": 4 * nu},
+                "h2d_bytes_per_step": 4 * nu, "d2h_bytes_per_step": 4 * nu,
+                "path": "hg_function_copy_canonical (pinned host -> device) + hg_apply_function "
+                        "+ hg_function_copy_canonical (device -> pinned host), 3 streams"},
         "gpu_launches": args.steps,
         "clocks": clk,
     }
+    if rank == 0 and not args.no_reftet:
+        out["reftet"] = reftet_comparison(stream)
+    if rank == 0 and not args.no_cube6:
+        out["cube6"] = cube6_comparison(stream)
     if rank == 0 and not args.no_gmg:
         out["gmg"] = gmg_comparison(stream)
+    if rank == 0 and not args.no_learned_kernels:
+        out["learned_kernels"] = learned_kernels_comparison(stream, samples=args.learned_samples)
     if rank == 0 and not args.no_batch:
         out["batch"] = batch_comparison(stream)
     if rank == 0 and not args.no_p2:

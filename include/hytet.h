@@ -80,7 +80,7 @@ enum {
                             stored point kept in HBM (16 values per stored DoF
                             and level: 15 weights and the inverse centre weight;
                             FP64 and FP32 copies) and streamed by the apply     */
-  HG_OP_N1_CURLCURL = 7  /* lowest-order Nedelec (first kind) alpha curl curl +
+  HG_OP_N1_CURLCURL = 7, /* lowest-order Nedelec (first kind) alpha curl curl +
                             beta I, coeff = {alpha >= 0, beta > 0}: one DoF per
                             micro-edge (tangential line integral, oriented from
                             the lower to the higher canonical vertex key),
@@ -88,6 +88,8 @@ enum {
                             points (vertex points stay 0); element-wise 6x6
                             matrices; apply, residual, Jacobi and Chebyshev
                             steps; multigrid with Hiptmair smoothing           */
+  HG_OP_P1_DIVKGRAD_SURROGATE = 8 /* HG_OP_P1_DIVKGRAD with polynomial surrogate
+                            stencils (Sec. 5.2): made by hg_op_create_surrogate */
 };
 
 typedef struct hg_mesh hg_mesh;
@@ -154,6 +156,88 @@ int hg_to_canonical(const hg_hier* hier, int space, int level, int dtype, const 
                     void* canonical, void* stream);
 int hg_from_canonical(const hg_hier* hier, int space, int level, int dtype,
                       const void* canonical, void* stored, void* stream);
+
+/* ------------------------------------------------------------- functions --
+ * A finite-element function on a level range (Sec. 5.1: one vector per level
+ * of the hierarchy).  hg_function_create makes an empty function of `space`
+ * and element type `dtype` (HG_F32/HG_F64) on the levels of `hier`; the
+ * function keeps a pointer to the hierarchy, which must outlive it.
+ * hg_function_bind attaches the caller's device buffer dev_ptr (a stored
+ * vector of that level, at least n_stored elements of dtype, 16-byte
+ * aligned; NULL unbinds) to `level`; the library never frees it.
+ * hg_function_data returns the bound pointer (NULL if none).
+ * Errors: HG_ERR_INVALID_ARG (null handle, short or unaligned buffer, bad
+ * dtype), HG_ERR_LEVEL_RANGE, HG_ERR_UNSUPPORTED (space). */
+typedef struct hg_func hg_func;
+int hg_function_create(const hg_hier* hier, int space, int dtype, hg_func** out);
+void hg_function_destroy(hg_func* f);
+int hg_function_bind(hg_func* f, int level, void* dev_ptr, int64_t nbytes);
+int hg_function_data(const hg_func* f, int level, void** dev_ptr);
+
+/* Copy the function's vector on `level` to or from HOST memory in canonical
+ * order (one value per unique DoF, the order of hg_canonical_info).
+ *   host       : n values of host_dtype (HG_F32/HG_F64); pinned memory makes
+ *                the call fully asynchronous, pageable memory is allowed
+ *   n          : must equal the level's n_unique
+ *   dir        : HG_COPY_FROM_HOST: host -> device, then every stored copy of
+ *                a DoF set (padding untouched); HG_COPY_TO_HOST: one value
+ *                per DoF gathered, then device -> host
+ * A host dtype other than the function's is converted on the device
+ * (rounding to nearest).  Stream-ordered on `stream`: a TO_HOST result is in
+ * `host` once the stream has been synchronised.  The first copy on a level
+ * allocates the function's staging buffer (n_unique * 8 bytes, so it must
+ * not be the first inside a stream capture); copies of one function on one
+ * level share that buffer, so the caller orders them (one stream, or events).
+ * Errors: HG_ERR_INVALID_ARG (n, dtype, direction, unbound level),
+ * HG_ERR_LEVEL_RANGE, HG_ERR_UNSUPPORTED (no exact lattice), HG_ERR_CUDA. */
+enum { HG_COPY_TO_HOST = 0, HG_COPY_FROM_HOST = 1 };
+int hg_function_copy_canonical(hg_func* f, int level, void* host, int host_dtype, int64_t n,
+                               int dir, void* stream);
+
+/* hg_apply on the functions' bound vectors of `level` (same hierarchy and
+ * space as the operator, same element type; x and y distinct functions). */
+int hg_apply_function(const hg_op* op, int level, const hg_func* x, hg_func* y, int mode, int mask,
+                      void* stream);
+
+/* ------------------------------------------------ distribution over ranks --
+ * (Sec. 2: macro primitives distributed over processes, one ghost-layer
+ * exchange per operator application.)  Host only; no device is touched.
+ *
+ * hg_partition_cells: part[c] in 0..nparts-1 for each macro cell c (nc int32,
+ * caller-owned): recursive coordinate bisection of the cell centroids (cut
+ * along the longest extent, cells ordered by that coordinate, then the
+ * others, then id; set sizes in proportion to the parts on either side).
+ * Deterministic.  HG_ERR_INVALID_ARG unless 1 <= nparts <= nc.
+ *
+ * hg_exchange_plan: what rank `rank` sends, receives and sums on `level`
+ * when each rank stores only its own cells, in ascending global cell id,
+ * with the single-device cell stride (local stored index = local cell *
+ * stride + t_{n+1}(i,j,k)).  The points planned are the interface points
+ * whose copies lie on two or more ranks, this rank's among them, in a fixed
+ * global order (faces, edges, vertices in mesh order, points in primitive
+ * order).  After a local application that leaves at those points the
+ * partial sum of each copy's own cell, the rank
+ *   - sends to rank r the partials at send_idx[off_r .. off_r+send_count[r])
+ *     (off_r = sum of the counts of ranks below r): its copies of the points
+ *     it shares with r, point by point, copies in ascending cell id;
+ *   - receives recv_count[r] partials from r in r's matching order, the
+ *     buffers of all ranks concatenated by ascending rank;
+ *   - for point p, sums the terms point_start[p] .. point_start[p+1]-1 in
+ *     that order (all copies in ascending global cell id): term_src >= 0 is a
+ *     local stored index, term_src = -(1 + s) is slot s of the concatenated
+ *     receive buffer; and writes the sum to the local stored indices
+ *     target_idx[target_start[p] .. target_start[p+1]-1] (its own copies).
+ * This is the summation order of the single-device kernels, so the result
+ * is identical.  sizes (host int64[6]) receives: number of send entries,
+ * receive entries, points, terms, targets and the cell stride; call with the
+ * arrays NULL to size them (send_count, recv_count: nparts entries;
+ * point_start, target_start: points + 1).  Errors: HG_ERR_INVALID_ARG,
+ * HG_ERR_LEVEL_RANGE (level outside 0..9). */
+int hg_partition_cells(const hg_mesh* mesh, int nparts, int32_t* part);
+int hg_exchange_plan(const hg_mesh* mesh, int level, const int32_t* part, int nparts, int rank,
+                     int64_t sizes[6], int64_t* send_count, int64_t* send_idx,
+                     int64_t* recv_count, int64_t* point_start, int64_t* term_src,
+                     int64_t* target_start, int64_t* target_idx);
 
 /* Synchronise `stream` and report whether any kernel of this hierarchy gave
  * up a bounded wait (HG_ERR_TIMEOUT; the word is then cleared).  Kernels
@@ -236,6 +320,26 @@ int hg_interface_dump(const hg_hier* hier, int space, int level, int64_t* out,
  * (Sec. 5.2: constant-coefficient stencils precomputed per macro primitive,
  * element matrices on the fly for variable coefficients). */
 int hg_op_create(const hg_hier* hier, int kind, const double* coeff, hg_op** out);
+
+/* Surrogate operator of -div(k grad) (Sec. 5.2, surrogate operators: the
+ * stencil weights of a variable-coefficient operator vary smoothly over a
+ * macro cell and are replaced by low-degree polynomials of the position).
+ * Per level, macro cell and stencil direction d (the 15 lattice directions),
+ * the exact weights A[p, p+d] at the cell's interior points p = (i, j, k)
+ * (i, j, k >= 1, i + j + k <= n - 1) are fitted by least squares with the
+ * polynomials of total degree <= `degree` in (i/n, j/n, k/n); interior rows
+ * use the fitted weights, every other row (points on macro faces, edges,
+ * vertices) stays exact (element-wise, as HG_OP_P1_DIVKGRAD).  When a level
+ * has too few interior points to fix every coefficient, the fit is the
+ * least-squares projection onto the polynomials the points separate (the
+ * fitted values are unique).  k as for HG_OP_P1_DIVKGRAD; degree 0..4, else
+ * HG_ERR_INVALID_ARG.  The fit runs once per level in FP64 on the device
+ * (a QR factorisation of the polynomial basis at the interior points on the
+ * host, the projections of the weights on the device); the polynomials are
+ * evaluated on the fly, per lattice row by Horner's rule in i.  Apply,
+ * residual, Jacobi, Gauss-Seidel and Chebyshev steps and multigrid work as
+ * for the other P1 kinds; the diagonal is the surrogate's own. */
+int hg_op_create_surrogate(const hg_hier* hier, const double* k, int degree, hg_op** out);
 
 /* Kernel of the P1 constant-stencil operators (apply, residual, Jacobi,
  * Gauss-Seidel and Chebyshev steps), process-wide, for calls made after it:
@@ -430,6 +534,11 @@ int hg_vcycle(hg_gmg* g, int level, int dtype, void* x, const void* b, void* str
  * HG_ERR_NOT_CONVERGED when the cap is reached (x holds the last iterate). */
 int hg_solve(hg_gmg* g, int precision, double* x, const double* b, double rel_tol, int max_iter,
              int* iters, double* rel_res, void* stream);
+
+/* hg_solve on the functions' bound vectors of the finest level lmax (FP64
+ * functions of the operator's hierarchy and space). */
+int hg_solve_function(hg_gmg* g, int precision, hg_func* x, const hg_func* b, double rel_tol,
+                      int max_iter, int* iters, double* rel_res, void* stream);
 
 /* Relative residuals of the last solve (entry 0 = 1 for x = 0); *n gets the
  * count, at most cap values are written to out (host). */

@@ -23,6 +23,7 @@ HG_MASK_INNER, HG_MASK_ALL = 0, 1
 HG_OP_P1_LAPLACE, HG_OP_P1_MASS, HG_OP_P1_DIVKGRAD = 0, 1, 2
 HG_OP_P1_DIVKGRAD_STORED = 6
 HG_OP_N1_CURLCURL = 7
+HG_OP_P1_DIVKGRAD_SURROGATE = 8
 HG_OP_P2_LAPLACE, HG_OP_P2_MASS, HG_OP_P2_DIVKGRAD = 3, 4, 5
 
 _P = ctypes.c_void_p
@@ -44,11 +45,21 @@ SIGNATURES = {
     "hg_canonical_info": (_I, [_P, _I, _I, _P, _P, _P]),
     "hg_to_canonical": (_I, [_P, _I, _I, _I, _P, _P, _P]),
     "hg_from_canonical": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+    "hg_function_create": (_I, [_P, _I, _I, ctypes.POINTER(_P)]),
+    "hg_function_destroy": (None, [_P]),
+    "hg_function_bind": (_I, [_P, _I, _P, _L]),
+    "hg_function_data": (_I, [_P, _I, ctypes.POINTER(_P)]),
+    "hg_function_copy_canonical": (_I, [_P, _I, _P, _I, _L, _I, _P]),
+    "hg_apply_function": (_I, [_P, _I, _P, _P, _I, _I, _P]),
+    "hg_solve_function": (_I, [_P, _I, _P, _P, _D, _I, ctypes.POINTER(ctypes.c_int), _PD, _P]),
     "hg_index_tw": (_I, [_L, _L, _L, _L, _PL]),
     "hg_index_enumerate": (_I, [_L, _P, _P]),
     "hg_interface_dump": (_I, [_P, _I, _I, _P, _PL, _PL, _P]),
     "hg_op_create": (_I, [_P, _I, _P, ctypes.POINTER(_P)]),
     "hg_op_destroy": (None, [_P]),
+    "hg_op_create_surrogate": (_I, [_P, _P, _I, ctypes.POINTER(_P)]),
+    "hg_partition_cells": (_I, [_P, _I, _P]),
+    "hg_exchange_plan": (_I, [_P, _I, _P, _I, _I, _P, _P, _P, _P, _P, _P, _P, _P]),
     "hg_apply": (_I, [_P, _I, _I, _P, _P, _I, _I, _P]),
     "hg_residual": (_I, [_P, _I, _I, _P, _P, _P, _P]),
     "hg_jacobi": (_I, [_P, _I, _I, _D, _P, _P, _P, _P]),
@@ -101,6 +112,7 @@ SIGNATURES = {
 }
 
 HG_BATCH_GRAPH, HG_BATCH_AUTOTUNE = 1, 2
+HG_COPY_TO_HOST, HG_COPY_FROM_HOST = 0, 1
 
 HG_PREC_F64, HG_PREC_MIXED = 0, 1
 HG_SMOOTH_JACOBI, HG_SMOOTH_GS, HG_SMOOTH_CHEB = 0, 1, 2
@@ -189,6 +201,33 @@ class Mesh:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.hg_mesh_destroy(self._h)
             self._h = None
+
+
+def partition_cells(mesh: "Mesh", nparts):
+    """Part (0..nparts-1) of every macro cell (hg_partition_cells; host only)."""
+    part = np.empty(mesh.n_cells, dtype=np.int32)
+    _call("hg_partition_cells", mesh._h, int(nparts), part.ctypes.data_as(_P))
+    return part
+
+
+def exchange_plan(mesh: "Mesh", level, part, rank):
+    """hg_exchange_plan of `rank` on `level` (host only) as NumPy arrays."""
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    nparts = int(part.max()) + 1 if part.size else 1
+    sz = np.zeros(6, dtype=np.int64)
+    args = (mesh._h, int(level), part.ctypes.data_as(_P), nparts, int(rank))
+    _call("hg_exchange_plan", *args, sz.ctypes.data_as(_P), *([None] * 7))
+    ns, nr, npt, nt, ntg, stride = (int(v) for v in sz)
+    out = {"send_count": np.zeros(nparts, np.int64), "send_idx": np.zeros(ns, np.int64),
+           "recv_count": np.zeros(nparts, np.int64), "point_start": np.zeros(npt + 1, np.int64),
+           "term_src": np.zeros(nt, np.int64), "target_start": np.zeros(npt + 1, np.int64),
+           "target_idx": np.zeros(ntg, np.int64)}
+    _call("hg_exchange_plan", *args, sz.ctypes.data_as(_P),
+          *[out[k].ctypes.data_as(_P) for k in ("send_count", "send_idx", "recv_count",
+                                                 "point_start", "term_src", "target_start",
+                                                 "target_idx")])
+    out["stride"] = stride
+    return out
 
 
 class Hierarchy:
@@ -307,15 +346,76 @@ class Hierarchy:
             self._h = None
 
 
+def _host_ptr(a, n):
+    """Data pointer and element code of a contiguous host array (NumPy or a CPU
+    torch tensor, float32/float64) of exactly n values."""
+    if isinstance(a, np.ndarray):
+        if not a.flags.c_contiguous or a.dtype not in (np.float32, np.float64) or a.size != n:
+            raise ValueError(f"expected a contiguous float32/float64 array of {n} values")
+        return ctypes.c_void_p(a.ctypes.data), (HG_F64 if a.dtype == np.float64 else HG_F32)
+    if a.is_cuda or not a.is_contiguous() or a.numel() != n:
+        raise ValueError(f"expected a contiguous host tensor of {n} values")
+    return ctypes.c_void_p(a.data_ptr()), _dtype_code(a)
+
+
+class Function:
+    """A finite-element function on the levels of a hierarchy (Sec. 5.1): one
+    stored vector per level, bound through the C ABI (the tensors are kept
+    alive here), with copies from and to host memory in canonical order."""
+
+    def __init__(self, hier: Hierarchy, dtype, space=HG_SPACE_P1, levels=None):
+        import torch
+        h = _P()
+        self.dtype = dtype
+        code = HG_F64 if dtype == torch.float64 else HG_F32
+        _call("hg_function_create", hier._h, space, code, ctypes.byref(h))
+        self._h = h
+        self.hier, self.space = hier, space
+        self._t = {}
+        top = hier.lmax - (1 if space == HG_SPACE_P2 else 0)
+        for level in (levels if levels is not None else range(hier.lmin, top + 1)):
+            self.bind(level, hier.zeros(level, dtype, space))
+
+    def bind(self, level, t):
+        ns = self.hier.size(level, self.space)[0]
+        if t.dtype != self.dtype:
+            raise TypeError(f"vector of dtype {t.dtype} where {self.dtype} is expected")
+        _call("hg_function_bind", self._h, level, _ptr(t, ns), t.element_size() * t.numel())
+        self._t[level] = t
+
+    def __getitem__(self, level):
+        return self._t[level]
+
+    def copy_from_host(self, level, host, stream=None):
+        """Host values in canonical order -> every stored copy on `level`."""
+        nu = self.hier.size(level, self.space)[1]
+        p, code = _host_ptr(host, nu)
+        _call("hg_function_copy_canonical", self._h, level, p, code, nu, HG_COPY_FROM_HOST,
+              _stream(stream))
+
+    def copy_to_host(self, level, host, stream=None):
+        """One value per unique DoF of `level` into `host` (canonical order);
+        valid once `stream` has been synchronised."""
+        nu = self.hier.size(level, self.space)[1]
+        p, code = _host_ptr(host, nu)
+        _call("hg_function_copy_canonical", self._h, level, p, code, nu, HG_COPY_TO_HOST,
+              _stream(stream))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.hg_function_destroy(self._h)
+            self._h = None
+
+
 class Operator:
     """A matrix-free operator (Sec. 5.2) on every level of a hierarchy."""
 
-    def __init__(self, hier: Hierarchy, kind=HG_OP_P1_LAPLACE, coeff=None):
+    def __init__(self, hier: Hierarchy, kind=HG_OP_P1_LAPLACE, coeff=None, degree=None):
         h = _P()
         carr = None
         if coeff is not None:
             carr = np.ascontiguousarray(coeff, dtype=np.float64).ravel()
-            if kind in (HG_OP_P1_DIVKGRAD, HG_OP_P1_DIVKGRAD_STORED):
+            if kind in (HG_OP_P1_DIVKGRAD, HG_OP_P1_DIVKGRAD_STORED, HG_OP_P1_DIVKGRAD_SURROGATE):
                 need = hier.size(hier.lmax)[1]     # k at the unique vertices of level lmax
             elif kind in (HG_OP_P2_DIVKGRAD, HG_OP_N1_CURLCURL):
                 need = 2                           # {a, b} / {alpha, beta}
@@ -324,8 +424,14 @@ class Operator:
             if carr.size != need:
                 raise ValueError(f"operator kind {kind} takes {need} coefficient values, "
                                  f"got {carr.size}")
-        _call("hg_op_create", hier._h, kind, carr.ctypes.data_as(_P) if carr is not None else None,
-              ctypes.byref(h))
+        if kind == HG_OP_P1_DIVKGRAD_SURROGATE:
+            if degree is None or carr is None:
+                raise ValueError("the surrogate operator takes the coefficient k and a degree")
+            _call("hg_op_create_surrogate", hier._h, carr.ctypes.data_as(_P), int(degree),
+                  ctypes.byref(h))
+        else:
+            _call("hg_op_create", hier._h, kind,
+                  carr.ctypes.data_as(_P) if carr is not None else None, ctypes.byref(h))
         self._h = h
         self.hier = hier
         self.kind = kind
@@ -338,6 +444,10 @@ class Operator:
         self.hier._vec(level, self.space, x.dtype, x, y)
         _call("hg_apply", self._h, level, _dtype_code(x), _ptr(x), _ptr(y), mode, mask,
               _stream(stream))
+
+    def apply_function(self, level, x: Function, y: Function, mode=HG_REPLACE,
+                       mask=HG_MASK_INNER, stream=None):
+        _call("hg_apply_function", self._h, level, x._h, y._h, mode, mask, _stream(stream))
 
     def residual(self, level, x, b, r, stream=None):
         self.hier._vec(level, self.space, x.dtype, x, b, r)
@@ -438,6 +548,14 @@ class GMG:
                            ctypes.byref(rel), _stream(stream))
         if r != 0 and (check or r != -5):
             raise HGError("hg_solve", r, lib().hg_last_error().decode())
+        return it.value, rel.value
+
+    def solve_function(self, x: Function, b: Function, tol=1e-8, max_iter=100,
+                       precision=HG_PREC_F64, stream=None):
+        it = ctypes.c_int()
+        rel = ctypes.c_double()
+        _call("hg_solve_function", self._h, precision, x._h, b._h, tol, max_iter,
+              ctypes.byref(it), ctypes.byref(rel), _stream(stream))
         return it.value, rel.value
 
     def set_learned(self, mlp=None):

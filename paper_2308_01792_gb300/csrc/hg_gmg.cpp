@@ -511,6 +511,7 @@ Gmg::~Gmg() {
 using namespace hg;
 
 struct hg_gmg : Gmg {};
+struct hg_func : Func {};
 struct hg_op : Op {};
 struct hg_mlp : Mlp {};
 
@@ -645,6 +646,24 @@ int hg_solve(hg_gmg* g, int precision, double* x, const double* b, double rel_to
     return HG_ERR_INVALID_ARG;
   }
   return g->solve(precision, x, b, rel_tol, max_iter, iters, rel_res, (cudaStream_t)stream);
+}
+
+int hg_solve_function(hg_gmg* g, int precision, hg_func* x, const hg_func* b, double rel_tol,
+                      int max_iter, int* iters, double* rel_res, void* stream) {
+  if (!g || !x || !b || x == b) {
+    set_error("hg_solve_function: null or identical functions");
+    return HG_ERR_INVALID_ARG;
+  }
+  if (x->hier != g->hier || b->hier != g->hier || x->space != g->op->space ||
+      b->space != g->op->space || x->dtype != HG_F64 || b->dtype != HG_F64) {
+    set_error("hg_solve_function: x and b must be FP64 functions of the operator's space");
+    return HG_ERR_INVALID_ARG;
+  }
+  void* xp = x->data(g->lmax);
+  const void* bp = b->data(g->lmax);
+  if (!xp || !bp) return HG_ERR_INVALID_ARG;
+  return hg_solve(g, precision, (double*)xp, (const double*)bp, rel_tol, max_iter, iters, rel_res,
+                  stream);
 }
 
 int hg_gmg_set_learned(hg_gmg* g, const hg_mlp* mlp) {

@@ -930,6 +930,10 @@ int Op::build(const Hier* h, int kind_, const double* coeff) {
     if (int r = build_divkgrad(coeff)) return r;
     return build_stored();
   }
+  if (kind == HG_OP_P1_DIVKGRAD_SURROGATE) {
+    set_error("HG_OP_P1_DIVKGRAD_SURROGATE operators are made by hg_op_create_surrogate");
+    return HG_ERR_INVALID_ARG;
+  }
   if (kind != HG_OP_P1_LAPLACE && kind != HG_OP_P1_MASS) {
     set_error("operator kind %d not available in this build", kind);
     return HG_ERR_UNSUPPORTED;
@@ -1115,6 +1119,180 @@ int Op::build_stored() {
   return HG_OK;
 }
 
+// Polynomial surrogate stencils (Sec. 5.2, surrogate operators).  Per level:
+// the interior points p of a cell (i, j, k >= 1, i + j + k <= n - 1, order
+// k, j, i) and the polynomial basis at them, B[p][t] = xi^a eta^b zeta^c
+// (xi = i/n - 1/4, ...; terms by a, then b, then c; a + b + c <= degree);
+// B = Q R by modified Gram-Schmidt with a second orthogonalisation pass,
+// columns that the points do not separate (residual below 1e-9 of their
+// norm) dropped; the exact stencils S of every stored point (FP64, the
+// operator's own point sum); on the device M = Q^T S per cell and direction;
+// on the host the coefficients c = R^-1 M of the kept terms (0 for the
+// dropped ones).  The fitted weights B c are the least-squares projection of
+// the exact ones.  Then the surrogate's own diagonal replaces the exact one.
+int Op::build_surrogate(const double* coeff, int degree) {
+  const Hier* h = hier;
+  if (degree < 0 || degree > kSurMaxDegree) {
+    set_error("surrogate degree %d outside 0..%d", degree, kSurMaxDegree);
+    return HG_ERR_INVALID_ARG;
+  }
+  if (h->lmax > 9) {
+    set_error("surrogate: level %d beyond the row encoding", h->lmax);
+    return HG_ERR_UNSUPPORTED;
+  }
+  if (int r = build_divkgrad(coeff)) return r;
+  sdeg = degree;
+  const int nt = sur_nterm(degree);
+  const int nl = h->lmax - h->lmin + 1;
+  const int64_t nc = h->mesh->nc;
+  for (int dt = 0; dt < 2; ++dt) scoef[dt].assign(nl, nullptr);
+  ssegs.assign(nl, nullptr);
+  n_ssegs.assign(nl, 0);
+  for (int l = h->lmin; l <= h->lmax; ++l) {
+    const int li = l - h->lmin;
+    const LevelDev& L = h->lv[li].dev;
+    const int n = 1 << l, w = n + 1;
+    std::vector<int> pidx, segs;
+    std::vector<double> B;
+    for (int k = 1; k <= n - 1; ++k)
+      for (int j = 1; j + k <= n - 1; ++j) {
+        for (int i0 = 1; i0 + j + k <= n - 1; i0 += 32) segs.push_back(j | (k << 10) | (i0 << 20));
+        for (int i = 1; i + j + k <= n - 1; ++i) {
+          pidx.push_back((int)tw(w, i, j, k));
+          const double v[3] = {(double)i / n - 0.25, (double)j / n - 0.25, (double)k / n - 0.25};
+          for (int a = 0; a <= degree; ++a)
+            for (int b = 0; a + b <= degree; ++b)
+              for (int c = 0; a + b + c <= degree; ++c)
+                B.push_back(std::pow(v[0], a) * std::pow(v[1], b) * std::pow(v[2], c));
+        }
+      }
+    const int64_t P = (int64_t)pidx.size();
+    n_ssegs[li] = (int)segs.size();
+    if (!segs.empty())
+      if (int r = upload(&ssegs[li], segs)) return r;
+    std::vector<double> coef(nc * kNDir * nt, 0.0);
+    if (P > 0) {
+      // modified Gram-Schmidt on the columns of B, twice, dropping dependent ones
+      std::vector<std::vector<double>> Qc;
+      std::vector<int> kept;
+      std::vector<std::vector<double>> Rc;  // column t' of R (length t'+1)
+      for (int t = 0; t < nt; ++t) {
+        std::vector<double> v(P);
+        double n0 = 0.0;
+        for (int64_t p = 0; p < P; ++p) {
+          v[p] = B[p * nt + t];
+          n0 += v[p] * v[p];
+        }
+        n0 = std::sqrt(n0);
+        std::vector<double> rcol(Qc.size() + 1, 0.0);
+        for (int pass = 0; pass < 2; ++pass)
+          for (size_t s2 = 0; s2 < Qc.size(); ++s2) {
+            double r = 0.0;
+            for (int64_t p = 0; p < P; ++p) r += Qc[s2][p] * v[p];
+            for (int64_t p = 0; p < P; ++p) v[p] -= r * Qc[s2][p];
+            rcol[s2] += r;
+          }
+        double nv = 0.0;
+        for (int64_t p = 0; p < P; ++p) nv += v[p] * v[p];
+        nv = std::sqrt(nv);
+        if (!(n0 > 0.0) || nv <= 1e-9 * n0) continue;
+        for (int64_t p = 0; p < P; ++p) v[p] /= nv;
+        rcol.back() = nv;
+        Qc.push_back(std::move(v));
+        Rc.push_back(std::move(rcol));
+        kept.push_back(t);
+      }
+      const int T = (int)kept.size();
+      std::vector<double> Q(P * T);
+      for (int64_t p = 0; p < P; ++p)
+        for (int t = 0; t < T; ++t) Q[p * T + t] = Qc[t][p];
+      double *S = nullptr, *dQ = nullptr, *dM = nullptr;
+      int* dp = nullptr;
+      auto cleanup = [&]() {
+        cudaFree(S);
+        cudaFree(dQ);
+        cudaFree(dM);
+        cudaFree(dp);
+      };
+      int rc = HG_OK;
+      std::vector<double> M(nc * kNDir * T);
+      do {
+        if (cudaMalloc(&S, (size_t)16 * L.n_stored * sizeof(double)) != cudaSuccess ||
+            cudaMalloc(&dM, M.size() * sizeof(double)) != cudaSuccess) {
+          set_error("surrogate: out of device memory for the fit of level %d", l);
+          rc = HG_ERR_CUDA;
+          break;
+        }
+        if ((rc = upload(&dQ, Q)) || (rc = upload(&dp, pidx))) break;
+        VarCoef vc{vk[HG_F64][li], vK[HG_F64][li], nullptr};
+        if ((rc = launch_divkgrad_stencil(L, HG_F64, vc, S, 0))) break;
+        if ((rc = launch_surrogate_moments(L, S, dp, (int)P, dQ, T, dM, 0))) break;
+        if (cudaMemcpy(M.data(), dM, M.size() * sizeof(double), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+          set_error("surrogate: %s", cudaGetErrorString(cudaGetLastError()));
+          rc = HG_ERR_CUDA;
+        }
+      } while (0);
+      cleanup();
+      if (rc) return rc;
+      // c = R^-1 (Q^T w) per cell and direction (back substitution)
+      for (int64_t c = 0; c < nc; ++c)
+        for (int d = 0; d < kNDir; ++d) {
+          const double* m = &M[(c * kNDir + d) * T];
+          std::vector<double> x(T);
+          for (int t = T - 1; t >= 0; --t) {
+            double r = m[t];
+            for (int u = t + 1; u < T; ++u) r -= Rc[u][t] * x[u];
+            x[t] = r / Rc[t][t];
+          }
+          for (int t = 0; t < T; ++t) coef[(c * kNDir + d) * nt + kept[t]] = x[t];
+        }
+    }
+    std::vector<float> coef32(coef.begin(), coef.end());
+    double* d64 = nullptr;
+    float* d32 = nullptr;
+    if (int r = upload(&d64, coef)) return r;
+    scoef[HG_F64][li] = d64;
+    if (int r = upload(&d32, coef32)) return r;
+    scoef[HG_F32][li] = d32;
+    // the surrogate's diagonal (all DoFs, FP64) -> 1/diag where nonzero
+    double* diag = nullptr;
+    HG_CUDA(cudaMalloc(&diag, L.n_stored * sizeof(double)));
+    HG_CUDA(cudaMemset(diag, 0, L.n_stored * sizeof(double)));
+    StencilArgs a{};
+    a.x = diag;  // unused by the diagonal mode, must be non-null
+    a.out = diag;
+    a.op = OP_DIAG;
+    a.mask = HG_MASK_ALL;
+    VarCoef vc{vk[HG_F64][li], vK[HG_F64][li], nullptr};
+    SurCoef sc{degree, scoef[HG_F64][li], ssegs[li], n_ssegs[li]};
+    int rc = launch_p1_surrogate(L, HG_F64, a, vc, sc, 0);
+    std::vector<double> dh(L.n_stored);
+    if (!rc && cudaMemcpy(dh.data(), diag, L.n_stored * sizeof(double), cudaMemcpyDeviceToHost) !=
+                   cudaSuccess) {
+      set_error("surrogate: %s", cudaGetErrorString(cudaGetLastError()));
+      rc = HG_ERR_CUDA;
+    }
+    cudaFree(diag);
+    if (rc) return rc;
+    std::vector<double> inv(L.n_stored, 0.0);
+    std::vector<float> inv32(L.n_stored, 0.0f);
+    for (int64_t q = 0; q < L.n_stored; ++q)
+      if (dh[q] != 0.0) {
+        inv[q] = 1.0 / dh[q];
+        inv32[q] = (float)inv[q];
+      }
+    cudaFree(vinv[HG_F64][li]);
+    cudaFree(vinv[HG_F32][li]);
+    vinv[HG_F64][li] = vinv[HG_F32][li] = nullptr;
+    if (int r = upload(&d64, inv)) return r;
+    vinv[HG_F64][li] = d64;
+    if (int r = upload(&d32, inv32)) return r;
+    vinv[HG_F32][li] = d32;
+  }
+  return HG_OK;
+}
+
 int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
   if (space == HG_SPACE_P2) {
     const int li = level - lmin;
@@ -1135,6 +1313,11 @@ int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
     VarCoef vc{vk[dtype][li], vK[dtype][li], vinv[dtype][li]};
     return launch_p1_divkgrad(L, dtype, a, vc, s);
   }
+  if (kind == HG_OP_P1_DIVKGRAD_SURROGATE) {
+    VarCoef vc{vk[dtype][li], vK[dtype][li], vinv[dtype][li]};
+    SurCoef sc{sdeg, scoef[dtype][li], ssegs[li], n_ssegs[li]};
+    return launch_p1_surrogate(L, dtype, a, vc, sc, s);
+  }
   if (kind == HG_OP_P1_DIVKGRAD_STORED) {
     a.sten = nullptr;
     a.sst = sst[dtype][li];
@@ -1153,8 +1336,9 @@ Op::~Op() {
   for (auto p : sten64) cudaFree(p);
   for (auto p : sten32) cudaFree(p);
   for (int dt = 0; dt < 2; ++dt)
-    for (auto* v : {&vk[dt], &vK[dt], &vinv[dt], &sst[dt]})
+    for (auto* v : {&vk[dt], &vK[dt], &vinv[dt], &sst[dt], &scoef[dt]})
       for (void* p : *v) cudaFree(p);
+  for (auto p : ssegs) cudaFree(p);
   cudaFree(n1sign);
 }
 
@@ -1368,6 +1552,18 @@ int hg_op_create(const hg_hier* h, int kind, const double* coeff, hg_op** out) {
   HG_CHECK(h && out, HG_ERR_INVALID_ARG, "hg_op_create: null argument");
   auto op = std::make_unique<hg_op>();
   if (int r = op->build(h, kind, coeff)) return r;
+  *out = op.release();
+  return HG_OK;
+}
+
+int hg_op_create_surrogate(const hg_hier* h, const double* k, int degree, hg_op** out) {
+  HG_CHECK(h && out, HG_ERR_INVALID_ARG, "hg_op_create_surrogate: null argument");
+  auto op = std::make_unique<hg_op>();
+  op->hier = h;
+  op->kind = HG_OP_P1_DIVKGRAD_SURROGATE;
+  op->lmin = h->lmin;
+  op->lmax = h->lmax;
+  if (int r = op->build_surrogate(k, degree)) return r;
   *out = op.release();
   return HG_OK;
 }

@@ -111,6 +111,13 @@ struct Op {
   // stored-stencil P1 (per level): per stored point 16 values, point-major [n_stored][16]:
   // the 15 partial-stencil weights and the inverse centre weight
   std::vector<void*> sst[2];
+  // surrogate P1 (per level): polynomial coefficients [ncells][15][nterm] per
+  // dtype and the interior row segments of one cell (j | k << 10 | i0 << 20)
+  int sdeg = -1;
+  std::vector<void*> scoef[2];
+  std::vector<int*> ssegs;
+  std::vector<int> n_ssegs;
+  int build_surrogate(const double* coeff, int degree);
 
   int build(const Hier* h, int kind, const double* coeff);
   int build_divkgrad(const double* coeff);
@@ -152,6 +159,22 @@ int n1_prolong_table(const N1ProlongTable** out);
 enum { N1_PROLONG = 0, N1_RESTRICT = 1, N1_GRAD = 2, N1_GRADT = 3, N1_GRAD_ADD = 4 };
 int launch_n1_transfer(int which, const LevelDev& F, const LevelDev& C, int dtype,
                        const int8_t* sign, const void* src, void* dst, cudaStream_t s);
+
+// A function on a level range (Sec. 5.1): one stored vector per level of one
+// space and element type, in caller-owned device memory bound level by level,
+// plus the library's device staging buffers for copies from and to host
+// memory in canonical order.
+struct Func {
+  const Hier* hier = nullptr;
+  int space = HG_SPACE_P1;
+  int dtype = HG_F64;
+  std::vector<void*> ptr;        // per lattice index of the hierarchy (null = unbound)
+  std::vector<void*> stage;      // per lattice index, n_unique * 8 bytes once used
+  // The bound stored vector of `level`; sets the error message and returns
+  // null if the level is outside the hierarchy or unbound.
+  void* data(int level) const;
+  ~Func();
+};
 
 // Parameters and optimiser state of the learned smoother network (device).
 struct Mlp {

@@ -338,6 +338,25 @@ struct VarCoef {
 };
 int launch_p1_divkgrad(const LevelDev& L, int dtype, const StencilArgs& a, const VarCoef& vc,
                        cudaStream_t s);
+// Polynomial surrogate of the div-k-grad operator: degree, coefficients
+// [ncells][15][nterm] (terms ordered by the power of i, then of j, then of
+// k, in the shifted coordinates i/n - 1/4, j/n - 1/4, k/n - 1/4) and the
+// interior row segments of one cell (j | k << 10 | i0 << 20, up to 32 points).
+struct SurCoef {
+  int degree;
+  const void* coef;
+  const int* segs;
+  int n_segs_cell;
+};
+constexpr int kSurMaxDegree = 4;
+__host__ __device__ constexpr int sur_nterm(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
+int launch_p1_surrogate(const LevelDev& L, int dtype, const StencilArgs& a, const VarCoef& vc,
+                        const SurCoef& sc, cudaStream_t s);
+// Projections M[cell][d][t] = sum over the P interior points p of one cell of
+// Q[p][t] * S[16 * (cell * stride + pidx[p]) + d] (FP64, t < T; S: the exact
+// stored stencils), for the least-squares fit of the surrogate.
+int launch_surrogate_moments(const LevelDev& L, const double* S, const int* pidx, int P,
+                             const double* Q, int T, double* M, cudaStream_t s);
 // Stored stencils of the div-k-grad operator: S[16 q + d] = the weight of
 // direction d in the partial stencil of stored point q (zero outside the
 // lattice); S[16 q + 15] = 1 / S[16 q] for points inside a cell, else 0.
@@ -345,8 +364,12 @@ int launch_divkgrad_stencil(const LevelDev& L, int dtype, const VarCoef& vc, voi
                             cudaStream_t s);
 int launch_index_enumerate(int w, int64_t* out, cudaStream_t s);
 int launch_interface_dump(const LevelDev& L, int64_t* out, cudaStream_t s);
-int launch_to_canonical(const LevelDev& L, int dtype, const void* st, void* can, cudaStream_t s);
-int launch_from_canonical(const LevelDev& L, int dtype, const void* can, void* st, cudaStream_t s);
+// Stored <-> canonical order; can_dtype: element type of the canonical side
+// (-1 = dtype, else HG_F32/HG_F64, converted by rounding to nearest).
+int launch_to_canonical(const LevelDev& L, int dtype, const void* st, void* can, cudaStream_t s,
+                        int can_dtype = -1);
+int launch_from_canonical(const LevelDev& L, int dtype, const void* can, void* st, cudaStream_t s,
+                          int can_dtype = -1);
 int launch_restrict_p1(const LevelDev& F, const LevelDev& C, int dtype, const void* rf, void* rc,
                        cudaStream_t s);
 int launch_prolong_p1(const LevelDev& F, const LevelDev& C, int dtype, const void* ec, void* xf,

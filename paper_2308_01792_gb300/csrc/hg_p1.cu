@@ -388,21 +388,23 @@ __global__ void interface_dump_kernel(int n, int w, const int4* items, int n_ite
   }
 }
 
-template <typename T>
-__global__ void gather_kernel(const T* __restrict__ st, const int64_t* __restrict__ rep, int64_t nu,
-                              T* __restrict__ can) {
+// Stored <-> canonical copies; S is the source and D the destination element
+// type (a conversion rounds to nearest).
+template <typename S, typename D>
+__global__ void gather_kernel(const S* __restrict__ st, const int64_t* __restrict__ rep, int64_t nu,
+                              D* __restrict__ can) {
   for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < nu;
        u += (int64_t)gridDim.x * blockDim.x)
-    can[u] = st[rep[u]];
+    can[u] = (D)st[rep[u]];
 }
 
-template <typename T>
-__global__ void scatter_kernel(const T* __restrict__ can, const int32_t* __restrict__ canon,
-                               int64_t ns, T* __restrict__ st) {
+template <typename S, typename D>
+__global__ void scatter_kernel(const S* __restrict__ can, const int32_t* __restrict__ canon,
+                               int64_t ns, D* __restrict__ st) {
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < ns;
        q += (int64_t)gridDim.x * blockDim.x) {
     int32_t u = canon[q];
-    if (u >= 0) st[q] = can[u];
+    if (u >= 0) st[q] = (D)can[u];
   }
 }
 
@@ -694,27 +696,38 @@ int launch_interface_dump(const LevelDev& L, int64_t* out, cudaStream_t s) {
   return HG_OK;
 }
 
-int launch_to_canonical(const LevelDev& L, int dtype, const void* st, void* can, cudaStream_t s) {
+int launch_to_canonical(const LevelDev& L, int dtype, const void* st, void* can, cudaStream_t s,
+                        int can_dtype) {
+  if (can_dtype < 0) can_dtype = dtype;
   const int g = grid_for(L.n_unique);
-  if (dtype == HG_F64)
-    gather_kernel<double><<<g, kBlock, 0, s>>>((const double*)st, L.canon_rep, L.n_unique,
-                                               (double*)can);
+  const int64_t* rep = L.canon_rep;
+  const int64_t nu = L.n_unique;
+  if (dtype == HG_F64 && can_dtype == HG_F64)
+    gather_kernel<<<g, kBlock, 0, s>>>((const double*)st, rep, nu, (double*)can);
+  else if (dtype == HG_F64)
+    gather_kernel<<<g, kBlock, 0, s>>>((const double*)st, rep, nu, (float*)can);
+  else if (can_dtype == HG_F64)
+    gather_kernel<<<g, kBlock, 0, s>>>((const float*)st, rep, nu, (double*)can);
   else
-    gather_kernel<float><<<g, kBlock, 0, s>>>((const float*)st, L.canon_rep, L.n_unique,
-                                              (float*)can);
+    gather_kernel<<<g, kBlock, 0, s>>>((const float*)st, rep, nu, (float*)can);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
 
 int launch_from_canonical(const LevelDev& L, int dtype, const void* can, void* st,
-                          cudaStream_t s) {
+                          cudaStream_t s, int can_dtype) {
+  if (can_dtype < 0) can_dtype = dtype;
   const int g = grid_for(L.n_stored);
-  if (dtype == HG_F64)
-    scatter_kernel<double><<<g, kBlock, 0, s>>>((const double*)can, L.canon, L.n_stored,
-                                                (double*)st);
+  const int32_t* cn = L.canon;
+  const int64_t ns = L.n_stored;
+  if (dtype == HG_F64 && can_dtype == HG_F64)
+    scatter_kernel<<<g, kBlock, 0, s>>>((const double*)can, cn, ns, (double*)st);
+  else if (dtype == HG_F64)
+    scatter_kernel<<<g, kBlock, 0, s>>>((const float*)can, cn, ns, (double*)st);
+  else if (can_dtype == HG_F64)
+    scatter_kernel<<<g, kBlock, 0, s>>>((const double*)can, cn, ns, (float*)st);
   else
-    scatter_kernel<float><<<g, kBlock, 0, s>>>((const float*)can, L.canon, L.n_stored,
-                                               (float*)st);
+    scatter_kernel<<<g, kBlock, 0, s>>>((const float*)can, cn, ns, (float*)st);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }

@@ -127,6 +127,12 @@ struct VarArgs {
   int gs_colour;
   T* dvec;                // OP_CHEB: direction, updated in place
   T cheb_a;               // OP_CHEB: weight of the previous direction
+  // surrogate form: polynomial coefficients [ncells][15][nterm], degree and
+  // the interior row segments of one cell
+  const T* sc;
+  int sdeg;
+  const int* segs;
+  int n_segs_cell, n_segs;
 };
 
 // 15-point neighbourhood of a cell-local point from global memory (values
@@ -398,8 +404,93 @@ __device__ void var_plane_tile(const VarArgs<T>& A, int t, int lane,
   __syncwarp();
 }
 
+// Row segment t of the surrogate operator (Sec. 5.2, surrogates): up to 32
+// consecutive interior points (i0 + lane, j, k) of one lattice row.  The warp
+// first forms the row's one-dimensional coefficients rowc[d][m] (weight of
+// direction d = sum_m rowc[d][m] xi^m, xi = i/n - 1/4) from the cell's
+// polynomial in (xi, eta, zeta) at the row's eta = j/n - 1/4 and
+// zeta = k/n - 1/4; every lane then evaluates its point's 15 weights by
+// Horner's rule and applies them to the 15 neighbours of x (all inside the
+// cell's lattice for an interior point).
 template <typename T, int OP>
+__device__ void sur_segment(const VarArgs<T>& A, int t, int lane, T* __restrict__ rowc) {
+  const int cell = t / A.n_segs_cell;
+  const int sg = A.segs[t - cell * A.n_segs_cell];
+  const int j = sg & 1023, k = (sg >> 10) & 1023, i0 = sg >> 20;
+  const int n = A.n, w = A.w, q = A.sdeg, q1 = q + 1, nt = sur_nterm(q);
+  const T inv_n = T(1) / T(n);  // n is a power of two: exact
+  const T eta = T(j) * inv_n - T(0.25), zeta = T(k) * inv_n - T(0.25);
+  const T* __restrict__ C = A.sc + (int64_t)cell * kNDir * nt;
+  for (int e = lane; e < kNDir * q1; e += 32) {
+    const int d = e / q1, m = e - d * q1;
+    // terms with power m of xi follow those of the lower powers
+    int tt = 0;
+    for (int a = 0; a < m; ++a) tt += (q - a + 1) * (q - a + 2) / 2;
+    T acc = T(0), eb = T(1);
+    for (int b = 0; b <= q - m; ++b) {
+      T ec = eb;
+      for (int c = 0; c <= q - m - b; ++c) {
+        acc = fma(__ldg(C + d * nt + tt), ec, acc);
+        ++tt;
+        ec *= zeta;
+      }
+      eb *= eta;
+    }
+    rowc[e] = acc;
+  }
+  __syncwarp();
+  const int i = i0 + lane;
+  const bool ok = i + j + k <= n - 1;
+  const int ic = ok ? i : i0;  // lanes past the row's end evaluate its first point, unstored
+  const T xi = T(ic) * inv_n - T(0.25);
+  const int64_t base = (int64_t)cell * A.stride;
+  const int len = w - k - j;
+  const int r0 = row_start(w, j, k);
+  const int rjp = r0 + len, rjm = r0 - (len + 1);
+  const int rkp = r0 + ntri32(w - k - 1) + len, rkm = r0 - ntri32(w - k) - (len + 1);
+  const int rjmkp = rkp - len, rjpkm = rkm + len + 1;
+  const int rows[kNDir] = {r0,  r0,  r0,  rjp,   rjm,   rkp,   rkm,  rjp,
+                           rjm, rkp, rkm, rjmkp, rjpkm, rjmkp, rjpkm};
+  T acc = T(0), centre = T(0);
+#pragma unroll
+  for (int d = 0; d < kNDir; ++d) {
+    T wd = rowc[d * q1 + q];
+    for (int m = q - 1; m >= 0; --m) wd = fma(wd, xi, rowc[d * q1 + m]);
+    if (d == 0) centre = wd;
+    if (OP != OP_DIAG) {
+      int di, dj, dk;
+      dir_offset(d, di, dj, dk);
+      acc = fma(wd, __ldg(A.x + base + rows[d] + ic + di), acc);
+    }
+  }
+  if (OP == OP_DIAG) acc = centre;
+  if (ok) {
+    const int64_t idx = base + r0 + ic;
+    if (OP == OP_APPLY || OP == OP_DIAG) {
+      A.y[idx] = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[idx] + acc : acc;
+    } else if (OP == OP_RESID) {
+      A.y[idx] = A.b[idx] - acc;
+    } else {
+      const T x0 = A.x[idx];
+      if (OP == OP_GS) {
+        A.y[idx] = A.colour[idx] == A.gs_colour ? x0 + (A.b[idx] - acc) * A.invdiag[idx] : x0;
+      } else if (OP == OP_CHEB) {
+        T dn = A.omega * (A.b[idx] - acc) * A.invdiag[idx];
+        if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[idx];
+        A.dvec[idx] = dn;
+        A.y[idx] = x0 + dn;
+      } else {
+        A.y[idx] = x0 + A.omega * (A.b[idx] - acc) * A.invdiag[idx];
+      }
+    }
+  }
+  __syncwarp();
+}
+
+template <typename T, int OP, bool SUR>
 __global__ void __launch_bounds__(kBlock) p1var_kernel(VarArgs<T> A) {
+  // element rows of the cell (plane tiles) or the row coefficients of a
+  // surrogate segment (15 x (degree + 1) <= 75 values)
   __shared__ typename Row4<T>::type Ks[kWarps][24];
   const int lane = threadIdx.x & 31;
   const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -407,12 +498,18 @@ __global__ void __launch_bounds__(kBlock) p1var_kernel(VarArgs<T> A) {
     if (wg < A.n_items) var_interface_item<T, OP>(A, wg, lane);
   } else {
     const int t = wg - A.nb_items * kWarps;
-    if (t < A.n_tiles) var_plane_tile<T, OP>(A, t, lane, Ks[threadIdx.x >> 5]);
+    if (SUR) {
+      if (t < A.n_segs)
+        sur_segment<T, OP>(A, t, lane, reinterpret_cast<T*>(Ks[threadIdx.x >> 5]));
+    } else if (t < A.n_tiles) {
+      var_plane_tile<T, OP>(A, t, lane, Ks[threadIdx.x >> 5]);
+    }
   }
 }
 
-template <typename T, int OP>
-int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStream_t s) {
+template <typename T, int OP, bool SUR = false>
+int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStream_t s,
+            const SurCoef* sc = nullptr) {
   VarArgs<T> A;
   A.n = L.n;
   A.w = L.w;
@@ -438,25 +535,75 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.gs_colour = a.colour;
   A.dvec = (T*)a.dvec;
   A.cheb_a = (T)a.cheb_a;
-  const int grid = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
+  A.sc = nullptr;
+  A.sdeg = 0;
+  A.segs = nullptr;
+  A.n_segs_cell = A.n_segs = 0;
+  if (SUR) {
+    A.sc = (const T*)sc->coef;
+    A.sdeg = sc->degree;
+    A.segs = sc->segs;
+    A.n_segs_cell = sc->n_segs_cell;
+    A.n_segs = sc->n_segs_cell * L.ncells;
+  }
+  const int work = SUR ? A.n_segs : A.n_tiles;
+  const int grid = A.nb_items + (work + kWarps - 1) / kWarps;
   if (grid == 0) return HG_OK;
-  p1var_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
+  p1var_kernel<T, OP, SUR><<<grid, kBlock, 0, s>>>(A);
   HG_CUDA(cudaGetLastError());
   return HG_OK;
 }
 
-template <typename T>
-int run_var_op(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStream_t s) {
+template <typename T, bool SUR = false>
+int run_var_op(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStream_t s,
+               const SurCoef* sc = nullptr) {
   switch (a.op) {
-    case OP_APPLY: return run_var<T, OP_APPLY>(L, a, vc, s);
-    case OP_RESID: return run_var<T, OP_RESID>(L, a, vc, s);
-    case OP_JACOBI: return run_var<T, OP_JACOBI>(L, a, vc, s);
-    case OP_DIAG: return run_var<T, OP_DIAG>(L, a, vc, s);
-    case OP_GS: return run_var<T, OP_GS>(L, a, vc, s);
-    case OP_CHEB: return run_var<T, OP_CHEB>(L, a, vc, s);
+    case OP_APPLY: return run_var<T, OP_APPLY, SUR>(L, a, vc, s, sc);
+    case OP_RESID: return run_var<T, OP_RESID, SUR>(L, a, vc, s, sc);
+    case OP_JACOBI: return run_var<T, OP_JACOBI, SUR>(L, a, vc, s, sc);
+    case OP_DIAG: return run_var<T, OP_DIAG, SUR>(L, a, vc, s, sc);
+    case OP_GS: return run_var<T, OP_GS, SUR>(L, a, vc, s, sc);
+    case OP_CHEB: return run_var<T, OP_CHEB, SUR>(L, a, vc, s, sc);
   }
   set_error("unknown cell operation %d", a.op);
   return HG_ERR_INVALID_ARG;
+}
+
+// Least-squares projections of the surrogate fit: block (cell, d) sums
+// Q[p][t] * S_d(p) over the cell's interior points in a fixed order (thread
+// strides, then a shared-memory tree), so the result is deterministic.
+constexpr int kMomThreads = 256;
+__global__ void __launch_bounds__(kMomThreads) surrogate_moments_kernel(
+    const double* __restrict__ S, int64_t stride, const int* __restrict__ pidx, int P,
+    const double* __restrict__ Q, int T, double* __restrict__ M) {
+  constexpr int kMaxT = sur_nterm(kSurMaxDegree);
+  __shared__ double red[kMomThreads];
+  const int cell = blockIdx.x / kNDir, d = blockIdx.x - cell * kNDir;
+  double acc[kMaxT];
+#pragma unroll
+  for (int t = 0; t < kMaxT; ++t) acc[t] = 0.0;
+  for (int p = threadIdx.x; p < P; p += kMomThreads) {
+    const double sv = S[16 * ((int64_t)cell * stride + pidx[p]) + d];
+    const double* qp = Q + (int64_t)p * T;
+#pragma unroll
+    for (int t = 0; t < kMaxT; ++t)
+      if (t < T) acc[t] = fma(qp[t], sv, acc[t]);
+  }
+#pragma unroll 1
+  for (int t = 0; t < T; ++t) {
+    double v = 0.0;
+#pragma unroll
+    for (int u = 0; u < kMaxT; ++u)
+      if (u == t) v = acc[u];
+    red[threadIdx.x] = v;
+    __syncthreads();
+    for (int h = kMomThreads / 2; h > 0; h >>= 1) {
+      if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) M[((int64_t)cell * kNDir + d) * T + t] = red[0];
+    __syncthreads();
+  }
 }
 
 // Partial stencils of every stored point: one warp per lattice row of a
@@ -509,6 +656,29 @@ int run_stencil(const LevelDev& L, const VarCoef& vc, void* S, cudaStream_t s) {
 int launch_p1_divkgrad(const LevelDev& L, int dtype, const StencilArgs& a, const VarCoef& vc,
                        cudaStream_t s) {
   return dtype == HG_F64 ? run_var_op<double>(L, a, vc, s) : run_var_op<float>(L, a, vc, s);
+}
+
+int launch_p1_surrogate(const LevelDev& L, int dtype, const StencilArgs& a, const VarCoef& vc,
+                        const SurCoef& sc, cudaStream_t s) {
+  if (sc.degree < 0 || sc.degree > kSurMaxDegree || L.n > 512) {
+    set_error("surrogate: degree %d or level size %d outside the kernel's range", sc.degree, L.n);
+    return HG_ERR_UNSUPPORTED;
+  }
+  return dtype == HG_F64 ? run_var_op<double, true>(L, a, vc, s, &sc)
+                         : run_var_op<float, true>(L, a, vc, s, &sc);
+}
+
+int launch_surrogate_moments(const LevelDev& L, const double* S, const int* pidx, int P,
+                             const double* Q, int T, double* M, cudaStream_t s) {
+  if (T < 1 || T > sur_nterm(kSurMaxDegree)) {
+    set_error("surrogate: %d basis functions outside 1..%d", T, sur_nterm(kSurMaxDegree));
+    return HG_ERR_INVALID_ARG;
+  }
+  if (L.ncells == 0 || P == 0) return HG_OK;
+  surrogate_moments_kernel<<<L.ncells * kNDir, kMomThreads, 0, s>>>(S, L.cell_stride, pidx, P, Q, T,
+                                                                   M);
+  HG_CUDA(cudaGetLastError());
+  return HG_OK;
 }
 
 int launch_divkgrad_stencil(const LevelDev& L, int dtype, const VarCoef& vc, void* S,
