@@ -641,6 +641,33 @@ def kernels_comparison(stream):
             rec("dot_f32", tm(lambda: H.dot(L, x, b, stream=stream), 10), 2 * w * nu,
                 "includes the host read of the result")
         del x, b, y
+    # the three constant-stencil kernels on the same applies (FP32 and FP64;
+    # the 384-cell vectors of this leg, then the headline mesh with 16
+    # rotating pairs)
+    modes = {"windows": hg.HG_P1_KERNEL_WINDOWS, "stream": hg.HG_P1_KERNEL_STREAM,
+             "march": hg.HG_P1_KERNEL_MARCH}
+    m6 = sg.kuhn_cube(1)
+    H6 = hg.Hierarchy(hg.Mesh(m6.xyz, m6.cells), LEVEL, LEVEL)
+    op6 = hg.Operator(H6)
+    nu6 = H6.size(LEVEL)[1]
+    for dt, w in ((torch.float32, 4), (torch.float64, 8)):
+        tag = "f32" if w == 4 else "f64"
+        x = H.from_canonical(L, torch.tensor(sg.uniform_vector(21, nu), dtype=dt, device="cuda"))
+        y = torch.zeros_like(x)
+        xs6 = [H6.from_canonical(LEVEL, torch.tensor(sg.uniform_vector(40 + q, nu6), dtype=dt,
+                                                     device="cuda")) for q in range(16)]
+        ys6 = [torch.zeros_like(v) for v in xs6]
+        for name, mode in modes.items():
+            hg.set_p1_kernel(mode)
+            rec(f"apply_{tag}_{name}", tm(lambda: op.apply(L, x, y, stream=stream)), 2 * w * nu)
+            it6 = iter(range(1 << 30))
+
+            def ap6():
+                q = next(it6) % 16
+                op6.apply(LEVEL, xs6[q], ys6[q], stream=stream)
+            rec(f"apply_{tag}_{name}_cube6_L7", tm(ap6, 64), 2 * w * nu6)
+        hg.set_p1_kernel(hg.HG_P1_KERNEL_AUTO)
+        del x, y, xs6, ys6
     # the copy ceiling: a device-to-device copy moving the apply's algorithmic
     # bytes (4 B read + 4 B written per unique DoF) at both sizes, HBM-cold
     # (rotating buffers), CUDA events over 20 copies after 3 warm-up
@@ -735,6 +762,32 @@ def stencil_comparison(stream, m=4, L=6, solve=True):
         "hbm": {"achieved": gbs_fly, "peak": peak, "unit": "GB/s", "frac": gbs_fly / peak,
                 "algorithmic_bytes_per_launch": 12 * nu, "peak_source": f"{kind} hbm_gbs"}}
     out["stored_vs_onthefly_apply_speedup"] = out["onthefly"]["apply_us"] / out["stored"]["apply_us"]
+    # polynomial surrogates of degree 2 and 3: apply time, and the distance of
+    # their result from the exact operator's on the same x (INNER rows)
+    y_ex = torch.zeros_like(x)
+    fly.apply(L, x, y_ex, stream=stream)
+    for q in (2, 3):
+        t0 = time.perf_counter()
+        sur = hg.Operator(H, hg.HG_OP_P1_DIVKGRAD_SURROGATE, coeff=k, degree=q)
+        t_setup = time.perf_counter() - t0
+        for _ in range(5):
+            sur.apply(L, x, y, stream=stream)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(50):
+            sur.apply(L, x, y, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 50 * 1e-3
+        err = float((y - y_ex).abs().max() / y_ex.abs().max())
+        gbs = 8 * nu / t / 1e9
+        out[f"surrogate_q{q}"] = {
+            "apply_us": t * 1e6, "gdof_per_s": nu / t / 1e9, "setup_s": t_setup,
+            "rel_max_diff_vs_exact": err,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                         "frac": gbs / peak, "algorithmic_bytes_per_launch": 8 * nu,
+                         "peak_source": f"{kind} hbm_gbs"}}
+        del sur
     if not solve:
         return out
     bc = sg.uniform_vector(9, nu)

@@ -254,6 +254,13 @@ int hg_device_status(const hg_hier* hier, void* stream);
  * kernels' lane walk against the lattice on the CPU. */
 int hg_plane_tiles(int level, int* out, int* n_tiles);
 
+/* The column-march items of the constant-stencil kernel (HG_P1_KERNEL_MARCH)
+ * on one cell lattice of `level` (host, needs no GPU; the same for every
+ * cell), 2 ints per item: (k | i0 << 16, j0 | j1 << 16): columns i0..i0+31 of
+ * plane k, rows j0..j1-1.  *n_items gets the count; out may be NULL.  For the
+ * CPU emulation of the kernel's loads in the tests. */
+int hg_march_items(int level, int* out, int* n_items);
+
 /* The plan of the streaming constant-stencil apply kernel for one level of a
  * mesh with `ncells` macro cells, split over `nctas` CTAs, for dtype
  * HG_F32/HG_F64 (host, needs no GPU).  copies: 4 ints per copy (cell, first
@@ -350,10 +357,15 @@ int hg_op_create_surrogate(const hg_hier* hier, const double* k, int degree, hg_
  *     FP64 arithmetic dominates;
  *   HG_P1_KERNEL_WINDOWS / HG_P1_KERNEL_STREAM: always that kernel (the
  *     streaming one falls back to plane windows on levels whose staged
- *     planes do not fit in shared memory).
+ *     planes do not fit in shared memory);
+ *   HG_P1_KERNEL_MARCH: the column-march kernel (one launch: each warp holds
+ *     32 interior columns of one plane and marches up to 16 rows, keeping the
+ *     values of the rows it has read in registers; interface items as in the
+ *     plane-window kernel).
  * Both give the same results up to rounding order.  Other values:
  * HG_ERR_INVALID_ARG.  Not synchronised with calls in flight. */
-enum { HG_P1_KERNEL_AUTO = 0, HG_P1_KERNEL_WINDOWS = 1, HG_P1_KERNEL_STREAM = 2 };
+enum { HG_P1_KERNEL_AUTO = 0, HG_P1_KERNEL_WINDOWS = 1, HG_P1_KERNEL_STREAM = 2,
+       HG_P1_KERNEL_MARCH = 3 };
 int hg_set_p1_kernel(int mode);
 
 /* Class table of the lowest-order Nedelec prolongation (host, needs no GPU).

@@ -101,6 +101,7 @@ SIGNATURES = {
     "hg_plane_tiles": (_I, [_I, _P, ctypes.POINTER(ctypes.c_int)]),
     "hg_stream_plan": (_I, [_I, _I, _I, _I, _P, _P, _P, _P, _P]),
     "hg_set_p1_kernel": (_I, [_I]),
+    "hg_march_items": (_I, [_I, _P, ctypes.POINTER(ctypes.c_int)]),
     "hg_stream_layout": (_I, [_I, _I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_int)]),
     "hg_p2_anchors": (_I, [_I, _P, _P, ctypes.POINTER(ctypes.c_int)]),
@@ -749,7 +750,16 @@ def plane_tiles(level):
     return out[:n.value]
 
 
-HG_P1_KERNEL_AUTO, HG_P1_KERNEL_WINDOWS, HG_P1_KERNEL_STREAM = 0, 1, 2
+def march_items(level):
+    """The column-march kernel's items of one cell lattice (host): (n, 2) int32."""
+    n = ctypes.c_int()
+    _call("hg_march_items", level, None, ctypes.byref(n))
+    out = np.zeros((max(n.value, 1), 2), dtype=np.int32)
+    _call("hg_march_items", level, out.ctypes.data_as(_P), ctypes.byref(n))
+    return out[:n.value]
+
+
+HG_P1_KERNEL_AUTO, HG_P1_KERNEL_WINDOWS, HG_P1_KERNEL_STREAM, HG_P1_KERNEL_MARCH = 0, 1, 2, 3
 
 
 def set_p1_kernel(mode):

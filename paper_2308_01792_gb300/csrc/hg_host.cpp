@@ -553,6 +553,9 @@ int Hier::build_level(int l) {
   const std::vector<int4> ptiles = plane_tiles(n);
   L.n_ptiles_cell = (int)ptiles.size();
   if (int r = upload(&L.ptiles, ptiles)) return r;
+  const std::vector<int2> march = march_items(n);
+  L.n_march_cell = (int)march.size();
+  if (int r = upload(&L.march, march)) return r;
   // canonical numbering by exact lattice coordinates
   if (mesh->grid_denom) {
     std::vector<int64_t> keys(L.n_stored, -1);
@@ -642,6 +645,7 @@ int Hier::build_level(int l) {
   if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
       (L.n_items && (!L.items || !L.item_prim)) ||
       (L.n_citems && !L.citems) || (L.n_ptiles_cell && !L.ptiles) ||
+      (L.n_march_cell && !L.march) ||
       (L.n_mitems && (!L.mitems || !L.mlanes)) || !L.splan[0].cta_items || !L.splan[1].cta_items ||
       (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
     set_error("internal: level %d device tables incomplete", l);
@@ -770,6 +774,7 @@ Hier::~Hier() {
     }
     cudaFree(L.colour);
     cudaFree(L.ptiles);
+    cudaFree(L.march);
     cudaFree(L.items);
     cudaFree(L.item_prim);
   }
@@ -894,6 +899,21 @@ void p1_cell_stencils(const Mesh& m, int64_t c, int n, int kind, double S[16][16
 // 1..30, halo lanes 0 and 31), a tile up to kPlaneSteps windows; a tile is
 // (k | windows << 16, lane-0 offset, j0 << 16 | i0, 0) with (j0, i0) the
 // lattice row and column of lane 0's offset.
+// Column-march items: the cell-interior points (i, j, k >= 1, i + j + k <= n-1)
+// of plane k in strips of 32 columns i0..i0+31 (i0 = 1, 33, ...), each strip
+// cut into bands of kMarchRows rows j0..j1-1 that hold at least one interior
+// point of column i0: (k | i0 << 16, j0 | j1 << 16).
+std::vector<int2> march_items(int n) {
+  std::vector<int2> v;
+  for (int k = 1; k <= n - 3; ++k)
+    for (int i0 = 1; i0 <= n - 2 - k; i0 += 32) {
+      const int jmax = n - 1 - k - i0;
+      for (int j0 = 1; j0 <= jmax; j0 += kMarchRows)
+        v.push_back({k | (i0 << 16), j0 | (std::min(j0 + kMarchRows, jmax + 1) << 16)});
+    }
+  return v;
+}
+
 std::vector<int4> plane_tiles(int n) {
   const int w = n + 1;
   std::vector<int4> ptiles;
@@ -1488,6 +1508,18 @@ int hg_plane_tiles(int level, int* out, int* n_tiles) {
       out[4 * q + 1] = t[q].y;
       out[4 * q + 2] = t[q].z;
       out[4 * q + 3] = t[q].w;
+    }
+  return HG_OK;
+}
+
+int hg_march_items(int level, int* out, int* n_items) {
+  HG_CHECK(level >= 0 && level <= 12 && n_items, HG_ERR_INVALID_ARG, "hg_march_items: bad argument");
+  const std::vector<int2> t = march_items(1 << level);
+  *n_items = (int)t.size();
+  if (out)
+    for (size_t q = 0; q < t.size(); ++q) {
+      out[2 * q] = t[q].x;
+      out[2 * q + 1] = t[q].y;
     }
   return HG_OK;
 }

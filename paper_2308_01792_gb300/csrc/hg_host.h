@@ -83,6 +83,8 @@ struct Hier {
 int lattice_index(const Hier* h, int space, int level);
 // Plane-window tiles of one cell lattice with n intervals (the same for every cell).
 std::vector<int4> plane_tiles(int n);
+// Column-march items of one cell lattice with n intervals (the same for every cell).
+std::vector<int2> march_items(int n);
 // Anchors of the P2/N1 colour phases (n intervals), off[9] colour offsets.
 std::vector<uint32_t> p2_anchors(int n, int off[9]);
 

@@ -196,6 +196,8 @@ struct LevelDev {
   StreamPlanDev splan[2];    // the streaming kernel's plans for HG_F32 and HG_F64
   int4* ptiles;              // plane-window tiles of ONE cell (the same for every cell):
   int n_ptiles_cell;         //   (k | windows << 16, lane-0 offset z, j0 << 16 | i0, 0)
+  int2* march;               // column-march items of ONE cell: (k | i0 << 16, j0 | j1 << 16),
+  int n_march_cell;          //   columns i0..i0+31 of plane k, rows j0..j1-1
   uint8_t* colour;           // Gauss-Seidel colour (0..3) per stored point, or null
 };
 
@@ -205,6 +207,11 @@ struct LevelDev {
 #define HG_PLANE_STEPS 16
 #endif
 constexpr int kPlaneSteps = HG_PLANE_STEPS;
+// Rows marched by one column-march item of the constant-stencil kernels.
+#ifndef HG_MARCH_ROWS
+#define HG_MARCH_ROWS 16
+#endif
+constexpr int kMarchRows = HG_MARCH_ROWS;
 
 // Dense FP64 coarse-grid solver data.
 struct CoarseDev {

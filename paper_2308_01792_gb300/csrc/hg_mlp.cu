@@ -393,7 +393,16 @@ __device__ __forceinline__ void s_neighbourhood(const float* __restrict__ r,
 }
 
 // x_out = x + omega s (+ N(s) at macro-cell-interior DoFs); Dirichlet DoFs
-// keep x.  One warp per lattice row, 32 points per step (two 16-row tiles).
+// keep x.  One warp per lattice row (cell, j, k), windows of 30 points: lane
+// l holds i = i0 - 1 + l, lanes 1..30 produce outputs and lanes 0 and 31 are
+// the i -/+ 1 halo.  In rows that hold cell-interior points (j, k >= 1,
+// row length >= 3) every lane forms s = r / D at its i on the seven
+// neighbour rows (plane k rows j, j+1, j-1; plane k+1 rows j, j-1; plane k-1
+// rows j, j+1, each one coalesced load of r and of 1/D with a warp-uniform
+// base) and takes the i +/- 1 neighbours by shuffle; the interior points'
+// 15 values go through the network as two 16-row tiles.  Loads of lanes past
+// the row's end stay inside the padded cell (at most 30 elements past its
+// last point) and feed no output.
 __global__ void __launch_bounds__(kMlpThreads) learned_step_kernel(
     int n, int64_t stride, const uint8_t* __restrict__ flags, int n_rows, const float* __restrict__ x,
     const float* __restrict__ r, const float* __restrict__ inv, float omega, const float* W1,
@@ -401,53 +410,82 @@ __global__ void __launch_bounds__(kMlpThreads) learned_step_kernel(
   __shared__ __align__(16) __nv_bfloat16 sX[kMlpWarps][32 * 16];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = n + 1;
-  WFrag F;
-  load_wfrag(F, W1, W2, w3, lane);
+  const unsigned F = 0xffffffffu;
+  WFrag Wf;
+  load_wfrag(Wf, W1, W2, w3, lane);
   for (int row = blockIdx.x * kMlpWarps + warp; row < n_rows; row += gridDim.x * kMlpWarps) {
     int cell, j, k;
     mlp_row(w, row, cell, j, k);
     const int64_t base = (int64_t)cell * stride;
-    const int rs = row_start(w, j, k);
+    const float* __restrict__ rc = r + base;
+    const float* __restrict__ ic = inv + base;
+    const int len = w - k - j;
+    const int r0 = row_start(w, j, k);
     const uint8_t* fl = flags + cell * 16;
-    for (int i0 = 0; i0 + j + k <= n; i0 += 32) {
-      const int i = i0 + lane;
-      const bool valid = i + j + k <= n;
-      const int cls = valid ? point_class(n, i, j, k) : 1;
-      float v[16];
-      if (valid && cls == 0) {
-        s_neighbourhood(r + base, inv + base, w, i, j, k, v);
-      } else {
+    const bool nbr = j >= 1 && k >= 1 && len >= 3;
+    // neighbour row starts (valid only when nbr): j+1, j-1, (k+1, j), (k+1, j-1), (k-1, j), (k-1, j+1)
+    const int rjp = r0 + len, rjm = r0 - (len + 1);
+    const int rkp = r0 + ntri32(w - k - 1) + len, rkm = r0 - ntri32(w - k) - (len + 1);
+    const int rjmkp = rkp - len, rjpkm = rkm + len + 1;
+    for (int i0 = 0; i0 < len; i0 += 30) {
+      const int i = i0 - 1 + lane;
+      const int il = i < 0 ? 0 : i;
+      const float s0 = __ldg(rc + r0 + il) * __ldg(ic + r0 + il);
+      const bool out = lane >= 1 && lane <= 30 && i <= len - 1;
+      const bool interior = nbr && out && i >= 1 && i <= len - 2;
+      if (nbr) {
+        float sr[7];
+        const int rows[7] = {r0, rjp, rjm, rkp, rjmkp, rkm, rjpkm};
+        sr[0] = s0;
 #pragma unroll
-        for (int d = 0; d < 16; ++d) v[d] = 0.f;
+        for (int m = 1; m < 7; ++m) sr[m] = __ldg(rc + rows[m] + il) * __ldg(ic + rows[m] + il);
+        // direction order of the network's features (see the header comment)
+        float v[16];
+        v[0] = sr[0];
+        v[1] = __shfl_down_sync(F, sr[0], 1);
+        v[2] = __shfl_up_sync(F, sr[0], 1);
+        v[3] = sr[1];
+        v[4] = sr[2];
+        v[5] = sr[3];
+        v[6] = sr[5];
+        v[7] = __shfl_up_sync(F, sr[1], 1);
+        v[8] = __shfl_down_sync(F, sr[2], 1);
+        v[9] = __shfl_up_sync(F, sr[3], 1);
+        v[10] = __shfl_down_sync(F, sr[5], 1);
+        v[11] = sr[4];
+        v[12] = sr[6];
+        v[13] = __shfl_down_sync(F, sr[4], 1);
+        v[14] = __shfl_up_sync(F, sr[6], 1);
+        v[15] = 0.f;
+#pragma unroll
+        for (int d = 0; d < 16; d += 2)
+          reinterpret_cast<uint32_t*>(sX[warp])[(lane * 16 + d) / 2] =
+              interior ? pack_bf16(v[d], v[d + 1]) : 0u;
+        __syncwarp();
       }
-#pragma unroll
-      for (int d = 0; d < 16; d += 2)
-        reinterpret_cast<uint32_t*>(sX[warp])[(lane * 16 + d) / 2] = pack_bf16(v[d], v[d + 1]);
-      __syncwarp();
-      float z1[4][4], z2[4][4], oa0, oa8, ob0, ob8;
-      mlp_tile_forward(F, sX[warp], lane, z1, z2, oa0, oa8);
-      mlp_tile_forward(F, sX[warp] + 16 * 16, lane, z1, z2, ob0, ob8);
-      // rows of the tiles: lane g -> row g (tile a), g+8, 16+g (tile b), 24+g
-      const int g = lane >> 2;
       float corr = 0.f;
-      // fetch the correction of this lane's row from the group holding it
-      const float cand0 = __shfl_sync(0xffffffffu, oa0, (lane & 7) * 4);
-      const float cand8 = __shfl_sync(0xffffffffu, oa8, ((lane - 8) & 7) * 4);
-      const float cand16 = __shfl_sync(0xffffffffu, ob0, ((lane - 16) & 7) * 4);
-      const float cand24 = __shfl_sync(0xffffffffu, ob8, ((lane - 24) & 7) * 4);
-      corr = lane < 8 ? cand0 : lane < 16 ? cand8 : lane < 24 ? cand16 : cand24;
-      (void)g;
-      if (valid) {
-        const int64_t idx = base + rs + i;
+      if (nbr) {
+        float z1[4][4], z2[4][4], oa0, oa8, ob0, ob8;
+        mlp_tile_forward(Wf, sX[warp], lane, z1, z2, oa0, oa8);
+        mlp_tile_forward(Wf, sX[warp] + 16 * 16, lane, z1, z2, ob0, ob8);
+        // rows of the tiles: lane g -> row g (tile a), g+8, 16+g (tile b), 24+g
+        const float cand0 = __shfl_sync(F, oa0, (lane & 7) * 4);
+        const float cand8 = __shfl_sync(F, oa8, ((lane - 8) & 7) * 4);
+        const float cand16 = __shfl_sync(F, ob0, ((lane - 16) & 7) * 4);
+        const float cand24 = __shfl_sync(F, ob8, ((lane - 24) & 7) * 4);
+        corr = lane < 8 ? cand0 : lane < 16 ? cand8 : lane < 24 ? cand16 : cand24;
+        __syncwarp();
+      }
+      if (out) {
+        const int64_t idx = base + r0 + i;
+        const int cls = point_class(n, i, j, k);
         const uint8_t f = fl[cls];
         if (f & CF_DIRICHLET) {
           xo[idx] = x[idx];
         } else {
-          const float s = r[idx] * inv[idx];
-          xo[idx] = x[idx] + omega * s + (cls == 0 ? corr : 0.f);
+          xo[idx] = x[idx] + omega * s0 + (interior ? corr : 0.f);
         }
       }
-      __syncwarp();
     }
   }
 }

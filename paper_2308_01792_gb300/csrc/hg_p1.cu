@@ -212,6 +212,98 @@ __device__ __forceinline__ void plane_tile(const FusedArgs<T>& A, int t, int lan
   }
 }
 
+// Column-march item t: lane l holds interior column i = i0 + l of plane k and
+// marches rows j0..j1-1.  The centre row's three values (i-1, i, i+1) of the
+// next row are loaded one step ahead and rotate into the centre; the row
+// below's i+1 (and i) is the previous centre; the other neighbours are one
+// load each.  Columns past a row's last interior point are clamped to it:
+// their loads stay on interior points' neighbourhoods (in bounds) and they
+// store nothing.  The stencil sums are formed in the same order as in
+// plane_compute, so both kernels give the same bits.
+template <typename T, int OP, int PAT>
+__device__ __forceinline__ void march_item(const FusedArgs<T>& A, int t, int lane) {
+  const int cell = t / A.n_march_cell;
+  const int2 it = A.march[t - cell * A.n_march_cell];
+  const int k = it.x & 0xffff, i0 = it.x >> 16, j0 = it.y & 0xffff, j1 = it.y >> 16;
+  const int w = A.w;
+  const int64_t base = (int64_t)cell * A.stride;
+  const T* __restrict__ x = A.x + base;
+  T* __restrict__ y = A.y + base;
+  T s[kNDir];
+  {
+    const T* __restrict__ S = A.sten + (int64_t)cell * 256;
+#pragma unroll
+    for (int d = 0; d < kNDir; ++d) s[d] = __ldg(S + d);
+  }
+  const T wd = (OP == OP_JACOBI || OP == OP_CHEB) ? A.omega / s[0] : OP == OP_GS ? T(1) / s[0] : T(0);
+  const int Tp = ntri32(w - k - 1), Tm = ntri32(w - k);
+  const int i = i0 + lane;
+  int len = w - k - j0;
+  int r0 = row_start(w, j0, k);
+  int ic = min(i, len - 2);
+  T cm = __ldg(x + r0 + ic - 1), cc = __ldg(x + r0 + ic), cp = __ldg(x + r0 + ic + 1);
+  // row j0 - 1 at i and i + 1
+  T dnc = __ldg(x + r0 - len - 1 + ic), dnp = __ldg(x + r0 - len + ic);
+  for (int j = j0; j < j1; ++j) {
+    ic = min(i, len - 2);
+    const int rjp = r0 + len;
+    const T nm = __ldg(x + rjp + ic - 1), nc = __ldg(x + rjp + ic), np = __ldg(x + rjp + ic + 1);
+    const T p1m = __ldg(x + r0 + Tp + ic), m1p = __ldg(x + r0 - Tm + ic);
+    T acc;
+    if (PAT == kPat7) {
+      const T a0 = s[0] * cc + s[1] * cp + s[2] * cm + s[7] * nm + s[8] * dnp;
+      acc = a0 + (s[11] * p1m + s[12] * m1p);
+    } else {
+      const int rkp = r0 + Tp + len, rkm = r0 - Tm - len - 1;
+      const T p1c = __ldg(x + rkp + ic), p1cm = __ldg(x + rkp + ic - 1);
+      const T p1mp = __ldg(x + r0 + Tp + ic + 1);
+      const T m1c = __ldg(x + rkm + ic), m1cp = __ldg(x + rkm + ic + 1);
+      const T m1pm = __ldg(x + r0 - Tm + ic - 1);
+      const T a0 = s[0] * cc + s[1] * cp + s[2] * cm + s[3] * nc + s[4] * dnc + s[7] * nm +
+                   s[8] * dnp;
+      const T a1 = s[5] * p1c + s[9] * p1cm + s[11] * p1m + s[13] * p1mp;
+      const T a2 = s[6] * m1c + s[10] * m1cp + s[12] * m1p + s[14] * m1pm;
+      acc = a0 + (a1 + a2);
+    }
+    if (i <= len - 2) {
+      const int idx = r0 + i;
+      if (OP == OP_APPLY) {
+        y[idx] = A.mode == HG_ADD ? y[idx] + acc : acc;
+      } else if (OP == OP_RESID) {
+        y[idx] = A.b[base + idx] - acc;
+      } else if (OP == OP_GS) {
+        y[idx] = A.colour[base + idx] == A.gs_colour ? cc + (A.b[base + idx] - acc) * wd : cc;
+      } else if (OP == OP_CHEB) {
+        T dn = (A.b[base + idx] - acc) * wd;
+        if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[base + idx];
+        A.dvec[base + idx] = dn;
+        y[idx] = cc + dn;
+      } else {
+        y[idx] = cc + (A.b[base + idx] - acc) * wd;
+      }
+    }
+    dnc = cc;
+    dnp = cp;
+    cm = nm;
+    cc = nc;
+    cp = np;
+    r0 = rjp;
+    --len;
+  }
+}
+
+template <typename T, int OP, int PAT = 0>
+__global__ void __launch_bounds__(kBlock, 4) p1_march_kernel(FusedArgs<T> A) {
+  const int lane = threadIdx.x & 31;
+  const int wg = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if ((int)blockIdx.x < A.nb_items) {
+    if (wg < A.n_items) interface_item<T, OP, false>(A, wg, lane);
+  } else {
+    const int t = wg - A.nb_items * kWarps;
+    if (t < A.n_march) march_item<T, OP, PAT>(A, t, lane);
+  }
+}
+
 // Block `blk` of one operator application: interface items first, then tiles.
 template <typename T, int OP, int R, bool ST = false, int PAT = 0>
 __device__ __forceinline__ void p1_block(const FusedArgs<T>& A, int blk) {
@@ -309,13 +401,26 @@ FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
   A.dvec = (T*)a.dvec;
   A.cheb_a = (T)a.cheb_a;
   A.err = L.err;
+  A.march = L.march;
+  A.n_march_cell = L.n_march_cell;
+  A.n_march = L.n_march_cell * L.ncells;
   return A;
 }
 
 template <typename T, int OP>
-int run_p1(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
+int run_p1(const LevelDev& L, const StencilArgs& a, cudaStream_t s, bool march) {
   const int n_items = L.n_citems;
   FusedArgs<T> A = fused_args<T>(L, a, n_items);
+  if (march && !a.sst) {
+    const int grid = A.nb_items + (A.n_march + kWarps - 1) / kWarps;
+    if (grid == 0) return HG_OK;
+    if (a.pattern == kPat7)
+      p1_march_kernel<T, OP, kPat7><<<grid, kBlock, 0, s>>>(A);
+    else
+      p1_march_kernel<T, OP><<<grid, kBlock, 0, s>>>(A);
+    HG_CUDA(cudaGetLastError());
+    return HG_OK;
+  }
   const int grid = A.nb_items + (A.n_tiles + kWarps - 1) / kWarps;
   if (grid == 0) return HG_OK;
   if (a.sst)
@@ -329,13 +434,13 @@ int run_p1(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
 }
 
 template <typename T>
-int run_p1_op(const LevelDev& L, const StencilArgs& a, cudaStream_t s) {
+int run_p1_op(const LevelDev& L, const StencilArgs& a, cudaStream_t s, bool march = false) {
   switch (a.op) {
-    case OP_APPLY: return run_p1<T, OP_APPLY>(L, a, s);
-    case OP_RESID: return run_p1<T, OP_RESID>(L, a, s);
-    case OP_JACOBI: return run_p1<T, OP_JACOBI>(L, a, s);
-    case OP_GS: return run_p1<T, OP_GS>(L, a, s);
-    case OP_CHEB: return run_p1<T, OP_CHEB>(L, a, s);
+    case OP_APPLY: return run_p1<T, OP_APPLY>(L, a, s, march);
+    case OP_RESID: return run_p1<T, OP_RESID>(L, a, s, march);
+    case OP_JACOBI: return run_p1<T, OP_JACOBI>(L, a, s, march);
+    case OP_GS: return run_p1<T, OP_GS>(L, a, s, march);
+    case OP_CHEB: return run_p1<T, OP_CHEB>(L, a, s, march);
   }
   set_error("unknown cell operation %d", a.op);
   return HG_ERR_INVALID_ARG;
@@ -662,7 +767,8 @@ constexpr int64_t kStreamAutoPoints = int64_t(8) << 20;
 }  // namespace
 
 int set_p1_kernel(int mode) {
-  if (mode != HG_P1_KERNEL_AUTO && mode != HG_P1_KERNEL_WINDOWS && mode != HG_P1_KERNEL_STREAM) {
+  if (mode != HG_P1_KERNEL_AUTO && mode != HG_P1_KERNEL_WINDOWS && mode != HG_P1_KERNEL_STREAM &&
+      mode != HG_P1_KERNEL_MARCH) {
     set_error("hg_set_p1_kernel: unknown mode %d", mode);
     return HG_ERR_INVALID_ARG;
   }
@@ -678,7 +784,8 @@ int launch_p1_const(const LevelDev& L, int dtype, const StencilArgs& a, cudaStre
                       (mode == HG_P1_KERNEL_STREAM ||
                        (mode == HG_P1_KERNEL_AUTO && dtype == HG_F32 && L.n_stored >= kStreamAutoPoints));
   if (stream) return launch_p1_stream(L, dtype, a, s);
-  return dtype == HG_F64 ? run_p1_op<double>(L, a, s) : run_p1_op<float>(L, a, s);
+  const bool march = mode == HG_P1_KERNEL_MARCH;
+  return dtype == HG_F64 ? run_p1_op<double>(L, a, s, march) : run_p1_op<float>(L, a, s, march);
 }
 
 int launch_index_enumerate(int w, int64_t* out, cudaStream_t s) {

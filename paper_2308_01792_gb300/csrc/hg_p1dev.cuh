@@ -30,6 +30,8 @@ struct FusedArgs {
   T* y;
   const T* sten;
   const T* sst;           // stored stencils [nst][16] (ST kernels) instead of sten
+  const int2* march;      // column-march items of one cell (march kernel)
+  int n_march_cell, n_march;
   T omega;
   int mode, mask;
   const uint8_t* colour;  // OP_GS: colour per stored point
