@@ -278,6 +278,23 @@ def gmg_comparison(stream):
         if use:
             out[name]["fallbacks"] = G.learned_fallbacks()
         del G
+    # fewer smoothing steps per level: Jacobi and learned V(2,2) and V(1,1)
+    for nu in (2, 1):
+        for name, use in ((f"mixed_f32_ir_v{nu}{nu}", False), (f"learned_mixed_v{nu}{nu}", True)):
+            G = hg.GMG(op, nu1=nu, nu2=nu, inner_cycles=INNER_CYCLES)
+            G.set_learned(net if use else None)
+            x = H.zeros(6, torch.float64)
+            G.solve(x, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            it, rel = G.solve(x, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED,
+                              stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out[name] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel}
+            if use:
+                out[name]["fallbacks"] = G.learned_fallbacks()
+            del G
     out["learned_vs_plain_f64_speedup"] = out["plain_f64"]["s"] / out["learned_mixed"]["s"]
     out["learned_vs_mixed_speedup"] = out["mixed_f32_ir"]["s"] / out["learned_mixed"]["s"]
     # Chebyshev-accelerated Jacobi of order 2, V(1,1), FP32 cycles in FP64
@@ -1240,6 +1257,20 @@ def main():
         clk["window"] = (f"0.5 s of the same apply (untimed) before the timed region "
                          f"({ms:.1f} ms) and the region itself")
     ms_step, value = aggregate_replicas(ms, nu, args.steps, pg, "cuda")
+    # the same bytes moved by a plain device copy (torch copy_, a library
+    # kernel) over the same rotation of buffers: the ceiling at this size
+    cp_src = [torch.empty(nu, dtype=dt, device="cuda").fill_(1.0) for _ in range(N_PAIRS)]
+    cp_dst = [torch.empty_like(v) for v in cp_src]
+    for q in range(3):
+        cp_dst[q].copy_(cp_src[q])
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for q in range(args.steps):
+        cp_dst[q % N_PAIRS].copy_(cp_src[q % N_PAIRS])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    copy_us = e0.elapsed_time(e1) / args.steps * 1e3
+    del cp_src, cp_dst
 
     # end to end through the public API with host buffers: every step copies
     # its canonical input from pinned host memory into a function of the
@@ -1299,9 +1330,15 @@ def main():
                    "parallelism": f"replicas{ws}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "p1_fused_kernel<float,APPLY> (one launch per apply)",
+                     "kernel": "p1_fused_kernel<float,APPLY,kPat7> (plane windows, one launch "
+                               "per apply)",
                      "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch":
-                         BYTES_PER_DOF * nu},
+                         BYTES_PER_DOF * nu,
+                     "copy_same_bytes": {
+                         "us": copy_us, "frac_of_peak": BYTES_PER_DOF * nu / (copy_us * 1e-6) / 1e9
+                         / peak, "apply_rate_over_copy_rate": copy_us / (ms_step * 1e3),
+                         "note": "torch copy_ of the apply's 8 B per DoF, same rotation: the "
+                                 "ceiling of a launch of this size"}},
         "e2e": {"value": nu / (e2e_ms * 1e-3) / 1e9, "unit": "GDoF/s",
                 "h2d_bytes_per_step": 4 * nu, "d2h_bytes_per_step": 4 * nu,
                 "path": "hg_function_copy_canonical (pinned host -> device) + hg_apply_function "

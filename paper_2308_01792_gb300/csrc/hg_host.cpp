@@ -1176,7 +1176,8 @@ int Op::build_surrogate(const double* coeff, int degree) {
     std::vector<double> B;
     for (int k = 1; k <= n - 1; ++k)
       for (int j = 1; j + k <= n - 1; ++j) {
-        for (int i0 = 1; i0 + j + k <= n - 1; i0 += 32) segs.push_back(j | (k << 10) | (i0 << 20));
+        if ((j - 1) % kSurRows == 0 && j + k <= n - 2)
+          segs.push_back(j | (k << 10) | (std::min(j + kSurRows, n - 1 - k) << 20));
         for (int i = 1; i + j + k <= n - 1; ++i) {
           pidx.push_back((int)tw(w, i, j, k));
           const double v[3] = {(double)i / n - 0.25, (double)j / n - 0.25, (double)k / n - 0.25};

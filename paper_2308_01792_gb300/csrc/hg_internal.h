@@ -348,7 +348,8 @@ int launch_p1_divkgrad(const LevelDev& L, int dtype, const StencilArgs& a, const
 // Polynomial surrogate of the div-k-grad operator: degree, coefficients
 // [ncells][15][nterm] (terms ordered by the power of i, then of j, then of
 // k, in the shifted coordinates i/n - 1/4, j/n - 1/4, k/n - 1/4) and the
-// interior row segments of one cell (j | k << 10 | i0 << 20, up to 32 points).
+// bands of interior rows of one cell (j0 | k << 10 | j1 << 20: rows
+// j0..j1-1 of plane k, at most kSurRows of them).
 struct SurCoef {
   int degree;
   const void* coef;
@@ -356,6 +357,7 @@ struct SurCoef {
   int n_segs_cell;
 };
 constexpr int kSurMaxDegree = 4;
+constexpr int kSurRows = 8;
 __host__ __device__ constexpr int sur_nterm(int q) { return (q + 1) * (q + 2) * (q + 3) / 6; }
 int launch_p1_surrogate(const LevelDev& L, int dtype, const StencilArgs& a, const VarCoef& vc,
                         const SurCoef& sc, cudaStream_t s);

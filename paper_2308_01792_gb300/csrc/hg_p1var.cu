@@ -128,7 +128,7 @@ struct VarArgs {
   T* dvec;                // OP_CHEB: direction, updated in place
   T cheb_a;               // OP_CHEB: weight of the previous direction
   // surrogate form: polynomial coefficients [ncells][15][nterm], degree and
-  // the interior row segments of one cell
+  // the bands of interior rows of one cell (j0 | k << 10 | j1 << 20)
   const T* sc;
   int sdeg;
   const int* segs;
@@ -404,87 +404,105 @@ __device__ void var_plane_tile(const VarArgs<T>& A, int t, int lane,
   __syncwarp();
 }
 
-// Row segment t of the surrogate operator (Sec. 5.2, surrogates): up to 32
-// consecutive interior points (i0 + lane, j, k) of one lattice row.  The warp
-// first forms the row's one-dimensional coefficients rowc[d][m] (weight of
-// direction d = sum_m rowc[d][m] xi^m, xi = i/n - 1/4) from the cell's
-// polynomial in (xi, eta, zeta) at the row's eta = j/n - 1/4 and
-// zeta = k/n - 1/4; every lane then evaluates its point's 15 weights by
-// Horner's rule and applies them to the 15 neighbours of x (all inside the
-// cell's lattice for an interior point).
-template <typename T, int OP>
-__device__ void sur_segment(const VarArgs<T>& A, int t, int lane, T* __restrict__ rowc) {
+// Band t of the surrogate operator (Sec. 5.2, surrogates): rows j0..j1-1 of
+// plane k of one cell, cell-interior points only.  Lane d < 15 first forms
+// the plane's coefficients of direction d in (xi, eta) at the plane's
+// zeta = k/n - 1/4 (C2[a][b] = sum_c C[d][a,b,c] zeta^c); per row it forms
+// rowc[d][m] = sum_b C2[m][b] eta^b (eta = j/n - 1/4) in shared memory, and
+// every lane then evaluates its point's 15 weights by Horner's rule in
+// xi = i/n - 1/4 and applies them to the 15 neighbours of x (all inside the
+// cell's lattice for an interior point).  Q: the degree, fixed at compile time.
+template <typename T, int OP, int Q>
+__device__ void sur_band(const VarArgs<T>& A, int t, int lane, T* __restrict__ rowc) {
+  constexpr int Q1 = Q + 1, NT = sur_nterm(Q);
   const int cell = t / A.n_segs_cell;
   const int sg = A.segs[t - cell * A.n_segs_cell];
-  const int j = sg & 1023, k = (sg >> 10) & 1023, i0 = sg >> 20;
-  const int n = A.n, w = A.w, q = A.sdeg, q1 = q + 1, nt = sur_nterm(q);
+  const int j0 = sg & 1023, k = (sg >> 10) & 1023, j1 = sg >> 20;
+  const int n = A.n, w = A.w;
   const T inv_n = T(1) / T(n);  // n is a power of two: exact
-  const T eta = T(j) * inv_n - T(0.25), zeta = T(k) * inv_n - T(0.25);
-  const T* __restrict__ C = A.sc + (int64_t)cell * kNDir * nt;
-  for (int e = lane; e < kNDir * q1; e += 32) {
-    const int d = e / q1, m = e - d * q1;
-    // terms with power m of xi follow those of the lower powers
-    int tt = 0;
-    for (int a = 0; a < m; ++a) tt += (q - a + 1) * (q - a + 2) / 2;
-    T acc = T(0), eb = T(1);
-    for (int b = 0; b <= q - m; ++b) {
-      T ec = eb;
-      for (int c = 0; c <= q - m - b; ++c) {
-        acc = fma(__ldg(C + d * nt + tt), ec, acc);
-        ++tt;
-        ec *= zeta;
-      }
-      eb *= eta;
-    }
-    rowc[e] = acc;
-  }
-  __syncwarp();
-  const int i = i0 + lane;
-  const bool ok = i + j + k <= n - 1;
-  const int ic = ok ? i : i0;  // lanes past the row's end evaluate its first point, unstored
-  const T xi = T(ic) * inv_n - T(0.25);
-  const int64_t base = (int64_t)cell * A.stride;
-  const int len = w - k - j;
-  const int r0 = row_start(w, j, k);
-  const int rjp = r0 + len, rjm = r0 - (len + 1);
-  const int rkp = r0 + ntri32(w - k - 1) + len, rkm = r0 - ntri32(w - k) - (len + 1);
-  const int rjmkp = rkp - len, rjpkm = rkm + len + 1;
-  const int rows[kNDir] = {r0,  r0,  r0,  rjp,   rjm,   rkp,   rkm,  rjp,
-                           rjm, rkp, rkm, rjmkp, rjpkm, rjmkp, rjpkm};
-  T acc = T(0), centre = T(0);
+  const T zeta = T(k) * inv_n - T(0.25);
+  T c2[Q1][Q1];
 #pragma unroll
-  for (int d = 0; d < kNDir; ++d) {
-    T wd = rowc[d * q1 + q];
-    for (int m = q - 1; m >= 0; --m) wd = fma(wd, xi, rowc[d * q1 + m]);
-    if (d == 0) centre = wd;
-    if (OP != OP_DIAG) {
-      int di, dj, dk;
-      dir_offset(d, di, dj, dk);
-      acc = fma(wd, __ldg(A.x + base + rows[d] + ic + di), acc);
-    }
+  for (int a = 0; a < Q1; ++a)
+#pragma unroll
+    for (int b = 0; b < Q1; ++b) c2[a][b] = T(0);
+  if (lane < kNDir) {
+    const T* __restrict__ C = A.sc + ((int64_t)cell * kNDir + lane) * NT;
+    int tt = 0;
+#pragma unroll
+    for (int a = 0; a <= Q; ++a)
+#pragma unroll
+      for (int b = 0; a + b <= Q; ++b) {
+        // Horner in zeta over the terms c = 0..Q-a-b (stored in ascending c)
+        T acc = T(0);
+#pragma unroll
+        for (int c = Q - a - b; c >= 0; --c) acc = fma(acc, zeta, __ldg(C + tt + c));
+        tt += Q - a - b + 1;
+        c2[a][b] = acc;
+      }
   }
-  if (OP == OP_DIAG) acc = centre;
-  if (ok) {
-    const int64_t idx = base + r0 + ic;
-    if (OP == OP_APPLY || OP == OP_DIAG) {
-      A.y[idx] = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[idx] + acc : acc;
-    } else if (OP == OP_RESID) {
-      A.y[idx] = A.b[idx] - acc;
-    } else {
-      const T x0 = A.x[idx];
-      if (OP == OP_GS) {
-        A.y[idx] = A.colour[idx] == A.gs_colour ? x0 + (A.b[idx] - acc) * A.invdiag[idx] : x0;
-      } else if (OP == OP_CHEB) {
-        T dn = A.omega * (A.b[idx] - acc) * A.invdiag[idx];
-        if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[idx];
-        A.dvec[idx] = dn;
-        A.y[idx] = x0 + dn;
-      } else {
-        A.y[idx] = x0 + A.omega * (A.b[idx] - acc) * A.invdiag[idx];
+  const int64_t base = (int64_t)cell * A.stride;
+  for (int j = j0; j < j1; ++j) {
+    const T eta = T(j) * inv_n - T(0.25);
+    if (lane < kNDir) {
+#pragma unroll
+      for (int m = 0; m <= Q; ++m) {
+        T acc = T(0);
+#pragma unroll
+        for (int b = Q - m; b >= 0; --b) acc = fma(acc, eta, c2[m][b]);
+        rowc[lane * Q1 + m] = acc;
       }
     }
+    __syncwarp();
+    const int len = w - k - j;
+    const int r0 = row_start(w, j, k);
+    const int rjp = r0 + len, rjm = r0 - (len + 1);
+    const int rkp = r0 + ntri32(w - k - 1) + len, rkm = r0 - ntri32(w - k) - (len + 1);
+    const int rjmkp = rkp - len, rjpkm = rkm + len + 1;
+    const int rows[kNDir] = {r0,  r0,  r0,  rjp,   rjm,   rkp,   rkm,  rjp,
+                             rjm, rkp, rkm, rjmkp, rjpkm, rjmkp, rjpkm};
+    for (int i0 = 1; i0 <= len - 2; i0 += 32) {
+      const int i = i0 + lane;
+      const bool ok = i <= len - 2;
+      const int ic = ok ? i : i0;  // lanes past the row's last interior point: unstored
+      const T xi = T(ic) * inv_n - T(0.25);
+      T acc = T(0), centre = T(0);
+#pragma unroll
+      for (int d = 0; d < kNDir; ++d) {
+        T wd = rowc[d * Q1 + Q];
+#pragma unroll
+        for (int m = Q - 1; m >= 0; --m) wd = fma(wd, xi, rowc[d * Q1 + m]);
+        if (d == 0) centre = wd;
+        if (OP != OP_DIAG) {
+          int di, dj, dk;
+          dir_offset(d, di, dj, dk);
+          acc = fma(wd, __ldg(A.x + base + rows[d] + ic + di), acc);
+        }
+      }
+      if (OP == OP_DIAG) acc = centre;
+      if (ok) {
+        const int64_t idx = base + r0 + ic;
+        if (OP == OP_APPLY || OP == OP_DIAG) {
+          A.y[idx] = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[idx] + acc : acc;
+        } else if (OP == OP_RESID) {
+          A.y[idx] = A.b[idx] - acc;
+        } else {
+          const T x0 = A.x[idx];
+          if (OP == OP_GS) {
+            A.y[idx] = A.colour[idx] == A.gs_colour ? x0 + (A.b[idx] - acc) * A.invdiag[idx] : x0;
+          } else if (OP == OP_CHEB) {
+            T dn = A.omega * (A.b[idx] - acc) * A.invdiag[idx];
+            if (A.cheb_a != T(0)) dn += A.cheb_a * A.dvec[idx];
+            A.dvec[idx] = dn;
+            A.y[idx] = x0 + dn;
+          } else {
+            A.y[idx] = x0 + A.omega * (A.b[idx] - acc) * A.invdiag[idx];
+          }
+        }
+      }
+    }
+    __syncwarp();
   }
-  __syncwarp();
 }
 
 template <typename T, int OP, bool SUR>
@@ -499,8 +517,16 @@ __global__ void __launch_bounds__(kBlock) p1var_kernel(VarArgs<T> A) {
   } else {
     const int t = wg - A.nb_items * kWarps;
     if (SUR) {
-      if (t < A.n_segs)
-        sur_segment<T, OP>(A, t, lane, reinterpret_cast<T*>(Ks[threadIdx.x >> 5]));
+      if (t < A.n_segs) {
+        T* rowc = reinterpret_cast<T*>(Ks[threadIdx.x >> 5]);
+        switch (A.sdeg) {
+          case 0: sur_band<T, OP, 0>(A, t, lane, rowc); break;
+          case 1: sur_band<T, OP, 1>(A, t, lane, rowc); break;
+          case 2: sur_band<T, OP, 2>(A, t, lane, rowc); break;
+          case 3: sur_band<T, OP, 3>(A, t, lane, rowc); break;
+          default: sur_band<T, OP, 4>(A, t, lane, rowc); break;
+        }
+      }
     } else if (t < A.n_tiles) {
       var_plane_tile<T, OP>(A, t, lane, Ks[threadIdx.x >> 5]);
     }
