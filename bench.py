@@ -542,6 +542,8 @@ def n1_solve_comparison(stream, level=6, m=2):
     Hiptmair's hybrid smoother (weighted Jacobi, omega = 1/2, in the edge and
     the potential space), coarsest level 1.  Solves to 1e-8 relative residual
     with FP32 V(2,2) cycles in FP64 refinement and with FP64 V(2,2) cycles,
+    and one FP32 FMG pass with 5 V(1,1) per level; then the paper's
+    smoother, order-2 Chebyshev in both spaces: the mixed solve with V(1,1)
     and one FP32 FMG pass with 5 V(1,1) per level."""
     import torch
     import paper_2308_01792_gb300 as hg
@@ -577,6 +579,33 @@ def n1_solve_comparison(stream, level=6, m=2):
         out[name] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel,
                      "timed_after_warmup": True}
     out["mixed_vs_f64_speedup"] = out["plain_f64"]["s"] / out["mixed_f32_ir"]["s"]
+    del G
+    # the paper's smoother: order-2 Chebyshev in both spaces, V(1,1)
+    G = hg.GMG(op, nu1=1, nu2=1, lmin=1, inner_cycles=INNER_CYCLES, smoother=hg.HG_SMOOTH_CHEB)
+    x = H.zeros(level, torch.float64, space=P2)
+    G.solve(x, b, tol=1e-8, max_iter=100, precision=hg.HG_PREC_MIXED, stream=stream, check=False)
+    torch.cuda.synchronize()
+    x.zero_()
+    e0.record(stream)
+    it, rel = G.solve(x, b, tol=1e-8, max_iter=100, precision=hg.HG_PREC_MIXED, stream=stream,
+                      check=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["mixed_f32_ir_cheb2_v11"] = {"s": e0.elapsed_time(e1) / 1e3, "iters": it, "rel_res": rel,
+                                     "timed_after_warmup": True}
+    xf = H.zeros(level, torch.float32, space=P2)
+    bf = b.float()
+    G.fmg(level, xf, bf, cycles=5, stream=stream)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    G.fmg(level, xf, bf, cycles=5, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    r = H.zeros(level, torch.float64, space=P2)
+    op.residual(level, xf.double(), b, r)
+    out["fmg_f32_cheb2"] = {"s": e0.elapsed_time(e1) / 1e3, "cycles_per_level": 5,
+                            "rel_res": float(np.sqrt(H.dot(level, r, r, space=P2) /
+                                                     H.dot(level, b, b, space=P2)))}
     del G
     G = hg.GMG(op, nu1=1, nu2=1, omega=0.5, lmin=1)
     xf = H.zeros(level, torch.float32, space=P2)

@@ -494,12 +494,15 @@ int hg_dot_noalloc(const hg_hier* hier, int space, int level, int dtype, const v
  * FP64 solve on the coarsest level (dense Cholesky inverse, <= 2048
  * unknowns; built at creation by applying the operator to unit vectors).
  * Every P1 and P2 operator kind is accepted.  For HG_OP_N1_CURLCURL the
- * smoothing is Hiptmair's hybrid scheme (Sec. 6): a weighted-Jacobi step on
- * the edge operator, the residual taken to the P1 potential space by G^T, a
- * weighted-Jacobi step with G^T A G = beta * (P1 Laplacian) and the
- * correction G e_p added; N1 transfers; weighted Jacobi only, omega in
- * (0, 0.6] (lambda_max(D^-1 A) exceeds 3 for the edge matrices; 1/2 is the
- * tested choice), else HG_ERR_INVALID_ARG. */
+ * smoothing is Hiptmair's hybrid scheme (Sec. 6): a smoothing step on the
+ * edge operator, the residual taken to the P1 potential space by G^T, a
+ * smoothing step from zero with G^T A G = beta * (P1 Laplacian) and the
+ * correction G e_p added; N1 transfers.  Smoothers: HG_SMOOTH_JACOBI
+ * (weighted Jacobi in both spaces, omega in (0, 0.6]: lambda_max(D^-1 A)
+ * exceeds 3 for the edge matrices; 1/2 is the tested choice; else
+ * HG_ERR_INVALID_ARG) or HG_SMOOTH_CHEB (cheb_order Chebyshev steps in both
+ * spaces on [cheb_lo, cheb_hi] times each space's lambda_max, the paper's
+ * choice); HG_SMOOTH_GS: HG_ERR_UNSUPPORTED. */
 enum { HG_PREC_F64 = 0,   /* plain FP64 V-cycles                                  */
        HG_PREC_MIXED = 1  /* FP32 V-cycles inside FP64 iterative refinement: the
                              outer residual, norms and coarse solve stay FP64   */
@@ -573,6 +576,13 @@ int hg_gmg_lambda(const hg_gmg* g, int level, double* lam);
 int hg_gmg_set_lambda(hg_gmg* g, int level, double lam);
 int hg_gmg_power_lambda(hg_gmg* g, int level, const double* v0, int iters, double* lam,
                         void* stream);
+/* Nedelec multigrid with Chebyshev smoothing: lambda_max(D^-1 K) of the
+ * potential space (the P1 Laplacian K; D^-1 A is the same for beta K) per
+ * smoothed level, estimated at creation like the edge space's (power
+ * iteration from the SplitMix64 start vector of the P1 canonical DoFs);
+ * read and replace it.  HG_ERR_INVALID_ARG for other operators. */
+int hg_gmg_potential_lambda(const hg_gmg* g, int level, double* lam);
+int hg_gmg_set_potential_lambda(hg_gmg* g, int level, double lam);
 
 /* Full multigrid (nested iteration; the paper's solver in Sec. 6 runs five
  * V(1,1) cycles per level): b (stored vector of dtype on `level`) is

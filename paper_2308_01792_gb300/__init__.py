@@ -95,6 +95,8 @@ SIGNATURES = {
     "hg_batch_tuning": (_I, [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), _PD]),
     "hg_gmg_lambda": (_I, [_P, _I, _PD]),
     "hg_gmg_set_lambda": (_I, [_P, _I, _D]),
+    "hg_gmg_potential_lambda": (_I, [_P, _I, _PD]),
+    "hg_gmg_set_potential_lambda": (_I, [_P, _I, _D]),
     "hg_gmg_power_lambda": (_I, [_P, _I, _P, _I, _PD, _P]),
     "hg_fmg": (_I, [_P, _I, _I, _P, _P, _I, _P]),
     "hg_n1_prolong_table": (_I, [_P, _P, _P, _P, _P]),
@@ -529,6 +531,15 @@ class GMG:
 
     def set_lam(self, level, lam):
         _call("hg_gmg_set_lambda", self._h, level, float(lam))
+
+    def lam_potential(self, level):
+        """Nedelec multigrid: lambda_max(D^-1 K) of the potential space on `level`."""
+        v = ctypes.c_double()
+        _call("hg_gmg_potential_lambda", self._h, level, ctypes.byref(v))
+        return v.value
+
+    def set_lam_potential(self, level, lam):
+        _call("hg_gmg_set_potential_lambda", self._h, level, float(lam))
 
     def power_lambda(self, level, v0, iters=20, stream=None):
         """Power-iteration estimate of lambda_max(D^-1 A) from the FP64 stored vector v0."""

@@ -25,6 +25,7 @@ struct Gmg {
   enum { WX = 0, WB = 1, WR = 2, WT = 3, WD = 4, WF = 5, NWORK = 6 };
   std::vector<void*> work[2][NWORK];  // [dtype][kind][level - lmin]
   std::vector<double> lam;         // Chebyshev: lambda_max(D^-1 A) per level - lmin
+  std::vector<double> lam_p;       // Nedelec + Chebyshev: lambda_max of the potential space
   double* r64 = nullptr;          // FP64 residual at lmax
   float* b32 = nullptr;           // scaled FP32 residual at lmax
   float* d32 = nullptr;           // FP32 correction at lmax
@@ -38,7 +39,8 @@ struct Gmg {
   // Nedelec operators: Hiptmair smoothing with the P1 Laplacian of the same
   // hierarchy as the potential-space operator (G^T A G = beta K_P1)
   Op* pot = nullptr;
-  std::vector<void*> pwork[2][3];   // [dtype][residual, correction, zero][level - lmin]
+  // [dtype][residual, correction, zero, second iterate, direction][level - lmin]
+  std::vector<void*> pwork[2][5];
   bool is_n1() const { return op->kind == HG_OP_N1_CURLCURL; }
 
   const LevelDev& L(int l) const { return op->dev(l); }
@@ -63,7 +65,7 @@ struct Gmg {
 
   int alloc_pot(int dt) {
     if (!pwork[dt][0].empty()) return HG_OK;
-    for (int kind = 0; kind < 3; ++kind) {
+    for (int kind = 0; kind < 5; ++kind) {
       pwork[dt][kind].assign(lmax - lmin + 1, nullptr);
       for (int l = lmin + 1; l <= lmax; ++l) {
         const size_t nb = pot->dev(l).n_stored * (dt == HG_F64 ? 8 : 4);
@@ -87,10 +89,15 @@ struct Gmg {
                                     : launch_prolong_p1(L(l), L(l - 1), dt, ec, xf, s);
   }
 
-  // Hiptmair hybrid smoothing (Sec. 6): per step a weighted-Jacobi step on A,
-  // the residual taken to the potential space by G^T, one weighted-Jacobi step
-  // from zero with G^T A G = beta K_P1 (weight omega / beta on the P1
-  // Laplacian), and the correction G e_p added; the steps ping-pong x and t.
+  // Hiptmair hybrid smoothing (Sec. 6): per step a smoothing step on A in the
+  // edge space, the residual taken to the potential space by G^T, a
+  // smoothing step from zero with G^T A G = beta K_P1, and the correction
+  // G e_p added; the steps ping-pong x and t.  Jacobi (weight omega; in the
+  // potential space omega / beta on the P1 Laplacian, exact from zero) or,
+  // with HG_SMOOTH_CHEB, cheb_order Chebyshev steps in both spaces (the
+  // paper's choice).  The potential iteration runs in y = beta e_p, for which
+  // it is the plain Chebyshev iteration on K_P1 y = G^T r (D^-1 A is the same
+  // for beta K_P1 and K_P1), and G y / beta is added.
   int smooth_hiptmair(int l, int dt, void* x, const void* b, int nu, cudaStream_t s) {
     void* t = W(dt, WT, l);
     void* r = W(dt, WR, l);
@@ -98,24 +105,65 @@ struct Gmg {
     void* ep = pwork[dt][1][l - lmin];
     void* z = pwork[dt][2][l - lmin];
     const LevelDev& Lp = pot->dev(l);
+    const bool cheb = prm.smoother == HG_SMOOTH_CHEB;
     for (int q = 0; q < nu; ++q) {
       const void* src = (q % 2 == 0) ? x : t;
       void* dst = (q % 2 == 0) ? t : x;
-      if (int e = cell_op(l, dt, OP_JACOBI, src, b, dst, s)) return e;
+      if (cheb) {
+        // the iterates alternate between r and dst so that the last lands in dst
+        if (int e = cheb_poly(op, l, dt, lam[l - lmin], src, b, dst, r, W(dt, WD, l), s)) return e;
+      } else {
+        if (int e = cell_op(l, dt, OP_JACOBI, src, b, dst, s)) return e;
+      }
       if (int e = cell_op(l, dt, OP_RESID, dst, b, r, s)) return e;
       if (int e = launch_n1_transfer(N1_GRADT, L(l), Lp, dt, op->n1sign, r, rp, s)) return e;
-      StencilArgs a{};
-      a.x = z;
-      a.b = rp;
-      a.out = ep;
-      a.op = OP_JACOBI;
-      a.mode = HG_REPLACE;
-      a.mask = HG_MASK_INNER;
-      a.omega = prm.omega / op->n1beta;
-      if (int e = pot->launch(l, dt, a, s)) return e;
-      if (int e = launch_n1_transfer(N1_GRAD_ADD, L(l), Lp, dt, op->n1sign, ep, dst, s)) return e;
+      if (cheb) {
+        if (int e = cheb_poly(pot, l, dt, lam_p[l - lmin], z, rp, ep, pwork[dt][3][l - lmin],
+                              pwork[dt][4][l - lmin], s))
+          return e;
+        if (int e = launch_n1_transfer(N1_GRAD_ADD, L(l), Lp, dt, op->n1sign, ep, dst, s,
+                                       1.0 / op->n1beta))
+          return e;
+      } else {
+        StencilArgs a{};
+        a.x = z;
+        a.b = rp;
+        a.out = ep;
+        a.op = OP_JACOBI;
+        a.mode = HG_REPLACE;
+        a.mask = HG_MASK_INNER;
+        a.omega = prm.omega / op->n1beta;
+        if (int e = pot->launch(l, dt, a, s)) return e;
+        if (int e = launch_n1_transfer(N1_GRAD_ADD, L(l), Lp, dt, op->n1sign, ep, dst, s)) return e;
+      }
     }
     if (nu % 2) HG_CUDA(cudaMemcpyAsync(x, t, bytes(l, dt), cudaMemcpyDeviceToDevice, s));
+    return HG_OK;
+  }
+
+  // One Chebyshev polynomial (cheb_order steps on [cheb_lo, cheb_hi] lam) of
+  // operator o from x0 towards o^-1 b; the iterates alternate between `tmp`
+  // and `out` so that the last lands in `out` (x0 is only read); d: the
+  // direction vector.
+  int cheb_poly(const Op* o, int l, int dt, double lm, const void* x0, const void* b, void* out,
+                void* tmp, void* d, cudaStream_t s) {
+    const double theta = 0.5 * (prm.cheb_hi + prm.cheb_lo) * lm;
+    const double delta = 0.5 * (prm.cheb_hi - prm.cheb_lo) * lm;
+    const double sigma = theta / delta;
+    double rho = 1.0 / sigma;
+    const void* cur = x0;
+    for (int k = 0; k < prm.cheb_order; ++k) {
+      void* nxt = ((prm.cheb_order - 1 - k) % 2 == 0) ? out : tmp;
+      double a = 0.0, beta = 1.0 / theta;
+      if (k > 0) {
+        const double rho_new = 1.0 / (2.0 * sigma - rho);
+        a = rho_new * rho;
+        beta = 2.0 * rho_new / delta;
+        rho = rho_new;
+      }
+      if (int r = cheb_op(l, dt, cur, b, nxt, d, a, beta, s, o)) return r;
+      cur = nxt;
+    }
     return HG_OK;
   }
 
@@ -144,7 +192,7 @@ struct Gmg {
 
   // One Chebyshev step: d = a d + beta D^-1 (b - A x), out = x + d.
   int cheb_op(int l, int dt, const void* x, const void* b, void* out, void* d, double a,
-              double beta, cudaStream_t s) {
+              double beta, cudaStream_t s, const Op* o = nullptr) {
     StencilArgs st{};
     st.x = x;
     st.b = b;
@@ -155,32 +203,55 @@ struct Gmg {
     st.omega = beta;
     st.dvec = d;
     st.cheb_a = a;
-    return op->launch(l, dt, st, s);
+    return (o ? o : op)->launch(l, dt, st, s);
   }
 
   // Power iteration for lambda_max(D^-1 A) on level l (FP64): v = masked v0,
   // then `iters` times w = D^-1 A v / ||v||, lambda = ||w||, v = w.  The
   // normalisation rides in the step's residual weight (b = 0, beta = -1/||v||).
-  int power_lambda(int l, const double* v0, int iters, double* out, cudaStream_t s) {
+  int power_lambda(int l, const double* v0, int iters, double* out, cudaStream_t s,
+                   bool potential = false) {
     if (int r = alloc_work(HG_F64)) return r;
-    double* zero = (double*)W(HG_F64, WB, l);
-    double* v = (double*)W(HG_F64, WX, l);
-    double* w = (double*)W(HG_F64, WD, l);
-    double* scratch = (double*)W(HG_F64, WT, l);
-    HG_CUDA(cudaMemsetAsync(zero, 0, bytes(l, HG_F64), s));
-    HG_CUDA(cudaMemsetAsync(w, 0, bytes(l, HG_F64), s));
+    const Op* o = potential ? pot : op;
+    const LevelDev& Lv = o->dev(l);
+    const size_t nb = Lv.n_stored * sizeof(double);
+    double* zero = (double*)(potential ? pwork[HG_F64][2][l - lmin] : W(HG_F64, WB, l));
+    double* v = (double*)(potential ? pwork[HG_F64][0][l - lmin] : W(HG_F64, WX, l));
+    double* w = (double*)(potential ? pwork[HG_F64][1][l - lmin] : W(HG_F64, WD, l));
+    double* scratch = (double*)(potential ? pwork[HG_F64][3][l - lmin] : W(HG_F64, WT, l));
+    HG_CUDA(cudaMemsetAsync(zero, 0, nb, s));
+    HG_CUDA(cudaMemsetAsync(w, 0, nb, s));
+    auto dotp = [&](const double* a, const double* b, double* res) {
+      if (!potential) return dot(l, HG_F64, a, b, res, s);
+      if (int r = launch_dot(Lv, HG_F64, a, b, HG_MASK_INNER, dot_scratch, dot_dev, s)) return r;
+      HG_CUDA(cudaMemcpyAsync(dot_host, dot_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+      if (int r = hier->fetch_error(s)) return r;
+      HG_CUDA(cudaStreamSynchronize(s));
+      *res = *dot_host;
+      return hier->check_error();
+    };
     // v = v0 on the non-Dirichlet DoFs, 0 elsewhere (residual of x = 0)
-    if (int r = cell_op(l, HG_F64, OP_RESID, zero, v0, v, s)) return r;
+    {
+      StencilArgs a{};
+      a.x = zero;
+      a.b = v0;
+      a.out = v;
+      a.op = OP_RESID;
+      a.mode = HG_REPLACE;
+      a.mask = HG_MASK_INNER;
+      if (int r = o->launch(l, HG_F64, a, s)) return r;
+    }
     double vv;
-    if (int r = dot(l, HG_F64, v, v, &vv, s)) return r;
+    if (int r = dotp(v, v, &vv)) return r;
     if (!(vv > 0.0)) {
       set_error("power iteration: start vector is zero on the non-Dirichlet DoFs");
       return HG_ERR_INVALID_ARG;
     }
     double lam_k = 0.0;
     for (int k = 0; k < iters; ++k) {
-      if (int r = cheb_op(l, HG_F64, v, zero, scratch, w, 0.0, -1.0 / std::sqrt(vv), s)) return r;
-      if (int r = dot(l, HG_F64, w, w, &vv, s)) return r;
+      if (int r = cheb_op(l, HG_F64, v, zero, scratch, w, 0.0, -1.0 / std::sqrt(vv), s, o))
+        return r;
+      if (int r = dotp(w, w, &vv)) return r;
       lam_k = std::sqrt(vv);
       if (!(vv > 0.0)) break;
       std::swap(v, w);
@@ -193,8 +264,11 @@ struct Gmg {
   // Flood 2014) of the canonical DoF index, mapped to [-1, 1).
   int estimate_lambdas(cudaStream_t s) {
     lam.assign(lmax - lmin + 1, 0.0);
+    lam_p.assign(lmax - lmin + 1, 0.0);
+    for (int sp = 0; sp < (is_n1() ? 2 : 1); ++sp)
     for (int l = lmin + 1; l <= lmax; ++l) {
-      const LevelHost& H = op->host(l);
+      const bool potential = sp == 1;
+      const LevelHost& H = (potential ? pot : op)->host(l);
       std::vector<double> v(H.dev.n_stored, 0.0);
       for (int64_t q = 0; q < H.dev.n_stored; ++q) {
         const int64_t u = H.canon[q];
@@ -208,7 +282,8 @@ struct Gmg {
       double* dv = nullptr;
       HG_CUDA(cudaMalloc(&dv, v.size() * sizeof(double)));
       cudaError_t e = cudaMemcpy(dv, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice);
-      int r = e == cudaSuccess ? power_lambda(l, dv, prm.cheb_iters, &lam[l - lmin], s)
+      double* dst = potential ? &lam_p[l - lmin] : &lam[l - lmin];
+      int r = e == cudaSuccess ? power_lambda(l, dv, prm.cheb_iters, dst, s, potential)
                                : cuda_fail(e, "cudaMemcpy(power start vector)");
       cudaError_t e2 = cudaStreamSynchronize(s);
       cudaFree(dv);
@@ -552,11 +627,12 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
               op->lmax);
     return HG_ERR_LEVEL_RANGE;
   }
-  if (op->kind == HG_OP_N1_CURLCURL && g->prm.smoother != HG_SMOOTH_JACOBI) {
-    set_error("Nedelec multigrid: Hiptmair smoothing with weighted Jacobi in both spaces only");
+  if (op->kind == HG_OP_N1_CURLCURL && g->prm.smoother == HG_SMOOTH_GS) {
+    set_error("Nedelec multigrid: Hiptmair smoothing with weighted Jacobi or Chebyshev only");
     return HG_ERR_UNSUPPORTED;
   }
-  if (op->kind == HG_OP_N1_CURLCURL && !(g->prm.omega > 0.0 && g->prm.omega <= 0.6)) {
+  if (op->kind == HG_OP_N1_CURLCURL && g->prm.smoother == HG_SMOOTH_JACOBI &&
+      !(g->prm.omega > 0.0 && g->prm.omega <= 0.6)) {
     // lambda_max(D^-1 A) of the edge matrices exceeds 3: larger weights diverge
     set_error("Nedelec multigrid: Jacobi weight %g outside (0, 0.6]", g->prm.omega);
     return HG_ERR_INVALID_ARG;
@@ -610,6 +686,7 @@ int hg_gmg_create(const hg_op* op, const hg_gmg_params* prm, hg_gmg** out) {
     if (int r = g->estimate_lambdas(0)) return r;
   } else {
     g->lam.assign(g->lmax - g->lmin + 1, 0.0);
+    g->lam_p.assign(g->lmax - g->lmin + 1, 0.0);
   }
   *out = g.release();
   return HG_OK;
@@ -728,6 +805,27 @@ int hg_gmg_set_lambda(hg_gmg* g, int level, double lam) {
     return HG_ERR_INVALID_ARG;
   }
   g->lam[level - g->lmin] = lam;
+  return HG_OK;
+}
+
+int hg_gmg_potential_lambda(const hg_gmg* g, int level, double* lam) {
+  if (int r = smoothed_level(g, level, "hg_gmg_potential_lambda")) return r;
+  if (!lam || !g->pot) {
+    set_error("hg_gmg_potential_lambda: null output or not a Nedelec multigrid");
+    return HG_ERR_INVALID_ARG;
+  }
+  *lam = g->lam_p[level - g->lmin];
+  return HG_OK;
+}
+
+int hg_gmg_set_potential_lambda(hg_gmg* g, int level, double lam) {
+  if (int r = smoothed_level(g, level, "hg_gmg_set_potential_lambda")) return r;
+  if (!g->pot || !(lam > 0.0) || !std::isfinite(lam)) {
+    set_error("hg_gmg_set_potential_lambda: not a Nedelec multigrid, or lambda %g not positive "
+              "and finite", lam);
+    return HG_ERR_INVALID_ARG;
+  }
+  g->lam_p[level - g->lmin] = lam;
   return HG_OK;
 }
 

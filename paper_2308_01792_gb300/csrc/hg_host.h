@@ -157,10 +157,12 @@ int n1_prolong_table(const N1ProlongTable** out);
 // N1 transfers between lattices F (fine, level l+1) and C (level l) with the
 // per-cell orientation signs (int8 [ncells][8]): N1_PROLONG xf += P ec,
 // N1_RESTRICT rc = P^T rf (fine N1 level l, coarse l-1); N1_GRAD u = G phi
-// (P1 level l on C to N1 level l on F), N1_GRADT rp = G^T r.
+// (P1 level l on C to N1 level l on F), N1_GRADT rp = G^T r, N1_GRAD_ADD
+// u += scale G phi.
 enum { N1_PROLONG = 0, N1_RESTRICT = 1, N1_GRAD = 2, N1_GRADT = 3, N1_GRAD_ADD = 4 };
 int launch_n1_transfer(int which, const LevelDev& F, const LevelDev& C, int dtype,
-                       const int8_t* sign, const void* src, void* dst, cudaStream_t s);
+                       const int8_t* sign, const void* src, void* dst, cudaStream_t s,
+                       double scale = 1.0);
 
 // A function on a level range (Sec. 5.1): one stored vector per level of one
 // space and element type, in caller-owned device memory bound level by level,

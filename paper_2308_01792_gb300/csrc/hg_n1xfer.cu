@@ -109,6 +109,7 @@ struct NDesc {
   const int8_t* sign;         // [ncells][8] orientation sign per lattice direction
   const T* src;
   T* dst;
+  T scale;                    // N1_GRAD_ADD: u += scale * G phi
 };
 
 // Coarse N1 function's DoF at fine point (I,J,K) of one cell (0 at vertex points).
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kNBlock) n1_grad_kernel(NDesc<T> D) {
       const T b = phi[tw32(wc, (i + d[0]) >> 1, (j + d[1]) >> 1, (k + d[2]) >> 1)];
       v = T(s[par - 1]) * (b - a);
     }
-    u[i] = ADD ? u[i] + v : v;
+    u[i] = ADD ? u[i] + D.scale * v : v;
   }
 }
 
@@ -333,12 +334,13 @@ NDesc<T> ndesc(const LevelDev& F, const LevelDev& C, const LevelDev& swept, cons
   D.sign = sign;
   D.src = (const T*)src;
   D.dst = (T*)dst;
+  D.scale = T(1);
   return D;
 }
 
 template <typename T>
 int run(int which, const LevelDev& F, const LevelDev& C, const int8_t* sign, const void* src,
-        void* dst, cudaStream_t s) {
+        void* dst, cudaStream_t s, double scale) {
   switch (which) {
     case 0: {  // prolongation: sweep F
       const NDesc<T> D = ndesc<T>(F, C, F, sign, src, dst);
@@ -354,6 +356,7 @@ int run(int which, const LevelDev& F, const LevelDev& C, const int8_t* sign, con
     case 4: {  // gradient (4: added): every row of F, no items
       NDesc<T> D = ndesc<T>(F, C, F, sign, src, dst);
       D.nb_items = 0;
+      D.scale = (T)scale;
       if (which == 2)
         n1_grad_kernel<T, false><<<blocks_of(D.n_rows), kNBlock, 0, s>>>(D);
       else
@@ -373,14 +376,15 @@ int run(int which, const LevelDev& F, const LevelDev& C, const int8_t* sign, con
 }  // namespace
 
 int launch_n1_transfer(int which, const LevelDev& F, const LevelDev& C, int dtype,
-                       const int8_t* sign, const void* src, void* dst, cudaStream_t s) {
+                       const int8_t* sign, const void* src, void* dst, cudaStream_t s,
+                       double scale) {
   if (int r = ensure_n1_tables()) return r;
   if (F.n != 2 * C.n) {
     set_error("N1 transfer: lattices are not consecutive levels");
     return HG_ERR_INVALID_ARG;
   }
-  return dtype == HG_F64 ? run<double>(which, F, C, sign, src, dst, s)
-                         : run<float>(which, F, C, sign, src, dst, s);
+  return dtype == HG_F64 ? run<double>(which, F, C, sign, src, dst, s, scale)
+                         : run<float>(which, F, C, sign, src, dst, s, scale);
 }
 
 }  // namespace hg
