@@ -123,9 +123,12 @@ def train(X, t, steps=2000, batch=65536, lr=2e-3, seed=11, mlp=None):
 
 
 def main(argv=None):
-    """Generate 2000 noise pairs on the 4x4x4 Kuhn cube at level 4 (fields of
-    seeds 1..250, 8 draws each), train, and save the parameters (.npy)."""
+    """Generate 2000 pairs on the 4x4x4 Kuhn cube at level 4 (fields of seeds
+    1..250, 8 per field): white-noise errors (default), states of the GPU
+    multigrid after the coarse correction (--pairs gmg), or half of each
+    (--pairs mixed); train, and save the parameters (.npy)."""
     import argparse
+    import torch
     import synthgen as sg
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", required=True)
@@ -133,8 +136,19 @@ def main(argv=None):
     ap.add_argument("--draws", type=int, default=8)
     ap.add_argument("--stride", type=int, default=16)
     ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--pairs", choices=["noise", "gmg", "mixed"], default="noise")
     a = ap.parse_args(argv)
-    X, t, npairs = make_noise_pairs(sg.kuhn_cube(4), 0, 4, range(1, a.seeds + 1), a.draws, a.stride)
+    macro = sg.kuhn_cube(4)
+    if a.pairs == "mixed":
+        H = Hierarchy(Mesh(macro.xyz, macro.cells), 0, 4)
+        half = range(1, a.seeds // 2 + 1)
+        Xn, tn, nn = make_noise_pairs(macro, 0, 4, half, a.draws, a.stride, hier=H)
+        Xg, tg, ng = make_pairs(macro, 0, 4, half, a.draws, a.stride, hier=H)
+        X, t, npairs = torch.cat([Xn, Xg]), torch.cat([tn, tg]), nn + ng
+    elif a.pairs == "gmg":
+        X, t, npairs = make_pairs(macro, 0, 4, range(1, a.seeds + 1), a.draws, a.stride)
+    else:
+        X, t, npairs = make_noise_pairs(macro, 0, 4, range(1, a.seeds + 1), a.draws, a.stride)
     net, loss = train(X, t, steps=a.steps, batch=65536, lr=1e-3)
     np.save(a.out, net.params())
     print(f"{npairs} pairs, {len(t)} samples, final loss {loss:.6g}, zero-net loss "
