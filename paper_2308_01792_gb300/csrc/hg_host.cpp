@@ -496,6 +496,26 @@ int Hier::build_level(int l) {
   }
   L.n_citems = (int)citems.size();
   if (int r = upload(&L.citems, citems)) return r;
+  {
+    // the point each lane of an apply item works on (what the kernels would
+    // otherwise derive from the primitive's point index and the copy)
+    std::vector<uint32_t> cijk((size_t)L.n_citems * 32, 0u);
+    for (int q = 0; q < L.n_citems; ++q) {
+      const int4 it = citems[q];
+      const int dim = it.z & 15, C = (it.z >> 4) & 255;
+      if (C > 32) continue;
+      for (int lane = 0; lane < 32; ++lane) {
+        const int pt = lane / C, c = lane - pt * C;
+        const bool act = pt < it.w;
+        int wts[3];
+        prim_point_weights(dim, n, it.y + (act ? pt : 0), wts);
+        int i, j, k;
+        copy_local_ijk(copies[it.x + (act ? c : 0)], dim, wts, i, j, k);
+        cijk[(size_t)q * 32 + lane] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
+      }
+    }
+    if (int r = upload(&L.cijk, cijk)) return r;
+  }
   // the same items restricted to primitives with two or more copies (the
   // streaming kernel forms every single-copy point inside its runs)
   std::vector<int4> mitems;
@@ -644,7 +664,7 @@ int Hier::build_level(int l) {
   // every table a kernel reads must be on the device
   if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
       (L.n_items && (!L.items || !L.item_prim)) ||
-      (L.n_citems && !L.citems) || (L.n_ptiles_cell && !L.ptiles) ||
+      (L.n_citems && (!L.citems || !L.cijk)) || (L.n_ptiles_cell && !L.ptiles) ||
       (L.n_march_cell && !L.march) ||
       (L.n_mitems && (!L.mitems || !L.mlanes)) || !L.splan[0].cta_items || !L.splan[1].cta_items ||
       (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
@@ -764,6 +784,7 @@ Hier::~Hier() {
     cudaFree(L.copies);
     cudaFree(L.prim_point_base);
     cudaFree(L.citems);
+    cudaFree(L.cijk);
     cudaFree(L.mitems);
     cudaFree(L.mlanes);
     for (auto& D : L.splan) {

@@ -21,6 +21,7 @@ struct FusedArgs {
   int n_tiles_cell;
   int n_tiles;        // all cells
   const int4* items;  // apply items (first_copy, p0, dim | ncopies<<4 | dirichlet<<12, points)
+  const uint32_t* cijk;  // per item and lane the copy's cell-local point (i | j<<10 | k<<20)
   int n_items;
   int nb_items;       // blocks holding interface items (first in the grid)
   const IfacePrim* prims;
@@ -112,12 +113,10 @@ __device__ __forceinline__ void cell_partial_load(const T* __restrict__ x, const
   const int rkp = r0 + ntri32(w - k - 1) + L, rkm = r0 - ntri32(w - k) - (L + 1);
   const int rjmkp = rkp - L, rjpkm = rkm + L + 1;
   const int rows[15] = {r0, r0, r0, rjp, rjm, rkp, rkm, rjp, rjm, rkp, rkm, rjmkp, rjpkm, rjmkp, rjpkm};
-  if (ST) {
-    T inv;
-    load_sten16(S, sv, inv);
-  } else {
-#pragma unroll
-    for (int d = 0; d < kNDir; ++d) sv[d] = __ldg(S + d);
+  {
+    // stored stencils and the 16-value class stencils alike: 16-byte vectors
+    T unused;
+    load_sten16(S, sv, unused);
   }
 #pragma unroll
   for (int d = 0; d < kNDir; ++d) {
@@ -216,12 +215,11 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
   const int n = A.n, w = A.w;
   const int pt = lane / C, c = lane - pt * C;
   const bool act = pt < it.w;
-  int wts[3];
-  prim_weights(dim, n, it.y + (act ? pt : 0), wts);
-  const IfaceCopy cpy = A.copies[it.x + (act ? c : 0)];
-  int i, j, k;
-  copy_local_ijk(cpy, dim, wts, i, j, k);
-  const int64_t cbase = (int64_t)cpy.cell * A.stride;
+  const int cell = A.copies[it.x + (act ? c : 0)].cell;
+  const uint32_t pk = __ldg(A.cijk + (int64_t)item * 32 + lane);
+  const int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
+  (void)dim;
+  const int64_t cbase = (int64_t)cell * A.stride;
   const int64_t g = cbase + tw32(w, i, j, k);
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
@@ -232,7 +230,7 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
       cell_partial_load<T, true>(A.x + cbase, A.sst + 16 * g, n, w, i, j, k, sv, xv);
     else
       cell_partial_load<T>(A.x + cbase,
-                           A.sten + (int64_t)cpy.cell * 256 + point_class(n, i, j, k) * 16, n, w,
+                           A.sten + (int64_t)cell * 256 + point_class(n, i, j, k) * 16, n, w,
                            i, j, k, sv, xv);
     const T part = dot15<T>(sv, xv);
     // partials of the point's C lanes, ascending copy (= cell) order

@@ -115,6 +115,7 @@ struct VarArgs {
   const int4* items;
   int n_items, nb_items;
   const IfaceCopy* copies;
+  const uint32_t* cijk;  // per item and lane the copy's cell-local point (i | j<<10 | k<<20)
   const T* x;
   const T* b;
   T* y;
@@ -254,11 +255,10 @@ __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
   const int n = A.n, w = A.w;
   const int pt = lane / C, c = lane - pt * C;
   const bool act = pt < it.w;
-  int wts[3];
-  prim_point_weights(dim, n, it.y + (act ? pt : 0), wts);
   const IfaceCopy cpy = A.copies[it.x + (act ? c : 0)];
-  int i, j, k;
-  copy_local_ijk(cpy, dim, wts, i, j, k);
+  const uint32_t pk = __ldg(A.cijk + (int64_t)item * 32 + lane);
+  const int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
+  (void)dim;
   const int64_t cbase = (int64_t)cpy.cell * A.stride;
   const int64_t g = cbase + tw32(w, i, j, k);
   T v;
@@ -545,6 +545,7 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.n_tiles = L.n_ptiles_cell * L.ncells;
   A.items = L.citems;
   A.n_items = L.n_citems;
+  A.cijk = L.cijk;
   A.nb_items = (A.n_items + kWarps - 1) / kWarps;
   A.copies = L.copies;
   A.x = (const T*)a.x;
