@@ -497,24 +497,27 @@ int Hier::build_level(int l) {
   L.n_citems = (int)citems.size();
   if (int r = upload(&L.citems, citems)) return r;
   {
-    // the point each lane of an apply item works on (what the kernels would
-    // otherwise derive from the primitive's point index and the copy)
-    std::vector<uint32_t> cijk((size_t)L.n_citems * 32, 0u);
+    // what each lane of an apply item works on (the kernels would otherwise
+    // derive it from the item, the primitive's point index and the copy)
+    std::vector<uint2> clane((size_t)L.n_citems * 32, uint2{0u, 63u << 24});
     for (int q = 0; q < L.n_citems; ++q) {
       const int4 it = citems[q];
-      const int dim = it.z & 15, C = (it.z >> 4) & 255;
+      const int dim = it.z & 15, C = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
       if (C > 32) continue;
       for (int lane = 0; lane < 32; ++lane) {
         const int pt = lane / C, c = lane - pt * C;
         const bool act = pt < it.w;
         int wts[3];
         prim_point_weights(dim, n, it.y + (act ? pt : 0), wts);
+        const IfaceCopy& cp = copies[it.x + (act ? c : 0)];
         int i, j, k;
-        copy_local_ijk(copies[it.x + (act ? c : 0)], dim, wts, i, j, k);
-        cijk[(size_t)q * 32 + lane] = (uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20);
+        copy_local_ijk(cp, dim, wts, i, j, k);
+        clane[(size_t)q * 32 + lane] =
+            uint2{(uint32_t)i | ((uint32_t)j << 10) | ((uint32_t)k << 20) | ((uint32_t)dirichlet << 30),
+                  (uint32_t)cp.cell | ((uint32_t)C << 24) | ((uint32_t)act << 30)};
       }
     }
-    if (int r = upload(&L.cijk, cijk)) return r;
+    if (int r = upload(&L.clane, clane)) return r;
   }
   // the same items restricted to primitives with two or more copies (the
   // streaming kernel forms every single-copy point inside its runs)
@@ -664,7 +667,7 @@ int Hier::build_level(int l) {
   // every table a kernel reads must be on the device
   if (!L.cls_flags || (L.n_prims && (!L.prims || !L.copies || !L.prim_point_base)) ||
       (L.n_items && (!L.items || !L.item_prim)) ||
-      (L.n_citems && (!L.citems || !L.cijk)) || (L.n_ptiles_cell && !L.ptiles) ||
+      (L.n_citems && (!L.citems || !L.clane)) || (L.n_ptiles_cell && !L.ptiles) ||
       (L.n_march_cell && !L.march) ||
       (L.n_mitems && (!L.mitems || !L.mlanes)) || !L.splan[0].cta_items || !L.splan[1].cta_items ||
       (mesh->grid_denom && (!L.canon || !L.canon_rep))) {
@@ -727,6 +730,11 @@ int Hier::check_limits() const {
       return HG_ERR_UNSUPPORTED;
     }
   }
+  if (mesh->nc >= (int64_t(1) << 24)) {
+    set_error("%lld macro cells; at most 2^24 - 1 are supported (24-bit cell ids of the apply "
+              "items)", (long long)mesh->nc);
+    return HG_ERR_UNSUPPORTED;
+  }
   for (const auto* prims : {&mesh->faces, &mesh->edges, &mesh->verts})
     for (const auto& p : *prims)
       if (p.cells.size() > 255) {
@@ -784,7 +792,7 @@ Hier::~Hier() {
     cudaFree(L.copies);
     cudaFree(L.prim_point_base);
     cudaFree(L.citems);
-    cudaFree(L.cijk);
+    cudaFree(L.clane);
     cudaFree(L.mitems);
     cudaFree(L.mlanes);
     for (auto& D : L.splan) {

@@ -189,9 +189,11 @@ struct LevelDev {
   // operator-application work items
   int4* citems;              // interface items of the apply: (first_copy, p0, meta as above,
   int n_citems;              //   points); points = floor(32 / ncopies), one lane per copy
-  uint32_t* cijk;            // [n_citems * 32]: the cell-local point of each lane's copy,
-                             //   i | j << 10 | k << 20 (lanes past the item's points: point 0,
-                             //   copy 0; items of primitives with > 32 copies: unused)
+  uint2* clane;              // [n_citems * 32]: what each lane of an apply item works on,
+                             //   x = i | j << 10 | k << 20 | dirichlet << 30 (the copy's
+                             //   cell-local point), y = cell | C << 24 | active << 30 (C: the
+                             //   primitive's copies; lanes past the item's points: point 0,
+                             //   copy 0, not active; C = 63: more than 32 copies, serial path)
   int4* mitems;              // apply items of the primitives with >= 2 copies only
   int n_mitems, n_mitems_inner;  //   (non-Dirichlet first): the streaming kernel's exchange
   int2* mlanes;              // [n_mitems * 32]: per lane the copy's stored index and

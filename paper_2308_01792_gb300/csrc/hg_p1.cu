@@ -384,7 +384,7 @@ FusedArgs<T> fused_args(const LevelDev& L, const StencilArgs& a, int n_items) {
   A.n_tiles_cell = L.n_ptiles_cell;
   A.n_tiles = L.n_ptiles_cell * L.ncells;
   A.items = L.citems;
-  A.cijk = L.cijk;
+  A.clane = L.clane;
   A.n_items = n_items;
   A.nb_items = (n_items + kWarps - 1) / kWarps;
   A.prims = L.prims;

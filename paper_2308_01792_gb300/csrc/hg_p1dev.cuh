@@ -21,7 +21,7 @@ struct FusedArgs {
   int n_tiles_cell;
   int n_tiles;        // all cells
   const int4* items;  // apply items (first_copy, p0, dim | ncopies<<4 | dirichlet<<12, points)
-  const uint32_t* cijk;  // per item and lane the copy's cell-local point (i | j<<10 | k<<20)
+  const uint2* clane;  // per item and lane: point, Dirichlet flag, cell, copies, active
   int n_items;
   int nb_items;       // blocks holding interface items (first in the grid)
   const IfacePrim* prims;
@@ -204,21 +204,21 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
 }
 
 // Apply item: lane = pt * C + c takes copy c of point pt (C copies, C <= 32).
+// Everything a lane needs comes from one 8-byte entry of the lane table.
 template <typename T, int OP, bool ST>
 __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
-  const int4 it = A.items[item];
-  const int dim = it.z & 15, C = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
+  const uint2 e = __ldg(A.clane + (int64_t)item * 32 + lane);
+  const int C = (e.y >> 24) & 63;
   if (C > 32) {
-    interface_point_serial<T, OP, ST>(A, it, lane);
+    interface_point_serial<T, OP, ST>(A, A.items[item], lane);
     return;
   }
   const int n = A.n, w = A.w;
-  const int pt = lane / C, c = lane - pt * C;
-  const bool act = pt < it.w;
-  const int cell = A.copies[it.x + (act ? c : 0)].cell;
-  const uint32_t pk = __ldg(A.cijk + (int64_t)item * 32 + lane);
-  const int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
-  (void)dim;
+  const int pt = lane / C;
+  const bool act = (e.y >> 30) & 1u;
+  const int dirichlet = (e.x >> 30) & 1u;
+  const int cell = e.y & 0xffffff;
+  const int i = e.x & 1023, j = (e.x >> 10) & 1023, k = (e.x >> 20) & 1023;
   const int64_t cbase = (int64_t)cell * A.stride;
   const int64_t g = cbase + tw32(w, i, j, k);
   T v;

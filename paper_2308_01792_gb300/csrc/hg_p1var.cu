@@ -115,7 +115,7 @@ struct VarArgs {
   const int4* items;
   int n_items, nb_items;
   const IfaceCopy* copies;
-  const uint32_t* cijk;  // per item and lane the copy's cell-local point (i | j<<10 | k<<20)
+  const uint2* clane;  // per item and lane: point, Dirichlet flag, cell, copies, active
   const T* x;
   const T* b;
   T* y;
@@ -245,21 +245,20 @@ __device__ void var_interface_point(const VarArgs<T>& A, const int4& it, int lan
 
 template <typename T, int OP>
 __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
-  const int4 it = A.items[item];
-  const int dim = it.z & 15, C = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
+  const uint2 e = __ldg(A.clane + (int64_t)item * 32 + lane);
+  const int C = (e.y >> 24) & 63;
   if (C > 32) {
     // one lane per point, copies in turn (32-point item)
-    var_interface_point<T, OP>(A, it, lane);
+    var_interface_point<T, OP>(A, A.items[item], lane);
     return;
   }
   const int n = A.n, w = A.w;
-  const int pt = lane / C, c = lane - pt * C;
-  const bool act = pt < it.w;
-  const IfaceCopy cpy = A.copies[it.x + (act ? c : 0)];
-  const uint32_t pk = __ldg(A.cijk + (int64_t)item * 32 + lane);
-  const int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
-  (void)dim;
-  const int64_t cbase = (int64_t)cpy.cell * A.stride;
+  const int pt = lane / C;
+  const bool act = (e.y >> 30) & 1u;
+  const int dirichlet = (e.x >> 30) & 1u;
+  const int cell = e.y & 0xffffff;
+  const int i = e.x & 1023, j = (e.x >> 10) & 1023, k = (e.x >> 20) & 1023;
+  const int64_t cbase = (int64_t)cell * A.stride;
   const int64_t g = cbase + tw32(w, i, j, k);
   T v;
   if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER) && OP != OP_DIAG) {
@@ -273,7 +272,7 @@ __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
       gather15<T>(A.x + cbase, n, w, i, j, k, xv);
     }
     gather15<T>(A.kc + cbase, n, w, i, j, k, kv);
-    const T part = divkgrad_point<T, false>(xv, kv, A.K + (int64_t)cpy.cell * 96,
+    const T part = divkgrad_point<T, false>(xv, kv, A.K + (int64_t)cell * 96,
                                             incidence_mask(point_class(n, i, j, k)));
     T sum = T(0);
     const int g0 = pt * C;
@@ -545,7 +544,7 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.n_tiles = L.n_ptiles_cell * L.ncells;
   A.items = L.citems;
   A.n_items = L.n_citems;
-  A.cijk = L.cijk;
+  A.clane = L.clane;
   A.nb_items = (A.n_items + kWarps - 1) / kWarps;
   A.copies = L.copies;
   A.x = (const T*)a.x;
