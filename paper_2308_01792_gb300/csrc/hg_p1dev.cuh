@@ -203,40 +203,61 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
   }
 }
 
-// Apply item: lane = pt * C + c takes copy c of point pt (C copies, C <= 32).
-// Everything a lane needs comes from one 8-byte entry of the lane table.
-template <typename T, int OP, bool ST>
-__device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
-  const uint2 e = __ldg(A.clane + (int64_t)item * 32 + lane);
-  const int C = (e.y >> 24) & 63;
-  if (C > 32) {
-    interface_point_serial<T, OP, ST>(A, A.items[item], lane);
-    return;
-  }
-  const int n = A.n, w = A.w;
-  const int pt = lane / C;
-  const bool act = (e.y >> 30) & 1u;
-  const int dirichlet = (e.x >> 30) & 1u;
-  const int cell = e.y & 0xffffff;
-  const int i = e.x & 1023, j = (e.x >> 10) & 1023, k = (e.x >> 20) & 1023;
-  const int64_t cbase = (int64_t)cell * A.stride;
-  const int64_t g = cbase + tw32(w, i, j, k);
+// One lane of an apply item (lane = pt * C + c takes copy c of point pt, C <= 32
+// copies), decoded from its 8-byte entry of the lane table.
+struct ItemLane {
+  int C, pt, dirichlet, cell, i, j, k;
+  bool act;
+  int64_t cbase, g;
+};
+
+__device__ __forceinline__ ItemLane item_lane(const uint2 e, int lane, int w, int64_t stride) {
+  ItemLane L;
+  L.C = (e.y >> 24) & 63;
+  L.pt = lane / (L.C > 0 && L.C <= 32 ? L.C : 32);
+  L.act = (e.y >> 30) & 1u;
+  L.dirichlet = (e.x >> 30) & 1u;
+  L.cell = e.y & 0xffffff;
+  L.i = e.x & 1023;
+  L.j = (e.x >> 10) & 1023;
+  L.k = (e.x >> 20) & 1023;
+  L.cbase = (int64_t)L.cell * stride;
+  L.g = L.cbase + tw32(w, L.i, L.j, L.k);
+  return L;
+}
+
+// Whether the item's output is fixed by its Dirichlet primitive (no sum).
+template <int OP>
+__device__ __forceinline__ bool item_fixed(const ItemLane& L, int mask) {
+  return L.dirichlet && (OP != OP_APPLY || mask == HG_MASK_INNER);
+}
+
+// The lane's partial stencil and neighbour values (loads only).
+template <typename T, bool ST>
+__device__ __forceinline__ void item_load(const FusedArgs<T>& A, const ItemLane& L, T sv[kNDir],
+                                          T xv[kNDir]) {
+  if (ST)
+    cell_partial_load<T, true>(A.x + L.cbase, A.sst + 16 * L.g, A.n, A.w, L.i, L.j, L.k, sv, xv);
+  else
+    cell_partial_load<T>(A.x + L.cbase,
+                         A.sten + (int64_t)L.cell * 256 + point_class(A.n, L.i, L.j, L.k) * 16,
+                         A.n, A.w, L.i, L.j, L.k, sv, xv);
+}
+
+// Sum of the point's C partials in ascending copy (= cell) order by lane
+// exchange, the operation's output, written to the lane's copy.
+template <typename T, int OP>
+__device__ __forceinline__ void item_finish(const FusedArgs<T>& A, const ItemLane& L, bool fixed,
+                                            const T sv[kNDir], const T xv[kNDir]) {
+  const int64_t g = L.g;
   T v;
-  if (dirichlet && (OP != OP_APPLY || A.mask == HG_MASK_INNER)) {
+  if (fixed) {
     v = op_scaled(OP) ? A.x[g] : T(0);
   } else {
-    T sv[kNDir], xv[kNDir];
-    if (ST)
-      cell_partial_load<T, true>(A.x + cbase, A.sst + 16 * g, n, w, i, j, k, sv, xv);
-    else
-      cell_partial_load<T>(A.x + cbase,
-                           A.sten + (int64_t)cell * 256 + point_class(n, i, j, k) * 16, n, w,
-                           i, j, k, sv, xv);
     const T part = dot15<T>(sv, xv);
-    // partials of the point's C lanes, ascending copy (= cell) order
     T sum = T(0), diag = T(0);
-    const int g0 = pt * C;
-    for (int q = 0; q < C; ++q) {
+    const int g0 = L.pt * L.C;
+    for (int q = 0; q < L.C; ++q) {
       sum += __shfl_sync(0xffffffffu, part, (g0 + q) & 31);
       if (op_scaled(OP)) diag += __shfl_sync(0xffffffffu, sv[0], (g0 + q) & 31);
     }
@@ -249,14 +270,29 @@ __device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
     } else if (OP == OP_CHEB) {
       // every copy's lane reads and writes its own copy of d
       T dn = A.omega * (A.b[g] - sum) / diag;
-      if (A.cheb_a != T(0) && act) dn += A.cheb_a * A.dvec[g];
-      if (act) A.dvec[g] = dn;
+      if (A.cheb_a != T(0) && L.act) dn += A.cheb_a * A.dvec[g];
+      if (L.act) A.dvec[g] = dn;
       v = A.x[g] + dn;
     } else {
       v = A.x[g] + A.omega * (A.b[g] - sum) / diag;
     }
   }
-  if (act) A.y[g] = v;
+  if (L.act) A.y[g] = v;
+}
+
+// Apply item (C <= 32 copies: one lane per (point, copy); more: the serial path).
+template <typename T, int OP, bool ST>
+__device__ void interface_item(const FusedArgs<T>& A, int item, int lane) {
+  const uint2 e = __ldg(A.clane + (int64_t)item * 32 + lane);
+  if (((e.y >> 24) & 63) > 32) {
+    interface_point_serial<T, OP, ST>(A, A.items[item], lane);
+    return;
+  }
+  const ItemLane L = item_lane(e, lane, A.w, A.stride);
+  const bool fixed = item_fixed<OP>(L, A.mask);
+  T sv[kNDir], xv[kNDir];
+  if (!fixed) item_load<T, ST>(A, L, sv, xv);
+  item_finish<T, OP>(A, L, fixed, sv, xv);
 }
 
 }  // namespace
