@@ -505,8 +505,10 @@ int Hier::build_level(int l) {
       const int dim = it.z & 15, C = (it.z >> 4) & 255, dirichlet = (it.z >> 12) & 1;
       if (C > 32) continue;
       for (int lane = 0; lane < 32; ++lane) {
-        const int pt = lane / C, c = lane - pt * C;
-        const bool act = pt < it.w;
+        // copy-major lanes: lane = c * P + pt (P = 32 / C points), so that the lanes of
+        // one copy hold consecutive points of the primitive in one cell
+        const int P = 32 / C, c = lane / P, pt = lane - c * P;
+        const bool act = c < C && pt < it.w;
         int wts[3];
         prim_point_weights(dim, n, it.y + (act ? pt : 0), wts);
         const IfaceCopy& cp = copies[it.x + (act ? c : 0)];

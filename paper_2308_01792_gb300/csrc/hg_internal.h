@@ -189,7 +189,8 @@ struct LevelDev {
   // operator-application work items
   int4* citems;              // interface items of the apply: (first_copy, p0, meta as above,
   int n_citems;              //   points); points = floor(32 / ncopies), one lane per copy
-  uint2* clane;              // [n_citems * 32]: what each lane of an apply item works on,
+  uint2* clane;              // [n_citems * 32]: what each lane of an apply item works on
+                             //   (lane = c * P + pt: copy c of point pt, P = 32 / C points),
                              //   x = i | j << 10 | k << 20 | dirichlet << 30 (the copy's
                              //   cell-local point), y = cell | C << 24 | active << 30 (C: the
                              //   primitive's copies; lanes past the item's points: point 0,

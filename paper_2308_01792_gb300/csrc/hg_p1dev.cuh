@@ -203,10 +203,10 @@ __device__ void interface_point_serial(const FusedArgs<T>& A, const int4& it, in
   }
 }
 
-// One lane of an apply item (lane = pt * C + c takes copy c of point pt, C <= 32
-// copies), decoded from its 8-byte entry of the lane table.
+// One lane of an apply item (lane = c * P + pt takes copy c of point pt, C <= 32
+// copies, P = 32 / C points), decoded from its 8-byte entry of the lane table.
 struct ItemLane {
-  int C, pt, dirichlet, cell, i, j, k;
+  int C, P, pt, dirichlet, cell, i, j, k;
   bool act;
   int64_t cbase, g;
 };
@@ -214,7 +214,8 @@ struct ItemLane {
 __device__ __forceinline__ ItemLane item_lane(const uint2 e, int lane, int w, int64_t stride) {
   ItemLane L;
   L.C = (e.y >> 24) & 63;
-  L.pt = lane / (L.C > 0 && L.C <= 32 ? L.C : 32);
+  L.P = 32 / (L.C > 0 && L.C <= 32 ? L.C : 32);
+  L.pt = lane % L.P;
   L.act = (e.y >> 30) & 1u;
   L.dirichlet = (e.x >> 30) & 1u;
   L.cell = e.y & 0xffffff;
@@ -256,10 +257,10 @@ __device__ __forceinline__ void item_finish(const FusedArgs<T>& A, const ItemLan
   } else {
     const T part = dot15<T>(sv, xv);
     T sum = T(0), diag = T(0);
-    const int g0 = L.pt * L.C;
     for (int q = 0; q < L.C; ++q) {
-      sum += __shfl_sync(0xffffffffu, part, (g0 + q) & 31);
-      if (op_scaled(OP)) diag += __shfl_sync(0xffffffffu, sv[0], (g0 + q) & 31);
+      const int src = (q * L.P + L.pt) & 31;
+      sum += __shfl_sync(0xffffffffu, part, src);
+      if (op_scaled(OP)) diag += __shfl_sync(0xffffffffu, sv[0], src);
     }
     if (OP == OP_APPLY) {
       v = A.mode == HG_ADD ? A.y[g] + sum : sum;

@@ -156,7 +156,7 @@ __device__ __forceinline__ void gather15(const T* __restrict__ x, int n, int w, 
   }
 }
 
-// Apply item (lane = pt * C + c takes copy c of point pt, C <= 32 copies):
+// Apply item (lane = c * P + pt takes copy c of point pt, C <= 32 copies, P = 32 / C):
 // each lane gathers its copy's partial, the point's C partials are summed in
 // ascending cell order by lane exchange and written to every copy.
 template <typename T, int OP>
@@ -253,7 +253,7 @@ __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
     return;
   }
   const int n = A.n, w = A.w;
-  const int pt = lane / C;
+  const int P = 32 / C, pt = lane % P;  // lane = copy * P + point
   const bool act = (e.y >> 30) & 1u;
   const int dirichlet = (e.x >> 30) & 1u;
   const int cell = e.y & 0xffffff;
@@ -275,8 +275,7 @@ __device__ void var_interface_item(const VarArgs<T>& A, int item, int lane) {
     const T part = divkgrad_point<T, false>(xv, kv, A.K + (int64_t)cell * 96,
                                             incidence_mask(point_class(n, i, j, k)));
     T sum = T(0);
-    const int g0 = pt * C;
-    for (int q = 0; q < C; ++q) sum += __shfl_sync(0xffffffffu, part, (g0 + q) & 31);
+    for (int q = 0; q < C; ++q) sum += __shfl_sync(0xffffffffu, part, (q * P + pt) & 31);
     if (OP == OP_APPLY || OP == OP_DIAG) {
       v = (OP == OP_APPLY && A.mode == HG_ADD) ? A.y[g] + sum : sum;
     } else if (OP == OP_RESID) {
