@@ -52,8 +52,12 @@ def _peaks():
 
 
 def _kernel_source_sha():
-    src = os.path.join(ROOT, "paper_2308_01792_gb300", "csrc", "hg_p1.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    """Hash of the headline kernel's sources (the plane-window kernel and the
+    interface items it includes)."""
+    h = hashlib.sha256()
+    for f in ("hg_p1.cu", "hg_p1dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2308_01792_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _profiled_traffic():
