@@ -235,6 +235,12 @@ GMG_WORKLOAD = "cube384_L6_p1_lognormal_gmg_to_1e-8"
 # div-k-grad and the P2 problem, whose FP64 residuals cost 8 ms and 26 ms).
 # Plain FP64 solves do one V-cycle per residual as before.
 INNER_CYCLES = 3
+# The same for the 17 M-DoF log-normal problem of the multigrid and stencil
+# legs, measured on GB300 over 2..6: Jacobi V(3,3) 0.169 / 0.143 / 0.144 /
+# 0.135 / 0.117 s (9 / 6 / 5 / 4 / 3 steps), Chebyshev(2) V(1,1) 0.133 /
+# 0.123 / 0.099 / 0.113 / 0.097 s: six FP32 cycles per FP64 residual (8 ms
+# each on the fly) reach 1e-8 in 3 steps.
+LOGNORMAL_INNER_CYCLES = 6
 WEIGHTS = os.path.join(ROOT, "paper_2308_01792_gb300", "weights", "learned_smoother_cube384.npy")
 
 
@@ -263,13 +269,14 @@ def gmg_comparison(stream):
         net, loss = learned.train(X, t, steps=3000, batch=65536, lr=1e-3)
         trained = f"trained in bench: {npairs} noise pairs, loss {loss:.4g}"
     out = {"workload": GMG_WORKLOAD, "unique_dofs": int(len(xyz)), "tol": 1e-8,
-           "setup_s": setup_s, "weights": trained, "fp32_cycles_per_refinement_step": INNER_CYCLES}
+           "setup_s": setup_s, "weights": trained,
+           "fp32_cycles_per_refinement_step": LOGNORMAL_INNER_CYCLES}
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     for name, prec, use in (("plain_f64", hg.HG_PREC_F64, False),
                             ("mixed_f32_ir", hg.HG_PREC_MIXED, False),
                             ("learned_mixed", hg.HG_PREC_MIXED, True)):
-        G = hg.GMG(op, inner_cycles=INNER_CYCLES)
+        G = hg.GMG(op, inner_cycles=LOGNORMAL_INNER_CYCLES)
         G.set_learned(net if use else None)
         x = H.zeros(6, torch.float64)
         G.solve(x, b, tol=1e-8, max_iter=200, precision=prec, stream=stream)   # warm-up
@@ -285,7 +292,7 @@ def gmg_comparison(stream):
     # fewer smoothing steps per level: Jacobi and learned V(2,2) and V(1,1)
     for nu in (2, 1):
         for name, use in ((f"mixed_f32_ir_v{nu}{nu}", False), (f"learned_mixed_v{nu}{nu}", True)):
-            G = hg.GMG(op, nu1=nu, nu2=nu, inner_cycles=INNER_CYCLES)
+            G = hg.GMG(op, nu1=nu, nu2=nu, inner_cycles=LOGNORMAL_INNER_CYCLES)
             G.set_learned(net if use else None)
             x = H.zeros(6, torch.float64)
             G.solve(x, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
@@ -303,7 +310,7 @@ def gmg_comparison(stream):
     out["learned_vs_mixed_speedup"] = out["mixed_f32_ir"]["s"] / out["learned_mixed"]["s"]
     # Chebyshev-accelerated Jacobi of order 2, V(1,1), FP32 cycles in FP64
     # refinement; then full multigrid with 5 V(1,1) Chebyshev cycles per level
-    G = hg.GMG(op, nu1=1, nu2=1, inner_cycles=INNER_CYCLES, smoother=hg.HG_SMOOTH_CHEB)
+    G = hg.GMG(op, nu1=1, nu2=1, inner_cycles=LOGNORMAL_INNER_CYCLES, smoother=hg.HG_SMOOTH_CHEB)
     x = H.zeros(6, torch.float64)
     G.solve(x, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
     torch.cuda.synchronize()
@@ -844,8 +851,9 @@ def stencil_comparison(stream, m=4, L=6, solve=True):
     bc[dirich] = 0.0
     b = H.from_canonical(L, torch.tensor(bc, device="cuda"))
     for name, op, cheb in (("onthefly", fly, False), ("stored", st, False), ("stored", st, True)):
-        G = (hg.GMG(op, nu1=1, nu2=1, inner_cycles=INNER_CYCLES, smoother=hg.HG_SMOOTH_CHEB) if cheb
-             else hg.GMG(op, inner_cycles=INNER_CYCLES))
+        inner = LOGNORMAL_INNER_CYCLES
+        G = (hg.GMG(op, nu1=1, nu2=1, inner_cycles=inner, smoother=hg.HG_SMOOTH_CHEB) if cheb
+             else hg.GMG(op, inner_cycles=inner))
         xs = H.zeros(L, torch.float64)
         G.solve(xs, b, tol=1e-8, max_iter=200, precision=hg.HG_PREC_MIXED, stream=stream)
         torch.cuda.synchronize()
