@@ -535,17 +535,21 @@ int Hier::build_level(int l) {
   }
   L.n_mitems = (int)mitems.size();
   if (int r = upload(&L.mitems, mitems)) return r;
-  // per item and lane (point pt, copy c = lane - pt C): the copy's stored
-  // index and its class-stencil row cell * 16 + class ({-1, 0}: no copy; items
-  // of primitives with more than 32 copies derive theirs in the kernel)
+  // per item and lane (copy-major: lane = c * P + pt, copy c of point pt, P =
+  // 32 / C points, so that one copy's lanes hold consecutive points of the
+  // primitive in one cell): the copy's stored index and its class-stencil row
+  // cell * 16 + class ({-1, 0}: no copy; items of primitives with more than 32
+  // copies derive theirs in the kernel)
   {
     std::vector<int2> ml((size_t)L.n_mitems * 32, int2{-1, 0});
     for (int q = 0; q < L.n_mitems; ++q) {
       const int4 it = mitems[q];
       const int dim = it.z & 15, C = (it.z >> 4) & 255;
       if (C > 32) continue;
-      for (int lane = 0; lane < it.w * C && lane < 32; ++lane) {
-        const int pt = lane / C, c = lane - pt * C;
+      const int P = 32 / C;
+      for (int lane = 0; lane < 32; ++lane) {
+        const int c = lane / P, pt = lane - c * P;
+        if (c >= C || pt >= it.w) continue;
         int wts[3];
         prim_point_weights(dim, n, it.y + pt, wts);
         const IfaceCopy& cp = copies[it.x + c];

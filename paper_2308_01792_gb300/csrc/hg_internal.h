@@ -197,7 +197,8 @@ struct LevelDev {
                              //   copy 0, not active; C = 63: more than 32 copies, serial path)
   int4* mitems;              // apply items of the primitives with >= 2 copies only
   int n_mitems, n_mitems_inner;  //   (non-Dirichlet first): the streaming kernel's exchange
-  int2* mlanes;              // [n_mitems * 32]: per lane the copy's stored index and
+  int2* mlanes;              // [n_mitems * 32]: per lane (copy-major: lane = copy * (32 / C)
+                             //   + point) the copy's stored index and
                              //   cell * 16 + class ({-1, 0}: none; not for > 32 copies)
   StreamPlanDev splan[2];    // the streaming kernel's plans for HG_F32 and HG_F64
   int4* ptiles;              // plane-window tiles of ONE cell (the same for every cell):

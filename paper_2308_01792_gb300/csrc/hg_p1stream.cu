@@ -575,12 +575,13 @@ __global__ void __launch_bounds__(256) interface_sum_kernel(const __grid_constan
   const int64_t g = act ? ln.x : 0;
   const T mine = act ? A.y[g] : T(0);
   const T mdiag = op_scaled(OP) && act ? __ldg(A.sten + (int64_t)ln.y * 16) : T(0);
-  // the point's C lanes, ascending copy (= cell) order
-  const int b0 = lane / C * C;
+  // the point's C lanes (copy-major: lane = copy * P + point), ascending copy
+  // (= cell) order
+  const int P = 32 / C, pt = lane % P;
   T sum = T(0), diag = T(0);
   for (int q = 0; q < C; ++q) {
-    sum += __shfl_sync(0xffffffffu, mine, (b0 + q) & 31);
-    if (op_scaled(OP)) diag += __shfl_sync(0xffffffffu, mdiag, (b0 + q) & 31);
+    sum += __shfl_sync(0xffffffffu, mine, (q * P + pt) & 31);
+    if (op_scaled(OP)) diag += __shfl_sync(0xffffffffu, mdiag, (q * P + pt) & 31);
   }
   if (!act) return;
   A.y[g] = interface_output<T, OP>(A, g, sum, diag, false, 0, 0, 0, nullptr);
