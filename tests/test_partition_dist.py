@@ -1,6 +1,6 @@
 """Distribution of the macro cells over ranks (Sec. 2: primitives distributed
 over processes, one ghost-layer exchange per application) on the CPU, with
-gloo ranks (world size 2) and no GPU.
+gloo ranks (world sizes 2 and 3) and no GPU.
 
 The library's partition (hg_partition_cells) and exchange plan
 (hg_exchange_plan) are host code.  Each rank stores only its own cells;
@@ -120,22 +120,31 @@ def test_plan_pairs_and_covers_every_cross_rank_point(name, level, nparts):
         assert sorted(got) == want
 
 
-def _rank_main(rank, port, name, level, out):
+def _rank_main(rank, port, name, level, out, world=2):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
-    dist.init_process_group("gloo", rank=rank, world_size=2)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         macro = MESHES[name]
         M = hg.Mesh(macro.xyz, macro.cells)
-        part = hg.partition_cells(M, 2)
+        part = hg.partition_cells(M, world)
         P = hg.exchange_plan(M, level, part, rank)
         rm = RefinedMesh(macro, level)
         x = sg.uniform_vector(77, rm.n_vertices)
         y, gids, parts = _local_partials(macro, rm, part, rank, P["stride"], x)
-        # the exchange: partials of this rank's copies to the other rank
-        other = 1 - rank
-        sendbuf = torch.tensor(y[P["send_idx"]], dtype=torch.float64)
-        recvbuf = torch.zeros(int(P["recv_count"][other]), dtype=torch.float64)
-        reqs = [dist.isend(sendbuf, other), dist.irecv(recvbuf, other)]
+        # the exchange: this rank's partials to every rank it shares points
+        # with, in the plan's order; receive buffers concatenated by rank
+        sends = np.concatenate([[0], np.cumsum(P["send_count"])])
+        recvs = np.concatenate([[0], np.cumsum(P["recv_count"])])
+        recvbuf = torch.zeros(int(recvs[-1]), dtype=torch.float64)
+        reqs = []
+        for r in range(world):
+            if r == rank:
+                continue
+            if P["send_count"][r]:
+                sb = torch.tensor(y[P["send_idx"][sends[r]:sends[r + 1]]], dtype=torch.float64)
+                reqs.append(dist.isend(sb, r))
+            if P["recv_count"][r]:
+                reqs.append(dist.irecv(recvbuf[recvs[r]:recvs[r + 1]], r))
         for q in reqs:
             q.wait()
         recv = recvbuf.numpy()
@@ -170,14 +179,17 @@ def _rank_main(rank, port, name, level, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name,level", [("cube2", 2), ("cube2perm", 3)])
-def test_two_rank_exchange_reproduces_the_global_apply(name, level):
-    port = 29500 + (os.getpid() + level) % 1000
+@pytest.mark.parametrize("name,level,world", [("cube2", 2, 2), ("cube2perm", 3, 2),
+                                              ("cube2", 2, 3)])
+def test_rank_exchange_reproduces_the_global_apply(name, level, world):
+    """World size 2, and 3 (edges and vertices then hold copies on three ranks,
+    each sending to both others)."""
+    port = 29500 + (os.getpid() + 7 * level + world) % 1000
     with mp.Manager() as m:
         out = m.dict()
-        mp.spawn(_rank_main, args=(port, name, level, out), nprocs=2, join=True)
+        mp.spawn(_rank_main, args=(port, name, level, out, world), nprocs=world, join=True)
         res = dict(out)
-    for rank in (0, 1):
+    for rank in range(world):
         r = res[rank]
         assert r["n_points"] > 0
         assert r["exact_order"], r
