@@ -1203,6 +1203,7 @@ int Op::build_surrogate(const double* coeff, int degree) {
   for (int dt = 0; dt < 2; ++dt) scoef[dt].assign(nl, nullptr);
   ssegs.assign(nl, nullptr);
   n_ssegs.assign(nl, 0);
+  spat.assign(nl, 0);
   for (int l = h->lmin; l <= h->lmax; ++l) {
     const int li = l - h->lmin;
     const LevelDev& L = h->lv[li].dev;
@@ -1304,6 +1305,21 @@ int Op::build_surrogate(const double* coeff, int degree) {
           for (int t = 0; t < T; ++t) coef[(c * kNDir + d) * nt + kept[t]] = x[t];
         }
     }
+    // seven-point fit: every coefficient of the other eight directions is an
+    // exact zero in every cell (the weights there are exact zeros, as on
+    // Kuhn-ordered cubes)
+    {
+      bool pat7 = true;
+      for (int64_t c = 0; c < nc && pat7; ++c)
+        for (int d = 0; d < kNDir && pat7; ++d)
+          if (!((kPat7Mask >> d) & 1u))
+            for (int t = 0; t < nt; ++t)
+              if (coef[(c * kNDir + d) * nt + t] != 0.0) {
+                pat7 = false;
+                break;
+              }
+      spat[li] = pat7 ? kPat7 : 0;
+    }
     std::vector<float> coef32(coef.begin(), coef.end());
     double* d64 = nullptr;
     float* d32 = nullptr;
@@ -1321,7 +1337,7 @@ int Op::build_surrogate(const double* coeff, int degree) {
     a.op = OP_DIAG;
     a.mask = HG_MASK_ALL;
     VarCoef vc{vk[HG_F64][li], vK[HG_F64][li], nullptr};
-    SurCoef sc{degree, scoef[HG_F64][li], ssegs[li], n_ssegs[li]};
+    SurCoef sc{degree, scoef[HG_F64][li], ssegs[li], n_ssegs[li], spat[li]};
     int rc = launch_p1_surrogate(L, HG_F64, a, vc, sc, 0);
     std::vector<double> dh(L.n_stored);
     if (!rc && cudaMemcpy(dh.data(), diag, L.n_stored * sizeof(double), cudaMemcpyDeviceToHost) !=
@@ -1371,7 +1387,7 @@ int Op::launch(int level, int dtype, StencilArgs a, cudaStream_t s) const {
   }
   if (kind == HG_OP_P1_DIVKGRAD_SURROGATE) {
     VarCoef vc{vk[dtype][li], vK[dtype][li], vinv[dtype][li]};
-    SurCoef sc{sdeg, scoef[dtype][li], ssegs[li], n_ssegs[li]};
+    SurCoef sc{sdeg, scoef[dtype][li], ssegs[li], n_ssegs[li], spat[li]};
     return launch_p1_surrogate(L, dtype, a, vc, sc, s);
   }
   if (kind == HG_OP_P1_DIVKGRAD_STORED) {

@@ -119,6 +119,7 @@ struct Op {
   std::vector<void*> scoef[2];
   std::vector<int*> ssegs;
   std::vector<int> n_ssegs;
+  std::vector<int> spat;        // per level: kPat7 when the fit vanishes outside it
   int build_surrogate(const double* coeff, int degree);
 
   int build(const Hier* h, int kind, const double* coeff);

@@ -362,6 +362,7 @@ struct SurCoef {
   const void* coef;
   const int* segs;
   int n_segs_cell;
+  int pattern;  // kPat7: every cell's fitted weights vanish outside the seven-point subset
 };
 constexpr int kSurMaxDegree = 4;
 constexpr int kSurRows = 8;

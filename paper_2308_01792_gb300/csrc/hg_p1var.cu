@@ -134,6 +134,7 @@ struct VarArgs {
   int sdeg;
   const int* segs;
   int n_segs_cell, n_segs;
+  int spat;  // surrogate: kPat7 when the fitted weights vanish outside the seven-point subset
 };
 
 // 15-point neighbourhood of a cell-local point from global memory (values
@@ -410,7 +411,10 @@ __device__ void var_plane_tile(const VarArgs<T>& A, int t, int lane,
 // every lane then evaluates its point's 15 weights by Horner's rule in
 // xi = i/n - 1/4 and applies them to the 15 neighbours of x (all inside the
 // cell's lattice for an interior point).  Q: the degree, fixed at compile time.
-template <typename T, int OP, int Q>
+// PAT = kPat7: the directions outside the seven-point subset have exactly
+// zero coefficients in every cell; their terms (exact zeros) are left out,
+// which changes no sum.
+template <typename T, int OP, int Q, int PAT>
 __device__ void sur_band(const VarArgs<T>& A, int t, int lane, T* __restrict__ rowc) {
   constexpr int Q1 = Q + 1, NT = sur_nterm(Q);
   const int cell = t / A.n_segs_cell;
@@ -464,9 +468,10 @@ __device__ void sur_band(const VarArgs<T>& A, int t, int lane, T* __restrict__ r
       const bool ok = i <= len - 2;
       const int ic = ok ? i : i0;  // lanes past the row's last interior point: unstored
       const T xi = T(ic) * inv_n - T(0.25);
-      T acc = T(0), centre = T(0);
+          T acc = T(0), centre = T(0);
 #pragma unroll
       for (int d = 0; d < kNDir; ++d) {
+        if (PAT == kPat7 && !((kPat7Mask >> d) & 1u)) continue;
         T wd = rowc[d * Q1 + Q];
 #pragma unroll
         for (int m = Q - 1; m >= 0; --m) wd = fma(wd, xi, rowc[d * Q1 + m]);
@@ -517,12 +522,22 @@ __global__ void __launch_bounds__(kBlock) p1var_kernel(VarArgs<T> A) {
     if (SUR) {
       if (t < A.n_segs) {
         T* rowc = reinterpret_cast<T*>(Ks[threadIdx.x >> 5]);
-        switch (A.sdeg) {
-          case 0: sur_band<T, OP, 0>(A, t, lane, rowc); break;
-          case 1: sur_band<T, OP, 1>(A, t, lane, rowc); break;
-          case 2: sur_band<T, OP, 2>(A, t, lane, rowc); break;
-          case 3: sur_band<T, OP, 3>(A, t, lane, rowc); break;
-          default: sur_band<T, OP, 4>(A, t, lane, rowc); break;
+        if (A.spat == kPat7) {
+          switch (A.sdeg) {
+            case 0: sur_band<T, OP, 0, kPat7>(A, t, lane, rowc); break;
+            case 1: sur_band<T, OP, 1, kPat7>(A, t, lane, rowc); break;
+            case 2: sur_band<T, OP, 2, kPat7>(A, t, lane, rowc); break;
+            case 3: sur_band<T, OP, 3, kPat7>(A, t, lane, rowc); break;
+            default: sur_band<T, OP, 4, kPat7>(A, t, lane, rowc); break;
+          }
+        } else {
+          switch (A.sdeg) {
+            case 0: sur_band<T, OP, 0, 0>(A, t, lane, rowc); break;
+            case 1: sur_band<T, OP, 1, 0>(A, t, lane, rowc); break;
+            case 2: sur_band<T, OP, 2, 0>(A, t, lane, rowc); break;
+            case 3: sur_band<T, OP, 3, 0>(A, t, lane, rowc); break;
+            default: sur_band<T, OP, 4, 0>(A, t, lane, rowc); break;
+          }
         }
       }
     } else if (t < A.n_tiles) {
@@ -564,7 +579,9 @@ int run_var(const LevelDev& L, const StencilArgs& a, const VarCoef& vc, cudaStre
   A.sdeg = 0;
   A.segs = nullptr;
   A.n_segs_cell = A.n_segs = 0;
+  A.spat = 0;
   if (SUR) {
+    A.spat = sc->pattern;
     A.sc = (const T*)sc->coef;
     A.sdeg = sc->degree;
     A.segs = sc->segs;
