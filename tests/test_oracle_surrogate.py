@@ -58,3 +58,37 @@ def test_exact_operator_is_the_multigrid_oracles_operator():
     S = su.SurrogateLevel(sg.kuhn_cube(1), 3, kf)
     lev = gmg.Level(sg.kuhn_cube(1), 3, kind="divkgrad", coeff=kf)
     assert abs(S.A - lev.A_full).max() <= 1e-14 * abs(lev.A_full).max()
+
+
+def test_fitted_weights_are_the_least_squares_projection():
+    """The fitted interior weights w_s = B c satisfy the normal equations
+    B^T (w - w_s) = 0 for the monomial basis B of the interior points (a
+    wrong basis, a wrong point set or a dropped term fails it)."""
+    S = su.SurrogateLevel(sg.kuhn_cube(1), 4, sg.sinprod_coefficient(*sg.SINPROD_AB))
+    for q in (1, 2, 3):
+        A = S.surrogate(q)
+        ex = su.exponents(q)
+        u = S.ijk / S.n
+        B = np.stack([u[:, 0] ** a * u[:, 1] ** b * u[:, 2] ** c for a, b, c in ex], axis=1)
+        for ids, nb, w in S.cells:
+            ws = np.stack([np.asarray(A[ids, nb[:, d]]).ravel() for d in range(len(su.DIRS))],
+                          axis=1)
+            r = B.T @ (w - ws)
+            assert np.abs(r).max() <= 1e-10 * np.abs(B.T @ w).max(), q
+
+
+def test_seven_point_cube_weights_vanish_outside_the_seven_directions():
+    """On a Kuhn-ordered cube the exact div-k-grad weights (any k) are exact
+    zeros outside centre, +-(1,0,0), +-(1,-1,0), +-(0,-1,1), so every fitted
+    coefficient there is zero: what the library's seven-point surrogate path
+    relies on."""
+    S = su.SurrogateLevel(sg.kuhn_cube(1), 3, sg.sinprod_coefficient(*sg.SINPROD_AB))
+    seven = {(0, 0, 0), (1, 0, 0), (-1, 0, 0), (1, -1, 0), (-1, 1, 0), (0, -1, 1), (0, 1, -1)}
+    off = [d for d, v in enumerate(su.DIRS) if tuple(v) not in seven]
+    assert len(off) == 8
+    for ids, nb, w in S.cells:
+        assert np.all(w[:, off] == 0.0)
+    A = S.surrogate(3)
+    for ids, nb, w in S.cells:
+        for d in off:
+            assert np.all(np.asarray(A[ids, nb[:, d]]).ravel() == 0.0)
