@@ -1227,14 +1227,23 @@ def make_parser():
     return ap
 
 
-def main():
-    args = make_parser().parse_args()
+LEGS = ("gmg", "batch", "p2", "stencil", "kernels", "n1", "n1_solve", "reftet", "cube6",
+        "learned_kernels", "cpu_baseline")
+
+
+def apply_only(args):
+    """--only a,b: skip every leg not named (the headline apply and its e2e
+    pass always run)."""
     if args.only is not None:
         keep = set(args.only.split(","))
-        for leg in ("gmg", "batch", "p2", "stencil", "kernels", "n1", "n1_solve", "reftet",
-                    "cube6", "learned_kernels", "cpu_baseline"):
+        for leg in LEGS:
             if leg not in keep:
                 setattr(args, "no_" + leg, True)
+    return args
+
+
+def main():
+    args = apply_only(make_parser().parse_args())
     if args.impl == "reference":
         return run_reference(args)
 

@@ -110,3 +110,18 @@ def test_profile_command_lines_parse_with_the_current_bench():
     for name, argv in cmds:
         args = ap.parse_args(argv)
         assert args.impl == "gb300", name
+
+
+def test_only_keeps_the_named_legs_and_every_leg_has_a_switch():
+    import bench
+    ap = bench.make_parser()
+    for leg in bench.LEGS:
+        assert hasattr(ap.parse_args([]), "no_" + leg), leg
+        assert getattr(ap.parse_args([]), "no_" + leg) is False
+    a = bench.apply_only(ap.parse_args(["--only", "gmg,kernels"]))
+    assert not a.no_gmg and not a.no_kernels
+    assert all(getattr(a, "no_" + leg) for leg in bench.LEGS if leg not in ("gmg", "kernels"))
+    a = bench.apply_only(ap.parse_args(["--only", "headline"]))
+    assert all(getattr(a, "no_" + leg) for leg in bench.LEGS)
+    a = bench.apply_only(ap.parse_args([]))
+    assert not any(getattr(a, "no_" + leg) for leg in bench.LEGS)
