@@ -1,0 +1,111 @@
+"""Planted mistakes in the oracle (CPU): each test replaces one oracle function
+by a copy with a plausible mistake and checks that the pins of that function
+(the tests of tests/test_oracle_*.py, called directly) catch it.  A pin set
+that still passes with the mistake in place would not pin the function."""
+import numpy as np
+import pytest
+
+import synthgen as sg
+from oracle import fem, gmg, indexing, learned, mesh
+
+import test_oracle_fem as pf
+import test_oracle_gmg as pg
+import test_oracle_indexing as pi
+import test_oracle_learned as pl
+import test_oracle_mesh as pm
+
+
+def _caught(*pins):
+    """True if at least one of the pins (callables without arguments) fails."""
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            return True
+    return False
+
+
+def test_pins_pass_on_the_oracle_as_written():
+    assert not _caught(pf.test_p1_element_matrices_closed_forms,
+                       lambda: pf.test_kuhn_cube_laplacian_is_h_times_7_point(1, 3),
+                       pi.test_tw_worked_example_w3,
+                       pg.test_chebyshev_error_polynomial_on_diagonal_matrix,
+                       lambda: pl.test_one_hot_network_reads_the_neighbour_in_the_cells_frame(0),
+                       lambda: pm.test_bey_equals_lattice_subgroups(2))
+
+
+def test_a_missing_volume_factor_in_the_p1_stiffness_is_caught(monkeypatch):
+    def wrong(X):
+        G, vol = fem.bary_gradients(X)
+        return np.einsum("tid,tjd->tij", G, G)              # |T| dropped
+    monkeypatch.setattr(fem, "p1_stiffness", wrong)
+    assert _caught(pf.test_p1_element_matrices_closed_forms,
+                   lambda: pf.test_kuhn_cube_laplacian_is_h_times_7_point(1, 3))
+
+
+def test_a_gradient_of_the_wrong_vertex_in_the_p1_stiffness_is_caught(monkeypatch):
+    def wrong(X):
+        G, vol = fem.bary_gradients(X)
+        G = G[:, [1, 0, 2, 3]]                               # two vertices swapped
+        return vol[:, None, None] * np.einsum("tid,tjd->tij", G, G)
+    monkeypatch.setattr(fem, "p1_stiffness", wrong)
+    assert _caught(pf.test_p1_element_matrices_closed_forms)
+
+
+def test_a_wrong_term_in_the_index_function_is_caught(monkeypatch):
+    def wrong(w, i, j, k):
+        return (indexing.n_tet(w) - indexing.n_tet(w - k) + indexing.n_tri(w - k + 1)
+                - indexing.n_tri(w - k - j + 1) + i)         # rows of length w - k - j + 1
+    monkeypatch.setattr(indexing, "tw", wrong)
+    assert _caught(pi.test_tw_worked_example_w3, lambda: pi.test_tw_closed_form_equals_loop_order_counting(4))
+
+
+def test_a_wrong_chebyshev_recurrence_is_caught(monkeypatch):
+    def wrong(A, D, x, b, lam_max, order=2, lo=0.1, hi=1.1):
+        a, c = lo * lam_max, hi * lam_max
+        theta, delta = 0.5 * (c + a), 0.5 * (c - a)
+        sigma = theta / delta
+        rho = 1.0 / sigma
+        d = (b - A @ x) / (D * theta)
+        x = x + d
+        for _ in range(order - 1):
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            d = rho_new * rho * d + (rho_new / delta) * ((b - A @ x) / D)   # factor 2 dropped
+            x = x + d
+            rho = rho_new
+        return x
+    monkeypatch.setattr(gmg, "chebyshev", wrong)
+    assert _caught(pg.test_chebyshev_error_polynomial_on_diagonal_matrix)
+
+
+def test_wrong_prolongation_weights_are_caught(monkeypatch):
+    original = gmg.p1_prolongation
+
+    def wrong(fine, coarse):
+        P = original(fine, coarse).tocoo()
+        v = np.where(P.data == 0.5, 0.25, P.data)            # midpoints from a quarter of each end
+        return type(P)((v, (P.row, P.col)), shape=P.shape).tocsr()
+    monkeypatch.setattr(gmg, "p1_prolongation", wrong)
+    assert _caught(lambda: pg.test_prolongation_reproduces_linear_and_quadratic_functions(
+        sg.kuhn_cube(1)))
+
+
+def test_swapped_feature_directions_in_the_learned_step_are_caught(monkeypatch):
+    dirs = learned.DIRS.copy()
+    dirs[[7, 8]] = dirs[[8, 7]]                                # (-1,1,0) and (1,-1,0) swapped
+    monkeypatch.setattr(learned, "DIRS", dirs)
+    assert _caught(lambda: pl.test_one_hot_network_reads_the_neighbour_in_the_cells_frame(0))
+
+
+def test_a_wrong_inner_diagonal_in_bey_refinement_is_caught(monkeypatch):
+    def wrong(t):
+        v0, v1, v2, v3 = t[:, 0], t[:, 1], t[:, 2], t[:, 3]
+        m01, m02, m03 = (v0 + v1) // 2, (v0 + v2) // 2, (v0 + v3) // 2
+        m12, m13, m23 = (v1 + v2) // 2, (v1 + v3) // 2, (v2 + v3) // 2
+        # the octahedron split along v01-v23 instead of v02-v13
+        kids = [(v0, m01, m02, m03), (m01, v1, m12, m13), (m02, m12, v2, m23),
+                (m03, m13, m23, v3), (m01, m23, m02, m03), (m01, m23, m03, m13),
+                (m01, m23, m13, m12), (m01, m23, m12, m02)]
+        return np.stack([np.stack(k, axis=1) for k in kids], axis=1).reshape(-1, 4, 3)
+    monkeypatch.setattr(mesh, "bey_children", wrong)
+    assert _caught(lambda: pm.test_bey_equals_lattice_subgroups(1), pm.test_inner_edge_is_v02_v13)
