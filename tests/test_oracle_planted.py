@@ -6,13 +6,16 @@ import numpy as np
 import pytest
 
 import synthgen as sg
-from oracle import fem, gmg, indexing, learned, mesh
+from oracle import fem, gmg, indexing, learned, mesh, mlp, nedelec, quadrature, surrogate
 
 import test_oracle_fem as pf
 import test_oracle_gmg as pg
 import test_oracle_indexing as pi
 import test_oracle_learned as pl
 import test_oracle_mesh as pm
+import test_oracle_mlp as pn
+import test_oracle_nedelec as pe
+import test_oracle_surrogate as ps
 
 
 def _caught(*pins):
@@ -31,7 +34,18 @@ def test_pins_pass_on_the_oracle_as_written():
                        pi.test_tw_worked_example_w3,
                        pg.test_chebyshev_error_polynomial_on_diagonal_matrix,
                        lambda: pl.test_one_hot_network_reads_the_neighbour_in_the_cells_frame(0),
-                       lambda: pm.test_bey_equals_lattice_subgroups(2))
+                       lambda: pm.test_bey_equals_lattice_subgroups(2),
+                       lambda: pf.test_p2_stiffness_and_mass_invariants(sg.kuhn_cube(1)),
+                       pf.test_p2_stiffness_with_linear_k_matches_an_independent_rule,
+                       pf.test_p1_divkgrad_is_the_exact_integral_for_linear_k,
+                       pf.test_quadrature_exactness,
+                       pg.test_chebyshev_order_one_is_weighted_jacobi,
+                       pg.test_colour_gauss_seidel_is_the_sequential_sweep,
+                       pn.test_gradient_matches_finite_differences,
+                       pn.test_single_hidden_unit_closed_form,
+                       lambda: pl.test_zero_network_is_weighted_jacobi(0),
+                       pe.test_basis_curls_by_finite_differences,
+                       lambda: ps.test_surrogate_is_exact_for_polynomial_coefficients(sg.kuhn_cube(1)))
 
 
 def test_a_missing_volume_factor_in_the_p1_stiffness_is_caught(monkeypatch):
@@ -109,3 +123,97 @@ def test_a_wrong_inner_diagonal_in_bey_refinement_is_caught(monkeypatch):
         return np.stack([np.stack(k, axis=1) for k in kids], axis=1).reshape(-1, 4, 3)
     monkeypatch.setattr(mesh, "bey_children", wrong)
     assert _caught(lambda: pm.test_bey_equals_lattice_subgroups(1), pm.test_inner_edge_is_v02_v13)
+
+
+def test_a_lumped_p1_mass_is_caught(monkeypatch):
+    def wrong(X):
+        _, vol = fem.bary_gradients(X)
+        return vol[:, None, None] * (np.eye(4) / 4.0)[None]  # row sums kept, the matrix lumped
+    monkeypatch.setattr(fem, "p1_mass", wrong)
+    assert _caught(pf.test_p1_element_matrices_closed_forms)
+
+
+def test_a_wrong_p2_edge_gradient_is_caught(monkeypatch):
+    def wrong(lam, G):
+        B = np.empty((G.shape[0], 10, 3))
+        for i in range(4):
+            B[:, i] = (4.0 * lam[i] - 1.0) * G[:, i]
+        for e, (i, j) in enumerate(fem.P2_EDGES):
+            B[:, 4 + e] = 2.0 * (lam[i] * G[:, j] + lam[j] * G[:, i])   # factor 4 halved
+        return B
+    monkeypatch.setattr(fem, "p2_basis_gradients", wrong)
+    assert _caught(lambda: pf.test_p2_stiffness_and_mass_invariants(sg.kuhn_cube(1)),
+                   pf.test_p2_stiffness_with_linear_k_matches_an_independent_rule)
+
+
+def test_a_div_k_grad_coefficient_taken_at_one_vertex_is_caught(monkeypatch):
+    def wrong(X, k_vertex):
+        return k_vertex[:, 0][:, None, None] * fem.p1_stiffness(X)   # not the cell mean
+    monkeypatch.setattr(fem, "p1_divkgrad", wrong)
+    assert _caught(pf.test_p1_divkgrad_is_the_exact_integral_for_linear_k)
+
+
+def test_jacobi_without_its_weight_is_caught(monkeypatch):
+    monkeypatch.setattr(gmg, "jacobi", lambda A, D, x, b, omega: x + (b - A @ x) / D)
+    assert _caught(pg.test_chebyshev_order_one_is_weighted_jacobi)
+
+
+def test_gauss_seidel_with_one_residual_per_sweep_is_caught(monkeypatch):
+    def wrong(A, D, x, b, colour):
+        r = b - A @ x                                        # not refreshed between colours
+        return x + r / D
+    monkeypatch.setattr(gmg, "gauss_seidel_colours", wrong)
+    assert _caught(pg.test_colour_gauss_seidel_is_the_sequential_sweep)
+
+
+def test_a_missing_second_relu_in_the_network_is_caught(monkeypatch):
+    def wrong(W1, W2, w3, X):
+        z1 = X @ W1.T
+        h1 = np.maximum(z1, 0.0)
+        z2 = h1 @ W2.T
+        h2 = z2                                              # second ReLU dropped
+        return h2 @ w3, (X, z1, h1, z2, h2)
+    monkeypatch.setattr(mlp, "forward", wrong)
+    assert _caught(pn.test_gradient_matches_finite_differences,
+                   pn.test_single_hidden_unit_closed_form)
+
+
+def test_a_learned_step_without_the_jacobi_weight_is_caught(monkeypatch):
+    original = learned.learned_step
+
+    def wrong(macro, rm, x, r, D, W1, W2, w3, omega, forward=None):
+        return original(macro, rm, x, r, D, W1, W2, w3, 1.0, forward)
+    monkeypatch.setattr(learned, "learned_step", wrong)
+    assert _caught(lambda: pl.test_zero_network_is_weighted_jacobi(0))
+
+
+def test_a_whitney_function_of_the_opposite_orientation_is_caught(monkeypatch):
+    def wrong(lam, G):
+        out = np.empty(lam.shape[:-1] + (6, 3))
+        for e, (a, b) in enumerate(nedelec.LOCAL_EDGES):
+            out[..., e, :] = lam[..., b, None] * G[a] - lam[..., a, None] * G[b]
+        return out
+    monkeypatch.setattr(nedelec, "whitney", wrong)
+    assert _caught(pe.test_basis_curls_by_finite_differences)
+
+
+def test_a_surrogate_basis_missing_its_top_degree_is_caught(monkeypatch):
+    import itertools
+
+    def wrong(degree):
+        return [e for e in itertools.product(range(degree + 1), repeat=3) if sum(e) < max(degree, 1)]
+    monkeypatch.setattr(surrogate, "exponents", wrong)
+    assert _caught(lambda: ps.test_surrogate_is_exact_for_polynomial_coefficients(sg.kuhn_cube(1)))
+
+
+def test_a_perturbed_quadrature_weight_is_caught(monkeypatch):
+    original = quadrature.sym14
+
+    def wrong():
+        bary, w = original()
+        w = w.copy()
+        w[0] += 1e-3
+        w[-1] -= 1e-3                                        # total weight kept
+        return bary, w
+    monkeypatch.setattr(quadrature, "sym14", wrong)
+    assert _caught(pf.test_quadrature_exactness)
