@@ -368,6 +368,8 @@ class Function:
 
     def __init__(self, hier: Hierarchy, dtype, space=HG_SPACE_P1, levels=None):
         import torch
+        if dtype not in (torch.float32, torch.float64):
+            raise TypeError(f"a function holds float32 or float64 vectors, not {dtype}")
         h = _P()
         self.dtype = dtype
         code = HG_F64 if dtype == torch.float64 else HG_F32

@@ -104,3 +104,30 @@ def test_network_calls_check_samples_and_targets():
         net.grad(FakeRows((100, 16), torch.bfloat16), FakeTensor(100, torch.float64))
     with pytest.raises(ValueError, match="need 100"):
         net.train(FakeRows((100, 16), torch.bfloat16), FakeTensor(50, torch.float32), 1, 10, 1e-3)
+
+
+def test_function_calls_check_their_buffers_first():
+    """Functions: element type at creation, the bound tensor's dtype, and the
+    host buffer of a canonical copy (contiguous host float32/float64 memory of
+    exactly the level's unique DoF count) are checked before the library is
+    called."""
+    import numpy as np
+    H = hg.Hierarchy.__new__(hg.Hierarchy)
+    H._h, H.lmin, H.lmax, H._n_stored = None, 1, 3, {}
+    H.size = lambda level, space=hg.HG_SPACE_P1: (1024, 729, 0, 0)
+    with pytest.raises(TypeError, match="float32 or float64"):
+        hg.Function(H, torch.bfloat16)
+    f = hg.Function.__new__(hg.Function)
+    f._h, f.hier, f.space, f.dtype, f._t = None, H, hg.HG_SPACE_P1, torch.float64, {}
+    with pytest.raises(TypeError):
+        f.bind(3, FakeTensor(1024, torch.float32))
+    with pytest.raises(ValueError, match="729"):
+        f.copy_from_host(3, np.zeros(728))
+    with pytest.raises(ValueError):
+        f.copy_to_host(3, np.zeros(729, dtype=np.int64))
+    with pytest.raises(ValueError):
+        f.copy_to_host(3, np.zeros(1458)[::2])                  # not contiguous
+    with pytest.raises(ValueError, match="host tensor"):
+        f.copy_from_host(3, FakeTensor(729))                    # device memory
+    with pytest.raises(ValueError, match="host tensor"):
+        f.copy_from_host(3, FakeTensor(729, cuda=False, contiguous=False))
