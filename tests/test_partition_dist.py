@@ -70,6 +70,23 @@ def test_partition_is_balanced_and_deterministic(nparts):
         hg.partition_cells(M, 49)
 
 
+def test_exchange_plan_refuses_bad_arguments():
+    m = MESHES["cube2"]
+    M = hg.Mesh(m.xyz, m.cells)
+    part = hg.partition_cells(M, 2)
+    with pytest.raises(hg.HGError):
+        hg.exchange_plan(M, 2, part, 2)                   # rank outside 0..nparts-1
+    bad = part.copy()
+    bad[5] = -1
+    with pytest.raises(hg.HGError, match="outside"):
+        hg.exchange_plan(M, 2, bad, 0)                    # a cell without a valid part
+    with pytest.raises(hg.HGError, match="level"):
+        hg.exchange_plan(M, 10, part, 0)
+    one = np.zeros_like(part)
+    P = hg.exchange_plan(M, 2, one, 0)                    # one rank: nothing to exchange
+    assert len(P["point_start"]) == 1 and len(P["send_idx"]) == 0 and len(P["target_idx"]) == 0
+
+
 def test_bisection_cuts_across_the_longest_extent():
     """Two parts of the 2x2x2 cube: the cut is a coordinate plane through the
     middle, so each part is the cells of one half (centroids on one side)."""
