@@ -45,7 +45,12 @@ def test_pins_pass_on_the_oracle_as_written():
                        pn.test_single_hidden_unit_closed_form,
                        lambda: pl.test_zero_network_is_weighted_jacobi(0),
                        pe.test_basis_curls_by_finite_differences,
-                       lambda: ps.test_surrogate_is_exact_for_polynomial_coefficients(sg.kuhn_cube(1)))
+                       lambda: ps.test_surrogate_is_exact_for_polynomial_coefficients(sg.kuhn_cube(1)),
+                       pg.test_fmg_coarse_start_is_the_galerkin_projection,
+                       pg.test_power_iteration_finds_the_largest_eigenvalue,
+                       lambda: pe.test_prolongation_commutes_with_gradient_and_reproduces_rotations(
+                           pe.PERM, 2),
+                       pe.test_hiptmair_vcycle_is_level_independent_and_needs_the_potential_step)
 
 
 def test_a_missing_volume_factor_in_the_p1_stiffness_is_caught(monkeypatch):
@@ -217,3 +222,63 @@ def test_a_perturbed_quadrature_weight_is_caught(monkeypatch):
         return bary, w
     monkeypatch.setattr(quadrature, "sym14", wrong)
     assert _caught(pf.test_quadrature_exactness)
+
+
+def test_an_fmg_that_ignores_the_coarser_solution_is_caught(monkeypatch):
+    def wrong(H, b, cycles=5, nu1=1, nu2=1, smoother=None, **kw):
+        bs = {H.lmax: b}
+        for l in range(H.lmax, H.lmin, -1):
+            bs[l - 1] = H.P[l].T @ bs[l]
+        x = None
+        for l in range(H.lmin + 1, H.lmax + 1):
+            x = np.zeros_like(bs[l])                          # no prolongated start
+            for _ in range(cycles):
+                x = gmg.vcycle(H, l, x, bs[l], nu1, nu2, smoother=smoother, **kw)
+        return x
+    monkeypatch.setattr(gmg, "fmg", wrong)
+    assert _caught(pg.test_fmg_coarse_start_is_the_galerkin_projection)
+
+
+def test_a_power_iteration_without_normalisation_is_caught(monkeypatch):
+    def wrong(A, D, v0, iters=20):
+        v = v0 / np.linalg.norm(v0)
+        lam = 0.0
+        for _ in range(iters):
+            w = (A @ v) / D
+            lam = np.linalg.norm(w)
+            v = w                                             # not normalised
+        return lam
+    monkeypatch.setattr(gmg, "power_lambda_max", wrong)
+    assert _caught(pg.test_power_iteration_finds_the_largest_eigenvalue)
+
+
+def test_a_p2_prolongation_with_wrong_edge_functions_is_caught(monkeypatch):
+    original = gmg.p2_prolongation
+
+    def wrong(fine, coarse):
+        P = original(fine, coarse).tocoo()
+        v = np.where(np.isclose(P.data, 0.75), 0.5, P.data)   # 4 l_i l_j at (3/4, 1/4) off
+        return type(P)((v, (P.row, P.col)), shape=P.shape).tocsr()
+    monkeypatch.setattr(gmg, "p2_prolongation", wrong)
+    assert _caught(lambda: pg.test_prolongation_reproduces_linear_and_quadratic_functions(
+        sg.kuhn_cube(1)))
+
+
+def test_a_nedelec_prolongation_without_the_coarse_orientation_is_caught(monkeypatch):
+    import copy
+    original = nedelec.nedelec_prolongation
+
+    def wrong(fine, coarse):
+        c = copy.copy(coarse)
+        c.sign = np.ones_like(coarse.sign)                    # the cells' edge signs dropped
+        return original(fine, c)
+    monkeypatch.setattr(nedelec, "nedelec_prolongation", wrong)
+    assert _caught(lambda: pe.test_prolongation_commutes_with_gradient_and_reproduces_rotations(
+        pe.PERM, 2))
+
+
+def test_a_hiptmair_step_without_its_potential_correction_is_caught(monkeypatch):
+    def wrong(lev, x, b, edge_smoother, potential_smoother):
+        return edge_smoother(lev.A, lev.D, x, b)              # potential space left out
+    monkeypatch.setattr(nedelec, "hiptmair_step", wrong)
+    assert _caught(pe.test_hiptmair_vcycle_is_level_independent_and_needs_the_potential_step)
