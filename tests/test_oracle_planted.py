@@ -50,7 +50,10 @@ def test_pins_pass_on_the_oracle_as_written():
                        pg.test_power_iteration_finds_the_largest_eigenvalue,
                        lambda: pe.test_prolongation_commutes_with_gradient_and_reproduces_rotations(
                            pe.PERM, 2),
-                       pe.test_hiptmair_vcycle_is_level_independent_and_needs_the_potential_step)
+                       pe.test_hiptmair_vcycle_is_level_independent_and_needs_the_potential_step,
+                       pn.test_bf16_rounding_is_round_to_nearest_even,
+                       pn.test_adam_first_step_is_lr_times_sign,
+                       pl.test_samples_are_normalised_and_count_every_stride)
 
 
 def test_a_missing_volume_factor_in_the_p1_stiffness_is_caught(monkeypatch):
@@ -282,3 +285,33 @@ def test_a_hiptmair_step_without_its_potential_correction_is_caught(monkeypatch)
         return edge_smoother(lev.A, lev.D, x, b)              # potential space left out
     monkeypatch.setattr(nedelec, "hiptmair_step", wrong)
     assert _caught(pe.test_hiptmair_vcycle_is_level_independent_and_needs_the_potential_step)
+
+
+def test_bf16_by_truncation_is_caught(monkeypatch):
+    def wrong(a):
+        f = np.asarray(a, dtype=np.float32)
+        u = f.view(np.uint32)
+        return ((u >> 16) << 16).astype(np.uint32).view(np.float32).astype(np.float64)
+    monkeypatch.setattr(mlp, "bf16", wrong)
+    assert _caught(pn.test_bf16_rounding_is_round_to_nearest_even)
+
+
+def test_adam_without_bias_correction_is_caught(monkeypatch):
+    def wrong(params, grads, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        for p, g, mi, vi in zip(params, grads, m, v):
+            mi *= b1
+            mi += (1 - b1) * g
+            vi *= b2
+            vi += (1 - b2) * g * g
+            p -= lr * mi / (np.sqrt(vi) + eps)
+    monkeypatch.setattr(mlp, "adam_step", wrong)
+    assert _caught(pn.test_adam_first_step_is_lr_times_sign)
+
+
+def test_training_targets_without_the_jacobi_part_are_caught(monkeypatch):
+    original = learned.learned_samples
+
+    def wrong(macro, rm, r, D, xstar, x, omega, stride, offset):
+        return original(macro, rm, r, D, xstar, x, 0.0, stride, offset)   # target e, not e - omega s
+    monkeypatch.setattr(learned, "learned_samples", wrong)
+    assert _caught(pl.test_samples_are_normalised_and_count_every_stride)
