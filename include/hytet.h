@@ -228,7 +228,10 @@ int hg_apply_function(const hg_op* op, int level, const hg_func* x, hg_func* y, 
  *     receive buffer; and writes the sum to the local stored indices
  *     target_idx[target_start[p] .. target_start[p+1]-1] (its own copies).
  * This is the summation order of the single-device kernels, so the result
- * is identical.  sizes (host int64[6]) receives: number of send entries,
+ * is identical.  For norms and dots each point counts once, at the copy of
+ * its lowest-id cell: a planned point is owned by this rank iff its first
+ * term is local (term_src[point_start[p]] >= 0, that index being the owned
+ * copy).  sizes (host int64[6]) receives: number of send entries,
  * receive entries, points, terms, targets and the cell stride; call with the
  * arrays NULL to size them (send_count, recv_count: nparts entries;
  * point_start, target_start: points + 1).  Errors: HG_ERR_INVALID_ARG,
