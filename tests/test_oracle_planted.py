@@ -53,7 +53,10 @@ def test_pins_pass_on_the_oracle_as_written():
                        pe.test_hiptmair_vcycle_is_level_independent_and_needs_the_potential_step,
                        pn.test_bf16_rounding_is_round_to_nearest_even,
                        pn.test_adam_first_step_is_lr_times_sign,
-                       pl.test_samples_are_normalised_and_count_every_stride)
+                       pl.test_samples_are_normalised_and_count_every_stride,
+                       lambda: pi.test_subgroup_widths_count_every_micro_primitive(3),
+                       lambda: pf.test_p1_laplace_symmetric_zero_rowsum_patch(sg.kuhn_cube(1), 2),
+                       pe.test_mass_matrix_by_quadrature)
 
 
 def test_a_missing_volume_factor_in_the_p1_stiffness_is_caught(monkeypatch):
@@ -315,3 +318,40 @@ def test_training_targets_without_the_jacobi_part_are_caught(monkeypatch):
         return original(macro, rm, r, D, xstar, x, 0.0, stride, offset)   # target e, not e - omega s
     monkeypatch.setattr(learned, "learned_samples", wrong)
     assert _caught(pl.test_samples_are_normalised_and_count_every_stride)
+
+
+def test_the_printed_xyz_down_face_width_is_caught(monkeypatch):
+    original = indexing.subgroup_widths
+
+    def wrong(level):
+        wd = dict(original(level))
+        wd[("face", "xyz-down")] = 2 ** level - 2            # Table 1 as printed
+        return wd
+    monkeypatch.setattr(indexing, "subgroup_widths", wrong)
+    assert _caught(lambda: pi.test_subgroup_widths_count_every_micro_primitive(3))
+
+
+def test_boundary_vertices_missing_from_the_dirichlet_set_are_caught(monkeypatch):
+    def wrong(cell_ids, n_vertices):
+        f = mesh.faces_of(cell_ids)
+        uf, cnt = np.unique(f, axis=0, return_counts=True)
+        mask = np.zeros(n_vertices, dtype=bool)
+        mask[uf[cnt == 1][:, :2].ravel()] = True             # the third vertex of each face left out
+        return mask
+    monkeypatch.setattr(mesh, "dirichlet_vertices", wrong)
+    assert _caught(lambda: pf.test_p1_laplace_symmetric_zero_rowsum_patch(sg.kuhn_cube(1), 2))
+
+
+def test_a_nedelec_mass_with_a_dropped_term_is_caught(monkeypatch):
+    def wrong(X):
+        G, vol = fem.bary_gradients(X)
+        GG = np.einsum("tid,tjd->tij", G, G)
+        L = (np.ones((4, 4)) + np.eye(4)) / 20.0
+        M = np.empty((X.shape[0], 6, 6))
+        for e, (a, b) in enumerate(nedelec.LOCAL_EDGES):
+            for f, (c, d) in enumerate(nedelec.LOCAL_EDGES):
+                M[:, e, f] = (L[a, c] * GG[:, b, d] - L[a, d] * GG[:, b, c]
+                              - L[b, c] * GG[:, a, d])             # + L[b, d] GG[a, c] dropped
+        return vol[:, None, None] * M
+    monkeypatch.setattr(nedelec, "mass_local", wrong)
+    assert _caught(pe.test_mass_matrix_by_quadrature)
